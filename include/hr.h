@@ -1,0 +1,248 @@
+/*
+ * hr — stochastic gradient, Hessian and Hessian-vector-product estimation of
+ * a Gaussian-smoothed rendering loss on one GB300 GPU (sm_103a).
+ *
+ * Method: Wang, Fischer, Ritschel, "Stochastic Gradient Estimation for
+ * Higher-order Differentiable Rendering".  The loss f(theta) (a renderer
+ * followed by an image-space L2 loss against a target) is smoothed by a
+ * Gaussian in parameter space,
+ *     fbar(theta) = E_{tau ~ N(0, sigma^2 I)} f(theta + tau)         (Sec. 3.1)
+ * and its derivatives are estimated by Monte Carlo over perturbations tau
+ * drawn by importance sampling the positive and negative lobes of the
+ * Gaussian derivative kernels: gradient (Sec. 3.2, Eq. "gradient"),
+ * Hessian (Sec. 3.3), HVP (Sec. 3.4) and the aggregate strategy that samples
+ * the mixture of all element kernels and renders once per sample (Sec. 3.5,
+ * Tab. 1).  Each estimate is
+ *     est_e = 1/(2P) * sum_m w_e(tau_m) * f(theta + tau_m)
+ * over the 2P perturbations (P antithetic +/- pairs) of a request.
+ *
+ * Conventions shared by every entry point
+ * ---------------------------------------
+ * - Return value: HR_OK (0) or a negative hr_status.  No exception crosses
+ *   the ABI.  hr_last_error() gives a message for the calling thread's most
+ *   recent failure.
+ * - Memory: pointers named h_* / plain are HOST memory; pointers named d_*
+ *   are DEVICE memory of the current CUDA device.  The library copies what it
+ *   needs and never frees or retains caller memory after a call returns.
+ * - Streams: opts->stream (a cudaStream_t, NULL = the library's own stream;
+ *   to run on the legacy default stream pass cudaStreamLegacy).
+ *   Host-pointer calls are synchronous; the *_dev call is asynchronous on
+ *   that stream.
+ * - Validation happens before any launch: n must match the scene, M even and
+ *   >= 2, sigma > 0, sizes within the stated maxima; otherwise
+ *   HR_ERR_INVALID_ARG and nothing is launched.
+ * - Thread safety: calls on different scenes may run concurrently from
+ *   different threads; calls on one scene are serialised by the library.
+ */
+#ifndef HR_H
+#define HR_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef int32_t hr_status;
+#define HR_OK 0
+#define HR_ERR_INVALID_ARG (-1)
+#define HR_ERR_OOM (-2)
+#define HR_ERR_CUDA (-3)
+#define HR_ERR_TIMEOUT (-4)
+#define HR_ERR_BUSY (-5)
+#define HR_ERR_UNSUPPORTED (-6)
+
+/* Scene kinds (synthetic stand-ins for the paper's tasks, Sec. 4.1):
+ * DISC2D     one hard-edged disc, 2 params (centre x, y in [0,1]^2), grayscale;
+ * REVOLVE3D  closed triangle mesh of a surface of revolution, 2 params
+ *            (rotation about x, then y), flat Lambert shading, RGB;
+ * PTBOX      path-traced box: 12 axis-aligned quads, 3 spheres, 1 emitting
+ *            quad; 6 params (light centre xyz, sphere-0 centre xyz), RGB;
+ * TRIS2D     coloured 2D triangles drawn in painter's order; params are a
+ *            subset (param_index) of the 9 raw values per triangle
+ *            (x0 y0 x1 y1 x2 y2 r g b). */
+#define HR_SCENE_DISC2D 0
+#define HR_SCENE_REVOLVE3D 1
+#define HR_SCENE_PTBOX 2
+#define HR_SCENE_TRIS2D 3
+
+/* Sampling strategy: element-wise importance sampling (one sample set of M
+ * perturbations per unique element: n for the gradient, n(n+1)/2 for the
+ * Hessian, Tab. 1 "IS") or aggregate sampling (one set of M for all
+ * elements, Tab. 1 "AIS"). */
+#define HR_ELEMENTWISE 0
+#define HR_AGGREGATE 1
+
+/* Estimated quantity */
+#define HR_GRAD 0
+#define HR_HESSIAN 1
+#define HR_HVP 2
+
+/* Maxima (validated) */
+#define HR_MAX_PARAMS 64
+#define HR_MAX_IMAGE_SIDE 1024
+#define HR_MAX_TRIANGLES 4096
+#define HR_MAX_VERTICES 4096
+#define HR_MAX_TRIS2D 32
+
+typedef struct hr_scene_s* hr_scene;
+
+/* Scene description.  All arrays are host memory, read during
+ * hr_create_scene only.  Fields that a kind does not use are ignored. */
+typedef struct {
+    int32_t kind;                 /* HR_SCENE_* */
+    int32_t width, height;        /* image size in pixels */
+    int32_t n_params;             /* DISC2D 2, REVOLVE3D 2, PTBOX 6, TRIS2D = len(param_index) */
+    const double* theta_target;   /* [n_params] target parameters */
+    const float* target_image;    /* optional [H][W][C] FP32 (C = 1 for DISC2D, else 3);
+                                     NULL: the library renders it at theta_target */
+    /* DISC2D */
+    float radius;
+    /* REVOLVE3D: model-space vertices [n_vertices][3], triangles [n_triangles][3]
+       (outward winding), albedo RGB, unit light direction, camera distance on +z
+       and projection scale (pixels per unit of X/Z) */
+    const float* vertices;
+    int32_t n_vertices;
+    const int32_t* triangles;
+    int32_t n_triangles;
+    float albedo[3];
+    float light[3];
+    float eye_dist;
+    float scale;
+    /* TRIS2D: raw params [n_tris][9], optimised subset param_index[n_params] */
+    const float* raw_params;
+    int32_t n_tris;
+    const int32_t* param_index;
+    /* PTBOX: quads [12] (axis, {plane, lo_u, lo_v, hi_u, hi_v}, albedo RGB),
+       spheres [3] (centre xyz, radius, albedo RGB; sphere 0 centre = params 3..5),
+       light half-size, camera z, tan(fov/2), pixel scale 2 tan(fov/2)/H,
+       emitted radiance RGB, samples per pixel, target samples per pixel,
+       path depth, and the seed of the target's path random numbers */
+    const int32_t* quad_axis;
+    const float* quad_geom;
+    const float* quad_albedo;
+    const float* sph_center;
+    const float* sph_radius;
+    const float* sph_albedo;
+    float light_half, cam_z, tan_half, pix_scale;
+    float emission[3];
+    int32_t spp, target_spp, depth;
+    uint64_t seed;
+} hr_scene_desc;
+
+/* Options of one estimate. */
+typedef struct {
+    double sigma;          /* smoothing bandwidth, > 0 */
+    int64_t n_perturb;     /* M: renders per request (aggregate) or per unique
+                              element (element-wise); even, >= 2 */
+    int32_t strategy;      /* HR_ELEMENTWISE or HR_AGGREGATE (HVP: aggregate only) */
+    uint64_t seed;         /* Philox key */
+    uint32_t request_id;   /* Philox counter word 3 */
+    uint32_t sub;          /* first sub-stream (counter word 2, low 24 bits);
+                              element e of element-wise sampling uses sub + e */
+    void* stream;          /* cudaStream_t or NULL */
+    /* Optional HOST outputs for inspection (may be NULL), in launch order
+       m = group * M + 2k + leg (leg 0 = + lobe):
+       out_tau [M_total][n] FP32 perturbations, out_weights [M_total][E] FP32,
+       out_losses [M_total] FP32 per-render losses, out_scale [E] FP64
+       A_e = 1/(2P) sum_m |w_e f_m|. */
+    float* out_tau;
+    float* out_weights;
+    float* out_losses;
+    double* out_scale;
+} hr_opts;
+
+/* Create a scene: uploads geometry, renders the target when target_image is
+ * NULL, and allocates its device workspace.  *out receives the handle. */
+hr_status hr_create_scene(const hr_scene_desc* desc, hr_scene* out);
+hr_status hr_destroy_scene(hr_scene scene);
+
+/* Smoothed gradient (Sec. 3.2): h_theta [n] host, h_out_g [n] host. */
+hr_status hr_estimate_grad(hr_scene scene, const double* h_theta, const hr_opts* opts, double* h_out_g);
+
+/* Smoothed Hessian (Sec. 3.3, 3.5): h_out_H [n][n] row-major, symmetric. */
+hr_status hr_estimate_hessian(hr_scene scene, const double* h_theta, const hr_opts* opts, double* h_out_H);
+
+/* Smoothed Hessian-vector product (Sec. 3.4, 3.5), aggregate strategy:
+ * the HVP kernel sum_j h_ij v_j sampled from the Hessian mixture, so that on
+ * the same samples it equals the aggregate Hessian times v. */
+hr_status hr_estimate_hvp(hr_scene scene, const double* h_theta, const double* h_v,
+                          const hr_opts* opts, double* h_out_Hv);
+
+/* Device-pointer form of the three estimates, asynchronous on opts->stream:
+ * d_theta [n], d_v [n] (HVP only, else NULL), d_out [n], [n][n] or [n]
+ * FP64 device memory.  Debug outputs in opts are ignored. */
+hr_status hr_estimate_dev(hr_scene scene, int32_t quantity, const double* d_theta, const double* d_v,
+                          const hr_opts* opts, double* d_out);
+
+/* ---------------------------------------------------------------------------
+ * Newton-CG (Sec. 2 "Newton Conjugate Gradient"): per step and instance, an
+ * aggregate gradient estimate g, then K linear-CG iterations on
+ * (H + lambda I) d = -g from d = 0, each Hessian product an aggregate HVP with
+ * fresh samples; alpha = r.r / p.(H + lambda I)p capped at Delta/|p| (the
+ * paper's trust-region step truncation), Fletcher-Reeves beta, exit on
+ * non-positive curvature (first iteration: step Delta along -g);
+ * lambda = lambda_rel |g|; theta += d.  B instances share the scene and run in
+ * the same launches; with use_graph the step is one CUDA graph replay.
+ * Sub-streams: gradient 64 s, product i: 64 s + 1 + i (s = step index);
+ * request id of instance b = request_base + b.
+ * ------------------------------------------------------------------------- */
+typedef struct hr_optstate_s* hr_optstate;
+
+typedef struct {
+    double sigma;
+    int32_t n_grad;        /* perturbations for the gradient (even) */
+    int32_t n_hvp;         /* perturbations per Hessian product (even) */
+    int32_t cg_iters;      /* K <= 63 */
+    double lambda_rel;     /* lambda = lambda_rel * |g| */
+    double trust_radius;   /* Delta */
+    uint64_t seed;
+    uint32_t request_base;
+    int32_t use_graph;     /* 1: capture the step once, replay it */
+    void* stream;
+} hr_cg_opts;
+
+typedef struct {
+    double grad_norm;
+    double lambda;
+    int32_t iters;         /* CG iterations taken */
+    int32_t exit_reason;   /* 0 max iterations, 1 non-positive curvature, 2 zero residual */
+    double step_norm;
+} hr_step_info;
+
+hr_status hr_optstate_create(hr_scene scene, int32_t n_instances, const double* h_theta0,
+                             const hr_cg_opts* opts, hr_optstate* out);
+hr_status hr_optstate_destroy(hr_optstate st);
+/* One step for all instances; h_info [n_instances] may be NULL. */
+hr_status hr_newton_cg_step(hr_scene scene, hr_optstate st, hr_step_info* h_info);
+/* Current parameters, h_theta [n_instances][n]. */
+hr_status hr_optstate_theta(hr_optstate st, double* h_theta);
+
+/* Render one image at h_params [n] (rounded to FP32) into h_img [H][W][C]
+ * (host).  For PTBOX the path random numbers are those of (seed, request,
+ * sub, pair k, tag) with spp samples per pixel (tag 2: perturbation renders,
+ * tag 3: the target); other kinds ignore these arguments.  Used to compare
+ * renderers pixel by pixel. */
+hr_status hr_render(hr_scene scene, const double* h_params, uint64_t seed, uint32_t request, uint32_t sub,
+                    uint32_t k, uint32_t tag, int32_t spp, float* h_img);
+
+/* Stage timing: when enabled (on != 0), every estimate records CUDA events
+ * on its stream around its three launches (sampler, render + loss, sums) and
+ * hr_profile_last writes their durations in milliseconds, ms[3], for the
+ * calling thread's last estimate on that scene (after it completed).
+ * Returns HR_ERR_INVALID_ARG when nothing was recorded. */
+hr_status hr_profile_enable(hr_scene scene, int32_t on);
+hr_status hr_profile_last(hr_scene scene, float* ms3);
+
+/* Thread-local message of the last failure (empty if none); returns the
+ * message length.  buf may be NULL to query the length. */
+size_t hr_last_error(char* buf, size_t len);
+
+/* Library version (major * 10000 + minor * 100 + patch). */
+int32_t hr_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* HR_H */

@@ -1,0 +1,529 @@
+// C-ABI entry points of libhr: scene lifetime, the three estimators, the
+// device-pointer form, single-image rendering, error reporting.
+#include <cmath>
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <mutex>
+#include <string>
+#include <vector>
+
+#include "hr.h"
+#include "hr_api_internal.h"
+#include "hr_device.cuh"
+#include "hr_internal.h"
+
+namespace hr {
+
+void launch_disc_loss(const DevScene&, const RenderBatch&, cudaStream_t);
+void launch_disc_image(const DevScene&, const float*, float*, cudaStream_t);
+void launch_revolve_loss(const DevScene&, const RenderBatch&, cudaStream_t);
+void launch_revolve_image(const DevScene&, const float*, float*, cudaStream_t);
+size_t revolve_smem_bytes(int nv, int nt, int W, int H);
+int revolve_tiles(int W, int H);
+void launch_tris2d_loss(const DevScene&, const RenderBatch&, cudaStream_t);
+void launch_tris2d_image(const DevScene&, const float*, float*, cudaStream_t);
+void launch_ptbox_loss(const DevScene&, const RenderBatch&, cudaStream_t);
+void launch_ptbox_image(const DevScene&, const float*, uint64_t, uint32_t, uint32_t, uint32_t, uint32_t, int, float*,
+                        cudaStream_t);
+
+int num_sms() {
+    static int n = 0;
+    if (n == 0) {
+        int dev = 0;
+        cudaGetDevice(&dev);
+        cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev);
+        if (n <= 0) n = 1;
+    }
+    return n;
+}
+
+void launch_render_loss(const DevScene& sc, const RenderBatch& b, cudaStream_t s) {
+    switch (sc.kind) {
+        case HR_SCENE_DISC2D: launch_disc_loss(sc, b, s); break;
+        case HR_SCENE_REVOLVE3D: launch_revolve_loss(sc, b, s); break;
+        case HR_SCENE_TRIS2D: launch_tris2d_loss(sc, b, s); break;
+        case HR_SCENE_PTBOX: launch_ptbox_loss(sc, b, s); break;
+    }
+}
+
+void launch_render_image(const DevScene& sc, const float* d_params, uint64_t seed, uint32_t request, uint32_t sub,
+                         uint32_t k, uint32_t tag, int spp, float* d_img, cudaStream_t s) {
+    switch (sc.kind) {
+        case HR_SCENE_DISC2D: launch_disc_image(sc, d_params, d_img, s); break;
+        case HR_SCENE_REVOLVE3D: launch_revolve_image(sc, d_params, d_img, s); break;
+        case HR_SCENE_TRIS2D: launch_tris2d_image(sc, d_params, d_img, s); break;
+        case HR_SCENE_PTBOX: launch_ptbox_image(sc, d_params, seed, request, sub, k, tag, spp, d_img, s); break;
+    }
+}
+
+// ---------------------------------------------------------------------------
+// errors
+// ---------------------------------------------------------------------------
+static thread_local std::string g_err;
+
+hr_status fail(hr_status code, const char* fmt, ...) {
+    char buf[512];
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(buf, sizeof buf, fmt, ap);
+    va_end(ap);
+    g_err = buf;
+    return code;
+}
+
+void clear_error() { g_err.clear(); }
+
+const std::string& last_error() { return g_err; }
+
+// ---------------------------------------------------------------------------
+// device buffer that grows on demand
+// ---------------------------------------------------------------------------
+cudaError_t DevBuf::reserve(size_t bytes) {
+    if (bytes <= cap) return cudaSuccess;
+    if (ptr) cudaFree(ptr);
+    ptr = nullptr;
+    cap = 0;
+    const cudaError_t e = cudaMalloc(&ptr, bytes);
+    if (e == cudaSuccess) cap = bytes;
+    return e;
+}
+void DevBuf::release() {
+    if (ptr) cudaFree(ptr);
+    ptr = nullptr;
+    cap = 0;
+}
+
+}  // namespace hr
+
+using namespace hr;
+
+namespace {
+
+template <class T>
+cudaError_t upload(T** dst, const T* src, size_t count) {
+    cudaError_t e = cudaMalloc((void**)dst, sizeof(T) * (count ? count : 1));
+    if (e != cudaSuccess) return e;
+    if (count) e = cudaMemcpy(*dst, src, sizeof(T) * count, cudaMemcpyHostToDevice);
+    return e;
+}
+
+__global__ void f64_to_f32_kernel(const double* in, float* out, int n) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < n) out[i] = __double2float_rn(in[i]);
+}
+
+int n_elements(int quantity, int n) { return quantity == HR_HESSIAN ? n * (n + 1) / 2 : n; }
+
+hr_status validate_opts(const hr_scene_s* s, int quantity, const hr_opts* o) {
+    if (!s) return fail(HR_ERR_INVALID_ARG, "scene is NULL");
+    if (!o) return fail(HR_ERR_INVALID_ARG, "opts is NULL");
+    if (!(o->sigma > 0.0) || !std::isfinite(o->sigma)) return fail(HR_ERR_INVALID_ARG, "sigma must be > 0");
+    if (o->n_perturb < 2 || (o->n_perturb & 1)) return fail(HR_ERR_INVALID_ARG, "n_perturb must be even and >= 2");
+    if (o->strategy != HR_ELEMENTWISE && o->strategy != HR_AGGREGATE)
+        return fail(HR_ERR_INVALID_ARG, "unknown strategy %d", o->strategy);
+    if (quantity == HR_HVP && o->strategy != HR_AGGREGATE)
+        return fail(HR_ERR_UNSUPPORTED, "the HVP is estimated with the aggregate strategy only");
+    const int n = s->sc.n;
+    const int G = o->strategy == HR_ELEMENTWISE ? n_elements(quantity, n) : 1;
+    const int64_t total = (int64_t)G * o->n_perturb;
+    if (o->n_perturb / 2 >= (1 << 24)) return fail(HR_ERR_INVALID_ARG, "at most 2^24 - 1 pairs per request");
+    if (total > (int64_t)1 << 28) return fail(HR_ERR_INVALID_ARG, "too many perturbations (%lld)", (long long)total);
+    if ((uint64_t)o->sub + (uint64_t)G > (1u << 24)) return fail(HR_ERR_INVALID_ARG, "sub-stream out of range");
+    return HR_OK;
+}
+
+}  // namespace
+
+// ---------------------------------------------------------------------------
+// estimator pipeline shared by the host- and device-pointer entry points
+// ---------------------------------------------------------------------------
+namespace hr {
+
+hr_status run_estimate(hr_scene_s* s, int quantity, const double* h_theta, const double* d_theta,
+                       const double* h_v, const double* d_v, const hr_opts* o, double* h_out, double* d_out) {
+    hr_status st = validate_opts(s, quantity, o);
+    if (st != HR_OK) return st;
+    DevScene& sc = s->sc;
+    Workspace& ws = s->ws;
+    const int n = sc.n;
+    const int E = n_elements(quantity, n);
+    const int G = o->strategy == HR_ELEMENTWISE ? E : 1;
+    const int64_t M = o->n_perturb;
+    const int P = (int)(M / 2);
+    const int64_t Mt = (int64_t)G * M;
+    cudaStream_t stream = o->stream ? (cudaStream_t)o->stream : s->stream;
+
+#define WS_TRY(x)                                                                              \
+    do {                                                                                       \
+        cudaError_t e_ = (x);                                                                  \
+        if (e_ != cudaSuccess) return fail(HR_ERR_OOM, "workspace: %s", cudaGetErrorString(e_)); \
+    } while (0)
+    WS_TRY(ws.theta32.reserve(sizeof(float) * n));
+    WS_TRY(ws.v.reserve(sizeof(double) * n));
+    WS_TRY(ws.tau.reserve(sizeof(float) * Mt * n));
+    WS_TRY(ws.w.reserve(sizeof(float) * Mt * E));
+    WS_TRY(ws.meta.reserve(sizeof(uint2) * Mt));
+    WS_TRY(ws.loss.reserve(sizeof(float) * Mt));
+    WS_TRY(ws.flat.reserve(sizeof(double) * E));
+    WS_TRY(ws.scale.reserve(sizeof(double) * E));
+    WS_TRY(ws.full.reserve(sizeof(double) * n * n));
+    WS_TRY(ws.groups.reserve(sizeof(SampleGroup) * G));
+#undef WS_TRY
+
+#define CU_TRY(x)                                                                               \
+    do {                                                                                        \
+        cudaError_t e_ = (x);                                                                   \
+        if (e_ != cudaSuccess) return fail(HR_ERR_CUDA, "%s: %s", #x, cudaGetErrorString(e_));  \
+    } while (0)
+    float* theta32 = (float*)ws.theta32.ptr;
+    if (h_theta) {
+        std::vector<float> t32(n);
+        for (int i = 0; i < n; ++i) t32[i] = (float)h_theta[i];
+        CU_TRY(cudaMemcpyAsync(theta32, t32.data(), sizeof(float) * n, cudaMemcpyHostToDevice, stream));
+        CU_TRY(cudaStreamSynchronize(stream));
+    } else {
+        f64_to_f32_kernel<<<(n + 127) / 128, 128, 0, stream>>>(d_theta, theta32, n);
+    }
+    const double* vdev = d_v;
+    if (quantity == HR_HVP && h_v) {
+        CU_TRY(cudaMemcpyAsync(ws.v.ptr, h_v, sizeof(double) * n, cudaMemcpyHostToDevice, stream));
+        vdev = (const double*)ws.v.ptr;
+    }
+    s->host_groups.resize(G);
+    for (int g = 0; g < G; ++g) {
+        SampleGroup& gr = s->host_groups[g];
+        gr.m0 = (int32_t)(g * M);
+        gr.P = P;
+        gr.lobe = quantity == HR_GRAD ? 0 : 1;
+        gr.quantity = quantity;
+        gr.sub = o->sub + (uint32_t)g;
+        gr.request = o->request_id;
+        gr.theta_row = 0;
+        gr.pad = 0;
+        if (o->strategy == HR_AGGREGATE) {
+            gr.comp_i = -1; gr.comp_j = -1;
+        } else if (quantity == HR_GRAD) {
+            gr.comp_i = g; gr.comp_j = g;
+        } else {
+            int r = 0, rem = g;
+            while (rem >= n - r) { rem -= n - r; ++r; }
+            gr.comp_i = r; gr.comp_j = r + rem;
+        }
+    }
+    CU_TRY(cudaMemcpyAsync(ws.groups.ptr, s->host_groups.data(), sizeof(SampleGroup) * G, cudaMemcpyHostToDevice,
+                           stream));
+    CU_TRY(cudaStreamSynchronize(stream));   // host group table may be reused by the next call
+
+    SampleArgs sa{};
+    sa.groups = (const SampleGroup*)ws.groups.ptr;
+    sa.n = n;
+    sa.E = E;
+    sa.sigma = o->sigma;
+    const double s2 = o->sigma * o->sigma;
+    sa.Zg = std::sqrt(2.0 / M_PI) / o->sigma;
+    sa.Zd = 4.0 * std::exp(-0.5) / (std::sqrt(2.0 * M_PI) * s2);
+    sa.Zo = sa.Zg * sa.Zg;
+    sa.seed = o->seed;
+    sa.v = vdev;
+    sa.tau = (float*)ws.tau.ptr;
+    sa.w = (float*)ws.w.ptr;
+    sa.invS = nullptr;
+    sa.meta = (uint2*)ws.meta.ptr;
+    if (s->profile) cudaEventRecord(s->ev[0], stream);
+    launch_sample(sa, G, P, stream);
+    if (s->profile) cudaEventRecord(s->ev[1], stream);
+
+    RenderBatch rb{};
+    rb.theta32 = theta32;
+    rb.tau = (const float*)ws.tau.ptr;
+    rb.meta = (const uint2*)ws.meta.ptr;
+    rb.loss = (float*)ws.loss.ptr;
+    rb.M = (int32_t)Mt;
+    rb.n = n;
+    rb.per_row = (int32_t)Mt;
+    rb.request0 = o->request_id;
+    rb.seed = o->seed;
+    launch_render_loss(sc, rb, stream);
+    if (s->profile) cudaEventRecord(s->ev[2], stream);
+
+    FinalizeArgs fa{};
+    fa.w = (const float*)ws.w.ptr;
+    fa.loss = (const float*)ws.loss.ptr;
+    fa.E = E;
+    fa.n = n;
+    fa.pairs2 = (int32_t)M;
+    fa.elementwise = o->strategy == HR_ELEMENTWISE;
+    fa.hessian = quantity == HR_HESSIAN;
+    fa.inv2P = 1.0 / (double)M;
+    fa.out_flat = (double*)ws.flat.ptr;
+    fa.out_scale = (double*)ws.scale.ptr;
+    fa.out_full = quantity == HR_HESSIAN ? (d_out ? d_out : (double*)ws.full.ptr) : nullptr;
+    if (quantity != HR_HESSIAN && d_out) fa.out_flat = d_out;
+    launch_finalize(fa, stream);
+    if (s->profile) {
+        cudaEventRecord(s->ev[3], stream);
+        s->profile_valid = true;
+    }
+    CU_TRY(cudaGetLastError());
+
+    if (h_out) {
+        if (quantity == HR_HESSIAN)
+            CU_TRY(cudaMemcpyAsync(h_out, ws.full.ptr, sizeof(double) * n * n, cudaMemcpyDeviceToHost, stream));
+        else
+            CU_TRY(cudaMemcpyAsync(h_out, ws.flat.ptr, sizeof(double) * n, cudaMemcpyDeviceToHost, stream));
+        if (o->out_tau)
+            CU_TRY(cudaMemcpyAsync(o->out_tau, ws.tau.ptr, sizeof(float) * Mt * n, cudaMemcpyDeviceToHost, stream));
+        if (o->out_weights)
+            CU_TRY(cudaMemcpyAsync(o->out_weights, ws.w.ptr, sizeof(float) * Mt * E, cudaMemcpyDeviceToHost, stream));
+        if (o->out_losses)
+            CU_TRY(cudaMemcpyAsync(o->out_losses, ws.loss.ptr, sizeof(float) * Mt, cudaMemcpyDeviceToHost, stream));
+        if (o->out_scale)
+            CU_TRY(cudaMemcpyAsync(o->out_scale, ws.scale.ptr, sizeof(double) * E, cudaMemcpyDeviceToHost, stream));
+        CU_TRY(cudaStreamSynchronize(stream));
+    }
+#undef CU_TRY
+    return HR_OK;
+}
+
+}  // namespace hr
+
+// ---------------------------------------------------------------------------
+// C ABI
+// ---------------------------------------------------------------------------
+extern "C" {
+
+int32_t hr_version(void) { return 100; }
+
+size_t hr_last_error(char* buf, size_t len) {
+    const std::string& e = last_error();
+    if (buf && len) {
+        const size_t c = e.size() < len - 1 ? e.size() : len - 1;
+        memcpy(buf, e.data(), c);
+        buf[c] = 0;
+    }
+    return e.size();
+}
+
+hr_status hr_create_scene(const hr_scene_desc* d, hr_scene* out) {
+    clear_error();
+    if (!d || !out) return fail(HR_ERR_INVALID_ARG, "desc/out is NULL");
+    *out = nullptr;
+    if (d->width < 1 || d->height < 1 || d->width > HR_MAX_IMAGE_SIDE || d->height > HR_MAX_IMAGE_SIDE)
+        return fail(HR_ERR_INVALID_ARG, "image size %dx%d out of range", d->width, d->height);
+    int expect_n = -1, C = 3;
+    switch (d->kind) {
+        case HR_SCENE_DISC2D: expect_n = 2; C = 1;
+            if (!(d->radius > 0.0f)) return fail(HR_ERR_INVALID_ARG, "disc radius must be > 0");
+            break;
+        case HR_SCENE_REVOLVE3D: expect_n = 2;
+            if (!d->vertices || !d->triangles || d->n_vertices < 3 || d->n_triangles < 1 ||
+                d->n_vertices > HR_MAX_VERTICES || d->n_triangles > 2048)
+                return fail(HR_ERR_INVALID_ARG, "mesh needs 3..%d vertices and 1..2048 triangles", HR_MAX_VERTICES);
+            if (d->width > 512 || d->height > 512) return fail(HR_ERR_UNSUPPORTED, "mesh images are at most 512x512");
+            for (int i = 0; i < 3 * d->n_triangles; ++i)
+                if (d->triangles[i] < 0 || d->triangles[i] >= d->n_vertices)
+                    return fail(HR_ERR_INVALID_ARG, "triangle index out of range");
+            if (!(d->eye_dist > 0.0f) || !(d->scale > 0.0f)) return fail(HR_ERR_INVALID_ARG, "bad camera");
+            break;
+        case HR_SCENE_PTBOX: expect_n = 6;
+            if (!d->quad_axis || !d->quad_geom || !d->quad_albedo || !d->sph_center || !d->sph_radius || !d->sph_albedo)
+                return fail(HR_ERR_INVALID_ARG, "path-traced box needs quads and spheres");
+            if (d->spp < 1 || d->target_spp < 1 || d->depth < 1 || d->depth > 15 || d->spp > 4096)
+                return fail(HR_ERR_INVALID_ARG, "spp/depth out of range");
+            if ((int64_t)d->width * d->height * (d->target_spp > d->spp ? d->target_spp : d->spp) >= ((int64_t)1 << 32))
+                return fail(HR_ERR_INVALID_ARG, "pixel samples exceed 2^32");
+            for (int q = 0; q < 12; ++q)
+                if (d->quad_axis[q] < 0 || d->quad_axis[q] > 2) return fail(HR_ERR_INVALID_ARG, "quad axis");
+            break;
+        case HR_SCENE_TRIS2D:
+            if (!d->raw_params || !d->param_index || d->n_tris < 1 || d->n_tris > HR_MAX_TRIS2D)
+                return fail(HR_ERR_INVALID_ARG, "need 1..%d triangles", HR_MAX_TRIS2D);
+            expect_n = d->n_params;
+            for (int j = 0; j < d->n_params; ++j)
+                if (d->param_index[j] < 0 || d->param_index[j] >= 9 * d->n_tris)
+                    return fail(HR_ERR_INVALID_ARG, "param_index out of range");
+            break;
+        default: return fail(HR_ERR_INVALID_ARG, "unknown scene kind %d", d->kind);
+    }
+    if (d->n_params != expect_n || d->n_params < 1 || d->n_params > HR_MAX_PARAMS)
+        return fail(HR_ERR_INVALID_ARG, "n_params %d invalid for this scene", d->n_params);
+    if (!d->theta_target && !d->target_image) return fail(HR_ERR_INVALID_ARG, "need theta_target or target_image");
+
+    hr_scene_s* s = new hr_scene_s();
+    DevScene& sc = s->sc;
+    sc.kind = d->kind; sc.W = d->width; sc.H = d->height; sc.C = C; sc.n = d->n_params;
+    cudaError_t e = cudaStreamCreateWithFlags(&s->stream, cudaStreamNonBlocking);
+    auto bail = [&](cudaError_t err, const char* what) {
+        hr_destroy_scene(s);
+        return fail(err == cudaErrorMemoryAllocation ? HR_ERR_OOM : HR_ERR_CUDA, "%s: %s", what, cudaGetErrorString(err));
+    };
+    if (e != cudaSuccess) { delete s; return fail(HR_ERR_CUDA, "stream: %s", cudaGetErrorString(e)); }
+    const size_t npx = (size_t)sc.W * sc.H * C;
+    if ((e = cudaMalloc(&sc.target, sizeof(float) * npx)) != cudaSuccess) return bail(e, "target");
+    switch (d->kind) {
+        case HR_SCENE_DISC2D: sc.radius = d->radius; break;
+        case HR_SCENE_REVOLVE3D: {
+            sc.nv = d->n_vertices; sc.nt = d->n_triangles;
+            for (int c = 0; c < 3; ++c) { sc.albedo[c] = d->albedo[c]; sc.light[c] = d->light[c]; }
+            sc.eye_dist = d->eye_dist; sc.scale = d->scale;
+            int dev = 0, maxsm = 0;
+            cudaGetDevice(&dev);
+            cudaDeviceGetAttribute(&maxsm, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
+            const size_t need = revolve_smem_bytes(sc.nv, sc.nt, sc.W, sc.H);
+            if (need + 1024 > (size_t)maxsm) {
+                hr_destroy_scene(s);
+                return fail(HR_ERR_UNSUPPORTED, "mesh needs %zu B of shared memory (device max %d)", need, maxsm);
+            }
+            if ((e = upload(&sc.verts, d->vertices, 3 * (size_t)sc.nv)) != cudaSuccess) return bail(e, "vertices");
+            if ((e = upload(&sc.tris, d->triangles, 3 * (size_t)sc.nt)) != cudaSuccess) return bail(e, "triangles");
+            if ((e = cudaMalloc(&sc.tnrm, sizeof(float) * 3 * sc.nt)) != cudaSuccess) return bail(e, "normals");
+            if ((e = cudaMalloc(&sc.tile_t2, sizeof(float) * revolve_tiles(sc.W, sc.H))) != cudaSuccess)
+                return bail(e, "tiles");
+            revolve_prepare(sc, s->stream);
+            break;
+        }
+        case HR_SCENE_TRIS2D:
+            sc.n_tris = d->n_tris;
+            if ((e = upload(&sc.raw, d->raw_params, 9 * (size_t)sc.n_tris)) != cudaSuccess) return bail(e, "raw");
+            if ((e = upload(&sc.pidx, d->param_index, (size_t)sc.n)) != cudaSuccess) return bail(e, "param_index");
+            break;
+        case HR_SCENE_PTBOX:
+            for (int q = 0; q < 12; ++q) {
+                sc.qaxis[q] = d->quad_axis[q];
+                for (int c = 0; c < 5; ++c) sc.qgeom[q][c] = d->quad_geom[5 * q + c];
+                for (int c = 0; c < 3; ++c) sc.qalb[q][c] = d->quad_albedo[3 * q + c];
+            }
+            for (int i = 0; i < 3; ++i) {
+                for (int c = 0; c < 3; ++c) { sc.sc_[i][c] = d->sph_center[3 * i + c]; sc.salb[i][c] = d->sph_albedo[3 * i + c]; }
+                sc.sr[i] = d->sph_radius[i];
+            }
+            sc.light_half = d->light_half; sc.cam_z = d->cam_z; sc.tan_half = d->tan_half; sc.pix_scale = d->pix_scale;
+            for (int c = 0; c < 3; ++c) sc.emission[c] = d->emission[c];
+            sc.spp = d->spp; sc.target_spp = d->target_spp; sc.depth = d->depth; sc.scene_seed = d->seed;
+            break;
+    }
+    if (d->target_image) {
+        if ((e = cudaMemcpy(sc.target, d->target_image, sizeof(float) * npx, cudaMemcpyHostToDevice)) != cudaSuccess)
+            return bail(e, "target upload");
+    } else {
+        std::vector<float> p32(sc.n);
+        for (int i = 0; i < sc.n; ++i) p32[i] = (float)d->theta_target[i];
+        float* dp = nullptr;
+        if ((e = upload(&dp, p32.data(), (size_t)sc.n)) != cudaSuccess) return bail(e, "target params");
+        launch_render_image(sc, dp, sc.scene_seed, 0, 0, 0, hr::TAG_TARGET, sc.target_spp, sc.target, s->stream);
+        e = cudaStreamSynchronize(s->stream);
+        cudaFree(dp);
+        if (e != cudaSuccess) return bail(e, "target render");
+    }
+    if (sc.kind == HR_SCENE_REVOLVE3D) revolve_tile_t2(sc, s->stream);
+    if ((e = cudaStreamSynchronize(s->stream)) != cudaSuccess) return bail(e, "scene setup");
+    if ((e = cudaGetLastError()) != cudaSuccess) return bail(e, "scene setup launch");
+    *out = s;
+    return HR_OK;
+}
+
+hr_status hr_destroy_scene(hr_scene s) {
+    if (!s) return HR_OK;
+    DevScene& sc = s->sc;
+    if (s->stream) cudaStreamSynchronize(s->stream);
+    cudaFree(sc.target); cudaFree(sc.verts); cudaFree(sc.tris); cudaFree(sc.tnrm); cudaFree(sc.tile_t2);
+    cudaFree(sc.raw); cudaFree(sc.pidx);
+    s->ws.release_all();
+    for (cudaEvent_t& e : s->ev)
+        if (e) cudaEventDestroy(e);
+    if (s->stream) cudaStreamDestroy(s->stream);
+    delete s;
+    return HR_OK;
+}
+
+hr_status hr_estimate_grad(hr_scene s, const double* theta, const hr_opts* o, double* out) {
+    clear_error();
+    if (!theta || !out) return fail(HR_ERR_INVALID_ARG, "theta/out is NULL");
+    if (!s) return fail(HR_ERR_INVALID_ARG, "scene is NULL");
+    std::lock_guard<std::mutex> lk(s->mu);
+    return run_estimate(s, HR_GRAD, theta, nullptr, nullptr, nullptr, o, out, nullptr);
+}
+
+hr_status hr_estimate_hessian(hr_scene s, const double* theta, const hr_opts* o, double* out) {
+    clear_error();
+    if (!theta || !out) return fail(HR_ERR_INVALID_ARG, "theta/out is NULL");
+    if (!s) return fail(HR_ERR_INVALID_ARG, "scene is NULL");
+    std::lock_guard<std::mutex> lk(s->mu);
+    return run_estimate(s, HR_HESSIAN, theta, nullptr, nullptr, nullptr, o, out, nullptr);
+}
+
+hr_status hr_estimate_hvp(hr_scene s, const double* theta, const double* v, const hr_opts* o, double* out) {
+    clear_error();
+    if (!theta || !out || !v) return fail(HR_ERR_INVALID_ARG, "theta/v/out is NULL");
+    if (!s) return fail(HR_ERR_INVALID_ARG, "scene is NULL");
+    std::lock_guard<std::mutex> lk(s->mu);
+    return run_estimate(s, HR_HVP, theta, nullptr, v, nullptr, o, out, nullptr);
+}
+
+hr_status hr_estimate_dev(hr_scene s, int32_t quantity, const double* d_theta, const double* d_v, const hr_opts* o,
+                          double* d_out) {
+    clear_error();
+    if (!s) return fail(HR_ERR_INVALID_ARG, "scene is NULL");
+    if (quantity < HR_GRAD || quantity > HR_HVP) return fail(HR_ERR_INVALID_ARG, "unknown quantity %d", quantity);
+    if (!d_theta || !d_out || (quantity == HR_HVP && !d_v)) return fail(HR_ERR_INVALID_ARG, "NULL device pointer");
+    std::lock_guard<std::mutex> lk(s->mu);
+    return run_estimate(s, quantity, nullptr, d_theta, nullptr, d_v, o, nullptr, d_out);
+}
+
+hr_status hr_profile_enable(hr_scene s, int32_t on) {
+    clear_error();
+    if (!s) return fail(HR_ERR_INVALID_ARG, "scene is NULL");
+    std::lock_guard<std::mutex> lk(s->mu);
+    if (on && !s->ev[0]) {
+        for (cudaEvent_t& e : s->ev) {
+            const cudaError_t err = cudaEventCreate(&e);
+            if (err != cudaSuccess) return fail(HR_ERR_CUDA, "event: %s", cudaGetErrorString(err));
+        }
+    }
+    s->profile = on != 0;
+    s->profile_valid = false;
+    return HR_OK;
+}
+
+hr_status hr_profile_last(hr_scene s, float* ms3) {
+    clear_error();
+    if (!s || !ms3) return fail(HR_ERR_INVALID_ARG, "NULL argument");
+    std::lock_guard<std::mutex> lk(s->mu);
+    if (!s->profile_valid) return fail(HR_ERR_INVALID_ARG, "no profiled estimate");
+    const cudaError_t es = cudaEventSynchronize(s->ev[3]);
+    if (es != cudaSuccess) return fail(HR_ERR_CUDA, "event: %s", cudaGetErrorString(es));
+    for (int i = 0; i < 3; ++i) {
+        const cudaError_t e = cudaEventElapsedTime(&ms3[i], s->ev[i], s->ev[i + 1]);
+        if (e != cudaSuccess) return fail(HR_ERR_CUDA, "event timing: %s", cudaGetErrorString(e));
+    }
+    return HR_OK;
+}
+
+hr_status hr_render(hr_scene s, const double* h_params, uint64_t seed, uint32_t request, uint32_t sub, uint32_t k,
+                    uint32_t tag, int32_t spp, float* h_img) {
+    clear_error();
+    if (!s || !h_params || !h_img) return fail(HR_ERR_INVALID_ARG, "NULL argument");
+    std::lock_guard<std::mutex> lk(s->mu);
+    DevScene& sc = s->sc;
+    if (sc.kind == HR_SCENE_PTBOX && (spp < 1 || (int64_t)sc.W * sc.H * spp >= ((int64_t)1 << 32)))
+        return fail(HR_ERR_INVALID_ARG, "spp out of range");
+    const size_t npx = (size_t)sc.W * sc.H * sc.C;
+    std::vector<float> p32(sc.n);
+    for (int i = 0; i < sc.n; ++i) p32[i] = (float)h_params[i];
+    if (s->ws.render_img.reserve(sizeof(float) * npx) != cudaSuccess ||
+        s->ws.render_params.reserve(sizeof(float) * sc.n) != cudaSuccess)
+        return fail(HR_ERR_OOM, "render buffers");
+    cudaError_t e = cudaMemcpy(s->ws.render_params.ptr, p32.data(), sizeof(float) * sc.n, cudaMemcpyHostToDevice);
+    if (e != cudaSuccess) return fail(HR_ERR_CUDA, "params: %s", cudaGetErrorString(e));
+    launch_render_image(sc, (const float*)s->ws.render_params.ptr, seed, request, sub, k, tag, spp,
+                        (float*)s->ws.render_img.ptr, s->stream);
+    if ((e = cudaGetLastError()) != cudaSuccess) return fail(HR_ERR_CUDA, "render: %s", cudaGetErrorString(e));
+    if ((e = cudaMemcpyAsync(h_img, s->ws.render_img.ptr, sizeof(float) * npx, cudaMemcpyDeviceToHost, s->stream)) !=
+            cudaSuccess ||
+        (e = cudaStreamSynchronize(s->stream)) != cudaSuccess)
+        return fail(HR_ERR_CUDA, "render: %s", cudaGetErrorString(e));
+    return HR_OK;
+}
+
+}  // extern "C"

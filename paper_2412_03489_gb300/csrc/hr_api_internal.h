@@ -1,0 +1,51 @@
+// Host-side objects behind the opaque C-ABI handles.
+#pragma once
+#include <cuda_runtime.h>
+
+#include <mutex>
+#include <string>
+#include <vector>
+
+#include "hr.h"
+#include "hr_internal.h"
+
+namespace hr {
+
+hr_status fail(hr_status code, const char* fmt, ...);
+void clear_error();
+const std::string& last_error();
+
+// device buffer that grows on demand (contents are not preserved)
+struct DevBuf {
+    void* ptr = nullptr;
+    size_t cap = 0;
+    cudaError_t reserve(size_t bytes);
+    void release();
+};
+
+struct Workspace {
+    DevBuf theta32, v, tau, w, meta, loss, flat, scale, full, groups, render_img, render_params;
+    void release_all() {
+        for (DevBuf* b : {&theta32, &v, &tau, &w, &meta, &loss, &flat, &scale, &full, &groups, &render_img,
+                          &render_params})
+            b->release();
+    }
+};
+
+}  // namespace hr
+
+struct hr_scene_s {
+    hr::DevScene sc;
+    std::mutex mu;
+    cudaStream_t stream = nullptr;
+    hr::Workspace ws;
+    std::vector<hr::SampleGroup> host_groups;
+    bool profile = false;
+    bool profile_valid = false;
+    cudaEvent_t ev[4] = {nullptr, nullptr, nullptr, nullptr};
+};
+
+namespace hr {
+hr_status run_estimate(hr_scene_s* s, int quantity, const double* h_theta, const double* d_theta, const double* h_v,
+                       const double* d_v, const hr_opts* o, double* h_out, double* d_out);
+}

@@ -1,0 +1,111 @@
+// Host-side internal declarations of libhr (not part of the C ABI).
+#pragma once
+#include <cstdint>
+#include <cuda_runtime.h>
+
+namespace hr {
+
+// One sample group: P antithetic pairs drawn for one component choice
+// (element-wise) or from the mixture (aggregate), stored at perturbations
+// [m0, m0 + 2P).  Weight rows of width E start at row m0.
+struct SampleGroup {
+    int32_t m0;
+    int32_t P;
+    int32_t lobe;        // 0 gradient lobes, 1 Hessian lobes
+    int32_t comp_i;      // -1: aggregate
+    int32_t comp_j;
+    int32_t quantity;    // 0 grad, 1 hessian, 2 hvp with v, 3 hvp deferred (store n^2/S only)
+    uint32_t sub;        // Philox counter word 2 low 24 bits
+    uint32_t request;    // Philox counter word 3
+    int32_t theta_row;   // which parameter row the group perturbs (multi-instance)
+    int32_t pad;
+};
+
+struct SampleArgs {
+    const SampleGroup* groups;
+    int32_t n;
+    int32_t E;            // weight row width (0 if no weights written)
+    double sigma;
+    double Zg, Zd, Zo;
+    uint64_t seed;
+    const double* v;      // [n] for quantity 2
+    float* tau;           // [M][n]
+    float* w;             // [M][E] or null
+    float* invS;          // [M] n^2 / S (Hessian mixture) or null
+    uint2* meta;          // [M] (sub, pair k) or null
+    const int32_t* step;  // optional device step index s: every group's sub += 64 s
+};
+
+void launch_sample(const SampleArgs& a, int n_groups, int max_P, cudaStream_t s);
+
+struct FinalizeArgs {
+    const float* w;       // [M][E]
+    const float* loss;    // [M]
+    int32_t E;
+    int32_t n;
+    int32_t pairs2;       // 2P perturbations per element range
+    int32_t elementwise;  // element e sums rows [e*2P, (e+1)*2P), else [0, 2P)
+    int32_t hessian;      // also write the symmetric n x n matrix
+    double inv2P;
+    double* out_flat;     // [E]
+    double* out_scale;    // [E] or null
+    double* out_full;     // [n][n] or null
+};
+void launch_finalize(const FinalizeArgs& a, cudaStream_t s);
+
+// ---------------------------------------------------------------------------
+// render batches: perturbation m renders at RN32(theta32[row(m)] + tau[m])
+// ---------------------------------------------------------------------------
+struct RenderBatch {
+    const float* theta32;   // [rows][n]
+    const float* tau;       // [M][n]
+    const uint2* meta;      // [M] (sub, k): path random numbers (path tracer)
+    float* loss;            // [M]
+    int32_t M;
+    int32_t n;
+    int32_t per_row;        // perturbations per theta row
+    uint32_t request0;      // request id of row 0 (row r: request0 + r)
+    uint64_t seed;
+};
+
+struct DevScene;
+void launch_render_loss(const DevScene& sc, const RenderBatch& b, cudaStream_t s);
+// one image at params (FP32 [n]) -> img [H][W][C]
+void launch_render_image(const DevScene& sc, const float* d_params, uint64_t seed, uint32_t request,
+                         uint32_t sub, uint32_t k, uint32_t tag, int spp, float* d_img, cudaStream_t s);
+
+struct DevScene {
+    int kind = 0, W = 0, H = 0, C = 0, n = 0;
+    float* target = nullptr;      // [H][W][C]
+    // disc
+    float radius = 0.f;
+    // revolve
+    float* verts = nullptr;       // [nv][3]
+    int32_t* tris = nullptr;      // [nt][3]
+    float* tnrm = nullptr;        // [nt][3] unit model-space normals (FP32)
+    float* tile_t2 = nullptr;     // [tiles] sum of target^2 per 8x8 tile
+    int nv = 0, nt = 0;
+    float albedo[3] = {0, 0, 0}, light[3] = {0, 0, 0};
+    float eye_dist = 0.f, scale = 0.f;
+    size_t rv_smem = 0;
+    // tris2d
+    float* raw = nullptr;         // [n_tris][9]
+    int32_t* pidx = nullptr;      // [n]
+    int n_tris = 0;
+    // ptbox
+    int32_t qaxis[13] = {};
+    float qgeom[13][5] = {};
+    float qalb[13][3] = {};
+    float sc_[3][3] = {}, sr[3] = {}, salb[3][3] = {};
+    float light_half = 0.f, cam_z = 0.f, tan_half = 0.f, pix_scale = 0.f;
+    float emission[3] = {0, 0, 0};
+    int spp = 0, target_spp = 0, depth = 0;
+    uint64_t scene_seed = 0;
+};
+
+void revolve_prepare(DevScene& sc, cudaStream_t s);   // normals, smem size
+void revolve_tile_t2(DevScene& sc, cudaStream_t s);   // after the target exists
+
+int num_sms();
+
+}  // namespace hr

@@ -1,0 +1,63 @@
+// K2: hard-edged disc renderer fused with the L2 loss (stand-in for the Box2
+// plateau task, Sec. 4.1).  One warp renders one perturbation: pixel centre
+// ((x + 1/2)/W, (y + 1/2)/H) is inside when fma(dx, dx, dy*dy) < r*r in FP32,
+// value 1 inside, 0 outside.  With a 0/1 target every (v - t)^2 is 0 or 1 and
+// the FP32 sum is an exact integer count.
+#include "hr_device.cuh"
+#include "hr_internal.h"
+
+namespace hr {
+namespace {
+
+constexpr int kWarps = 8;
+
+__device__ __forceinline__ float disc_value(int x, int y, float invW_dummy, int W, int H, float cx, float cy, float r2) {
+    (void)invW_dummy;
+    const float px = __fdiv_rn(__fadd_rn((float)x, 0.5f), (float)W);
+    const float py = __fdiv_rn(__fadd_rn((float)y, 0.5f), (float)H);
+    const float dx = __fsub_rn(px, cx);
+    const float dy = __fsub_rn(py, cy);
+    const float d2 = __fmaf_rn(dx, dx, __fmul_rn(dy, dy));
+    return d2 < r2 ? 1.0f : 0.0f;
+}
+
+__global__ void __launch_bounds__(32 * kWarps) disc_loss_kernel(RenderBatch b, int W, int H, float radius,
+                                                                const float* __restrict__ target) {
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int m = blockIdx.x * kWarps + warp;
+    if (m >= b.M) return;
+    const int row = m / b.per_row;
+    const float cx = __fadd_rn(b.theta32[row * b.n + 0], b.tau[(size_t)m * b.n + 0]);
+    const float cy = __fadd_rn(b.theta32[row * b.n + 1], b.tau[(size_t)m * b.n + 1]);
+    const float r2 = __fmul_rn(radius, radius);
+    float acc = 0.0f;
+    const int npx = W * H;
+    for (int i = lane; i < npx; i += 32) {
+        const int y = i / W, x = i - y * W;
+        const float d = __fsub_rn(disc_value(x, y, 0.f, W, H, cx, cy, r2), target[i]);
+        acc = __fmaf_rn(d, d, acc);
+    }
+    acc = warp_sum(acc);
+    if (lane == 0) b.loss[m] = __fdiv_rn(acc, (float)npx);
+}
+
+__global__ void disc_image_kernel(const float* params, int W, int H, float radius, float* img) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= W * H) return;
+    const int y = i / W, x = i - y * W;
+    img[i] = disc_value(x, y, 0.f, W, H, params[0], params[1], __fmul_rn(radius, radius));
+}
+
+}  // namespace
+
+void launch_disc_loss(const DevScene& sc, const RenderBatch& b, cudaStream_t s) {
+    const int blocks = (b.M + kWarps - 1) / kWarps;
+    disc_loss_kernel<<<blocks, 32 * kWarps, 0, s>>>(b, sc.W, sc.H, sc.radius, sc.target);
+}
+
+void launch_disc_image(const DevScene& sc, const float* params, float* img, cudaStream_t s) {
+    const int npx = sc.W * sc.H;
+    disc_image_kernel<<<(npx + 255) / 256, 256, 0, s>>>(params, sc.W, sc.H, sc.radius, img);
+}
+
+}  // namespace hr

@@ -1,0 +1,300 @@
+// K5: path tracer of the procedural box (stand-in for the Shadow task of
+// Sec. 4.1) fused with the per-pixel L2 loss.  Rendering follows the
+// standard Monte Carlo estimator of the rendering equation (Sec. 3.1):
+// Lambertian surfaces, next-event estimation to the rectangular light at
+// every path vertex, cosine-weighted continuation, fixed depth.
+//
+// Scene: 12 axis-aligned quads (index 0..11), the light quad (12, horizontal,
+// emitting downward), 3 spheres (13..15); 16 primitives staged in shared
+// memory, tested brute force per ray (a BVH over 16 primitives costs more
+// node tests than it saves).  Rays, hits and all decisions in FP32 with the
+// operation order below; radiance in FP32.
+//
+// Path random numbers: Philox (pixel sample, (k << 8) | (vertex << 4) |
+// block, (tag << 24) | sub, request), key = seed; both legs of a pair share
+// them (common random numbers).  Vertex 0 = camera jitter; at vertices
+// 1..depth block 0 words 0,1 pick the light point, words 2,3 the first disc
+// try; blocks 1..3 hold tries 1..6; a cosine-weighted direction comes from a
+// unit-disc point (rejection from the square) lifted to the hemisphere.
+#include <cmath>
+
+#include "hr_device.cuh"
+#include "hr_internal.h"
+
+namespace hr {
+namespace {
+
+constexpr int kThreads = 256;
+constexpr int kLight = 12;
+constexpr float kInvPi = 0.318309886183790671538f;
+
+struct PtShared {
+    int axis[13];
+    float plane[13], lo_u[13], lo_v[13], hi_u[13], hi_v[13];
+    float alb[16][3];
+    float sc[3][3], sr[3], sr2[3];
+    float em[3];
+};
+
+__device__ __forceinline__ float dot3(const float* a, const float* b) {
+    return __fmaf_rn(a[2], b[2], __fmaf_rn(a[1], b[1], __fmul_rn(a[0], b[0])));
+}
+
+// closest hit with t > 0, ties to the lower primitive index
+__device__ int intersect(const PtShared& S, const float o[3], const float d[3], float& t_out) {
+    float best = INFINITY;
+    int prim = -1;
+#pragma unroll 1
+    for (int q = 0; q <= kLight; ++q) {
+        const int a = S.axis[q];
+        const int u = a == 0 ? 1 : 0, v = a == 2 ? 1 : 2;
+        if (d[a] == 0.0f) continue;
+        const float t = __fdiv_rn(__fsub_rn(S.plane[q], o[a]), d[a]);
+        if (!(t > 0.0f)) continue;
+        const float hu = __fmaf_rn(t, d[u], o[u]);
+        const float hv = __fmaf_rn(t, d[v], o[v]);
+        if (hu < S.lo_u[q] || hu > S.hi_u[q] || hv < S.lo_v[q] || hv > S.hi_v[q]) continue;
+        if (t < best) { best = t; prim = q; }
+    }
+#pragma unroll
+    for (int i = 0; i < 3; ++i) {
+        const float oc[3] = {__fsub_rn(o[0], S.sc[i][0]), __fsub_rn(o[1], S.sc[i][1]), __fsub_rn(o[2], S.sc[i][2])};
+        const float b = dot3(oc, d);
+        const float cc = __fsub_rn(dot3(oc, oc), S.sr2[i]);
+        const float disc = __fmaf_rn(b, b, -cc);
+        if (disc < 0.0f) continue;
+        const float sq = __fsqrt_rn(disc);
+        float t = __fsub_rn(-b, sq);
+        if (!(t > 0.0f)) {
+            t = __fsub_rn(sq, b);
+            if (!(t > 0.0f)) continue;
+        }
+        if (t < best) { best = t; prim = 13 + i; }
+    }
+    t_out = best;
+    return prim;
+}
+
+__device__ void radiance(const PtShared& S, int depth, uint64_t seed, uint32_t request, uint32_t c2, uint32_t k,
+                         uint32_t idx, float o[3], float d[3], float L[3]) {
+    float beta[3] = {1.0f, 1.0f, 1.0f};
+    float t;
+    int prim = intersect(S, o, d, t);
+    if (prim < 0) return;
+    if (prim == kLight) {
+        if (d[1] > 0.0f) { L[0] += S.em[0]; L[1] += S.em[1]; L[2] += S.em[2]; }
+        return;
+    }
+    const float area = __fmul_rn(__fsub_rn(S.hi_u[kLight], S.lo_u[kLight]), __fsub_rn(S.hi_v[kLight], S.lo_v[kLight]));
+    for (int v = 1; v <= depth; ++v) {
+        if (prim == kLight) return;
+        float x[3], n[3], o2[3];
+#pragma unroll
+        for (int c = 0; c < 3; ++c) x[c] = __fmaf_rn(t, d[c], o[c]);
+        if (prim <= kLight) {
+            const int a = S.axis[prim];
+            n[0] = n[1] = n[2] = 0.0f;
+            n[a] = d[a] > 0.0f ? -1.0f : 1.0f;
+        } else {
+            const int i = prim - 13;
+#pragma unroll
+            for (int c = 0; c < 3; ++c) n[c] = __fdiv_rn(__fsub_rn(x[c], S.sc[i][c]), S.sr[i]);
+            if (dot3(n, d) > 0.0f) { n[0] = -n[0]; n[1] = -n[1]; n[2] = -n[2]; }
+        }
+#pragma unroll
+        for (int c = 0; c < 3; ++c) o2[c] = __fmaf_rn(n[c], 1e-4f, x[c]);
+        const float* rho = S.alb[prim];
+        const uint32_t cbase = (k << 8) | ((uint32_t)v << 4);
+        const u32x4 w0 = philox_seed(seed, idx, cbase, c2, request);
+        // next-event estimation
+        {
+            const float ly[3] = {__fmaf_rn(u24f(w0.x), __fsub_rn(S.hi_u[kLight], S.lo_u[kLight]), S.lo_u[kLight]),
+                                 S.plane[kLight],
+                                 __fmaf_rn(u24f(w0.y), __fsub_rn(S.hi_v[kLight], S.lo_v[kLight]), S.lo_v[kLight])};
+            const float wv[3] = {__fsub_rn(ly[0], o2[0]), __fsub_rn(ly[1], o2[1]), __fsub_rn(ly[2], o2[2])};
+            const float dist2 = dot3(wv, wv);
+            const float dist = __fsqrt_rn(dist2);
+            float om[3] = {__fdiv_rn(wv[0], dist), __fdiv_rn(wv[1], dist), __fdiv_rn(wv[2], dist)};
+            const float cosx = dot3(n, om);
+            const float cosl = om[1];
+            if (cosx > 0.0f && cosl > 0.0f) {
+                float ts;
+                if (intersect(S, o2, om, ts) == kLight) {
+                    const float geo = cosx * cosl / dist2 * area * kInvPi;
+#pragma unroll
+                    for (int c = 0; c < 3; ++c) L[c] += beta[c] * rho[c] * S.em[c] * geo;
+                }
+            }
+        }
+        if (v == depth) return;
+        // cosine-weighted continuation
+        float a = 0.0f, b = 0.0f;
+        {
+            float ta = __fmaf_rn(u24f(w0.z), 2.0f, -1.0f), tb = __fmaf_rn(u24f(w0.w), 2.0f, -1.0f);
+            bool found = __fmaf_rn(ta, ta, __fmul_rn(tb, tb)) < 1.0f;
+            if (found) { a = ta; b = tb; }
+            for (uint32_t blk = 1; blk <= 3 && !found; ++blk) {
+                const u32x4 wb = philox_seed(seed, idx, cbase | blk, c2, request);
+                ta = __fmaf_rn(u24f(wb.x), 2.0f, -1.0f);
+                tb = __fmaf_rn(u24f(wb.y), 2.0f, -1.0f);
+                if (__fmaf_rn(ta, ta, __fmul_rn(tb, tb)) < 1.0f) { a = ta; b = tb; found = true; break; }
+                ta = __fmaf_rn(u24f(wb.z), 2.0f, -1.0f);
+                tb = __fmaf_rn(u24f(wb.w), 2.0f, -1.0f);
+                if (__fmaf_rn(ta, ta, __fmul_rn(tb, tb)) < 1.0f) { a = ta; b = tb; found = true; break; }
+            }
+        }
+        const float r2 = __fmaf_rn(a, a, __fmul_rn(b, b));
+        const float cz = __fsqrt_rn(__fsub_rn(1.0f, r2));
+        // orthonormal basis around n (Duff et al., "Building an Orthonormal
+        // Basis, Revisited", JCGT 2017)
+        const float sg = copysignf(1.0f, n[2]);
+        const float aa = __fdiv_rn(-1.0f, __fadd_rn(sg, n[2]));
+        const float bb = __fmul_rn(__fmul_rn(n[0], n[1]), aa);
+        const float t1[3] = {__fmaf_rn(__fmul_rn(sg, __fmul_rn(n[0], n[0])), aa, 1.0f), __fmul_rn(sg, bb),
+                             -__fmul_rn(sg, n[0])};
+        const float t2[3] = {bb, __fmaf_rn(__fmul_rn(n[1], n[1]), aa, sg), -n[1]};
+        float nd[3];
+#pragma unroll
+        for (int c = 0; c < 3; ++c) nd[c] = __fmaf_rn(cz, n[c], __fmaf_rn(b, t2[c], __fmul_rn(a, t1[c])));
+#pragma unroll
+        for (int c = 0; c < 3; ++c) beta[c] *= rho[c];
+        prim = intersect(S, o2, nd, t);
+        if (prim < 0) return;
+#pragma unroll
+        for (int c = 0; c < 3; ++c) { o[c] = o2[c]; d[c] = nd[c]; }
+    }
+}
+
+struct PtArgs {
+    int32_t qaxis[13];
+    float qgeom[13][5];
+    float qalb[13][3];
+    float sc[3][3], sr[3], salb[3][3];
+    float light_half, cam_z, tan_half, pix_scale;
+    float em[3];
+    int W, H, spp, depth;
+    const float* target;
+};
+
+__device__ void load_scene(const PtArgs& A, const float* p, PtShared& S) {
+    const int t = threadIdx.x;
+    if (t < 13) {
+        S.axis[t] = A.qaxis[t];
+        S.plane[t] = A.qgeom[t][0];
+        S.lo_u[t] = A.qgeom[t][1]; S.lo_v[t] = A.qgeom[t][2];
+        S.hi_u[t] = A.qgeom[t][3]; S.hi_v[t] = A.qgeom[t][4];
+        if (t < 12) { S.alb[t][0] = A.qalb[t][0]; S.alb[t][1] = A.qalb[t][1]; S.alb[t][2] = A.qalb[t][2]; }
+        else { S.alb[t][0] = S.alb[t][1] = S.alb[t][2] = 0.0f; }
+    } else if (t < 16) {
+        const int i = t - 13;
+        for (int c = 0; c < 3; ++c) { S.sc[i][c] = (i == 0) ? p[3 + c] : A.sc[i][c]; S.alb[t][c] = A.salb[i][c]; }
+        S.sr[i] = A.sr[i];
+        S.sr2[i] = __fmul_rn(A.sr[i], A.sr[i]);
+    } else if (t == 16) {
+        S.axis[kLight] = 1;
+        S.plane[kLight] = p[1];
+        S.lo_u[kLight] = __fsub_rn(p[0], A.light_half);
+        S.hi_u[kLight] = __fadd_rn(p[0], A.light_half);
+        S.lo_v[kLight] = __fsub_rn(p[2], A.light_half);
+        S.hi_v[kLight] = __fadd_rn(p[2], A.light_half);
+        S.em[0] = A.em[0]; S.em[1] = A.em[1]; S.em[2] = A.em[2];
+    }
+}
+
+template <bool kImage>
+__global__ void __launch_bounds__(kThreads)
+ptbox_kernel(PtArgs A, RenderBatch b, const float* __restrict__ img_params, uint64_t seed_img, uint32_t req_img,
+             uint32_t sub_img, uint32_t k_img, uint32_t tag_img, int spp_img, float* __restrict__ img) {
+    __shared__ PtShared S;
+    __shared__ float s_p[8];
+    __shared__ float s_part[kThreads / 32];
+    const int m = blockIdx.x;
+    const int tid = threadIdx.x;
+    uint64_t seed;
+    uint32_t request, sub, k, tag;
+    int spp;
+    if (kImage) {
+        if (tid < 6) s_p[tid] = img_params[tid];
+        seed = seed_img; request = req_img; sub = sub_img; k = k_img; tag = tag_img; spp = spp_img;
+    } else {
+        const int row = m / b.per_row;
+        if (tid < 6) s_p[tid] = __fadd_rn(b.theta32[row * b.n + tid], b.tau[(size_t)m * b.n + tid]);
+        seed = b.seed;
+        request = b.request0 + (uint32_t)row;
+        const uint2 mt = b.meta[m];
+        sub = mt.x; k = mt.y; tag = TAG_PATH; spp = A.spp;
+    }
+    __syncthreads();
+    load_scene(A, s_p, S);
+    __syncthreads();
+    const uint32_t c2 = (tag << 24) | (sub & 0xFFFFFFu);
+    const float inv_spp = 1.0f / (float)spp;
+    float acc = 0.0f;
+    const int npx = A.W * A.H;
+    for (int px = tid; px < npx; px += kThreads) {
+        const int y = px / A.W, x = px - y * A.W;
+        float L[3] = {0.0f, 0.0f, 0.0f};
+        for (int s = 0; s < spp; ++s) {
+            const uint32_t idx = (uint32_t)(px * spp + s);
+            const u32x4 wj = philox_seed(seed, idx, k << 8, c2, request);
+            const float fx = __fadd_rn((float)x, u24f(wj.x));
+            const float fy = __fadd_rn((float)y, u24f(wj.y));
+            float d[3] = {__fmaf_rn(fx, A.pix_scale, -A.tan_half), __fmaf_rn(-fy, A.pix_scale, A.tan_half), -1.0f};
+            const float len = __fsqrt_rn(dot3(d, d));
+            d[0] = __fdiv_rn(d[0], len); d[1] = __fdiv_rn(d[1], len); d[2] = __fdiv_rn(d[2], len);
+            float o[3] = {0.0f, 0.0f, A.cam_z};
+            radiance(S, A.depth, seed, request, c2, k, idx, o, d, L);
+        }
+        const size_t p3 = 3 * (size_t)px;
+        if (kImage) {
+            img[p3] = L[0] * inv_spp; img[p3 + 1] = L[1] * inv_spp; img[p3 + 2] = L[2] * inv_spp;
+        } else {
+            const float d0 = L[0] * inv_spp - A.target[p3];
+            const float d1 = L[1] * inv_spp - A.target[p3 + 1];
+            const float d2 = L[2] * inv_spp - A.target[p3 + 2];
+            acc += d0 * d0 + d1 * d1 + d2 * d2;
+        }
+    }
+    if (!kImage) {
+        acc = warp_sum(acc);
+        if ((tid & 31) == 0) s_part[tid >> 5] = acc;
+        __syncthreads();
+        if (tid == 0) {
+            float v = 0.0f;
+            for (int w = 0; w < kThreads / 32; ++w) v += s_part[w];
+            b.loss[m] = v / (float)(npx * 3);
+        }
+    }
+}
+
+PtArgs make_args(const DevScene& sc) {
+    PtArgs a;
+    for (int q = 0; q < 13; ++q) {
+        a.qaxis[q] = sc.qaxis[q];
+        for (int c = 0; c < 5; ++c) a.qgeom[q][c] = sc.qgeom[q][c];
+        for (int c = 0; c < 3; ++c) a.qalb[q][c] = sc.qalb[q][c];
+    }
+    for (int i = 0; i < 3; ++i) {
+        for (int c = 0; c < 3; ++c) { a.sc[i][c] = sc.sc_[i][c]; a.salb[i][c] = sc.salb[i][c]; }
+        a.sr[i] = sc.sr[i];
+    }
+    a.light_half = sc.light_half; a.cam_z = sc.cam_z; a.tan_half = sc.tan_half; a.pix_scale = sc.pix_scale;
+    for (int c = 0; c < 3; ++c) a.em[c] = sc.emission[c];
+    a.W = sc.W; a.H = sc.H; a.spp = sc.spp; a.depth = sc.depth;
+    a.target = sc.target;
+    return a;
+}
+
+}  // namespace
+
+void launch_ptbox_loss(const DevScene& sc, const RenderBatch& b, cudaStream_t s) {
+    ptbox_kernel<false><<<b.M, kThreads, 0, s>>>(make_args(sc), b, nullptr, 0, 0, 0, 0, 0, 0, nullptr);
+}
+
+void launch_ptbox_image(const DevScene& sc, const float* params, uint64_t seed, uint32_t request, uint32_t sub,
+                        uint32_t k, uint32_t tag, int spp, float* img, cudaStream_t s) {
+    RenderBatch b{};
+    ptbox_kernel<true><<<1, kThreads, 0, s>>>(make_args(sc), b, params, seed, request, sub, k, tag, spp, img);
+}
+
+}  // namespace hr

@@ -1,0 +1,375 @@
+// K3/K4: rasteriser of a triangle mesh (surface of revolution, stand-in for
+// the Mug task of Sec. 4.1) fused with the per-pixel L2 loss and the block
+// reduction, so that no image is written to HBM.
+//
+// One CTA (1024 threads, one per SM, persistent over perturbations) renders a
+// whole perturbation:
+//   1. rotation R = Rx(p0) Ry(p1) from RN32 of FP64 cos / sin;
+//   2. vertex transform and projection (FP32, fixed operation order);
+//   3. triangle setup: edge functions, back-face cull, depth plane of 1/Z,
+//      pixel bounding box, flat Lambert shade; surviving triangles are
+//      compacted into shared memory;
+//   4. binning into 8x8 pixel tiles (count, scan, fill; all in shared memory);
+//   5. warp-per-tile raster: each lane owns two pixels; nearest 1/Z wins,
+//      ties to the lower triangle index; (colour - target)^2 accumulated in
+//      registers; tiles with an empty bin add the precomputed sum of target^2;
+//   6. warp shuffle + block reduction to one FP32 loss per perturbation.
+// The FP32 sequences of steps 2-5 define the renderer (coverage and depth
+// decisions), so they use explicitly rounded intrinsics.
+#include <climits>
+#include <cmath>
+
+#include "hr_device.cuh"
+#include "hr_internal.h"
+
+namespace hr {
+namespace {
+
+constexpr int kThreads = 1024;
+constexpr int kWarps = kThreads / 32;
+constexpr int kTile = 8;
+constexpr int kEntryCap = 16384;
+
+struct __align__(16) TriRec {
+    float A0, B0, C0, A1;
+    float B1, C1, A2, B2;
+    float C2, Aw, Bw, Cw;
+    float shade;
+    int idx;
+    uint32_t xr;   // x_lo | x_hi << 16 (pixel columns whose centre is inside the bbox)
+    uint32_t yr;
+};
+
+struct RvArgs {
+    const float* verts;
+    const int32_t* tris;
+    const float* tnrm;
+    const float* target;
+    const float* tile_t2;
+    int nv, nt, W, H, TX, TY, T;
+    float alb0, alb1, alb2, l0, l1, l2, eye_dist, scale;
+};
+
+// pixel range [lo, hi] of centres c + 1/2 with mn <= c + 1/2 <= mx, c in [0, N)
+__device__ __forceinline__ bool pixel_range(float mn, float mx, int N, int& lo, int& hi) {
+    if (!(mx >= 0.5f) || !(mn <= (float)N - 0.5f)) return false;
+    lo = (mn <= 0.5f) ? 0 : (int)ceilf(__fsub_rn(mn, 0.5f));
+    hi = (mx >= (float)N - 0.5f) ? N - 1 : (int)floorf(__fsub_rn(mx, 0.5f));
+    return lo <= hi;
+}
+
+// exclusive scan of cnt[0..T) into off[0..T); returns the total (all threads)
+__device__ int block_scan(const int* cnt, int* off, int T, int* warp_tot) {
+    const int per = (T + kThreads - 1) / kThreads;
+    const int b = threadIdx.x * per;
+    int local = 0;
+    for (int i = 0; i < per; ++i)
+        if (b + i < T) local += cnt[b + i];
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    int incl = local;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const int v = __shfl_up_sync(0xffffffffu, incl, o);
+        if (lane >= o) incl += v;
+    }
+    if (lane == 31) warp_tot[warp] = incl;
+    __syncthreads();
+    if (warp == 0) {
+        int wv = warp_tot[lane];
+        int wi = wv;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const int v = __shfl_up_sync(0xffffffffu, wi, o);
+            if (lane >= o) wi += v;
+        }
+        warp_tot[lane] = wi - wv;       // exclusive warp offsets
+        if (lane == 31) warp_tot[32] = wi;
+    }
+    __syncthreads();
+    int run = warp_tot[warp] + incl - local;
+    for (int i = 0; i < per; ++i)
+        if (b + i < T) { off[b + i] = run; run += cnt[b + i]; }
+    const int total = warp_tot[32];
+    __syncthreads();
+    return total;
+}
+
+template <bool kImage>
+__global__ void __launch_bounds__(kThreads, 1)
+revolve_kernel(RvArgs P, RenderBatch b, const float* __restrict__ img_params, float* __restrict__ img) {
+    extern __shared__ __align__(16) unsigned char smem[];
+    TriRec* rec = reinterpret_cast<TriRec*>(smem);
+    float* vx = reinterpret_cast<float*>(rec + P.nt);
+    float* vy = vx + P.nv;
+    float* viz = vy + P.nv;
+    int* tcnt = reinterpret_cast<int*>(viz + P.nv);
+    int* toff = tcnt + P.T;
+    uint16_t* ent = reinterpret_cast<uint16_t*>(toff + P.T);
+
+    __shared__ float s_cs[4];
+    __shared__ float sR[9];
+    __shared__ float sL[3];
+    __shared__ int s_count;
+    __shared__ int s_wtot[33];
+    __shared__ float s_part[kWarps];
+
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    const int M = kImage ? 1 : b.M;
+    for (int m = kImage ? 0 : (int)blockIdx.x; m < M; m += kImage ? 1 : (int)gridDim.x) {
+        // ---- 1. parameters and rotation ----------------------------------
+        if (tid < 4) {
+            float p;
+            if (kImage) {
+                p = img_params[tid >> 1];
+            } else {
+                const int row = m / b.per_row;
+                const int d = tid >> 1;
+                p = __fadd_rn(b.theta32[row * b.n + d], b.tau[(size_t)m * b.n + d]);
+            }
+            const double a = (double)p;
+            s_cs[tid] = (float)((tid & 1) ? sin(a) : cos(a));   // ca, sa, cb, sb
+        }
+        for (int i = tid; i < P.T; i += kThreads) tcnt[i] = 0;
+        if (tid == 0) s_count = 0;
+        __syncthreads();
+        if (tid == 0) {
+            const float ca = s_cs[0], sa = s_cs[1], cb = s_cs[2], sb = s_cs[3];
+            sR[0] = cb;                 sR[1] = 0.0f; sR[2] = sb;
+            sR[3] = __fmul_rn(sa, sb);  sR[4] = ca;   sR[5] = -__fmul_rn(sa, cb);
+            sR[6] = -__fmul_rn(ca, sb); sR[7] = sa;   sR[8] = __fmul_rn(ca, cb);
+            // light in model space: R^T l (shading value only)
+            sL[0] = sR[0] * P.l0 + sR[3] * P.l1 + sR[6] * P.l2;
+            sL[1] = sR[1] * P.l0 + sR[4] * P.l1 + sR[7] * P.l2;
+            sL[2] = sR[2] * P.l0 + sR[5] * P.l1 + sR[8] * P.l2;
+        }
+        __syncthreads();
+        // ---- 2. vertices ---------------------------------------------------
+        const float halfW = __fmul_rn((float)P.W, 0.5f), halfH = __fmul_rn((float)P.H, 0.5f);
+        for (int v = tid; v < P.nv; v += kThreads) {
+            const float x = P.verts[3 * v], y = P.verts[3 * v + 1], z = P.verts[3 * v + 2];
+            const float X = __fmaf_rn(sR[2], z, __fmaf_rn(sR[1], y, __fmul_rn(sR[0], x)));
+            const float Y = __fmaf_rn(sR[5], z, __fmaf_rn(sR[4], y, __fmul_rn(sR[3], x)));
+            const float w2 = __fmaf_rn(sR[8], z, __fmaf_rn(sR[7], y, __fmul_rn(sR[6], x)));
+            const float Z = __fsub_rn(P.eye_dist, w2);
+            const float qx = __fdiv_rn(X, Z), qy = __fdiv_rn(Y, Z);
+            vx[v] = __fmaf_rn(P.scale, qx, halfW);
+            vy[v] = __fmaf_rn(-P.scale, qy, halfH);
+            viz[v] = (Z > 0.0f) ? __fdiv_rn(1.0f, Z) : -1.0f;
+        }
+        __syncthreads();
+        // ---- 3. triangle setup ----------------------------------------------
+        for (int t = tid; t < P.nt; t += kThreads) {
+            const int ia = P.tris[3 * t], ib = P.tris[3 * t + 1], ic = P.tris[3 * t + 2];
+            const float iza = viz[ia], izb = viz[ib], izc = viz[ic];
+            if (!(iza > 0.0f && izb > 0.0f && izc > 0.0f)) continue;
+            const float ax = vx[ia], ay = vy[ia], bx = vx[ib], by = vy[ib], cx = vx[ic], cy = vy[ic];
+            const Edge e0 = edge_of(bx, by, cx, cy);
+            const Edge e1 = edge_of(cx, cy, ax, ay);
+            const Edge e2 = edge_of(ax, ay, bx, by);
+            const float D2 = edge_eval(e2.A, e2.B, e2.C, cx, cy);
+            if (!(D2 > 0.0f)) continue;
+            int xlo, xhi, ylo, yhi;
+            const float mnx = fminf(fminf(ax, bx), cx), mxx = fmaxf(fmaxf(ax, bx), cx);
+            const float mny = fminf(fminf(ay, by), cy), mxy = fmaxf(fmaxf(ay, by), cy);
+            if (!pixel_range(mnx, mxx, P.W, xlo, xhi) || !pixel_range(mny, mxy, P.H, ylo, yhi)) continue;
+            const float invD = __fdiv_rn(1.0f, D2);
+            TriRec r;
+            r.A0 = e0.A; r.B0 = e0.B; r.C0 = e0.C;
+            r.A1 = e1.A; r.B1 = e1.B; r.C1 = e1.C;
+            r.A2 = e2.A; r.B2 = e2.B; r.C2 = e2.C;
+            r.Aw = __fmul_rn(__fmaf_rn(e2.A, izc, __fmaf_rn(e1.A, izb, __fmul_rn(e0.A, iza))), invD);
+            r.Bw = __fmul_rn(__fmaf_rn(e2.B, izc, __fmaf_rn(e1.B, izb, __fmul_rn(e0.B, iza))), invD);
+            r.Cw = __fmul_rn(__fmaf_rn(e2.C, izc, __fmaf_rn(e1.C, izb, __fmul_rn(e0.C, iza))), invD);
+            const float sh = P.tnrm[3 * t] * sL[0] + P.tnrm[3 * t + 1] * sL[1] + P.tnrm[3 * t + 2] * sL[2];
+            r.shade = fmaxf(sh, 0.0f);
+            r.idx = t;
+            r.xr = (uint32_t)xlo | ((uint32_t)xhi << 16);
+            r.yr = (uint32_t)ylo | ((uint32_t)yhi << 16);
+            const int slot = atomicAdd(&s_count, 1);
+            rec[slot] = r;
+        }
+        __syncthreads();
+        const int count = s_count;
+        // ---- 4. binning -----------------------------------------------------
+        for (int s = tid; s < count; s += kThreads) {
+            const uint32_t xr = rec[s].xr, yr = rec[s].yr;
+            const int tx0 = (int)(xr & 0xffffu) / kTile, tx1 = (int)(xr >> 16) / kTile;
+            const int ty0 = (int)(yr & 0xffffu) / kTile, ty1 = (int)(yr >> 16) / kTile;
+            for (int ty = ty0; ty <= ty1; ++ty)
+                for (int tx = tx0; tx <= tx1; ++tx) atomicAdd(&tcnt[ty * P.TX + tx], 1);
+        }
+        __syncthreads();
+        const int total = block_scan(tcnt, toff, P.T, s_wtot);
+        const bool overflow = total > kEntryCap;
+        for (int i = tid; i < P.T; i += kThreads) tcnt[i] = 0;   // becomes the fill cursor
+        __syncthreads();
+        if (!overflow) {
+            for (int s = tid; s < count; s += kThreads) {
+                const uint32_t xr = rec[s].xr, yr = rec[s].yr;
+                const int tx0 = (int)(xr & 0xffffu) / kTile, tx1 = (int)(xr >> 16) / kTile;
+                const int ty0 = (int)(yr & 0xffffu) / kTile, ty1 = (int)(yr >> 16) / kTile;
+                for (int ty = ty0; ty <= ty1; ++ty)
+                    for (int tx = tx0; tx <= tx1; ++tx) {
+                        const int tile = ty * P.TX + tx;
+                        const int pos = atomicAdd(&tcnt[tile], 1);
+                        ent[toff[tile] + pos] = (uint16_t)s;
+                    }
+            }
+        }
+        __syncthreads();
+        // ---- 5. raster + loss ------------------------------------------------
+        const int lx = lane & 7, ly = lane >> 3;
+        float acc = 0.0f;
+        for (int t = warp; t < P.T; t += kWarps) {
+            const int ty = t / P.TX, tx = t - ty * P.TX;
+            const int x = tx * kTile + lx, y0 = ty * kTile + ly, y1 = y0 + 4;
+            int beg, end;
+            if (overflow) { beg = 0; end = count; }
+            else { beg = toff[t]; end = (t + 1 < P.T) ? toff[t + 1] : total; }
+            if (!kImage && !overflow && beg == end) {
+                if (lane == 0) acc += P.tile_t2[t];
+                continue;
+            }
+            const float fx = __fadd_rn((float)x, 0.5f);
+            const float fy0 = __fadd_rn((float)y0, 0.5f), fy1 = __fadd_rn((float)y1, 0.5f);
+            float bw0 = -INFINITY, bw1 = -INFINITY, sh0 = 0.0f, sh1 = 0.0f;
+            int bi0 = INT_MAX, bi1 = INT_MAX;
+            for (int j = beg; j < end; ++j) {
+                const int s = overflow ? j : (int)ent[j];
+                const float4* rp = reinterpret_cast<const float4*>(&rec[s]);
+                const float4 q0 = rp[0], q1 = rp[1], q2 = rp[2], q3 = rp[3];
+                const uint32_t xr = __float_as_uint(q3.z), yr = __float_as_uint(q3.w);
+                const int ti = __float_as_int(q3.y);
+                const bool inx = x >= (int)(xr & 0xffffu) && x <= (int)(xr >> 16);
+                const int ylo = (int)(yr & 0xffffu), yhi = (int)(yr >> 16);
+                if (inx && y0 >= ylo && y0 <= yhi) {
+                    const float E0 = edge_eval(q0.x, q0.y, q0.z, fx, fy0);
+                    const float E1 = edge_eval(q0.w, q1.x, q1.y, fx, fy0);
+                    const float E2 = edge_eval(q1.z, q1.w, q2.x, fx, fy0);
+                    if (edge_in(q0.x, q0.y, E0) && edge_in(q0.w, q1.x, E1) && edge_in(q1.z, q1.w, E2)) {
+                        const float wz = edge_eval(q2.y, q2.z, q2.w, fx, fy0);
+                        if (wz > bw0 || (wz == bw0 && ti < bi0)) { bw0 = wz; bi0 = ti; sh0 = q3.x; }
+                    }
+                }
+                if (inx && y1 >= ylo && y1 <= yhi) {
+                    const float E0 = edge_eval(q0.x, q0.y, q0.z, fx, fy1);
+                    const float E1 = edge_eval(q0.w, q1.x, q1.y, fx, fy1);
+                    const float E2 = edge_eval(q1.z, q1.w, q2.x, fx, fy1);
+                    if (edge_in(q0.x, q0.y, E0) && edge_in(q0.w, q1.x, E1) && edge_in(q1.z, q1.w, E2)) {
+                        const float wz = edge_eval(q2.y, q2.z, q2.w, fx, fy1);
+                        if (wz > bw1 || (wz == bw1 && ti < bi1)) { bw1 = wz; bi1 = ti; sh1 = q3.x; }
+                    }
+                }
+            }
+            if (x < P.W) {
+#pragma unroll
+                for (int h = 0; h < 2; ++h) {
+                    const int y = h ? y1 : y0;
+                    if (y >= P.H) continue;
+                    const float shv = h ? sh1 : sh0;
+                    const bool hit = (h ? bi1 : bi0) != INT_MAX;
+                    const size_t pix = (size_t)y * P.W + x;
+                    const float c0 = hit ? shv * P.alb0 : 0.0f;
+                    const float c1 = hit ? shv * P.alb1 : 0.0f;
+                    const float c2 = hit ? shv * P.alb2 : 0.0f;
+                    if (kImage) {
+                        img[3 * pix] = c0; img[3 * pix + 1] = c1; img[3 * pix + 2] = c2;
+                    } else {
+                        const float d0 = c0 - P.target[3 * pix];
+                        const float d1 = c1 - P.target[3 * pix + 1];
+                        const float d2 = c2 - P.target[3 * pix + 2];
+                        acc += d0 * d0 + d1 * d1 + d2 * d2;
+                    }
+                }
+            }
+        }
+        // ---- 6. reduction -----------------------------------------------------
+        if (!kImage) {
+            acc = warp_sum(acc);
+            if (lane == 0) s_part[warp] = acc;
+            __syncthreads();
+            if (warp == 0) {
+                float v = s_part[lane];
+                v = warp_sum(v);
+                if (lane == 0) b.loss[m] = v / (float)(P.W * P.H * 3);
+            }
+        }
+        __syncthreads();
+    }
+}
+
+__global__ void normals_kernel(const float* verts, const int32_t* tris, int nt, float* tnrm) {
+    const int t = blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= nt) return;
+    const float* A = verts + 3 * tris[3 * t];
+    const float* B = verts + 3 * tris[3 * t + 1];
+    const float* C = verts + 3 * tris[3 * t + 2];
+    const double u0 = (double)B[0] - A[0], u1 = (double)B[1] - A[1], u2 = (double)B[2] - A[2];
+    const double v0 = (double)C[0] - A[0], v1 = (double)C[1] - A[1], v2 = (double)C[2] - A[2];
+    const double n0 = u1 * v2 - u2 * v1, n1 = u2 * v0 - u0 * v2, n2 = u0 * v1 - u1 * v0;
+    const double len = sqrt(n0 * n0 + n1 * n1 + n2 * n2);
+    const double inv = len > 0.0 ? 1.0 / len : 0.0;
+    tnrm[3 * t] = (float)(n0 * inv);
+    tnrm[3 * t + 1] = (float)(n1 * inv);
+    tnrm[3 * t + 2] = (float)(n2 * inv);
+}
+
+__global__ void tile_t2_kernel(const float* target, int W, int H, int TX, int T, float* out) {
+    const int t = blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= T) return;
+    const int ty = t / TX, tx = t - ty * TX;
+    float s = 0.0f;
+    for (int yy = 0; yy < kTile; ++yy)
+        for (int xx = 0; xx < kTile; ++xx) {
+            const int x = tx * kTile + xx, y = ty * kTile + yy;
+            if (x >= W || y >= H) continue;
+            const size_t p = (size_t)y * W + x;
+            for (int c = 0; c < 3; ++c) s += target[3 * p + c] * target[3 * p + c];
+        }
+    out[t] = s;
+}
+
+RvArgs make_args(const DevScene& sc) {
+    RvArgs a;
+    a.verts = sc.verts; a.tris = sc.tris; a.tnrm = sc.tnrm; a.target = sc.target; a.tile_t2 = sc.tile_t2;
+    a.nv = sc.nv; a.nt = sc.nt; a.W = sc.W; a.H = sc.H;
+    a.TX = (sc.W + kTile - 1) / kTile; a.TY = (sc.H + kTile - 1) / kTile; a.T = a.TX * a.TY;
+    a.alb0 = sc.albedo[0]; a.alb1 = sc.albedo[1]; a.alb2 = sc.albedo[2];
+    a.l0 = sc.light[0]; a.l1 = sc.light[1]; a.l2 = sc.light[2];
+    a.eye_dist = sc.eye_dist; a.scale = sc.scale;
+    return a;
+}
+
+}  // namespace
+
+size_t revolve_smem_bytes(int nv, int nt, int W, int H) {
+    const int T = ((W + kTile - 1) / kTile) * ((H + kTile - 1) / kTile);
+    return sizeof(TriRec) * (size_t)nt + 3 * sizeof(float) * (size_t)nv + 2 * sizeof(int) * (size_t)T +
+           sizeof(uint16_t) * kEntryCap;
+}
+
+void revolve_prepare(DevScene& sc, cudaStream_t s) {
+    normals_kernel<<<(sc.nt + 255) / 256, 256, 0, s>>>(sc.verts, sc.tris, sc.nt, sc.tnrm);
+    sc.rv_smem = revolve_smem_bytes(sc.nv, sc.nt, sc.W, sc.H);
+    cudaFuncSetAttribute(revolve_kernel<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sc.rv_smem);
+    cudaFuncSetAttribute(revolve_kernel<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sc.rv_smem);
+}
+
+void revolve_tile_t2(DevScene& sc, cudaStream_t s) {
+    const int TX = (sc.W + kTile - 1) / kTile, TY = (sc.H + kTile - 1) / kTile;
+    tile_t2_kernel<<<(TX * TY + 127) / 128, 128, 0, s>>>(sc.target, sc.W, sc.H, TX, TX * TY, sc.tile_t2);
+}
+
+int revolve_tiles(int W, int H) { return ((W + kTile - 1) / kTile) * ((H + kTile - 1) / kTile); }
+
+void launch_revolve_loss(const DevScene& sc, const RenderBatch& b, cudaStream_t s) {
+    const int grid = b.M < num_sms() ? b.M : num_sms();
+    revolve_kernel<false><<<grid, kThreads, sc.rv_smem, s>>>(make_args(sc), b, nullptr, nullptr);
+}
+
+void launch_revolve_image(const DevScene& sc, const float* params, float* img, cudaStream_t s) {
+    RenderBatch b{};
+    revolve_kernel<true><<<1, kThreads, sc.rv_smem, s>>>(make_args(sc), b, params, img);
+}
+
+}  // namespace hr

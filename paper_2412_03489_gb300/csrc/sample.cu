@@ -1,0 +1,266 @@
+// K1: perturbation sampler and kernel weights (Sec. 3.2-3.5).
+//
+// One thread draws one antithetic pair k of one sample group: a + leg from
+// the positive lobe and a - leg from the negative lobe of the chosen kernel,
+// every other dimension N(0, sigma^2) shared by both legs (Sec. 3.2,
+// separability; Suppl. "Smooth Gradient Marginalization").  Lobe samples are
+// computed in FP64 and rounded once to FP32: that FP32 value is the
+// perturbation every renderer sees.  Weights are evaluated in FP64 at the
+// FP32 perturbation and stored in FP32.
+//
+// Philox counter of pair k: (k, block, (1 << 24) | sub, request), key = seed.
+// Block 0 = (component word, lobe uniform a, lobe uniform b, sign word);
+// block 1 + b holds the Box-Muller uniforms of dims 4b .. 4b + 3.
+#include <cmath>
+
+#include "hr_device.cuh"
+#include "hr_internal.h"
+
+namespace hr {
+namespace {
+
+constexpr int kMaxN = 64;
+constexpr double kPi = 3.141592653589793238462643383279502884;
+
+// Root s > 0 of  log(s) - s + 1 + L = 0  for L >= 0, i.e. s e^{-s} = e^{-1-L}.
+// upper: the root s >= 1 (tails of the diagonal lobe, |t| > 1), else s <= 1.
+// Halley's method on the log form, started from the branch-point expansion
+// s = 1 +- u + u^2/3 (u = sqrt(2L)) or from the asymptotics of each branch.
+__device__ double lobe_root(double L, bool upper) {
+    const double u = sqrt(2.0 * L);
+    if (u < 1e-9) return upper ? 1.0 + u : 1.0 - u;
+    double s;
+    if (upper) {
+        s = (u < 2.0) ? 1.0 + u + u * u / 3.0 : (1.0 + L) + log(1.0 + L);
+    } else {
+        const double y = exp(-1.0 - L);
+        s = (u < 1.0) ? 1.0 - u + u * u / 3.0 : y * (1.0 + y);
+    }
+    for (int it = 0; it < 64; ++it) {
+        const double g = log(s) - s + 1.0 + L;
+        const double g1 = 1.0 / s - 1.0;
+        const double g2 = -1.0 / (s * s);
+        double sn = s - 2.0 * g * g1 / (2.0 * g1 * g1 - g * g2);
+        if (!(sn > 0.0)) sn = 0.5 * s;
+        if (upper && sn < 1.0) sn = 0.5 * (s + 1.0);
+        if (!upper && sn > 1.0) sn = 0.5 * (s + 1.0);
+        const bool done = fabs(sn - s) <= 4e-16 * sn;
+        s = sn;
+        if (done) break;
+    }
+    return s;
+}
+
+// Inverse of the diagonal-lobe CDF (standardised t = tau / sigma): with tail
+// mass m (or middle offset a = |c - 1/2|), t^2 e^{-t^2} = 16 m^2 / e, i.e.
+// s = t^2 solves s e^{-s} = e^{-1-L}, L = -log(16 m^2).
+__device__ double diag_inverse(double c) {
+    if (c < 0.25 || c > 0.75) {
+        const double m = c < 0.25 ? c : 1.0 - c;
+        const double m16 = 16.0 * m * m;
+        const double L = m16 < 0.5 ? -log(m16) : -log1p(-((1.0 - 4.0 * m) * (1.0 + 4.0 * m)));
+        const double t = sqrt(lobe_root(L, true));
+        return c < 0.25 ? -t : t;
+    }
+    const double d = c - 0.5;
+    if (d == 0.0) return 0.0;
+    const double a = fabs(d);
+    const double a16 = 16.0 * a * a;
+    const double L = a16 < 0.5 ? -log(a16) : -log1p(-((1.0 - 4.0 * a) * (1.0 + 4.0 * a)));
+    const double t = sqrt(lobe_root(L, false));
+    return d < 0.0 ? -t : t;
+}
+
+__device__ __forceinline__ int upper_index(int a, int b, int n) {
+    return a * n - a * (a - 1) / 2 + (b - a);
+}
+
+// S(tau): n^2 q(tau) / N(tau) for the Hessian mixture, O(n) via
+// sum_{i != j} |t_i t_j| = (sum |t_i|)^2 - sum t_i^2.
+__device__ double hess_mixture(const float* t, int n, double s2, double Zd, double Zo) {
+    const double s4 = s2 * s2;
+    double sd = 0.0, sa = 0.0, sq = 0.0;
+    for (int d = 0; d < n; ++d) {
+        const double x = (double)t[d];
+        sd += fabs(x * x - s2);
+        sa += fabs(x);
+        sq += x * x;
+    }
+    const double off = sa * sa - sq;
+    return (sd / s4 / Zd + (off > 0.0 ? off : 0.0) / s4 / Zo) / ((double)n * (double)n);
+}
+
+__device__ void write_weights(const SampleArgs& a, const SampleGroup& G, int m, const float* t, double sign) {
+    const int n = a.n;
+    const double s2 = a.sigma * a.sigma, s4 = s2 * s2;
+    if (G.quantity == 3) {
+        const double S = hess_mixture(t, n, s2, a.Zd, a.Zo);
+        a.invS[m] = (float)(S > 0.0 ? 1.0 / S : 0.0);
+        return;
+    }
+    float* wm = a.w + (size_t)m * a.E;
+    for (int e = 0; e < a.E; ++e) wm[e] = 0.0f;
+    if (G.comp_i >= 0) {
+        if (G.quantity == 0) {
+            wm[G.comp_i] = (float)(sign * a.Zg);
+        } else {
+            const int lo = min(G.comp_i, G.comp_j), hi = max(G.comp_i, G.comp_j);
+            wm[upper_index(lo, hi, n)] = (float)(sign * (lo == hi ? a.Zd : a.Zo));
+        }
+        return;
+    }
+    if (G.quantity == 0) {
+        double S = 0.0;
+        for (int d = 0; d < n; ++d) S += fabs((double)t[d] / s2);
+        S = S / a.Zg / (double)n;
+        for (int d = 0; d < n; ++d) wm[d] = (float)(S > 0.0 ? ((double)t[d] / s2) / S : 0.0);
+        return;
+    }
+    const double S = hess_mixture(t, n, s2, a.Zd, a.Zo);
+    if (!(S > 0.0)) return;
+    if (G.quantity == 1) {
+        int e = 0;
+        for (int i = 0; i < n; ++i) {
+            const double ti = (double)t[i];
+            for (int j = i; j < n; ++j, ++e) {
+                const double c = (i == j) ? (ti * ti - s2) / s4 : ti * (double)t[j] / s4;
+                wm[e] = (float)(c / S);
+            }
+        }
+    } else {
+        double tv = 0.0;
+        for (int d = 0; d < n; ++d) tv += (double)t[d] * a.v[d];
+        for (int k = 0; k < n; ++k) {
+            const double hv = (double)t[k] * tv / s4 - a.v[k] / s2;
+            wm[k] = (float)(hv / S);
+        }
+    }
+}
+
+__global__ void __launch_bounds__(128) sample_kernel(SampleArgs a) {
+    const SampleGroup G = a.groups[blockIdx.y];
+    const int k = blockIdx.x * blockDim.x + threadIdx.x;
+    if (k >= G.P) return;
+    const int n = a.n;
+    const double sigma = a.sigma;
+    const uint32_t sub = G.sub + (a.step ? 64u * (uint32_t)(*a.step) : 0u);
+    const uint32_t c2 = (TAG_SAMPLE << 24) | (sub & 0xFFFFFFu);
+    double g[kMaxN];
+    for (int d = 0; d < n; d += 4) {
+        const u32x4 r = philox_seed(a.seed, (uint32_t)k, (uint32_t)(1 + d / 4), c2, G.request);
+        const uint32_t words[4] = {r.x, r.y, r.z, r.w};
+#pragma unroll
+        for (int q = 0; q < 2; ++q) {
+            const double R = sqrt(-2.0 * log(u01d(words[2 * q])));
+            const double ph = 2.0 * kPi * u01d(words[2 * q + 1]);
+            if (d + 2 * q < n) g[d + 2 * q] = sigma * (R * cos(ph));
+            if (d + 2 * q + 1 < n) g[d + 2 * q + 1] = sigma * (R * sin(ph));
+        }
+    }
+    const u32x4 w0 = philox_seed(a.seed, (uint32_t)k, 0u, c2, G.request);
+    int i, j;
+    if (G.comp_i >= 0) {
+        i = G.comp_i;
+        j = G.lobe == 0 ? G.comp_i : G.comp_j;
+    } else if (G.lobe == 0) {
+        i = (int)(((uint64_t)w0.x * (uint64_t)n) >> 32);
+        j = i;
+    } else {
+        const int e = (int)(((uint64_t)w0.x * (uint64_t)(n * n)) >> 32);
+        i = e / n;
+        j = e - i * n;
+    }
+    const double ua = u01d(w0.y), ub = u01d(w0.z);
+    double pi_, pj, mi, mj;   // + / - leg values in dims i and j
+    if (G.lobe == 0) {
+        const double r = sigma * sqrt(-2.0 * log(ua));
+        pi_ = r; mi = -r; pj = pi_; mj = mi;
+    } else if (i == j) {
+        const double cp = ua < 0.5 ? 0.5 * ua : 0.5 + 0.5 * ua;
+        const double cm = 0.25 + 0.5 * ua;
+        pi_ = sigma * diag_inverse(cp);
+        mi = sigma * diag_inverse(cm);
+        pj = pi_; mj = mi;
+    } else {
+        const double ri = sigma * sqrt(-2.0 * log(ua));
+        const double rj = sigma * sqrt(-2.0 * log(ub));
+        const double sg = (w0.w & 1u) ? -1.0 : 1.0;
+        pi_ = sg * ri; pj = sg * rj;
+        mi = sg * ri; mj = -sg * rj;
+    }
+    const int mp = G.m0 + 2 * k, mm = mp + 1;
+    float* tp = a.tau + (size_t)mp * n;
+    float* tm = a.tau + (size_t)mm * n;
+    for (int d = 0; d < n; ++d) {
+        double vp = g[d], vm = g[d];
+        if (d == i) { vp = pi_; vm = mi; }
+        if (d == j) { vp = pj; vm = mj; }
+        tp[d] = (float)vp;
+        tm[d] = (float)vm;
+    }
+    if (a.meta) {
+        a.meta[mp] = make_uint2(sub, (uint32_t)k);
+        a.meta[mm] = make_uint2(sub, (uint32_t)k);
+    }
+    if (a.w || a.invS) {
+        write_weights(a, G, mp, tp, 1.0);
+        write_weights(a, G, mm, tm, -1.0);
+    }
+}
+
+// K6: estimator sums.  Element e sums w[m][e] * loss[m] over its row range in
+// a fixed order: 256 contiguous chunks, each a Kahan-compensated FP32 sum,
+// then an FP64 tree over the chunks, times 1/(2P).
+constexpr int kFinThreads = 256;
+
+__global__ void __launch_bounds__(kFinThreads) finalize_kernel(FinalizeArgs a) {
+    __shared__ double sh[kFinThreads], sa[kFinThreads];
+    const int e = blockIdx.x;
+    const int m0 = a.elementwise ? e * a.pairs2 : 0;
+    const int cnt = a.pairs2;
+    const int chunk = (cnt + kFinThreads - 1) / kFinThreads;
+    const int b = m0 + threadIdx.x * chunk;
+    const int end = min(m0 + cnt, b + chunk);
+    Kahan ks, ka;
+    for (int m = b; m < end; ++m) {
+        const float x = __fmul_rn(a.w[(size_t)m * a.E + e], a.loss[m]);
+        ks.add(x);
+        ka.add(fabsf(x));
+    }
+    sh[threadIdx.x] = (double)ks.s - (double)ks.c;
+    sa[threadIdx.x] = (double)ka.s - (double)ka.c;
+    __syncthreads();
+    for (int o = kFinThreads / 2; o > 0; o >>= 1) {
+        if (threadIdx.x < o) {
+            sh[threadIdx.x] += sh[threadIdx.x + o];
+            sa[threadIdx.x] += sa[threadIdx.x + o];
+        }
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) {
+        const double val = sh[0] * a.inv2P;
+        a.out_flat[e] = val;
+        if (a.out_scale) a.out_scale[e] = sa[0] * a.inv2P;
+        if (a.hessian && a.out_full) {
+            // e -> (row, col) of the upper triangle
+            int r = 0, rem = e;
+            while (rem >= a.n - r) { rem -= a.n - r; ++r; }
+            const int c = r + rem;
+            a.out_full[r * a.n + c] = val;
+            a.out_full[c * a.n + r] = val;
+        }
+    }
+}
+
+}  // namespace
+
+void launch_sample(const SampleArgs& a, int n_groups, int max_P, cudaStream_t s) {
+    dim3 grid((max_P + 127) / 128, n_groups);
+    sample_kernel<<<grid, 128, 0, s>>>(a);
+}
+
+void launch_finalize(const FinalizeArgs& a, cudaStream_t s) {
+    finalize_kernel<<<a.E, kFinThreads, 0, s>>>(a);
+}
+
+}  // namespace hr

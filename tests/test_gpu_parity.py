@@ -1,0 +1,231 @@
+"""GPU parity: the CUDA path through the C ABI against the oracle on the same
+seeded inputs and the same Philox samples.
+
+* perturbations: bit-exact (FP32 equality of every tau);
+* disc losses: bit-exact (0/1 pixels, exact integer counts);
+* raster images: identical coverage (same FP32 decision sequences), shading
+  within FP32 rounding;
+* estimates: |gpu - oracle| <= 1e-4 max(|oracle|, A_e) (see tests/parity.py).
+"""
+import numpy as np
+import pytest
+
+import oracle as O
+from paper_2412_03489_gb300 import build as hb
+from paper_2412_03489_gb300 import hr
+from paper_2412_03489_gb300 import workloads as wl
+from parity import assert_estimate_close, assert_losses_close, flat_of
+
+pytestmark = pytest.mark.gpu
+
+hb.build()
+
+Q = {"grad": hr.HR_GRAD, "hessian": hr.HR_HESSIAN, "hvp": hr.HR_HVP}
+S = {"elementwise": hr.HR_ELEMENTWISE, "aggregate": hr.HR_AGGREGATE}
+
+
+def run_both(sc, renderer, quantity, M, strategy, seed=11, request=3, sub=0, v=None, theta=None, scene=None):
+    theta = np.asarray(sc["theta_query"] if theta is None else theta, np.float64)
+    own = scene is None
+    Sc = hr.Scene(sc) if own else scene
+    out, dbg = Sc.estimate(Q[quantity], theta, sc["sigma"], M, S[strategy], seed, request, sub, v=v, debug=True)
+    ref = O.estimate(renderer, quantity, theta, sc["sigma"], M, strategy, seed, request, sub, v=v)
+    if own:
+        Sc.close()
+    return flat_of(quantity, out, sc["n_params"]), dbg, ref
+
+
+def check_samples(dbg, ref):
+    assert dbg["tau"].shape == ref.tau.shape
+    mism = np.count_nonzero(dbg["tau"] != ref.tau)
+    assert mism == 0, f"{mism} perturbation values differ"
+    # weights: FP32 of the FP64 value on both sides; compare to FP32 rounding
+    w32 = ref.w.astype(np.float32)
+    assert np.allclose(dbg["w"], w32, rtol=2e-7, atol=1e-30 + 2e-7 * np.abs(w32).max())
+
+
+# ---------------------------------------------------------------------------
+# disc (64 x 64, 2 params, sigma 0.05, 1024 samples)
+# ---------------------------------------------------------------------------
+@pytest.mark.parametrize("strategy", ["elementwise", "aggregate"])
+@pytest.mark.parametrize("quantity", ["hessian", "grad"])
+def test_disc_full_size(quantity, strategy):
+    sc = wl.disc_scene()
+    flat, dbg, ref = run_both(sc, O.DiscRenderer(sc), quantity, 1024, strategy)
+    check_samples(dbg, ref)
+    assert np.array_equal(dbg["losses"].astype(np.float64), ref.losses)
+    assert_estimate_close(flat, ref, what=f"disc {quantity} {strategy}")
+    assert np.allclose(dbg["scale"], ref.scale, rtol=1e-5)
+
+
+def test_disc_hvp_and_identity():
+    sc = wl.disc_scene()
+    v = np.array([0.3, -1.2])
+    flat, dbg, ref = run_both(sc, O.DiscRenderer(sc), "hvp", 1024, "aggregate", v=v)
+    check_samples(dbg, ref)
+    assert_estimate_close(flat, ref, what="disc hvp")
+    Hflat, _, _ = run_both(sc, O.DiscRenderer(sc), "hessian", 1024, "aggregate")
+    H = np.array([[Hflat[0], Hflat[1]], [Hflat[1], Hflat[2]]])
+    assert np.allclose(H @ v, flat, rtol=1e-5, atol=1e-5 * np.abs(ref.scale).max())
+
+
+@pytest.mark.parametrize("W,H,M", [(37, 23, 2), (1, 1, 6), (64, 64, 2)])
+def test_disc_ragged_and_minimum(W, H, M):
+    sc = wl.disc_scene(width=W, height=H)
+    flat, dbg, ref = run_both(sc, O.DiscRenderer(sc), "hessian", M, "aggregate")
+    check_samples(dbg, ref)
+    # exact mismatch counts; the loss is count / (W H) rounded once to FP32
+    npx = W * H
+    assert np.array_equal(np.rint(dbg["losses"].astype(np.float64) * npx), np.rint(ref.losses * npx))
+    assert np.all(np.abs(dbg["losses"] - ref.losses) <= np.spacing(np.float32(ref.losses)))
+    assert_estimate_close(flat, ref, what="disc ragged")
+
+
+# ---------------------------------------------------------------------------
+# surface of revolution (2048 triangles)
+# ---------------------------------------------------------------------------
+@pytest.mark.parametrize("size", [(64, 64), (50, 37), (256, 256)])
+def test_revolve_images_match(size):
+    W, H = size
+    sc = wl.revolve_scene(width=W, height=H)
+    Sc = hr.Scene(sc)
+    r = O.RevolveRenderer(sc)
+    g = np.random.default_rng(1)
+    for _ in range(3):
+        p = np.asarray(sc["theta_target"]) + g.normal(0, 0.3, 2)
+        gi = Sc.render(p).reshape(H, W, 3)
+        oi = r.image(p.astype(np.float32)).reshape(H, W, 3)
+        assert np.array_equal(gi.sum(-1) > 0, oi.sum(-1) > 0), "coverage differs"
+        assert np.allclose(gi, oi, rtol=1e-5, atol=1e-6)
+    # target
+    tgt = Sc.render(np.asarray(sc["theta_target"]))
+    assert np.allclose(tgt, r.target, rtol=1e-5, atol=1e-6)
+    Sc.close()
+
+
+@pytest.mark.parametrize("strategy", ["elementwise", "aggregate"])
+def test_revolve_small(strategy):
+    sc = wl.revolve_scene(width=72, height=56)
+    flat, dbg, ref = run_both(sc, O.RevolveRenderer(sc), "hessian", 128, strategy)
+    check_samples(dbg, ref)
+    assert_losses_close(dbg["losses"], ref.losses, 2e-5, "revolve losses")
+    assert_estimate_close(flat, ref, what=f"revolve {strategy}")
+
+
+def test_revolve_full_size_bench_configuration():
+    """256 x 256, 2048 triangles, sigma 0.1, 4096 aggregate samples: the bench
+    workload in its launch configuration, compared in full."""
+    sc = wl.revolve_scene()
+    flat, dbg, ref = run_both(sc, O.RevolveRenderer(sc), "hessian", 4096, "aggregate", seed=2024, request=0)
+    check_samples(dbg, ref)
+    assert_losses_close(dbg["losses"], ref.losses, 2e-5, "revolve losses")
+    assert_estimate_close(flat, ref, what="revolve full")
+
+
+# ---------------------------------------------------------------------------
+# coloured triangles
+# ---------------------------------------------------------------------------
+def test_tris2d_images_and_small_estimate():
+    sc = wl.tris2d_scene(width=80, height=60)
+    Sc = hr.Scene(sc)
+    r = O.Tris2dRenderer(sc)
+    for b in range(3):
+        p = sc["theta_init"][b]
+        gi = Sc.render(p)
+        oi = r.image(p.astype(np.float32))
+        assert np.array_equal(gi, oi)
+    v = sc["v"]
+    flat, dbg, ref = run_both(sc, r, "hvp", 32, "aggregate", v=v, scene=Sc)
+    check_samples(dbg, ref)
+    assert_losses_close(dbg["losses"], ref.losses, 2e-5, "tris2d losses")
+    assert_estimate_close(flat, ref, what="tris2d hvp")
+    flat, dbg, ref = run_both(sc, r, "grad", 32, "aggregate", scene=Sc)
+    assert_estimate_close(flat, ref, what="tris2d grad")
+    Sc.close()
+
+
+# ---------------------------------------------------------------------------
+# path tracer
+# ---------------------------------------------------------------------------
+def test_ptbox_images_match():
+    sc = wl.ptbox_scene(width=24, height=20, spp=2, target_spp=4)
+    Sc = hr.Scene(sc)
+    r = O.PtboxRenderer(sc)
+    p = np.asarray(sc["theta_query"])
+    gi = Sc.render(p, seed=5, request=2, sub=1, k=3, tag=hr.TAG_PATH, spp=2)
+    oi = r.image(p.astype(np.float32), 2, 5, 2, 1, 3, O.TAG_PATH)
+    assert np.allclose(gi, oi, rtol=2e-5, atol=2e-5 * oi.max())
+    assert np.allclose(Sc.render(np.asarray(sc["theta_target"]), seed=sc["seed"], tag=hr.TAG_TARGET, spp=4),
+                       r.target, rtol=2e-5, atol=2e-5 * r.target.max())
+    Sc.close()
+
+
+def test_ptbox_hvp_small():
+    sc = wl.ptbox_scene(width=20, height=16, spp=2, target_spp=4)
+    flat, dbg, ref = run_both(sc, O.PtboxRenderer(sc), "hvp", 16, "aggregate", v=sc["v"])
+    check_samples(dbg, ref)
+    assert_losses_close(dbg["losses"], ref.losses, 1e-4, "ptbox losses")
+    assert_estimate_close(flat, ref, what="ptbox hvp")
+
+
+# ---------------------------------------------------------------------------
+# Newton-CG
+# ---------------------------------------------------------------------------
+@pytest.mark.parametrize("use_graph", [0, 1])
+def test_newton_cg_step_matches_oracle(use_graph):
+    sc = wl.tris2d_scene(width=48, height=40, n_instances=3)
+    Sc = hr.Scene(sc)
+    r = O.Tris2dRenderer(sc)
+    B, n = 3, sc["n_params"]
+    opts = hr.hr_cg_opts()
+    opts.sigma, opts.n_grad, opts.n_hvp, opts.cg_iters = sc["sigma"], 16, 8, 4
+    opts.lambda_rel, opts.trust_radius, opts.seed, opts.request_base, opts.use_graph = 1e-3, 0.05, 99, 10, use_graph
+    th0 = np.ascontiguousarray(sc["theta_init"][:B], np.float64)
+    st = hr.hr_optstate_create(Sc.handle, B, th0, opts)
+    info = (hr.hr_step_info * B)()
+    ref_th = th0.copy()
+    for step in range(2):
+        hr.hr_newton_cg_step(Sc.handle, st, info)
+        got = np.zeros((B, n))
+        hr.hr_optstate_theta(st, got)
+        for b in range(B):
+            new, inf = O.newton_cg_step(r, ref_th[b], sc["sigma"], 16, 8, 4, 1e-3, 0.05, 99, 10 + b, step)
+            d_ref, d_gpu = new - ref_th[b], got[b] - ref_th[b]
+            assert info[b].iters == inf.iters
+            assert np.allclose(d_gpu, d_ref, rtol=1e-3, atol=1e-4 * np.linalg.norm(d_ref)), (step, b)
+            assert abs(info[b].grad_norm - inf.grad_norm) <= 1e-4 * inf.grad_norm
+            ref_th[b] = got[b]          # continue both from the GPU iterate
+    hr.hr_optstate_destroy(st)
+    Sc.close()
+
+
+# ---------------------------------------------------------------------------
+# device-pointer entry point and argument validation
+# ---------------------------------------------------------------------------
+def test_dev_entry_point_matches_host():
+    torch = pytest.importorskip("torch")
+    sc = wl.disc_scene()
+    Sc = hr.Scene(sc)
+    theta = np.asarray(sc["theta_query"], np.float64)
+    host = Sc.estimate(hr.HR_HESSIAN, theta, sc["sigma"], 256, hr.HR_AGGREGATE, 4, 4)
+    d_theta = torch.tensor(theta, dtype=torch.float64, device="cuda")
+    d_out = torch.zeros((2, 2), dtype=torch.float64, device="cuda")
+    o = hr.make_opts(sc["sigma"], 256, hr.HR_AGGREGATE, 4, 4, stream=torch.cuda.current_stream().cuda_stream)
+    hr.hr_estimate_dev(Sc.handle, hr.HR_HESSIAN, d_theta.data_ptr(), None, o, d_out.data_ptr())
+    torch.cuda.synchronize()
+    assert np.array_equal(d_out.cpu().numpy(), host)
+    Sc.close()
+
+
+def test_invalid_arguments_are_rejected():
+    sc = wl.disc_scene()
+    Sc = hr.Scene(sc)
+    theta = np.asarray(sc["theta_query"], np.float64)
+    for M, sigma, strat in [(3, 0.05, 1), (0, 0.05, 1), (64, -1.0, 1), (64, 0.05, 7)]:
+        with pytest.raises(hr.HRError):
+            Sc.estimate(hr.HR_HESSIAN, theta, sigma, M, strat, 1, 1)
+    with pytest.raises(hr.HRError):
+        Sc.estimate(hr.HR_HVP, theta, 0.05, 64, hr.HR_ELEMENTWISE, 1, 1, v=np.ones(2))
+    # the scene still works afterwards
+    Sc.estimate(hr.HR_HESSIAN, theta, 0.05, 64, hr.HR_AGGREGATE, 1, 1)
+    Sc.close()

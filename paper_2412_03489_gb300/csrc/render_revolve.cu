@@ -35,10 +35,19 @@ struct __align__(16) TriRec {
     float B1, C1, A2, B2;
     float C2, Aw, Bw, Cw;
     float shade;
-    int idx;
+    uint32_t key;  // triangle index | top-left flag of edge i at bit 29 + i
     uint32_t xr;   // x_lo | x_hi << 16 (pixel columns whose centre is inside the bbox)
     uint32_t yr;
 };
+
+// E > 0, or E == 0 on a top-left edge, is one compare: E > thr with thr = 0
+// or thr = -(smallest subnormal) (no float lies strictly between the two)
+__device__ __forceinline__ float tl_threshold(uint32_t key, int i) {
+    return ((key >> (29 + i)) & 1u) ? -0x1p-149f : 0.0f;
+}
+__device__ __forceinline__ uint32_t tl_bit(float A, float B) {
+    return (A > 0.0f || (A == 0.0f && B > 0.0f)) ? 1u : 0u;
+}
 
 struct RvArgs {
     const float* verts;
@@ -112,6 +121,8 @@ revolve_kernel(RvArgs P, RenderBatch b, const float* __restrict__ img_params, fl
     __shared__ int s_count;
     __shared__ int s_wtot[33];
     __shared__ float s_part[kWarps];
+    __shared__ int s_tile;
+    float* tshade = reinterpret_cast<float*>(ent + kEntryCap);   // [nt] shade by triangle index
 
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     const int M = kImage ? 1 : b.M;
@@ -130,7 +141,7 @@ revolve_kernel(RvArgs P, RenderBatch b, const float* __restrict__ img_params, fl
             s_cs[tid] = (float)((tid & 1) ? sin(a) : cos(a));   // ca, sa, cb, sb
         }
         for (int i = tid; i < P.T; i += kThreads) tcnt[i] = 0;
-        if (tid == 0) s_count = 0;
+        if (tid == 0) { s_count = 0; s_tile = 0; }
         __syncthreads();
         if (tid == 0) {
             const float ca = s_cs[0], sa = s_cs[1], cb = s_cs[2], sb = s_cs[3];
@@ -182,7 +193,8 @@ revolve_kernel(RvArgs P, RenderBatch b, const float* __restrict__ img_params, fl
             r.Cw = __fmul_rn(__fmaf_rn(e2.C, izc, __fmaf_rn(e1.C, izb, __fmul_rn(e0.C, iza))), invD);
             const float sh = P.tnrm[3 * t] * sL[0] + P.tnrm[3 * t + 1] * sL[1] + P.tnrm[3 * t + 2] * sL[2];
             r.shade = fmaxf(sh, 0.0f);
-            r.idx = t;
+            tshade[t] = r.shade;
+            r.key = (uint32_t)t | (tl_bit(e0.A, e0.B) << 29) | (tl_bit(e1.A, e1.B) << 30) | (tl_bit(e2.A, e2.B) << 31);
             r.xr = (uint32_t)xlo | ((uint32_t)xhi << 16);
             r.yr = (uint32_t)ylo | ((uint32_t)yhi << 16);
             const int slot = atomicAdd(&s_count, 1);
@@ -218,9 +230,15 @@ revolve_kernel(RvArgs P, RenderBatch b, const float* __restrict__ img_params, fl
         }
         __syncthreads();
         // ---- 5. raster + loss ------------------------------------------------
+        // warps fetch tiles dynamically (object tiles cost far more than
+        // background tiles); each lane owns pixels (x, y0) and (x, y0 + 4)
         const int lx = lane & 7, ly = lane >> 3;
         float acc = 0.0f;
-        for (int t = warp; t < P.T; t += kWarps) {
+        for (;;) {
+            int t = 0;
+            if (lane == 0) t = atomicAdd(&s_tile, 1);
+            t = __shfl_sync(0xffffffffu, t, 0);
+            if (t >= P.T) break;
             const int ty = t / P.TX, tx = t - ty * P.TX;
             const int x = tx * kTile + lx, y0 = ty * kTile + ly, y1 = y0 + 4;
             int beg, end;
@@ -230,56 +248,69 @@ revolve_kernel(RvArgs P, RenderBatch b, const float* __restrict__ img_params, fl
                 if (lane == 0) acc += P.tile_t2[t];
                 continue;
             }
+            const bool v0 = x < P.W && y0 < P.H, v1 = x < P.W && y1 < P.H;
+            float tg0[3] = {0.f, 0.f, 0.f}, tg1[3] = {0.f, 0.f, 0.f};
+            if (!kImage) {
+                if (v0) for (int c = 0; c < 3; ++c) tg0[c] = P.target[3 * ((size_t)y0 * P.W + x) + c];
+                if (v1) for (int c = 0; c < 3; ++c) tg1[c] = P.target[3 * ((size_t)y1 * P.W + x) + c];
+            }
             const float fx = __fadd_rn((float)x, 0.5f);
             const float fy0 = __fadd_rn((float)y0, 0.5f), fy1 = __fadd_rn((float)y1, 0.5f);
-            float bw0 = -INFINITY, bw1 = -INFINITY, sh0 = 0.0f, sh1 = 0.0f;
+            float bw0 = -INFINITY, bw1 = -INFINITY;
             int bi0 = INT_MAX, bi1 = INT_MAX;
             for (int j = beg; j < end; ++j) {
                 const int s = overflow ? j : (int)ent[j];
                 const float4* rp = reinterpret_cast<const float4*>(&rec[s]);
                 const float4 q0 = rp[0], q1 = rp[1], q2 = rp[2], q3 = rp[3];
+                const uint32_t key = __float_as_uint(q3.y);
                 const uint32_t xr = __float_as_uint(q3.z), yr = __float_as_uint(q3.w);
-                const int ti = __float_as_int(q3.y);
-                const bool inx = x >= (int)(xr & 0xffffu) && x <= (int)(xr >> 16);
-                const int ylo = (int)(yr & 0xffffu), yhi = (int)(yr >> 16);
-                if (inx && y0 >= ylo && y0 <= yhi) {
+                const int ti = (int)(key & 0x1FFFFFFFu);
+                const float th0 = tl_threshold(key, 0), th1 = tl_threshold(key, 1), th2 = tl_threshold(key, 2);
+                const int xlo = (int)(xr & 0xffffu), ylo = (int)(yr & 0xffffu);
+                const bool inx = (unsigned)(x - xlo) <= (xr >> 16) - (unsigned)xlo;
+                const unsigned yspan = (yr >> 16) - (unsigned)ylo;
+                {
                     const float E0 = edge_eval(q0.x, q0.y, q0.z, fx, fy0);
                     const float E1 = edge_eval(q0.w, q1.x, q1.y, fx, fy0);
                     const float E2 = edge_eval(q1.z, q1.w, q2.x, fx, fy0);
-                    if (edge_in(q0.x, q0.y, E0) && edge_in(q0.w, q1.x, E1) && edge_in(q1.z, q1.w, E2)) {
-                        const float wz = edge_eval(q2.y, q2.z, q2.w, fx, fy0);
-                        if (wz > bw0 || (wz == bw0 && ti < bi0)) { bw0 = wz; bi0 = ti; sh0 = q3.x; }
-                    }
+                    const float wz = edge_eval(q2.y, q2.z, q2.w, fx, fy0);
+                    const bool in = inx && ((unsigned)(y0 - ylo) <= yspan) && (E0 > th0) && (E1 > th1) && (E2 > th2);
+                    const bool better = in && (wz > bw0 || (wz == bw0 && ti < bi0));
+                    bw0 = better ? wz : bw0;
+                    bi0 = better ? ti : bi0;
                 }
-                if (inx && y1 >= ylo && y1 <= yhi) {
+                {
                     const float E0 = edge_eval(q0.x, q0.y, q0.z, fx, fy1);
                     const float E1 = edge_eval(q0.w, q1.x, q1.y, fx, fy1);
                     const float E2 = edge_eval(q1.z, q1.w, q2.x, fx, fy1);
-                    if (edge_in(q0.x, q0.y, E0) && edge_in(q0.w, q1.x, E1) && edge_in(q1.z, q1.w, E2)) {
-                        const float wz = edge_eval(q2.y, q2.z, q2.w, fx, fy1);
-                        if (wz > bw1 || (wz == bw1 && ti < bi1)) { bw1 = wz; bi1 = ti; sh1 = q3.x; }
-                    }
+                    const float wz = edge_eval(q2.y, q2.z, q2.w, fx, fy1);
+                    const bool in = inx && ((unsigned)(y1 - ylo) <= yspan) && (E0 > th0) && (E1 > th1) && (E2 > th2);
+                    const bool better = in && (wz > bw1 || (wz == bw1 && ti < bi1));
+                    bw1 = better ? wz : bw1;
+                    bi1 = better ? ti : bi1;
                 }
             }
-            if (x < P.W) {
-#pragma unroll
-                for (int h = 0; h < 2; ++h) {
-                    const int y = h ? y1 : y0;
-                    if (y >= P.H) continue;
-                    const float shv = h ? sh1 : sh0;
-                    const bool hit = (h ? bi1 : bi0) != INT_MAX;
-                    const size_t pix = (size_t)y * P.W + x;
-                    const float c0 = hit ? shv * P.alb0 : 0.0f;
-                    const float c1 = hit ? shv * P.alb1 : 0.0f;
-                    const float c2 = hit ? shv * P.alb2 : 0.0f;
-                    if (kImage) {
-                        img[3 * pix] = c0; img[3 * pix + 1] = c1; img[3 * pix + 2] = c2;
-                    } else {
-                        const float d0 = c0 - P.target[3 * pix];
-                        const float d1 = c1 - P.target[3 * pix + 1];
-                        const float d2 = c2 - P.target[3 * pix + 2];
-                        acc += d0 * d0 + d1 * d1 + d2 * d2;
-                    }
+            const float sh0 = bi0 != INT_MAX ? tshade[bi0] : 0.0f;
+            const float sh1 = bi1 != INT_MAX ? tshade[bi1] : 0.0f;
+            const float c00 = sh0 * P.alb0, c01 = sh0 * P.alb1, c02 = sh0 * P.alb2;
+            const float c10 = sh1 * P.alb0, c11 = sh1 * P.alb1, c12 = sh1 * P.alb2;
+            if (kImage) {
+                if (v0) {
+                    const size_t p = 3 * ((size_t)y0 * P.W + x);
+                    img[p] = c00; img[p + 1] = c01; img[p + 2] = c02;
+                }
+                if (v1) {
+                    const size_t p = 3 * ((size_t)y1 * P.W + x);
+                    img[p] = c10; img[p + 1] = c11; img[p + 2] = c12;
+                }
+            } else {
+                if (v0) {
+                    const float d0 = c00 - tg0[0], d1 = c01 - tg0[1], d2 = c02 - tg0[2];
+                    acc += d0 * d0 + d1 * d1 + d2 * d2;
+                }
+                if (v1) {
+                    const float d0 = c10 - tg1[0], d1 = c11 - tg1[1], d2 = c12 - tg1[2];
+                    acc += d0 * d0 + d1 * d1 + d2 * d2;
                 }
             }
         }
@@ -345,7 +376,7 @@ RvArgs make_args(const DevScene& sc) {
 size_t revolve_smem_bytes(int nv, int nt, int W, int H) {
     const int T = ((W + kTile - 1) / kTile) * ((H + kTile - 1) / kTile);
     return sizeof(TriRec) * (size_t)nt + 3 * sizeof(float) * (size_t)nv + 2 * sizeof(int) * (size_t)T +
-           sizeof(uint16_t) * kEntryCap;
+           sizeof(uint16_t) * kEntryCap + sizeof(float) * (size_t)nt;
 }
 
 void revolve_prepare(DevScene& sc, cudaStream_t s) {

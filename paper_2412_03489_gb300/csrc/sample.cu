@@ -137,7 +137,9 @@ __device__ void write_weights(const SampleArgs& a, const SampleGroup& G, int m, 
     }
 }
 
-__global__ void __launch_bounds__(128) sample_kernel(SampleArgs a) {
+constexpr int kSampleThreads = 32;   // FP64-latency bound: spread pairs over many SMs
+
+__global__ void __launch_bounds__(kSampleThreads) sample_kernel(SampleArgs a) {
     const SampleGroup G = a.groups[blockIdx.y];
     const int k = blockIdx.x * blockDim.x + threadIdx.x;
     if (k >= G.P) return;
@@ -145,18 +147,6 @@ __global__ void __launch_bounds__(128) sample_kernel(SampleArgs a) {
     const double sigma = a.sigma;
     const uint32_t sub = G.sub + (a.step ? 64u * (uint32_t)(*a.step) : 0u);
     const uint32_t c2 = (TAG_SAMPLE << 24) | (sub & 0xFFFFFFu);
-    double g[kMaxN];
-    for (int d = 0; d < n; d += 4) {
-        const u32x4 r = philox_seed(a.seed, (uint32_t)k, (uint32_t)(1 + d / 4), c2, G.request);
-        const uint32_t words[4] = {r.x, r.y, r.z, r.w};
-#pragma unroll
-        for (int q = 0; q < 2; ++q) {
-            const double R = sqrt(-2.0 * log(u01d(words[2 * q])));
-            const double ph = 2.0 * kPi * u01d(words[2 * q + 1]);
-            if (d + 2 * q < n) g[d + 2 * q] = sigma * (R * cos(ph));
-            if (d + 2 * q + 1 < n) g[d + 2 * q + 1] = sigma * (R * sin(ph));
-        }
-    }
     const u32x4 w0 = philox_seed(a.seed, (uint32_t)k, 0u, c2, G.request);
     int i, j;
     if (G.comp_i >= 0) {
@@ -169,6 +159,24 @@ __global__ void __launch_bounds__(128) sample_kernel(SampleArgs a) {
         const int e = (int)(((uint64_t)w0.x * (uint64_t)(n * n)) >> 32);
         i = e / n;
         j = e - i * n;
+    }
+    // Box-Muller dims (skipped where the lobe sample overwrites them; the
+    // words are the same either way)
+    double g[kMaxN];
+    for (int d = 0; d < n; d += 4) {
+        const bool need[4] = {d != i && d != j, d + 1 < n && d + 1 != i && d + 1 != j,
+                              d + 2 < n && d + 2 != i && d + 2 != j, d + 3 < n && d + 3 != i && d + 3 != j};
+        if (!(need[0] || need[1] || need[2] || need[3])) continue;
+        const u32x4 r = philox_seed(a.seed, (uint32_t)k, (uint32_t)(1 + d / 4), c2, G.request);
+        const uint32_t words[4] = {r.x, r.y, r.z, r.w};
+#pragma unroll
+        for (int q = 0; q < 2; ++q) {
+            if (!(need[2 * q] || need[2 * q + 1])) continue;
+            const double R = sqrt(-2.0 * log(u01d(words[2 * q])));
+            const double ph = 2.0 * kPi * u01d(words[2 * q + 1]);
+            if (need[2 * q]) g[d + 2 * q] = sigma * (R * cos(ph));
+            if (need[2 * q + 1]) g[d + 2 * q + 1] = sigma * (R * sin(ph));
+        }
     }
     const double ua = u01d(w0.y), ub = u01d(w0.z);
     double pi_, pj, mi, mj;   // + / - leg values in dims i and j
@@ -192,9 +200,10 @@ __global__ void __launch_bounds__(128) sample_kernel(SampleArgs a) {
     float* tp = a.tau + (size_t)mp * n;
     float* tm = a.tau + (size_t)mm * n;
     for (int d = 0; d < n; ++d) {
-        double vp = g[d], vm = g[d];
+        double vp, vm;
         if (d == i) { vp = pi_; vm = mi; }
-        if (d == j) { vp = pj; vm = mj; }
+        else if (d == j) { vp = pj; vm = mj; }
+        else { vp = g[d]; vm = g[d]; }
         tp[d] = (float)vp;
         tm[d] = (float)vm;
     }
@@ -255,8 +264,8 @@ __global__ void __launch_bounds__(kFinThreads) finalize_kernel(FinalizeArgs a) {
 }  // namespace
 
 void launch_sample(const SampleArgs& a, int n_groups, int max_P, cudaStream_t s) {
-    dim3 grid((max_P + 127) / 128, n_groups);
-    sample_kernel<<<grid, 128, 0, s>>>(a);
+    dim3 grid((max_P + kSampleThreads - 1) / kSampleThreads, n_groups);
+    sample_kernel<<<grid, kSampleThreads, 0, s>>>(a);
 }
 
 void launch_finalize(const FinalizeArgs& a, cudaStream_t s) {

@@ -176,6 +176,30 @@ hr_status hr_estimate_hvp(hr_scene scene, const double* h_theta, const double* h
 hr_status hr_estimate_dev(hr_scene scene, int32_t quantity, const double* d_theta, const double* d_v,
                           const hr_opts* opts, double* d_out);
 
+/* Device-pointer estimate that allocates nothing.  Same arguments, results
+ * and stream behaviour as hr_estimate_dev; the paper has no counterpart.
+ *
+ * For callers that cannot allocate device memory while they run: code that is
+ * being captured into a CUDA graph (cudaMalloc is not allowed during capture),
+ * real-time loops that must not take allocator locks or pay the device-wide
+ * synchronisation that cudaFree implies, and hosts that hand the library a
+ * fixed memory budget up front.  Its working memory is one fixed 4 MiB array
+ * of device memory inside the library, present on every GPU that loads the
+ * library until the process exits; a request needing more than that (about
+ * 130,000 perturbations for a 2 x 2 aggregate Hessian, fewer for larger n)
+ * fails with HR_ERR_INVALID_ARG before anything is launched, and
+ * hr_estimate_dev remains the entry point for such requests.
+ *
+ * The first call on each device looks up the array's device address
+ * (cudaGetSymbolAddress) with that device current; make that first call
+ * before any stream capture.  All calls share the one array and it keeps the
+ * last call's contents (every call overwrites all of it that it reads, so
+ * nothing needs clearing): two calls that can run at the same time on the GPU
+ * (different streams, or work not ordered one after the other) race and
+ * corrupt each other's results, so issue them in order on one stream. */
+hr_status hr_estimate_dev_noalloc(hr_scene scene, int32_t quantity, const double* d_theta, const double* d_v,
+                                  const hr_opts* opts, double* d_out);
+
 /* ---------------------------------------------------------------------------
  * Newton-CG (Sec. 2 "Newton Conjugate Gradient"): per step and instance, an
  * aggregate gradient estimate g, then K linear-CG iterations on

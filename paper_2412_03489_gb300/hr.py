@@ -83,6 +83,7 @@ def lib() -> ctypes.CDLL:
         L.hr_estimate_hessian.argtypes = [vp, _f64p, ctypes.POINTER(hr_opts), _f64p]
         L.hr_estimate_hvp.argtypes = [vp, _f64p, _f64p, ctypes.POINTER(hr_opts), _f64p]
         L.hr_estimate_dev.argtypes = [vp, ctypes.c_int32, vp, vp, ctypes.POINTER(hr_opts), vp]
+        L.hr_estimate_dev_noalloc.argtypes = [vp, ctypes.c_int32, vp, vp, ctypes.POINTER(hr_opts), vp]
         L.hr_render.argtypes = [vp, _f64p, ctypes.c_uint64, ctypes.c_uint32, ctypes.c_uint32, ctypes.c_uint32,
                                 ctypes.c_uint32, ctypes.c_int32, _f32p]
         L.hr_optstate_create.argtypes = [vp, ctypes.c_int32, _f64p, ctypes.POINTER(hr_cg_opts), ctypes.POINTER(vp)]
@@ -94,7 +95,7 @@ def lib() -> ctypes.CDLL:
         L.hr_last_error.argtypes = [ctypes.c_char_p, ctypes.c_size_t]
         L.hr_last_error.restype = ctypes.c_size_t
         for name in ("hr_create_scene", "hr_destroy_scene", "hr_estimate_grad", "hr_estimate_hessian",
-                     "hr_estimate_hvp", "hr_estimate_dev", "hr_render", "hr_optstate_create",
+                     "hr_estimate_hvp", "hr_estimate_dev", "hr_estimate_dev_noalloc", "hr_render", "hr_optstate_create",
                      "hr_optstate_destroy", "hr_newton_cg_step", "hr_optstate_theta", "hr_profile_enable",
                      "hr_profile_last"):
             getattr(L, name).restype = ctypes.c_int32
@@ -160,6 +161,11 @@ def hr_estimate_hvp(handle, theta, v, opts: hr_opts, out):
 
 def hr_estimate_dev(handle, quantity: int, d_theta: int, d_v, opts: hr_opts, d_out: int):
     check(lib().hr_estimate_dev(handle, quantity, d_theta, d_v, ctypes.byref(opts), d_out), "hr_estimate_dev")
+
+
+def hr_estimate_dev_noalloc(handle, quantity: int, d_theta: int, d_v, opts: hr_opts, d_out: int):
+    check(lib().hr_estimate_dev_noalloc(handle, quantity, d_theta, d_v, ctypes.byref(opts), d_out),
+          "hr_estimate_dev_noalloc")
 
 
 def hr_render(handle, params, seed, request, sub, k, tag, spp, out):

@@ -561,17 +561,20 @@ static void pt_setup(const or_ptbox_scene* s, const float p[6], pt_geom* g)
     }
 }
 
-/* closest hit with t > 0; ties go to the lower primitive index */
+/* closest hit with t > 0; ties go to the lower primitive index.  Plane
+ * distances use the ray's per-axis reciprocal: t = RN(RN(plane - o_a) * RN(1/d_a)). */
 static int pt_intersect(const pt_geom* g, const float o[3], const float d[3], float* t_out)
 {
     float best = INFINITY;
     int prim = -1;
+    float inv[3];
+    for (int c = 0; c < 3; ++c) inv[c] = 1.0f / d[c];
     for (int q = 0; q <= PT_LIGHT; ++q) {
         int a = g->axis[q];
         int u = a == 0 ? 1 : 0;
         int v = a == 2 ? 1 : 2;
         if (d[a] == 0.0f) continue;
-        float t = (g->plane[q] - o[a]) / d[a];
+        float t = (g->plane[q] - o[a]) * inv[a];
         if (!(t > 0.0f)) continue;
         float hu = fmaf(t, d[u], o[u]);
         float hv = fmaf(t, d[v], o[v]);
@@ -605,7 +608,8 @@ static void pt_normal(const pt_geom* g, int prim, const float x[3], const float 
         return;
     }
     int i = prim - 13;
-    for (int c = 0; c < 3; ++c) n[c] = (x[c] - g->sc[i][c]) / g->sr[i];
+    float ir = 1.0f / g->sr[i];
+    for (int c = 0; c < 3; ++c) n[c] = (x[c] - g->sc[i][c]) * ir;
     if (dot3f(n, d) > 0.0f) { n[0] = -n[0]; n[1] = -n[1]; n[2] = -n[2]; }
 }
 
@@ -618,8 +622,8 @@ static const float* pt_albedo(const or_ptbox_scene* s, int prim)
 
 static void pt_normalize(float v[3])
 {
-    float len = sqrtf(dot3f(v, v));
-    v[0] = v[0] / len; v[1] = v[1] / len; v[2] = v[2] / len;
+    float il = 1.0f / sqrtf(dot3f(v, v));
+    v[0] = v[0] * il; v[1] = v[1] * il; v[2] = v[2] * il;
 }
 
 /* one path sample; adds its radiance to L */
@@ -655,8 +659,8 @@ static void pt_path(const or_ptbox_scene* s, const pt_geom* g, int depth, uint64
             ly[2] = fmaf(ul2, g->hi_v[PT_LIGHT] - g->lo_v[PT_LIGHT], g->lo_v[PT_LIGHT]);
             float wv[3] = {ly[0] - o2[0], ly[1] - o2[1], ly[2] - o2[2]};
             float dist2 = dot3f(wv, wv);
-            float dist = sqrtf(dist2);
-            float om[3] = {wv[0] / dist, wv[1] / dist, wv[2] / dist};
+            float idist = 1.0f / sqrtf(dist2);
+            float om[3] = {wv[0] * idist, wv[1] * idist, wv[2] * idist};
             float cosx = dot3f(n, om);
             float cosl = om[1];
             if (cosx > 0.0f && cosl > 0.0f) {

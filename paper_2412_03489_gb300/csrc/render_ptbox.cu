@@ -32,7 +32,7 @@ struct PtShared {
     int axis[13];
     float plane[13], lo_u[13], lo_v[13], hi_u[13], hi_v[13];
     float alb[16][3];
-    float sc[3][3], sr[3], sr2[3];
+    float sc[3][3], sr[3], sr2[3], isr[3];
     float em[3];
 };
 
@@ -40,16 +40,18 @@ __device__ __forceinline__ float dot3(const float* a, const float* b) {
     return __fmaf_rn(a[2], b[2], __fmaf_rn(a[1], b[1], __fmul_rn(a[0], b[0])));
 }
 
-// closest hit with t > 0, ties to the lower primitive index
+// closest hit with t > 0, ties to the lower primitive index; plane distances
+// t = RN(RN(plane - o_a) * RN(1 / d_a)) with the ray's per-axis reciprocals
 __device__ int intersect(const PtShared& S, const float o[3], const float d[3], float& t_out) {
     float best = INFINITY;
     int prim = -1;
+    const float inv[3] = {__frcp_rn(d[0]), __frcp_rn(d[1]), __frcp_rn(d[2])};
 #pragma unroll 1
     for (int q = 0; q <= kLight; ++q) {
         const int a = S.axis[q];
         const int u = a == 0 ? 1 : 0, v = a == 2 ? 1 : 2;
         if (d[a] == 0.0f) continue;
-        const float t = __fdiv_rn(__fsub_rn(S.plane[q], o[a]), d[a]);
+        const float t = __fmul_rn(__fsub_rn(S.plane[q], o[a]), inv[a]);
         if (!(t > 0.0f)) continue;
         const float hu = __fmaf_rn(t, d[u], o[u]);
         const float hv = __fmaf_rn(t, d[v], o[v]);
@@ -98,7 +100,7 @@ __device__ void radiance(const PtShared& S, int depth, uint64_t seed, uint32_t r
         } else {
             const int i = prim - 13;
 #pragma unroll
-            for (int c = 0; c < 3; ++c) n[c] = __fdiv_rn(__fsub_rn(x[c], S.sc[i][c]), S.sr[i]);
+            for (int c = 0; c < 3; ++c) n[c] = __fmul_rn(__fsub_rn(x[c], S.sc[i][c]), S.isr[i]);
             if (dot3(n, d) > 0.0f) { n[0] = -n[0]; n[1] = -n[1]; n[2] = -n[2]; }
         }
 #pragma unroll
@@ -113,8 +115,8 @@ __device__ void radiance(const PtShared& S, int depth, uint64_t seed, uint32_t r
                                  __fmaf_rn(u24f(w0.y), __fsub_rn(S.hi_v[kLight], S.lo_v[kLight]), S.lo_v[kLight])};
             const float wv[3] = {__fsub_rn(ly[0], o2[0]), __fsub_rn(ly[1], o2[1]), __fsub_rn(ly[2], o2[2])};
             const float dist2 = dot3(wv, wv);
-            const float dist = __fsqrt_rn(dist2);
-            float om[3] = {__fdiv_rn(wv[0], dist), __fdiv_rn(wv[1], dist), __fdiv_rn(wv[2], dist)};
+            const float idist = __frcp_rn(__fsqrt_rn(dist2));
+            float om[3] = {__fmul_rn(wv[0], idist), __fmul_rn(wv[1], idist), __fmul_rn(wv[2], idist)};
             const float cosx = dot3(n, om);
             const float cosl = om[1];
             if (cosx > 0.0f && cosl > 0.0f) {
@@ -190,6 +192,7 @@ __device__ void load_scene(const PtArgs& A, const float* p, PtShared& S) {
         for (int c = 0; c < 3; ++c) { S.sc[i][c] = (i == 0) ? p[3 + c] : A.sc[i][c]; S.alb[t][c] = A.salb[i][c]; }
         S.sr[i] = A.sr[i];
         S.sr2[i] = __fmul_rn(A.sr[i], A.sr[i]);
+        S.isr[i] = __frcp_rn(A.sr[i]);
     } else if (t == 16) {
         S.axis[kLight] = 1;
         S.plane[kLight] = p[1];
@@ -217,11 +220,11 @@ ptbox_kernel(PtArgs A, RenderBatch b, const float* __restrict__ img_params, uint
         if (tid < 6) s_p[tid] = img_params[tid];
         seed = seed_img; request = req_img; sub = sub_img; k = k_img; tag = tag_img; spp = spp_img;
     } else {
-        const int row = m / b.per_row;
-        if (tid < 6) s_p[tid] = __fadd_rn(b.theta32[row * b.n + tid], b.tau[(size_t)m * b.n + tid]);
-        seed = b.seed;
-        request = b.request0 + (uint32_t)row;
-        const uint2 mt = b.meta[m];
+        const Pert pt = resolve(b, m);
+        if (tid < 6) s_p[tid] = __fadd_rn(pt.theta[tid], pt.tau[tid]);
+        seed = pt.seed;
+        request = pt.request;
+        const uint2 mt = *pt.meta;
         sub = mt.x; k = mt.y; tag = TAG_PATH; spp = A.spp;
     }
     __syncthreads();
@@ -240,8 +243,8 @@ ptbox_kernel(PtArgs A, RenderBatch b, const float* __restrict__ img_params, uint
             const float fx = __fadd_rn((float)x, u24f(wj.x));
             const float fy = __fadd_rn((float)y, u24f(wj.y));
             float d[3] = {__fmaf_rn(fx, A.pix_scale, -A.tan_half), __fmaf_rn(-fy, A.pix_scale, A.tan_half), -1.0f};
-            const float len = __fsqrt_rn(dot3(d, d));
-            d[0] = __fdiv_rn(d[0], len); d[1] = __fdiv_rn(d[1], len); d[2] = __fdiv_rn(d[2], len);
+            const float il = __frcp_rn(__fsqrt_rn(dot3(d, d)));
+            d[0] = __fmul_rn(d[0], il); d[1] = __fmul_rn(d[1], il); d[2] = __fmul_rn(d[2], il);
             float o[3] = {0.0f, 0.0f, A.cam_z};
             radiance(S, A.depth, seed, request, c2, k, idx, o, d, L);
         }
@@ -262,7 +265,7 @@ ptbox_kernel(PtArgs A, RenderBatch b, const float* __restrict__ img_params, uint
         if (tid == 0) {
             float v = 0.0f;
             for (int w = 0; w < kThreads / 32; ++w) v += s_part[w];
-            b.loss[m] = v / (float)(npx * 3);
+            *resolve(b, m).loss = v / (float)(npx * 3);
         }
     }
 }

@@ -170,6 +170,195 @@ def run_reference(args):
     return 0
 
 
+def _timed_steps(torch, stream, flush, fn, warmup, steps):
+    """CUDA-event time of `fn(i)` per step (L2 flushed before each, untimed)."""
+    for i in range(warmup):
+        flush.fill_(float(i))
+        fn(i)
+    torch.cuda.synchronize()
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    times = []
+    for i in range(steps):
+        flush.fill_(float(i))
+        ev0.record(stream)
+        fn(warmup + i)
+        ev1.record(stream)
+        ev1.synchronize()
+        times.append(ev0.elapsed_time(ev1))
+    return np.asarray(times)
+
+
+def run_secondary(args):
+    """The other configurations: disc Hessians, path-traced HVPs, batched
+    Newton-CG steps, and the serving mix against one-request-at-a-time."""
+    import torch
+    from paper_2412_03489_gb300 import hr
+    from paper_2412_03489_gb300 import workloads as wl
+    torch.cuda.set_device(0)
+    stream = torch.cuda.Stream()
+    torch.cuda.set_stream(stream)
+    flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda")
+    clocks = ClockSampler(0)
+    line = {"workload": args.workload, "n_gpus": 1, "steps": args.steps, "warmup": args.warmup, "data": "synthetic"}
+    if args.workload in ("disc", "ptbox"):
+        sc = wl.disc_scene() if args.workload == "disc" else wl.ptbox_scene()
+        S = hr.Scene(sc)
+        n = sc["n_params"]
+        d_theta = torch.tensor(sc["theta_query"], dtype=torch.float64, device="cuda")
+        d_v = torch.tensor(sc.get("v", np.ones(n)), dtype=torch.float64, device="cuda")
+        d_out = torch.zeros((n, n), dtype=torch.float64, device="cuda")
+        hr.hr_profile_enable(S.handle, True)
+        variants = ([("hessian_elementwise_3x1024", hr.HR_HESSIAN, hr.HR_ELEMENTWISE, 1024, 3 * 1024),
+                     ("hessian_aggregate_1024", hr.HR_HESSIAN, hr.HR_AGGREGATE, 1024, 1024)]
+                    if args.workload == "disc" else [("hvp_aggregate_8192", hr.HR_HVP, hr.HR_AGGREGATE, 8192, 8192)])
+        for name, q, strat, M, renders in variants:
+            stage = []
+
+            def fn(i):
+                o = hr.make_opts(sc["sigma"], M, strat, SEED, i, stream=stream.cuda_stream)
+                hr.hr_estimate_dev(S.handle, q, d_theta.data_ptr(), d_v.data_ptr() if q == hr.HR_HVP else None,
+                                   o, d_out.data_ptr())
+            times = []
+            for i in range(args.warmup + args.steps):
+                flush.fill_(float(i))
+                ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                ev0.record(stream)
+                fn(i)
+                ev1.record(stream)
+                ev1.synchronize()
+                if i >= args.warmup:
+                    times.append(ev0.elapsed_time(ev1))
+                    stage.append(hr.hr_profile_last(S.handle).astype(np.float64))
+            t = float(np.mean(times))
+            line[name] = {"estimates_per_s": 1e3 / t, "renders_per_s": renders * 1e3 / t, "ms_per_estimate": t,
+                          "latency_ms": {"p50": float(np.percentile(times, 50)),
+                                         "p99": float(np.percentile(times, 99))},
+                          "stage_ms": dict(zip(("sample", "render_loss", "sums"),
+                                               np.mean(stage, axis=0).tolist()))}
+        line["config"] = ({"workload": "disc2d 64x64 gray, r 0.2, 2 params, sigma 0.05"} if args.workload == "disc"
+                          else {"workload": "path-traced box 128x128 RGB, 4 spp, depth 3, 6 params, sigma 0.05, "
+                                            "aggregate HVP, 8192 perturbations"})
+        S.close()
+    elif args.workload == "newton":
+        sc = wl.tris2d_scene()
+        S = hr.Scene(sc)
+        B, n = 64, sc["n_params"]
+        opts = hr.hr_cg_opts()
+        opts.sigma, opts.n_grad, opts.n_hvp, opts.cg_iters = sc["sigma"], 32, 32, 10
+        opts.lambda_rel, opts.trust_radius, opts.seed, opts.request_base = 1e-3, 0.05, SEED, 0
+        opts.use_graph, opts.stream = 1, stream.cuda_stream
+        th0 = np.ascontiguousarray(sc["theta_init"], np.float64)
+        st = hr.hr_optstate_create(S.handle, B, th0, opts)
+        times = _timed_steps(torch, stream, flush, lambda i: hr.hr_newton_cg_step(S.handle, st, None),
+                             args.warmup, args.steps)
+        info = (hr.hr_step_info * B)()
+        hr.hr_newton_cg_step(S.handle, st, info)
+        t = float(np.mean(times))
+        renders = B * (32 + 10 * 32)
+        line.update({"metric": "Newton-CG steps/s (64 instances per launch, CUDA graph)",
+                     "instance_steps_per_s": B * 1e3 / t, "launch_steps_per_s": 1e3 / t, "ms_per_step": t,
+                     "renders_per_s": renders * 1e3 / t,
+                     "mean_cg_iters": float(np.mean([info[b].iters for b in range(B)])),
+                     "config": {"workload": "16 coloured triangles 256x256, 64 params, 64 instances, "
+                                            "32 gradient + 10 x 32 HVP renders per instance-step, graph-captured"}})
+        hr.hr_optstate_destroy(st)
+        S.close()
+    else:
+        line.update(serving_bench(torch, hr, wl))
+    line["clocks"] = clocks.stop()
+    print(json.dumps(line))
+    return 0
+
+
+def serving_bench(torch, hr, wl):
+    """Poisson arrivals through the server versus the plain one-request-at-a-
+    time entry points on the same request list."""
+    import threading
+    scenes = wl.serving_scenes()
+    S = {k: hr.Scene(v) for k, v in scenes.items()}
+    reqs = wl.serving_requests(scenes, n_requests=240)
+
+    def make(r):
+        o = hr.make_opts(r["sigma"], r["M"], r["strategy"], r["seed"], r["request"])
+        return hr.make_request(S[r["scene"]], r["quantity"], r["theta"], r["v"], o)
+
+    def out_for(r):
+        n = S[r["scene"]].n
+        return np.zeros((n, n) if r["quantity"] == hr.HR_HESSIAN else n)
+
+    # plain: one request at a time through hr_estimate_* (host pointers)
+    for r in reqs[:8]:
+        S[r["scene"]].estimate(r["quantity"], r["theta"], r["sigma"], r["M"], r["strategy"], r["seed"],
+                               r["request"], v=r["v"])
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    plain = []
+    for r in reqs:
+        plain.append(S[r["scene"]].estimate(r["quantity"], r["theta"], r["sigma"], r["M"], r["strategy"],
+                                            r["seed"], r["request"], v=r["v"]))
+    plain_s = time.perf_counter() - t0
+
+    srv = hr.hr_server_create(4 << 30, max_active=32, chunk=2048)
+    # warm the lanes
+    for r in reqs[:8]:
+        req, keep = make(r)
+        hr.hr_server_wait(srv, hr.hr_server_submit(srv, req), out_for(r), hr.hr_request_info())
+    # saturation: everything submitted at once
+    t0 = time.perf_counter()
+    tk = []
+    for r in reqs:
+        req, keep = make(r)
+        tk.append((hr.hr_server_submit(srv, req), keep, r))
+    sat = []
+    for t, keep, r in tk:
+        o = out_for(r)
+        hr.hr_server_wait(srv, t, o, hr.hr_request_info())
+        sat.append(o)
+    sat_s = time.perf_counter() - t0
+    same = all(np.array_equal(a, b) for a, b in zip(plain, sat))
+
+    # Poisson arrivals at 70 % of the saturated rate
+    rate = 0.7 * len(reqs) / sat_s
+    arrivals = np.cumsum(np.random.default_rng(0xC5).exponential(1.0 / rate, size=len(reqs)))
+    tickets = [None] * len(reqs)
+    ready = threading.Semaphore(0)
+
+    def submitter():
+        start = time.perf_counter()
+        for i, r in enumerate(reqs):
+            d = arrivals[i] - (time.perf_counter() - start)
+            if d > 0:
+                time.sleep(d)
+            req, keep = make(r)
+            tickets[i] = (hr.hr_server_submit(srv, req), keep)
+            ready.release()
+    th = threading.Thread(target=submitter)
+    t0 = time.perf_counter()
+    th.start()
+    lat = []
+    for i, r in enumerate(reqs):
+        ready.acquire()
+        info = hr.hr_request_info()
+        hr.hr_server_wait(srv, tickets[i][0], out_for(r), info)
+        lat.append(info.done_ms - info.submit_ms)
+    th.join()
+    poisson_s = time.perf_counter() - t0
+    hr.hr_server_destroy(srv)
+    for v in S.values():
+        v.close()
+    return {"metric": "estimates/s and p50/p99 latency, serving mix vs one request at a time",
+            "requests": len(reqs),
+            "plain_one_at_a_time": {"estimates_per_s": len(reqs) / plain_s},
+            "served_saturated": {"estimates_per_s": len(reqs) / sat_s,
+                                 "speedup_vs_plain": plain_s / sat_s, "results_identical_to_plain": same},
+            "served_poisson": {"arrival_rate_hz": rate, "estimates_per_s": len(reqs) / poisson_s,
+                               "latency_ms": {"p50": float(np.percentile(lat, 50)),
+                                              "p99": float(np.percentile(lat, 99))}},
+            "config": {"workload": "Poisson arrivals over 8 resident scenes (disc 64/512, mesh 128/256/512, "
+                                   "path-traced box 64, triangles 128 (n 64) / 256 (n 16)), 256..16384 samples, "
+                                   "grad / Hessian / HVP, element-wise and aggregate"}}
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -177,11 +366,16 @@ def main():
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="native", choices=["native", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--workload", default="revolve", choices=["revolve", "disc", "ptbox", "newton", "serving"],
+                    help="revolve (default) is the headline workload; the others report the remaining "
+                         "configurations in their own JSON lines")
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3
     if args.impl == "reference":
         return run_reference(args)
+    if args.workload != "revolve":
+        return run_secondary(args)
 
     import torch
     import torch.distributed as dist
@@ -216,7 +410,7 @@ def main():
     if world > 1:
         dist.barrier()
     clocks = ClockSampler(local)
-    times, render_ms = [], []
+    times, render_ms, stage_ms = [], [], []
     ev0 = torch.cuda.Event(enable_timing=True)
     ev1 = torch.cuda.Event(enable_timing=True)
     torch.cuda.synchronize()
@@ -227,7 +421,9 @@ def main():
         ev1.record(stream)
         ev1.synchronize()
         times.append(ev0.elapsed_time(ev1))
-        render_ms.append(float(hr.hr_profile_last(S.handle)[1]))
+        st = hr.hr_profile_last(S.handle)
+        stage_ms.append(st.astype(np.float64))
+        render_ms.append(float(st[1]))
     torch.cuda.synchronize()
     clk = clocks.stop()
     total_ms = float(np.sum(times))
@@ -273,6 +469,7 @@ def main():
                              "render_ms_per_launch": render_avg_s * 1e3},
                 "e2e": {"value": 1.0 / e2e_s, "unit": "estimates/s", "h2d_bytes_per_step": 8 + 40,
                         "d2h_bytes_per_step": 32},
+                "stage_ms": dict(zip(("sample", "render_loss", "sums"), np.mean(stage_ms, axis=0).tolist())),
                 "gpu_launches": 3 * args.steps,
                 "clocks": clk}
         if not args.no_cpu_baseline:

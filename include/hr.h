@@ -251,6 +251,58 @@ hr_status hr_optstate_theta(hr_optstate st, double* h_theta);
 hr_status hr_render(hr_scene scene, const double* h_params, uint64_t seed, uint32_t request, uint32_t sub,
                     uint32_t k, uint32_t tag, int32_t spp, float* h_img);
 
+/* ---------------------------------------------------------------------------
+ * Serving with continuous batching.  A server owns one device arena of
+ * hbm_budget bytes (allocated at creation) and a worker thread.  Submitted
+ * requests wait in a queue until a slot (max_active) and arena space for
+ * their state are free; once admitted, their perturbations are sampled and
+ * rendered in chunks, and every batched render launch carries chunks of all
+ * active requests on the same scene, so requests that arrive while others
+ * run join the next launch and their work overlaps on the device.  Scenes
+ * (geometry, targets) and Newton-CG states stay resident; a Newton-CG step
+ * request advances its state by one step.  A request's result does not
+ * depend on what else is in flight: each render and each request's sums run
+ * the same code in the same order as hr_estimate_*.
+ * ------------------------------------------------------------------------- */
+#define HR_NEWTON_STEP 3
+
+typedef struct hr_server_s* hr_server;
+
+typedef struct {
+    int64_t hbm_budget;     /* bytes of device memory for request state */
+    int32_t max_active;     /* requests admitted at once, 1..48 */
+    int32_t chunk;          /* perturbations per request per batched launch (0: 2048) */
+} hr_server_opts;
+
+typedef struct {
+    hr_scene scene;
+    int32_t quantity;       /* HR_GRAD, HR_HESSIAN, HR_HVP or HR_NEWTON_STEP */
+    const double* h_theta;  /* [n] host, copied at submission (estimates) */
+    const double* h_v;      /* [n] host, copied at submission (HVP) */
+    hr_opts opts;           /* sigma, n_perturb, strategy, seed, request_id, sub;
+                               stream and inspection outputs are ignored */
+    hr_optstate optstate;   /* HR_NEWTON_STEP: the state to advance (same scene) */
+} hr_request;
+
+typedef struct {
+    double submit_ms, admit_ms, done_ms;   /* host clock, ms since server creation */
+    int32_t status;                         /* HR_OK or the request's failure code */
+    int32_t batches;                        /* batched launches that carried its renders */
+} hr_request_info;
+
+hr_status hr_server_create(const hr_server_opts* opts, hr_server* out);
+/* Stops admitting, finishes admitted work, fails queued requests with
+ * HR_ERR_BUSY, frees the arena. */
+hr_status hr_server_destroy(hr_server srv);
+/* Queue a request (inputs copied); *ticket identifies it.  HR_ERR_OOM if its
+ * state can never fit the arena. */
+hr_status hr_server_submit(hr_server srv, const hr_request* req, uint64_t* ticket);
+/* Wait for a request.  h_out (host) receives n (gradient, HVP) or n*n
+ * (Hessian) doubles, or B hr_step_info records for HR_NEWTON_STEP; info may be
+ * NULL.  timeout_ms < 0 waits without limit; on timeout HR_ERR_TIMEOUT is
+ * returned and the ticket stays valid.  A ticket can be waited for once. */
+hr_status hr_server_wait(hr_server srv, uint64_t ticket, void* h_out, hr_request_info* info, int32_t timeout_ms);
+
 /* Stage timing: when enabled (on != 0), every estimate records CUDA events
  * on its stream around its three launches (sampler, render + loss, sums) and
  * hr_profile_last writes their durations in milliseconds, ms[3], for the

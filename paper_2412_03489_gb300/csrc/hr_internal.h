@@ -56,17 +56,72 @@ void launch_finalize(const FinalizeArgs& a, cudaStream_t s);
 // ---------------------------------------------------------------------------
 // render batches: perturbation m renders at RN32(theta32[row(m)] + tau[m])
 // ---------------------------------------------------------------------------
+// One request's slice of a batched launch (continuous batching): items
+// [start, start + count) of the launch render perturbations
+// [m_begin, m_begin + count) of that request.
+struct BatchRow {
+    const float* theta32;   // [n]
+    const float* tau;       // [M][n]
+    const uint2* meta;      // [M]
+    float* loss;            // [M]
+    uint64_t seed;
+    uint32_t request;
+    int32_t m_begin;
+    int32_t start;
+    int32_t pad;
+};
+constexpr int kMaxBatchRows = 48;
+
 struct RenderBatch {
     const float* theta32;   // [rows][n]
     const float* tau;       // [M][n]
     const uint2* meta;      // [M] (sub, k): path random numbers (path tracer)
     float* loss;            // [M]
-    int32_t M;
+    int32_t M;              // items in this launch
     int32_t n;
     int32_t per_row;        // perturbations per theta row
     uint32_t request0;      // request id of row 0 (row r: request0 + r)
     uint64_t seed;
+    int32_t table_rows;     // > 0: items map through `rows` instead
+    int32_t pad;
+    BatchRow rows[kMaxBatchRows];
 };
+
+// the perturbation behind item i of a launch
+struct Pert {
+    const float* theta;
+    const float* tau;
+    const uint2* meta;
+    float* loss;
+    uint64_t seed;
+    uint32_t request;
+};
+
+#ifdef __CUDACC__
+__device__ __forceinline__ Pert resolve(const RenderBatch& b, int i) {
+    Pert p;
+    if (b.table_rows > 0) {
+        int r = 0;
+        while (r + 1 < b.table_rows && b.rows[r + 1].start <= i) ++r;
+        const int m = b.rows[r].m_begin + (i - b.rows[r].start);
+        p.theta = b.rows[r].theta32;
+        p.tau = b.rows[r].tau + (size_t)m * b.n;
+        p.meta = b.rows[r].meta + m;
+        p.loss = b.rows[r].loss + m;
+        p.seed = b.rows[r].seed;
+        p.request = b.rows[r].request;
+    } else {
+        const int row = i / b.per_row;
+        p.theta = b.theta32 + (size_t)row * b.n;
+        p.tau = b.tau + (size_t)i * b.n;
+        p.meta = b.meta ? b.meta + i : nullptr;
+        p.loss = b.loss + i;
+        p.seed = b.seed;
+        p.request = b.request0 + (uint32_t)row;
+    }
+    return p;
+}
+#endif
 
 struct DevScene;
 void launch_render_loss(const DevScene& sc, const RenderBatch& b, cudaStream_t s);

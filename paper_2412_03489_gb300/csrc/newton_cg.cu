@@ -302,6 +302,22 @@ hr_status hr_newton_cg_step(hr_scene scene, hr_optstate st, hr_step_info* h_info
     clear_error();
     if (!scene || !st || st->scene != scene) return fail(HR_ERR_INVALID_ARG, "state does not belong to this scene");
     std::lock_guard<std::mutex> lk(scene->mu);
+    const hr_status s = hr::optstate_launch_step(st, h_info != nullptr);
+    if (s != HR_OK) return s;
+    const cudaError_t e = cudaStreamSynchronize(st->stream);
+    if (e != cudaSuccess) return fail(HR_ERR_CUDA, "step: %s", cudaGetErrorString(e));
+    if (h_info) memcpy(h_info, st->h_info, sizeof(hr_step_info) * st->B);
+    return HR_OK;
+}
+
+}  // extern "C"
+
+namespace hr {
+
+// One step on the state's stream (graph replay or direct launches) and, if
+// asked, the step records copied to the state's pinned buffer; returns
+// without waiting.
+hr_status optstate_launch_step(hr_optstate st, bool copy_info) {
     cudaError_t e;
     if (st->opts.use_graph) {
         if (!st->exec) {
@@ -322,16 +338,22 @@ hr_status hr_newton_cg_step(hr_scene scene, hr_optstate st, hr_step_info* h_info
         const hr_status s = enqueue_step(st);
         if (s != HR_OK) return s;
     }
-    if (h_info) {
+    if (copy_info) {
         if ((e = cudaMemcpyAsync(st->h_info, st->info.ptr, sizeof(hr_step_info) * st->B, cudaMemcpyDeviceToHost,
                                  st->stream)) != cudaSuccess)
             return fail(HR_ERR_CUDA, "info: %s", cudaGetErrorString(e));
     }
-    if ((e = cudaStreamSynchronize(st->stream)) != cudaSuccess)
-        return fail(HR_ERR_CUDA, "step: %s", cudaGetErrorString(e));
-    if (h_info) memcpy(h_info, st->h_info, sizeof(hr_step_info) * st->B);
     return HR_OK;
 }
+
+cudaStream_t optstate_stream(hr_optstate st) { return st->stream; }
+int optstate_instances(hr_optstate st) { return st->B; }
+hr_scene optstate_scene(hr_optstate st) { return st->scene; }
+void optstate_copy_info(hr_optstate st, hr_step_info* out) { memcpy(out, st->h_info, sizeof(hr_step_info) * st->B); }
+
+}  // namespace hr
+
+extern "C" {
 
 hr_status hr_optstate_theta(hr_optstate st, double* h_theta) {
     clear_error();

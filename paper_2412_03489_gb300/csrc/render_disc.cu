@@ -26,9 +26,9 @@ __global__ void __launch_bounds__(32 * kWarps) disc_loss_kernel(RenderBatch b, i
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int m = blockIdx.x * kWarps + warp;
     if (m >= b.M) return;
-    const int row = m / b.per_row;
-    const float cx = __fadd_rn(b.theta32[row * b.n + 0], b.tau[(size_t)m * b.n + 0]);
-    const float cy = __fadd_rn(b.theta32[row * b.n + 1], b.tau[(size_t)m * b.n + 1]);
+    const Pert pt = resolve(b, m);
+    const float cx = __fadd_rn(pt.theta[0], pt.tau[0]);
+    const float cy = __fadd_rn(pt.theta[1], pt.tau[1]);
     const float r2 = __fmul_rn(radius, radius);
     float acc = 0.0f;
     const int npx = W * H;
@@ -38,7 +38,7 @@ __global__ void __launch_bounds__(32 * kWarps) disc_loss_kernel(RenderBatch b, i
         acc = __fmaf_rn(d, d, acc);
     }
     acc = warp_sum(acc);
-    if (lane == 0) b.loss[m] = __fdiv_rn(acc, (float)npx);
+    if (lane == 0) *pt.loss = __fdiv_rn(acc, (float)npx);
 }
 
 __global__ void disc_image_kernel(const float* params, int W, int H, float radius, float* img) {

@@ -133,9 +133,9 @@ revolve_kernel(RvArgs P, RenderBatch b, const float* __restrict__ img_params, fl
             if (kImage) {
                 p = img_params[tid >> 1];
             } else {
-                const int row = m / b.per_row;
+                const Pert pt = resolve(b, m);
                 const int d = tid >> 1;
-                p = __fadd_rn(b.theta32[row * b.n + d], b.tau[(size_t)m * b.n + d]);
+                p = __fadd_rn(pt.theta[d], pt.tau[d]);
             }
             const double a = (double)p;
             s_cs[tid] = (float)((tid & 1) ? sin(a) : cos(a));   // ca, sa, cb, sb
@@ -232,8 +232,11 @@ revolve_kernel(RvArgs P, RenderBatch b, const float* __restrict__ img_params, fl
         // ---- 5. raster + loss ------------------------------------------------
         // warps fetch tiles dynamically (object tiles cost far more than
         // background tiles); each lane owns pixels (x, y0) and (x, y0 + 4)
+        // each tile's loss goes to its own slot (the fill cursor array is free
+        // again) and the slots are summed in tile order below, so the loss does
+        // not depend on which warp took which tile
+        float* tile_loss = reinterpret_cast<float*>(tcnt);
         const int lx = lane & 7, ly = lane >> 3;
-        float acc = 0.0f;
         for (;;) {
             int t = 0;
             if (lane == 0) t = atomicAdd(&s_tile, 1);
@@ -245,7 +248,7 @@ revolve_kernel(RvArgs P, RenderBatch b, const float* __restrict__ img_params, fl
             if (overflow) { beg = 0; end = count; }
             else { beg = toff[t]; end = (t + 1 < P.T) ? toff[t + 1] : total; }
             if (!kImage && !overflow && beg == end) {
-                if (lane == 0) acc += P.tile_t2[t];
+                if (lane == 0) tile_loss[t] = P.tile_t2[t];
                 continue;
             }
             const bool v0 = x < P.W && y0 < P.H, v1 = x < P.W && y1 < P.H;
@@ -304,6 +307,7 @@ revolve_kernel(RvArgs P, RenderBatch b, const float* __restrict__ img_params, fl
                     img[p] = c10; img[p + 1] = c11; img[p + 2] = c12;
                 }
             } else {
+                float acc = 0.0f;
                 if (v0) {
                     const float d0 = c00 - tg0[0], d1 = c01 - tg0[1], d2 = c02 - tg0[2];
                     acc += d0 * d0 + d1 * d1 + d2 * d2;
@@ -312,17 +316,23 @@ revolve_kernel(RvArgs P, RenderBatch b, const float* __restrict__ img_params, fl
                     const float d0 = c10 - tg1[0], d1 = c11 - tg1[1], d2 = c12 - tg1[2];
                     acc += d0 * d0 + d1 * d1 + d2 * d2;
                 }
+                acc = warp_sum(acc);
+                if (lane == 0) tile_loss[t] = acc;
             }
         }
         // ---- 6. reduction -----------------------------------------------------
         if (!kImage) {
+            __syncthreads();
+            // thread i sums tiles i, i + 1024, ...; then a fixed shuffle tree
+            float acc = 0.0f;
+            for (int t = tid; t < P.T; t += kThreads) acc += tile_loss[t];
             acc = warp_sum(acc);
             if (lane == 0) s_part[warp] = acc;
             __syncthreads();
             if (warp == 0) {
                 float v = s_part[lane];
                 v = warp_sum(v);
-                if (lane == 0) b.loss[m] = v / (float)(P.W * P.H * 3);
+                if (lane == 0) *resolve(b, m).loss = v / (float)(P.W * P.H * 3);
             }
         }
         __syncthreads();

@@ -70,9 +70,8 @@ tris2d_kernel(RenderBatch b, const float* __restrict__ raw, const int32_t* __res
         // img_params holds all raw params of the optimised subset
         for (int j = tid; j < (int)(b.n); j += kThreads) s_raw[pidx[j]] = img_params[j];
     } else {
-        const int row = m / b.per_row;
-        for (int j = tid; j < n; j += kThreads)
-            s_raw[pidx[j]] = __fadd_rn(b.theta32[row * n + j], b.tau[(size_t)m * n + j]);
+        const Pert pt = resolve(b, m);
+        for (int j = tid; j < n; j += kThreads) s_raw[pidx[j]] = __fadd_rn(pt.theta[j], pt.tau[j]);
     }
     __syncthreads();
     if (tid < n_tris) s_valid[tid] = setup_tri(&s_raw[9 * tid], W, H, s_rec[tid]) ? 1 : 0;
@@ -127,7 +126,7 @@ tris2d_kernel(RenderBatch b, const float* __restrict__ raw, const int32_t* __res
         if (tid == 0) {
             float v = 0.0f;
             for (int w = 0; w < kThreads / 32; ++w) v += s_part[w];
-            b.loss[m] = v / (float)(W * H * 3);
+            *resolve(b, m).loss = v / (float)(W * H * 3);
         }
     }
 }

@@ -36,7 +36,13 @@ __device__ double lobe_root(double L, bool upper) {
         const double y = exp(-1.0 - L);
         s = (u < 1.0) ? 1.0 - u + u * u / 3.0 : y * (1.0 + y);
     }
-    for (int it = 0; it < 64; ++it) {
+    // Stops at a relative step of 4e-16, or once a step fails to halve the
+    // previous one: the residual log(s) - s + 1 + L carries rounding noise of
+    // about 1e-16 max(|log s|, s, L), which for small s (the middle of the
+    // lobe near c = 1/2) sits far above 4e-16 s, so the step can stall at
+    // that noise level without meeting the relative test.
+    double prev = INFINITY;
+    for (int it = 0; it < 16; ++it) {
         const double g = log(s) - s + 1.0 + L;
         const double g1 = 1.0 / s - 1.0;
         const double g2 = -1.0 / (s * s);
@@ -44,9 +50,11 @@ __device__ double lobe_root(double L, bool upper) {
         if (!(sn > 0.0)) sn = 0.5 * s;
         if (upper && sn < 1.0) sn = 0.5 * (s + 1.0);
         if (!upper && sn > 1.0) sn = 0.5 * (s + 1.0);
-        const bool done = fabs(sn - s) <= 4e-16 * sn;
+        const double step = fabs(sn - s);
         s = sn;
-        if (done) break;
+        if (step <= 4e-16 * s) break;
+        if (it >= 2 && step >= 0.5 * prev) break;
+        prev = step;
     }
     return s;
 }

@@ -62,6 +62,23 @@ class hr_step_info(ctypes.Structure):
                 ("exit_reason", ctypes.c_int32), ("step_norm", ctypes.c_double)]
 
 
+class hr_server_opts(ctypes.Structure):
+    _fields_ = [("hbm_budget", ctypes.c_int64), ("max_active", ctypes.c_int32), ("chunk", ctypes.c_int32)]
+
+
+class hr_request(ctypes.Structure):
+    _fields_ = [("scene", ctypes.c_void_p), ("quantity", ctypes.c_int32), ("h_theta", _f64p), ("h_v", _f64p),
+                ("opts", hr_opts), ("optstate", ctypes.c_void_p)]
+
+
+class hr_request_info(ctypes.Structure):
+    _fields_ = [("submit_ms", ctypes.c_double), ("admit_ms", ctypes.c_double), ("done_ms", ctypes.c_double),
+                ("status", ctypes.c_int32), ("batches", ctypes.c_int32)]
+
+
+HR_NEWTON_STEP = 3
+
+
 class HRError(RuntimeError):
     pass
 
@@ -92,12 +109,17 @@ def lib() -> ctypes.CDLL:
         L.hr_optstate_theta.argtypes = [vp, _f64p]
         L.hr_profile_enable.argtypes = [vp, ctypes.c_int32]
         L.hr_profile_last.argtypes = [vp, _f32p]
+        L.hr_server_create.argtypes = [ctypes.POINTER(hr_server_opts), ctypes.POINTER(vp)]
+        L.hr_server_destroy.argtypes = [vp]
+        L.hr_server_submit.argtypes = [vp, ctypes.POINTER(hr_request), ctypes.POINTER(ctypes.c_uint64)]
+        L.hr_server_wait.argtypes = [vp, ctypes.c_uint64, vp, ctypes.POINTER(hr_request_info), ctypes.c_int32]
         L.hr_last_error.argtypes = [ctypes.c_char_p, ctypes.c_size_t]
         L.hr_last_error.restype = ctypes.c_size_t
         for name in ("hr_create_scene", "hr_destroy_scene", "hr_estimate_grad", "hr_estimate_hessian",
                      "hr_estimate_hvp", "hr_estimate_dev", "hr_estimate_dev_noalloc", "hr_render", "hr_optstate_create",
                      "hr_optstate_destroy", "hr_newton_cg_step", "hr_optstate_theta", "hr_profile_enable",
-                     "hr_profile_last"):
+                     "hr_profile_last", "hr_server_create", "hr_server_destroy", "hr_server_submit",
+                     "hr_server_wait"):
             getattr(L, name).restype = ctypes.c_int32
         L.hr_version.restype = ctypes.c_int32
         _lib = L
@@ -293,3 +315,48 @@ class Scene:
         spp = int(self.sc.get("spp", 1)) if spp is None else spp
         hr_render(self.handle, np.ascontiguousarray(params, np.float64), seed, request, sub, k, tag, spp, img)
         return img
+
+
+# ---------------------------------------------------------------------------
+# serving
+# ---------------------------------------------------------------------------
+def hr_server_create(hbm_budget: int, max_active: int = 32, chunk: int = 0) -> int:
+    o = hr_server_opts(int(hbm_budget), int(max_active), int(chunk))
+    h = ctypes.c_void_p()
+    check(lib().hr_server_create(ctypes.byref(o), ctypes.byref(h)), "hr_server_create")
+    return h.value
+
+
+def hr_server_destroy(srv: int) -> None:
+    check(lib().hr_server_destroy(srv), "hr_server_destroy")
+
+
+def hr_server_submit(srv: int, req: hr_request) -> int:
+    t = ctypes.c_uint64()
+    check(lib().hr_server_submit(srv, ctypes.byref(req), ctypes.byref(t)), "hr_server_submit")
+    return t.value
+
+
+def hr_server_wait(srv: int, ticket: int, out, info: hr_request_info, timeout_ms: int = 120000) -> None:
+    ptr = None if out is None else (out.ctypes.data if isinstance(out, np.ndarray) else ctypes.addressof(out))
+    check(lib().hr_server_wait(srv, ticket, ptr, ctypes.byref(info), int(timeout_ms)), "hr_server_wait")
+
+
+def make_request(scene: "Scene", quantity: int, theta=None, v=None, opts: hr_opts = None, optstate=None):
+    """Build an hr_request; returns (request, keep-alive arrays)."""
+    r = hr_request()
+    r.scene = scene.handle
+    r.quantity = int(quantity)
+    keep = []
+    if theta is not None:
+        th = np.ascontiguousarray(theta, np.float64)
+        keep.append(th)
+        r.h_theta = _ptr(th, _f64p)
+    if v is not None:
+        vv = np.ascontiguousarray(v, np.float64)
+        keep.append(vv)
+        r.h_v = _ptr(vv, _f64p)
+    if opts is not None:
+        r.opts = opts
+    r.optstate = optstate
+    return r, keep

@@ -185,3 +185,45 @@ def tris2d_scene(seed: int = 0xC3, width: int = 256, height: int = 256,
 def scaled(scene_fn, **kw) -> dict:
     """Call a scene builder with overrides (small parity sizes)."""
     return scene_fn(**kw)
+
+
+# ---------------------------------------------------------------------------
+# Serving mix: resident scenes of every kind and a seeded request stream with
+# Poisson arrivals (parameter dims 2..64, 256..16384 samples, 64^2..512^2).
+# ---------------------------------------------------------------------------
+def serving_scenes() -> dict:
+    return {
+        "disc64": disc_scene(),
+        "disc512": disc_scene(seed=0xD5, width=512, height=512),
+        "revolve128": revolve_scene(seed=0xE1, width=128, height=128),
+        "revolve256": revolve_scene(),
+        "revolve512": revolve_scene(seed=0xE5, width=512, height=512),
+        "pt64": ptbox_scene(seed=0xF2, width=64, height=64, spp=2, target_spp=16),
+        "tris128_n64": tris2d_scene(seed=0xA3, width=128, height=128, n_instances=1),
+        "tris256_n16": tris2d_scene(seed=0xA4, width=256, height=256, n_params=16, n_instances=1),
+    }
+
+
+# (scene, quantity, strategy, samples); quantity 0 grad, 1 Hessian, 2 HVP;
+# strategy 0 element-wise, 1 aggregate
+SERVING_KINDS = [
+    ("disc64", 1, 0, 1024), ("disc64", 1, 1, 16384), ("disc64", 0, 1, 4096), ("disc512", 1, 1, 256),
+    ("revolve128", 1, 1, 2048), ("revolve256", 1, 1, 4096), ("revolve256", 2, 1, 1024), ("revolve512", 1, 1, 256),
+    ("pt64", 2, 1, 256), ("tris128_n64", 2, 1, 512), ("tris128_n64", 0, 1, 1024), ("tris256_n16", 2, 1, 256),
+]
+
+
+def serving_requests(scenes: dict, n_requests: int = 240, rate_hz: float = 1000.0, seed: int = 0xC4) -> list:
+    g = _rng(seed)
+    t = 0.0
+    reqs = []
+    for i in range(n_requests):
+        t += g.exponential(1.0 / rate_hz)
+        name, q, strat, M = SERVING_KINDS[int(g.integers(len(SERVING_KINDS)))]
+        sc = scenes[name]
+        n = sc["n_params"]
+        theta = np.asarray(sc["theta_query"], np.float64) + g.normal(0.0, 0.01, n)
+        v = g.normal(size=n) if q == 2 else None
+        reqs.append(dict(scene=name, quantity=q, strategy=strat, M=M, theta=theta, v=v,
+                         sigma=sc["sigma"], seed=1 + i, request=i, arrival_s=t))
+    return reqs

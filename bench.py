@@ -170,6 +170,20 @@ def run_reference(args):
     return 0
 
 
+def whole_job_rate(local_ms, steps, world, device):
+    """Estimates per second of the whole job: every rank runs `steps` independent
+    estimates (replicas, no data-path collective); the job takes as long as
+    its slowest rank, so the time is the max over ranks.  Returns (rate, max ms)."""
+    if world > 1:
+        import torch
+        import torch.distributed as dist
+        t = torch.tensor([local_ms], dtype=torch.float64, device=device)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        local_ms = float(t.item())
+        dist.barrier()
+    return world * steps / (local_ms / 1e3), local_ms
+
+
 def _timed_steps(torch, stream, flush, fn, warmup, steps):
     """CUDA-event time of `fn(i)` per step (L2 flushed before each, untimed)."""
     for i in range(warmup):
@@ -426,13 +440,7 @@ def main():
         render_ms.append(float(st[1]))
     torch.cuda.synchronize()
     clk = clocks.stop()
-    total_ms = float(np.sum(times))
-    if world > 1:
-        t = torch.tensor([total_ms], device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        total_ms = float(t.item())
-        dist.barrier()
-    value = world * args.steps / (total_ms / 1e3)
+    value, total_ms = whole_job_rate(float(np.sum(times)), args.steps, world, "cuda")
 
     # end to end through the host-pointer entry point
     hr.hr_profile_enable(S.handle, False)

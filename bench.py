@@ -277,11 +277,45 @@ def run_secondary(args):
                                             "32 gradient + 10 x 32 HVP renders per instance-step, graph-captured"}})
         hr.hr_optstate_destroy(st)
         S.close()
+    elif args.workload == "boxes":
+        line.update(boxes_variance_bench(hr, wl))
     else:
         line.update(serving_bench(torch, hr, wl))
     line["clocks"] = clocks.stop()
     print(json.dumps(line))
     return 0
+
+
+def boxes_variance_bench(hr, wl):
+    """Box2 / Box10 plateau tasks: Hessian variance per render of element-wise
+    IS, aggregate IS and plain Gaussian sampling at equal renders (the paper's
+    variance analysis), from 64 independent estimates each, and their rate."""
+    out = {"metric": "Hessian variance per render and estimates/s, Box2 / Box10 (squares)"}
+    for K in (1, 5):
+        sc = wl.boxes_scene(n_boxes=K)
+        S = hr.Scene(sc)
+        n = 2 * K
+        E = n * (n + 1) // 2
+        th = np.asarray(sc["theta_target"]) + 0.05
+        renders = 3 * 1024 if K == 1 else E * 64
+        res = {}
+        for name, strat in (("elementwise", hr.HR_ELEMENTWISE), ("aggregate", hr.HR_AGGREGATE),
+                            ("plain", hr.HR_PLAIN)):
+            M = renders // E if strat == hr.HR_ELEMENTWISE else renders
+            M -= M % 2
+            ests = []
+            t0 = time.perf_counter()
+            for rq in range(64):
+                H = S.estimate(hr.HR_HESSIAN, th, sc["sigma"], M, strat, 7, rq)
+                ests.append(H[np.triu_indices(n)])
+            dt = time.perf_counter() - t0
+            var = np.var(np.asarray(ests), axis=0, ddof=1)
+            res[name] = {"renders_per_estimate": M * (E if strat == hr.HR_ELEMENTWISE else 1),
+                         "mean_variance_per_render": float(np.mean(var) * renders),
+                         "estimates_per_s": 64 / dt}
+        out[f"box{2 * K}"] = res
+        S.close()
+    return out
 
 
 def serving_bench(torch, hr, wl):
@@ -380,7 +414,7 @@ def main():
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="native", choices=["native", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--workload", default="revolve", choices=["revolve", "disc", "ptbox", "newton", "serving"],
+    ap.add_argument("--workload", default="revolve", choices=["revolve", "disc", "ptbox", "newton", "serving", "boxes"],
                     help="revolve (default) is the headline workload; the others report the remaining "
                          "configurations in their own JSON lines")
     args = ap.parse_args()

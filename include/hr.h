@@ -61,18 +61,25 @@ typedef int32_t hr_status;
  *            quad; 6 params (light centre xyz, sphere-0 centre xyz), RGB;
  * TRIS2D     coloured 2D triangles drawn in painter's order; params are a
  *            subset (param_index) of the 9 raw values per triangle
- *            (x0 y0 x1 y1 x2 y2 r g b). */
+ *            (x0 y0 x1 y1 x2 y2 r g b);
+ * BOXES2D    K = n_params / 2 axis-aligned squares (the Box2 / Box10 plateau
+ *            tasks), params = square centres, grayscale; a pixel centre is 1
+ *            inside any square (|dx| < h and |dy| < h in FP32). */
 #define HR_SCENE_DISC2D 0
 #define HR_SCENE_REVOLVE3D 1
 #define HR_SCENE_PTBOX 2
 #define HR_SCENE_TRIS2D 3
+#define HR_SCENE_BOXES2D 4
 
 /* Sampling strategy: element-wise importance sampling (one sample set of M
  * perturbations per unique element: n for the gradient, n(n+1)/2 for the
- * Hessian, Tab. 1 "IS") or aggregate sampling (one set of M for all
- * elements, Tab. 1 "AIS"). */
+ * Hessian, n rows for the HVP; Tab. 1 IS column), aggregate sampling (one set
+ * of M for all elements, Tab. 1 AIS column), or no importance sampling
+ * (tau ~ N(0, sigma^2 I) with antithetic legs +tau / -tau, weight = the kernel
+ * factor; Tab. 1 no-IS column). */
 #define HR_ELEMENTWISE 0
 #define HR_AGGREGATE 1
+#define HR_PLAIN 2
 
 /* Estimated quantity */
 #define HR_GRAD 0
@@ -93,11 +100,12 @@ typedef struct hr_scene_s* hr_scene;
 typedef struct {
     int32_t kind;                 /* HR_SCENE_* */
     int32_t width, height;        /* image size in pixels */
-    int32_t n_params;             /* DISC2D 2, REVOLVE3D 2, PTBOX 6, TRIS2D = len(param_index) */
+    int32_t n_params;             /* DISC2D 2, REVOLVE3D 2, PTBOX 6, TRIS2D = len(param_index),
+                                     BOXES2D 2K (K <= 32) */
     const double* theta_target;   /* [n_params] target parameters */
     const float* target_image;    /* optional [H][W][C] FP32 (C = 1 for DISC2D, else 3);
                                      NULL: the library renders it at theta_target */
-    /* DISC2D */
+    /* DISC2D: disc radius; BOXES2D: square half-size */
     float radius;
     /* REVOLVE3D: model-space vertices [n_vertices][3], triangles [n_triangles][3]
        (outward winding), albedo RGB, unit light direction, camera distance on +z
@@ -136,7 +144,7 @@ typedef struct {
     double sigma;          /* smoothing bandwidth, > 0 */
     int64_t n_perturb;     /* M: renders per request (aggregate) or per unique
                               element (element-wise); even, >= 2 */
-    int32_t strategy;      /* HR_ELEMENTWISE or HR_AGGREGATE (HVP: aggregate only) */
+    int32_t strategy;      /* HR_ELEMENTWISE, HR_AGGREGATE or HR_PLAIN */
     uint64_t seed;         /* Philox key */
     uint32_t request_id;   /* Philox counter word 3 */
     uint32_t sub;          /* first sub-stream (counter word 2, low 24 bits);
@@ -164,11 +172,23 @@ hr_status hr_estimate_grad(hr_scene scene, const double* h_theta, const hr_opts*
 /* Smoothed Hessian (Sec. 3.3, 3.5): h_out_H [n][n] row-major, symmetric. */
 hr_status hr_estimate_hessian(hr_scene scene, const double* h_theta, const hr_opts* opts, double* h_out_H);
 
-/* Smoothed Hessian-vector product (Sec. 3.4, 3.5), aggregate strategy:
- * the HVP kernel sum_j h_ij v_j sampled from the Hessian mixture, so that on
- * the same samples it equals the aggregate Hessian times v. */
+/* Smoothed Hessian-vector product (Sec. 3.4, 3.5): the HVP kernel
+ * sum_j h_ij v_j.  Aggregate: sampled from the Hessian mixture (M renders),
+ * so that on the same samples it equals the aggregate Hessian times v.
+ * Element-wise (Tab. 1 IS column, n sample sets of M): output row i draws
+ * lobe (i, j) with probability |v_j| Z_ij / sum_l |v_l| Z_il and is weighted by
+ * the row kernel over that mixture. */
 hr_status hr_estimate_hvp(hr_scene scene, const double* h_theta, const double* h_v,
                           const hr_opts* opts, double* h_out_Hv);
+
+/* HVP as the central difference of two smoothed-gradient estimates,
+ * (g(theta + eps v) - g(theta - eps v)) / (2 eps) (Sec. 2 central differences
+ * of gradients; Sec. 3.4), both estimates on the same perturbations (common
+ * random numbers): one sampling pass, 2 M renders per sample set (element-wise
+ * gradient: n sets).  theta +- eps v is formed in FP64 and rounded to FP32.
+ * Inspection outputs in opts are ignored.  eps > 0. */
+hr_status hr_estimate_hvp_fd(hr_scene scene, const double* h_theta, const double* h_v, double eps,
+                             const hr_opts* opts, double* h_out_Hv);
 
 /* Device-pointer form of the three estimates, asynchronous on opts->stream:
  * d_theta [n], d_v [n] (HVP only, else NULL), d_out [n], [n][n] or [n]

@@ -76,6 +76,8 @@ def lib():
         L.or_weights.restype = ctypes.c_int
         L.or_disc_loss.argtypes = [ctypes.c_int, ctypes.c_int, ctypes.c_float, _f32p, _f32p, _f32p]
         L.or_disc_loss.restype = ctypes.c_double
+        L.or_boxes_loss.argtypes = [ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_float, _f32p, _f32p, _f32p]
+        L.or_boxes_loss.restype = ctypes.c_double
         L.or_revolve_loss.argtypes = [ctypes.POINTER(_RevolveScene), _f32p, _f32p, _f32p]
         L.or_revolve_loss.restype = ctypes.c_double
         L.or_tris2d_loss.argtypes = [ctypes.POINTER(_Tris2dScene), _f32p, _f32p, _f32p]
@@ -90,6 +92,9 @@ def lib():
                                      ctypes.c_uint64, ctypes.c_uint32, ctypes.c_uint32, ctypes.c_uint32,
                                      ctypes.c_uint32, ctypes.c_uint32, _f64p]
         L.or_perturb.argtypes = [ctypes.c_int, _f64p, _f32p, _f32p]
+        L.or_draw_hvp_rows.argtypes = [ctypes.c_int, ctypes.c_double, _f64p, ctypes.c_int64, ctypes.c_uint64,
+                                       ctypes.c_uint32, ctypes.c_uint32, ctypes.c_int, _f32p, _i32p]
+        L.or_draw_hvp_rows.restype = ctypes.c_int
         _lib = L
     return _lib
 
@@ -147,6 +152,18 @@ def draw(lobe: int, n: int, sigma: float, P: int, seed: int, request: int, sub: 
     comp = np.zeros(P, np.int32)
     rc = lib().or_draw(lobe, n, sigma, P, seed, request & 0xFFFFFFFF, sub, comp_i, comp_j,
                        _p(tau, _f32p), _p(comp, _i32p))
+    assert rc == 0
+    return tau, comp
+
+
+def draw_hvp_rows(n: int, sigma: float, v, P: int, seed: int, request: int, sub: int, row: int):
+    """Element-wise HVP pairs for output `row` (component j drawn from the
+    |v|-weighted row mixture)."""
+    tau = np.zeros((2 * P, n), np.float32)
+    comp = np.zeros(P, np.int32)
+    vv = np.ascontiguousarray(v, np.float64)
+    rc = lib().or_draw_hvp_rows(n, sigma, _p(vv, _f64p), P, seed, request & 0xFFFFFFFF, sub, row,
+                                _p(tau, _f32p), _p(comp, _i32p))
     assert rc == 0
     return tau, comp
 
@@ -210,6 +227,24 @@ class DiscRenderer(Renderer):
     def loss(self, p, ctx=None):
         p = np.ascontiguousarray(p, np.float32)
         return lib().or_disc_loss(self.W, self.H, self.r, _p(p, _f32p), _p(self.target, _f32p), None)
+
+
+class BoxesRenderer(Renderer):
+    def __init__(self, sc: dict, target=None):
+        self.W, self.H, self.h = sc["width"], sc["height"], np.float32(sc["half_size"])
+        self.n = sc["n_params"]
+        self.K = self.n // 2
+        self.target = target if target is not None else self.image(np.asarray(sc["theta_target"], np.float32))
+
+    def image(self, p):
+        img = np.zeros(self.W * self.H, np.float32)
+        p = np.ascontiguousarray(p, np.float32)
+        lib().or_boxes_loss(self.W, self.H, self.K, self.h, _p(p, _f32p), None, _p(img, _f32p))
+        return img
+
+    def loss(self, p, ctx=None):
+        p = np.ascontiguousarray(p, np.float32)
+        return lib().or_boxes_loss(self.W, self.H, self.K, self.h, _p(p, _f32p), _p(self.target, _f32p), None)
 
 
 class RevolveRenderer(Renderer):
@@ -315,13 +350,26 @@ class PtboxRenderer(Renderer):
 def renderer_for(sc: dict, **kw) -> Renderer:
     from paper_2412_03489_gb300 import workloads as wl
     return {wl.SCENE_DISC2D: DiscRenderer, wl.SCENE_REVOLVE3D: RevolveRenderer,
-            wl.SCENE_TRIS2D: Tris2dRenderer, wl.SCENE_PTBOX: PtboxRenderer}[sc["kind"]](sc, **kw)
+            wl.SCENE_TRIS2D: Tris2dRenderer, wl.SCENE_PTBOX: PtboxRenderer,
+            wl.SCENE_BOXES2D: BoxesRenderer}[sc["kind"]](sc, **kw)
 
 
 # --------------------------------------------------------------------------
 # estimators
 # --------------------------------------------------------------------------
 QUANTITY = {"grad": 0, "hessian": 1, "hvp": 2}
+
+
+def estimate_hvp_fd(r: Renderer, theta, v, eps: float, sigma: float, M: int, strategy: str, seed: int,
+                    request: int, sub: int = 0):
+    """HVP as the central difference of two smoothed-gradient estimates at
+    theta +- eps v (Sec. 2, central differences of gradients; Sec. 3.4) with
+    common random numbers: both use the same perturbations."""
+    theta = np.asarray(theta, np.float64)
+    v = np.asarray(v, np.float64)
+    gp = estimate(r, "grad", theta + eps * v, sigma, M, strategy, seed, request, sub)
+    gm = estimate(r, "grad", theta - eps * v, sigma, M, strategy, seed, request, sub)
+    return (gp.flat - gm.flat) / (2.0 * eps), gp, gm
 
 
 def elements(quantity: str, n: int):
@@ -370,14 +418,23 @@ def estimate(r: Renderer, quantity: str, theta, sigma: float, M: int, strategy: 
     P = M // 2
     if strategy == "aggregate":
         groups = [(-1, -1, sub)]
+    elif strategy == "plain":
+        groups = [(-3, -1, sub)]
+    elif strategy == "elementwise" and quantity == "hvp":
+        # one sample set per output row, drawn from the row's |v|-weighted mixture
+        groups = [(i, -2, sub + i) for i in range(n)]
     elif strategy == "elementwise":
         groups = [(i, j, sub + e) for e, (i, j) in enumerate(elements(quantity, n))]
     else:
         raise ValueError(strategy)
     taus, ws, ls, comps = [], [], [], []
     for ci, cj, s in groups:
-        tau, comp = draw(lobe, n, sigma, P, seed, request, s, ci, cj)
-        w = weights(q, n, sigma, tau, ci, cj, v)
+        if cj == -2:
+            tau, comp = draw_hvp_rows(n, sigma, v, P, seed, request, s, ci)
+            w = weights(3, n, sigma, tau, ci, -1, v)
+        else:
+            tau, comp = draw(lobe, n, sigma, P, seed, request, s, ci, cj)
+            w = weights(q, n, sigma, tau, ci, cj, v)
         if hasattr(r, "loss_batch"):
             # RN32(RN32(theta) + tau) row by row (IEEE single-precision add)
             losses = r.loss_batch(np.asarray(theta, np.float64).astype(np.float32)[None, :] + tau)

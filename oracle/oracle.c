@@ -161,11 +161,32 @@ double or_Zo(double s) { return or_Zg(s) * or_Zg(s); }
 /* ------------------------------------------------------------------------ */
 #define TAG_SAMPLE 1u
 
+/* Row mixture of the HVP kernel sum_j c_ij v_j (element-wise HVP): component
+ * j of row i is drawn with probability |v_j| Z_ij / sum_l |v_l| Z_il, the mass
+ * of |c_ij v_j N|; the cumulative table is summed in index order. */
+static int row_component(uint32_t word, int i, int n, double sigma, const double* v)
+{
+    double tot = 0.0;
+    for (int l = 0; l < n; ++l) tot += fabs(v[l]) * (l == i ? or_Zd(sigma) : or_Zo(sigma));
+    double u = or_u01(word) * tot, acc = 0.0;
+    int last = i;
+    for (int l = 0; l < n; ++l) {
+        double p = fabs(v[l]) * (l == i ? or_Zd(sigma) : or_Zo(sigma));
+        if (p > 0.0) last = l;
+        acc += p;
+        if (p > 0.0 && u < acc) return l;
+    }
+    return last;
+}
+
+static const double* g_row_v = 0;   /* v for row-mixture draws (set by or_draw_hvp_rows) */
+
 int or_draw(int lobe, int n, double sigma, int64_t P, uint64_t seed,
             uint32_t request, uint32_t sub, int comp_i, int comp_j,
             float* tau, int32_t* comp_out)
 {
     if (n < 1 || P < 1 || !(sigma > 0)) return -1;
+    if (comp_j == -2 && !g_row_v) return -1;
     double* g = (double*)malloc(sizeof(double) * n);
     double* tp = (double*)malloc(sizeof(double) * n);
     double* tm = (double*)malloc(sizeof(double) * n);
@@ -183,8 +204,21 @@ int or_draw(int lobe, int n, double sigma, int64_t P, uint64_t seed,
             double z = (d % 2 == 0) ? R * cos(2.0 * OR_PI * u2) : R * sin(2.0 * OR_PI * u2);
             g[d] = sigma * z;
         }
+        if (comp_i == -3) {
+            /* no importance sampling (Tab. 1 "no IS" column): tau ~ N(0, s^2 I),
+             * antithetic legs +tau and -tau */
+            for (int d = 0; d < n; ++d) {
+                tau[(2 * k) * n + d] = (float)g[d];
+                tau[(2 * k + 1) * n + d] = (float)(-g[d]);
+            }
+            if (comp_out) comp_out[k] = -1;
+            continue;
+        }
         int i, j;
-        if (comp_i >= 0) {
+        if (comp_i >= 0 && comp_j == -2) {
+            i = comp_i;
+            j = row_component(w[0], comp_i, n, sigma, g_row_v);
+        } else if (comp_i >= 0) {
             i = comp_i;
             j = lobe == 0 ? comp_i : comp_j;
         } else if (lobe == 0) {
@@ -240,6 +274,7 @@ int or_weights(int quantity, int n, double sigma, const double* v, int64_t M,
 {
     int E = quantity == 1 ? n * (n + 1) / 2 : n;
     double s2 = sigma * sigma, s4 = s2 * s2;
+    if (quantity == 3 && (!v || comp_i < 0)) return -1;
     double Zg = or_Zg(sigma), Zd = or_Zd(sigma), Zo = or_Zo(sigma);
     double* t = (double*)malloc(sizeof(double) * n);
     double* C = (double*)malloc(sizeof(double) * n * n);
@@ -247,6 +282,39 @@ int or_weights(int quantity, int n, double sigma, const double* v, int64_t M,
         double* wm = w + m * E;
         for (int e = 0; e < E; ++e) wm[e] = 0.0;
         double sign = (m % 2 == 0) ? 1.0 : -1.0;
+        if (comp_i == -3) {
+            /* plain Gaussian sampling: the weight is the kernel factor c(tau) */
+            for (int d = 0; d < n; ++d) t[d] = (double)tau[m * n + d];
+            if (quantity == 0) {
+                for (int d = 0; d < n; ++d) wm[d] = t[d] / s2;
+            } else {
+                int e = 0;
+                for (int a = 0; a < n; ++a) {
+                    double hv = 0.0;
+                    for (int b = 0; b < n; ++b) {
+                        double c = (a == b) ? (t[a] * t[a] - s2) / s4 : t[a] * t[b] / s4;
+                        if (quantity == 1 && b >= a) wm[e++] = c;
+                        if (quantity != 1) hv += c * v[b];
+                    }
+                    if (quantity != 1) wm[a] = hv;
+                }
+            }
+            continue;
+        }
+        if (quantity == 3) {
+            /* h_i^v / q_i with q_i the row mixture: (sum_j c_ij v_j) (sum_l |v_l| Z_il) / sum_j |v_j| |c_ij| */
+            for (int d = 0; d < n; ++d) t[d] = (double)tau[m * n + d];
+            int i = comp_i;
+            double hv = 0.0, den = 0.0, tot = 0.0;
+            for (int b = 0; b < n; ++b) {
+                double c = (b == i) ? (t[i] * t[i] - s2) / s4 : t[i] * t[b] / s4;
+                hv += c * v[b];
+                den += fabs(v[b]) * fabs(c);
+                tot += fabs(v[b]) * (b == i ? Zd : Zo);
+            }
+            wm[i] = den > 0.0 ? hv * tot / den : 0.0;
+            continue;
+        }
         if (comp_i >= 0) {
             if (quantity == 0) {
                 wm[comp_i] = sign * Zg;
@@ -313,6 +381,34 @@ double or_disc_loss(int W, int H, float r, const float p[2], const float* target
             if (target) {
                 double diff = v - (double)target[y * W + x];
                 acc += diff * diff;
+            }
+        }
+    }
+    return acc / ((double)W * (double)H);
+}
+
+/* ------------------------------------------------------------------------ */
+/* Squares renderer (the Box2 / Box10 plateau tasks of Sec. 4.1): K          */
+/* axis-aligned squares of half-size h centred at (p[2s], p[2s+1]); a pixel  */
+/* centre is 1 when it lies strictly inside any square, decided in FP32 as   */
+/* |px - cx| < h and |py - cy| < h.                                          */
+/* ------------------------------------------------------------------------ */
+double or_boxes_loss(int W, int H, int K, float h, const float* p, const float* target, float* img)
+{
+    double acc = 0.0;
+    for (int y = 0; y < H; ++y) {
+        for (int x = 0; x < W; ++x) {
+            float px = ((float)x + 0.5f) / (float)W;
+            float py = ((float)y + 0.5f) / (float)H;
+            double v = 0.0;
+            for (int k = 0; k < K; ++k) {
+                float dx = px - p[2 * k], dy = py - p[2 * k + 1];
+                if (fabsf(dx) < h && fabsf(dy) < h) { v = 1.0; break; }
+            }
+            if (img) img[y * W + x] = (float)v;
+            if (target) {
+                double d = v - (double)target[y * W + x];
+                acc += d * d;
             }
         }
     }
@@ -774,4 +870,15 @@ void or_ptbox_trace(const or_ptbox_scene* s, const float p[6], const float o[3],
 void or_perturb(int n, const double* theta, const float* tau, float* p)
 {
     for (int j = 0; j < n; ++j) p[j] = (float)theta[j] + tau[j];
+}
+
+/* Element-wise HVP draws: P pairs for output row i from its |v|-weighted
+ * row mixture (v is read during the call only). */
+int or_draw_hvp_rows(int n, double sigma, const double* v, int64_t P, uint64_t seed,
+                     uint32_t request, uint32_t sub, int row, float* tau, int32_t* comp_out)
+{
+    g_row_v = v;
+    int rc = or_draw(1, n, sigma, P, seed, request, sub, row, -2, tau, comp_out);
+    g_row_v = 0;
+    return rc;
 }

@@ -40,7 +40,8 @@ double or_Zo(double sigma);
 
 /* ---- sampling (Sec. 3.2-3.5) ----
  * lobe: 0 = gradient lobes, 1 = Hessian lobes.
- * comp_i < 0: aggregate (component drawn from Philox word 0).
+ * comp_i = -1: aggregate (component drawn from Philox word 0).
+ * comp_i = -3: no importance sampling: tau ~ N(0, s^2 I), legs +tau / -tau.
  * comp_i >= 0: element-wise importance sampling of element (comp_i, comp_j)
  *              (comp_j ignored for gradient lobes).
  * Writes tau[2P][n] as FP32 (the canonical perturbation) and, when comp_out is
@@ -50,9 +51,15 @@ int or_draw(int lobe, int n, double sigma, int64_t P, uint64_t seed,
             uint32_t request, uint32_t sub, int comp_i, int comp_j,
             float* tau, int32_t* comp_out);
 
+/* Element-wise HVP (Tab. 1 IS column): pairs for output row `row`, component
+ * (row, j) drawn with probability |v_j| Z_rowj / sum_l |v_l| Z_rowl. */
+int or_draw_hvp_rows(int n, double sigma, const double* v, int64_t P, uint64_t seed,
+                     uint32_t request, uint32_t sub, int row, float* tau, int32_t* comp_out);
+
 /* ---- estimator weights ----
  * quantity: 0 = gradient (E = n), 1 = Hessian upper triangle (E = n(n+1)/2),
- *           2 = HVP (E = n, needs v).
+ *           2 = HVP (E = n, needs v), 3 = element-wise HVP of row comp_i
+ *           (E = n, needs v; weight h_i^v / q_i of the row mixture).
  * For element-wise sampling (comp_i >= 0) the weight is +-Z of that element
  * and zero elsewhere.  Weights are evaluated at the FP32 perturbation.
  */
@@ -61,6 +68,8 @@ int or_weights(int quantity, int n, double sigma, const double* v, int64_t M,
 
 /* ---- renderers: loss of one image against a target ---- */
 /* disc: value 1 inside radius r of the centre p, else 0; grayscale. */
+/* squares: K axis-aligned squares of half-size h centred at p[2s], p[2s+1]. */
+double or_boxes_loss(int W, int H, int K, float h, const float* p, const float* target, float* img);
 double or_disc_loss(int W, int H, float r, const float p[2], const float* target, float* img);
 
 typedef struct {

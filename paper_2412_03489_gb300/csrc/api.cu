@@ -17,6 +17,8 @@ namespace hr {
 
 void launch_disc_loss(const DevScene&, const RenderBatch&, cudaStream_t);
 void launch_disc_image(const DevScene&, const float*, float*, cudaStream_t);
+void launch_boxes_loss(const DevScene&, const RenderBatch&, cudaStream_t);
+void launch_boxes_image(const DevScene&, const float*, float*, cudaStream_t);
 void launch_revolve_loss(const DevScene&, const RenderBatch&, cudaStream_t);
 void launch_revolve_image(const DevScene&, const float*, float*, cudaStream_t);
 size_t revolve_smem_bytes(int nv, int nt, int W, int H);
@@ -44,6 +46,7 @@ void launch_render_loss(const DevScene& sc, const RenderBatch& b, cudaStream_t s
         case HR_SCENE_REVOLVE3D: launch_revolve_loss(sc, b, s); break;
         case HR_SCENE_TRIS2D: launch_tris2d_loss(sc, b, s); break;
         case HR_SCENE_PTBOX: launch_ptbox_loss(sc, b, s); break;
+        case HR_SCENE_BOXES2D: launch_boxes_loss(sc, b, s); break;
     }
 }
 
@@ -54,6 +57,7 @@ void launch_render_image(const DevScene& sc, const float* d_params, uint64_t see
         case HR_SCENE_REVOLVE3D: launch_revolve_image(sc, d_params, d_img, s); break;
         case HR_SCENE_TRIS2D: launch_tris2d_image(sc, d_params, d_img, s); break;
         case HR_SCENE_PTBOX: launch_ptbox_image(sc, d_params, seed, request, sub, k, tag, spp, d_img, s); break;
+        case HR_SCENE_BOXES2D: launch_boxes_image(sc, d_params, d_img, s); break;
     }
 }
 
@@ -108,6 +112,11 @@ cudaError_t upload(T** dst, const T* src, size_t count) {
     return e;
 }
 
+__global__ void fd_combine_kernel(const double* gp, const double* gm, double inv2eps, int n, double* out) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < n) out[i] = (gp[i] - gm[i]) * inv2eps;
+}
+
 __global__ void f64_to_f32_kernel(const double* in, float* out, int n) {
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i < n) out[i] = __double2float_rn(in[i]);
@@ -120,10 +129,8 @@ hr_status validate_opts(const hr_scene_s* s, int quantity, const hr_opts* o) {
     if (!o) return fail(HR_ERR_INVALID_ARG, "opts is NULL");
     if (!(o->sigma > 0.0) || !std::isfinite(o->sigma)) return fail(HR_ERR_INVALID_ARG, "sigma must be > 0");
     if (o->n_perturb < 2 || (o->n_perturb & 1)) return fail(HR_ERR_INVALID_ARG, "n_perturb must be even and >= 2");
-    if (o->strategy != HR_ELEMENTWISE && o->strategy != HR_AGGREGATE)
+    if (o->strategy != HR_ELEMENTWISE && o->strategy != HR_AGGREGATE && o->strategy != HR_PLAIN)
         return fail(HR_ERR_INVALID_ARG, "unknown strategy %d", o->strategy);
-    if (quantity == HR_HVP && o->strategy != HR_AGGREGATE)
-        return fail(HR_ERR_UNSUPPORTED, "the HVP is estimated with the aggregate strategy only");
     const int n = s->sc.n;
     const int G = o->strategy == HR_ELEMENTWISE ? n_elements(quantity, n) : 1;
     const int64_t total = (int64_t)G * o->n_perturb;
@@ -203,8 +210,12 @@ hr_status run_estimate(hr_scene_s* s, int quantity, const double* h_theta, const
         gr.pad = 0;
         if (o->strategy == HR_AGGREGATE) {
             gr.comp_i = -1; gr.comp_j = -1;
+        } else if (o->strategy == HR_PLAIN) {
+            gr.comp_i = -3; gr.comp_j = -3;
         } else if (quantity == HR_GRAD) {
             gr.comp_i = g; gr.comp_j = g;
+        } else if (quantity == HR_HVP) {
+            gr.comp_i = g; gr.comp_j = -2; gr.quantity = 4;   // row g of the HVP, row-mixture draws
         } else {
             int r = 0, rem = g;
             while (rem >= n - r) { rem -= n - r; ++r; }
@@ -286,6 +297,103 @@ hr_status run_estimate(hr_scene_s* s, int quantity, const double* h_theta, const
     return HR_OK;
 }
 
+// Central difference of two gradient estimates on shared perturbations: the
+// sampler runs once, one launch renders both parameter rows (theta +- eps v)
+// through a two-row batch table, each row gets its own sums.
+hr_status run_hvp_fd(hr_scene_s* s, const double* h_theta, const double* h_v, double eps, const hr_opts* o,
+                     double* h_out) {
+    DevScene& sc = s->sc;
+    Workspace& ws = s->ws;
+    const int n = sc.n;
+    const int E = n;
+    const int G = o->strategy == HR_ELEMENTWISE ? n : 1;
+    const int64_t M = o->n_perturb;
+    const int P = (int)(M / 2);
+    const int64_t Mt = (int64_t)G * M;
+    cudaStream_t stream = o->stream ? (cudaStream_t)o->stream : s->stream;
+    if (ws.theta32.reserve(sizeof(float) * 2 * n) != cudaSuccess || ws.tau.reserve(sizeof(float) * Mt * n) != cudaSuccess ||
+        ws.w.reserve(sizeof(float) * Mt * E) != cudaSuccess || ws.meta.reserve(sizeof(uint2) * Mt) != cudaSuccess ||
+        ws.loss.reserve(sizeof(float) * 2 * Mt) != cudaSuccess || ws.flat.reserve(sizeof(double) * 3 * E) != cudaSuccess ||
+        ws.groups.reserve(sizeof(SampleGroup) * G) != cudaSuccess)
+        return fail(HR_ERR_OOM, "workspace");
+    std::vector<float> t32(2 * n);
+    for (int i = 0; i < n; ++i) {
+        t32[i] = (float)(h_theta[i] + eps * h_v[i]);
+        t32[n + i] = (float)(h_theta[i] - eps * h_v[i]);
+    }
+    s->host_groups.resize(G);
+    for (int g = 0; g < G; ++g) {
+        SampleGroup& gr = s->host_groups[g];
+        gr.m0 = (int32_t)(g * M);
+        gr.P = P;
+        gr.lobe = 0;
+        gr.quantity = HR_GRAD;
+        gr.sub = o->sub + (uint32_t)g;
+        gr.request = o->request_id;
+        gr.theta_row = 0;
+        gr.pad = 0;
+        gr.comp_i = o->strategy == HR_ELEMENTWISE ? g : (o->strategy == HR_PLAIN ? -3 : -1);
+        gr.comp_j = gr.comp_i;
+    }
+    cudaError_t e = cudaMemcpyAsync(ws.theta32.ptr, t32.data(), sizeof(float) * 2 * n, cudaMemcpyHostToDevice, stream);
+    if (e == cudaSuccess)
+        e = cudaMemcpyAsync(ws.groups.ptr, s->host_groups.data(), sizeof(SampleGroup) * G, cudaMemcpyHostToDevice,
+                            stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(stream);
+    if (e != cudaSuccess) return fail(HR_ERR_CUDA, "upload: %s", cudaGetErrorString(e));
+    SampleArgs sa{};
+    sa.groups = (const SampleGroup*)ws.groups.ptr;
+    sa.n = n;
+    sa.E = E;
+    sa.sigma = o->sigma;
+    sa.Zg = std::sqrt(2.0 / M_PI) / o->sigma;
+    sa.Zd = 4.0 * std::exp(-0.5) / (std::sqrt(2.0 * M_PI) * o->sigma * o->sigma);
+    sa.Zo = sa.Zg * sa.Zg;
+    sa.seed = o->seed;
+    sa.tau = (float*)ws.tau.ptr;
+    sa.w = (float*)ws.w.ptr;
+    sa.meta = (uint2*)ws.meta.ptr;
+    launch_sample(sa, G, P, stream);
+    RenderBatch rb{};
+    rb.M = (int32_t)(2 * Mt);
+    rb.n = n;
+    rb.per_row = 1;
+    rb.table_rows = 2;
+    for (int r = 0; r < 2; ++r) {
+        BatchRow& br = rb.rows[r];
+        br.theta32 = (const float*)ws.theta32.ptr + r * n;
+        br.tau = (const float*)ws.tau.ptr;
+        br.meta = (const uint2*)ws.meta.ptr;
+        br.loss = (float*)ws.loss.ptr + r * Mt;
+        br.seed = o->seed;
+        br.request = o->request_id;
+        br.m_begin = 0;
+        br.start = (int32_t)(r * Mt);
+        br.pad = 0;
+    }
+    launch_render_loss(sc, rb, stream);
+    double* flat = (double*)ws.flat.ptr;
+    for (int r = 0; r < 2; ++r) {
+        FinalizeArgs fa{};
+        fa.w = (const float*)ws.w.ptr;
+        fa.loss = (const float*)ws.loss.ptr + r * Mt;
+        fa.E = E;
+        fa.n = n;
+        fa.pairs2 = (int32_t)M;
+        fa.elementwise = o->strategy == HR_ELEMENTWISE;
+        fa.hessian = 0;
+        fa.inv2P = 1.0 / (double)M;
+        fa.out_flat = flat + r * E;
+        launch_finalize(fa, stream);
+    }
+    fd_combine_kernel<<<1, 64, 0, stream>>>(flat, flat + E, 0.5 / eps, n, flat + 2 * E);
+    if ((e = cudaGetLastError()) != cudaSuccess) return fail(HR_ERR_CUDA, "launch: %s", cudaGetErrorString(e));
+    if ((e = cudaMemcpyAsync(h_out, flat + 2 * E, sizeof(double) * n, cudaMemcpyDeviceToHost, stream)) != cudaSuccess ||
+        (e = cudaStreamSynchronize(stream)) != cudaSuccess)
+        return fail(HR_ERR_CUDA, "result: %s", cudaGetErrorString(e));
+    return HR_OK;
+}
+
 }  // namespace hr
 
 // ---------------------------------------------------------------------------
@@ -315,6 +423,11 @@ hr_status hr_create_scene(const hr_scene_desc* d, hr_scene* out) {
     switch (d->kind) {
         case HR_SCENE_DISC2D: expect_n = 2; C = 1;
             if (!(d->radius > 0.0f)) return fail(HR_ERR_INVALID_ARG, "disc radius must be > 0");
+            break;
+        case HR_SCENE_BOXES2D: C = 1;
+            if (!(d->radius > 0.0f)) return fail(HR_ERR_INVALID_ARG, "square half-size must be > 0");
+            if (d->n_params < 2 || (d->n_params & 1)) return fail(HR_ERR_INVALID_ARG, "n_params must be 2K");
+            expect_n = d->n_params;
             break;
         case HR_SCENE_REVOLVE3D: expect_n = 2;
             if (!d->vertices || !d->triangles || d->n_vertices < 3 || d->n_triangles < 1 ||
@@ -363,6 +476,7 @@ hr_status hr_create_scene(const hr_scene_desc* d, hr_scene* out) {
     if ((e = cudaMalloc(&sc.target, sizeof(float) * npx)) != cudaSuccess) return bail(e, "target");
     switch (d->kind) {
         case HR_SCENE_DISC2D: sc.radius = d->radius; break;
+        case HR_SCENE_BOXES2D: sc.radius = d->radius; break;
         case HR_SCENE_REVOLVE3D: {
             sc.nv = d->n_vertices; sc.nt = d->n_triangles;
             for (int c = 0; c < 3; ++c) { sc.albedo[c] = d->albedo[c]; sc.light[c] = d->light[c]; }
@@ -498,6 +612,17 @@ hr_status hr_profile_last(hr_scene s, float* ms3) {
         if (e != cudaSuccess) return fail(HR_ERR_CUDA, "event timing: %s", cudaGetErrorString(e));
     }
     return HR_OK;
+}
+
+hr_status hr_estimate_hvp_fd(hr_scene s, const double* h_theta, const double* h_v, double eps, const hr_opts* o,
+                             double* h_out) {
+    clear_error();
+    if (!s || !h_theta || !h_v || !h_out) return fail(HR_ERR_INVALID_ARG, "NULL argument");
+    if (!(eps > 0.0) || !std::isfinite(eps)) return fail(HR_ERR_INVALID_ARG, "eps must be > 0");
+    std::lock_guard<std::mutex> lk(s->mu);
+    hr_status st = validate_opts(s, HR_GRAD, o);
+    if (st != HR_OK) return st;
+    return run_hvp_fd(s, h_theta, h_v, eps, o, h_out);
 }
 
 hr_status hr_render(hr_scene s, const double* h_params, uint64_t seed, uint32_t request, uint32_t sub, uint32_t k,

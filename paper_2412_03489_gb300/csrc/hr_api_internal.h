@@ -52,6 +52,8 @@ int optstate_instances(hr_optstate st);
 hr_scene optstate_scene(hr_optstate st);
 void optstate_copy_info(hr_optstate st, hr_step_info* out);
 
+hr_status run_hvp_fd(hr_scene_s* s, const double* h_theta, const double* h_v, double eps, const hr_opts* o,
+                     double* h_out);
 hr_status run_estimate(hr_scene_s* s, int quantity, const double* h_theta, const double* d_theta, const double* h_v,
                        const double* d_v, const hr_opts* o, double* h_out, double* d_out);
 }

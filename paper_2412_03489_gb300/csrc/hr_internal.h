@@ -14,7 +14,8 @@ struct SampleGroup {
     int32_t lobe;        // 0 gradient lobes, 1 Hessian lobes
     int32_t comp_i;      // -1: aggregate
     int32_t comp_j;
-    int32_t quantity;    // 0 grad, 1 hessian, 2 hvp with v, 3 hvp deferred (store n^2/S only)
+    int32_t quantity;    // 0 grad, 1 hessian, 2 hvp with v, 3 hvp deferred (store n^2/S only),
+                         // 4 element-wise hvp of row comp_i (comp_j = -2: row-mixture component)
     uint32_t sub;        // Philox counter word 2 low 24 bits
     uint32_t request;    // Philox counter word 3
     int32_t theta_row;   // which parameter row the group perturbs (multi-instance)

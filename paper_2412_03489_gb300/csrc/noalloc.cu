@@ -52,7 +52,7 @@ size_t align256(size_t x) { return (x + 255) & ~size_t(255); }
 // The sample-group table, written on the device so that the call needs no
 // host staging: group g draws P pairs for element g (element-wise) or from
 // the mixture (aggregate).
-__global__ void fill_groups_kernel(SampleGroup* groups, int G, int n, int quantity, int elementwise, int M,
+__global__ void fill_groups_kernel(SampleGroup* groups, int G, int n, int quantity, int strategy, int M,
                                    uint32_t sub, uint32_t request) {
     const int g = blockIdx.x * blockDim.x + threadIdx.x;
     if (g >= G) return;
@@ -65,10 +65,14 @@ __global__ void fill_groups_kernel(SampleGroup* groups, int G, int n, int quanti
     gr.request = request;
     gr.theta_row = 0;
     gr.pad = 0;
-    if (!elementwise) {
+    if (strategy == HR_AGGREGATE) {
         gr.comp_i = -1; gr.comp_j = -1;
+    } else if (strategy == HR_PLAIN) {
+        gr.comp_i = -3; gr.comp_j = -3;
     } else if (quantity == HR_GRAD) {
         gr.comp_i = g; gr.comp_j = g;
+    } else if (quantity == HR_HVP) {
+        gr.comp_i = g; gr.comp_j = -2; gr.quantity = 4;
     } else {
         int r = 0, rem = g;
         while (rem >= n - r) { rem -= n - r; ++r; }
@@ -95,10 +99,8 @@ extern "C" hr_status hr_estimate_dev_noalloc(hr_scene s, int32_t quantity, const
     if (!d_theta || !d_out || (quantity == HR_HVP && !d_v)) return fail(HR_ERR_INVALID_ARG, "NULL device pointer");
     if (!(o->sigma > 0.0) || !std::isfinite(o->sigma)) return fail(HR_ERR_INVALID_ARG, "sigma must be > 0");
     if (o->n_perturb < 2 || (o->n_perturb & 1)) return fail(HR_ERR_INVALID_ARG, "n_perturb must be even and >= 2");
-    if (o->strategy != HR_ELEMENTWISE && o->strategy != HR_AGGREGATE)
+    if (o->strategy != HR_ELEMENTWISE && o->strategy != HR_AGGREGATE && o->strategy != HR_PLAIN)
         return fail(HR_ERR_INVALID_ARG, "unknown strategy %d", o->strategy);
-    if (quantity == HR_HVP && o->strategy != HR_AGGREGATE)
-        return fail(HR_ERR_UNSUPPORTED, "the HVP is estimated with the aggregate strategy only");
     const DevScene& sc = s->sc;
     const int n = sc.n;
     const int E = quantity == HR_HESSIAN ? n * (n + 1) / 2 : n;
@@ -131,8 +133,8 @@ extern "C" hr_status hr_estimate_dev_noalloc(hr_scene s, int32_t quantity, const
     float* theta32 = reinterpret_cast<float*>(base + off_theta);
     SampleGroup* groups = reinterpret_cast<SampleGroup*>(base + off_groups);
     theta_to_f32_kernel<<<(n + 127) / 128, 128, 0, stream>>>(d_theta, theta32, n);
-    fill_groups_kernel<<<(G + 127) / 128, 128, 0, stream>>>(groups, G, n, quantity, o->strategy == HR_ELEMENTWISE,
-                                                            (int)M, o->sub, o->request_id);
+    fill_groups_kernel<<<(G + 127) / 128, 128, 0, stream>>>(groups, G, n, quantity, o->strategy, (int)M, o->sub,
+                                                            o->request_id);
     SampleArgs sa{};
     sa.groups = groups;
     sa.n = n;

@@ -48,7 +48,57 @@ __global__ void disc_image_kernel(const float* params, int W, int H, float radiu
     img[i] = disc_value(x, y, 0.f, W, H, params[0], params[1], __fmul_rn(radius, radius));
 }
 
+// Squares (Box2 / Box10): K axis-aligned squares of half-size h; a pixel
+// centre is 1 when |px - cx| < h and |py - cy| < h for some square (FP32).
+__device__ __forceinline__ float boxes_value(int x, int y, int W, int H, const float* c, int K, float h) {
+    const float px = __fdiv_rn(__fadd_rn((float)x, 0.5f), (float)W);
+    const float py = __fdiv_rn(__fadd_rn((float)y, 0.5f), (float)H);
+    for (int k = 0; k < K; ++k)
+        if (fabsf(__fsub_rn(px, c[2 * k])) < h && fabsf(__fsub_rn(py, c[2 * k + 1])) < h) return 1.0f;
+    return 0.0f;
+}
+
+constexpr int kMaxBoxParams = 64;
+
+__global__ void __launch_bounds__(32 * kWarps) boxes_loss_kernel(RenderBatch b, int W, int H, float h,
+                                                                 const float* __restrict__ target) {
+    __shared__ float s_c[kWarps][kMaxBoxParams];
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int m = blockIdx.x * kWarps + warp;
+    if (m >= b.M) return;
+    const Pert pt = resolve(b, m);
+    for (int d = lane; d < b.n; d += 32) s_c[warp][d] = __fadd_rn(pt.theta[d], pt.tau[d]);
+    __syncwarp();
+    const int K = b.n / 2;
+    float acc = 0.0f;
+    const int npx = W * H;
+    for (int i = lane; i < npx; i += 32) {
+        const int y = i / W, x = i - y * W;
+        const float d = __fsub_rn(boxes_value(x, y, W, H, s_c[warp], K, h), target[i]);
+        acc = __fmaf_rn(d, d, acc);
+    }
+    acc = warp_sum(acc);
+    if (lane == 0) *pt.loss = __fdiv_rn(acc, (float)npx);
+}
+
+__global__ void boxes_image_kernel(const float* params, int K, int W, int H, float h, float* img) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= W * H) return;
+    const int y = i / W, x = i - y * W;
+    img[i] = boxes_value(x, y, W, H, params, K, h);
+}
+
 }  // namespace
+
+void launch_boxes_loss(const DevScene& sc, const RenderBatch& b, cudaStream_t s) {
+    const int blocks = (b.M + kWarps - 1) / kWarps;
+    boxes_loss_kernel<<<blocks, 32 * kWarps, 0, s>>>(b, sc.W, sc.H, sc.radius, sc.target);
+}
+
+void launch_boxes_image(const DevScene& sc, const float* params, float* img, cudaStream_t s) {
+    const int npx = sc.W * sc.H;
+    boxes_image_kernel<<<(npx + 255) / 256, 256, 0, s>>>(params, sc.n / 2, sc.W, sc.H, sc.radius, img);
+}
 
 void launch_disc_loss(const DevScene& sc, const RenderBatch& b, cudaStream_t s) {
     const int blocks = (b.M + kWarps - 1) / kWarps;

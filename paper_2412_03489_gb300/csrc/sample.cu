@@ -108,6 +108,38 @@ __device__ void write_weights(const SampleArgs& a, const SampleGroup& G, int m, 
     }
     float* wm = a.w + (size_t)m * a.E;
     for (int e = 0; e < a.E; ++e) wm[e] = 0.0f;
+    if (G.comp_i == -3) {
+        // plain Gaussian sampling: the weight is the kernel factor c(tau)
+        if (G.quantity == 0) {
+            for (int d = 0; d < n; ++d) wm[d] = (float)((double)t[d] / s2);
+        } else if (G.quantity == 1) {
+            int e = 0;
+            for (int i = 0; i < n; ++i) {
+                const double ti = (double)t[i];
+                for (int jj = i; jj < n; ++jj, ++e)
+                    wm[e] = (float)((i == jj) ? (ti * ti - s2) / s4 : ti * (double)t[jj] / s4);
+            }
+        } else {
+            double tv = 0.0;
+            for (int d = 0; d < n; ++d) tv += (double)t[d] * a.v[d];
+            for (int kk = 0; kk < n; ++kk) wm[kk] = (float)((double)t[kk] * tv / s4 - a.v[kk] / s2);
+        }
+        return;
+    }
+    if (G.quantity == 4) {
+        // element-wise HVP, row i: h_i^v / q_i of the row mixture
+        const int i = G.comp_i;
+        const double ti = (double)t[i];
+        double hv = 0.0, den = 0.0, tot = 0.0;
+        for (int b = 0; b < n; ++b) {
+            const double c = (b == i) ? (ti * ti - s2) / s4 : ti * (double)t[b] / s4;
+            hv += c * a.v[b];
+            den += fabs(a.v[b]) * fabs(c);
+            tot += fabs(a.v[b]) * (b == i ? a.Zd : a.Zo);
+        }
+        wm[i] = (float)(den > 0.0 ? hv * tot / den : 0.0);
+        return;
+    }
     if (G.comp_i >= 0) {
         if (G.quantity == 0) {
             wm[G.comp_i] = (float)(sign * a.Zg);
@@ -157,7 +189,27 @@ __global__ void __launch_bounds__(kSampleThreads) sample_kernel(SampleArgs a) {
     const uint32_t c2 = (TAG_SAMPLE << 24) | (sub & 0xFFFFFFu);
     const u32x4 w0 = philox_seed(a.seed, (uint32_t)k, 0u, c2, G.request);
     int i, j;
-    if (G.comp_i >= 0) {
+    if (G.comp_i == -3) {
+        i = -1; j = -1;            // no importance sampling: every dim Gaussian
+    } else if (G.comp_i >= 0 && G.comp_j == -2) {
+        // element-wise HVP: component j of row i with probability
+        // |v_j| Z_ij / sum_l |v_l| Z_il (cumulative sums in index order)
+        i = G.comp_i;
+        double tot = 0.0;
+        for (int l = 0; l < n; ++l) tot += fabs(a.v[l]) * (l == i ? a.Zd : a.Zo);
+        const double u = u01d(w0.x) * tot;
+        double acc = 0.0;
+        j = i;
+        int last = i;
+        bool found = false;
+        for (int l = 0; l < n; ++l) {
+            const double p = fabs(a.v[l]) * (l == i ? a.Zd : a.Zo);
+            if (p > 0.0) last = l;
+            acc += p;
+            if (!found && p > 0.0 && u < acc) { j = l; found = true; }
+        }
+        if (!found) j = last;
+    } else if (G.comp_i >= 0) {
         i = G.comp_i;
         j = G.lobe == 0 ? G.comp_i : G.comp_j;
     } else if (G.lobe == 0) {
@@ -187,8 +239,17 @@ __global__ void __launch_bounds__(kSampleThreads) sample_kernel(SampleArgs a) {
         }
     }
     const double ua = u01d(w0.y), ub = u01d(w0.z);
-    double pi_, pj, mi, mj;   // + / - leg values in dims i and j
-    if (G.lobe == 0) {
+    double pi_ = 0.0, pj = 0.0, mi = 0.0, mj = 0.0;   // + / - leg values in dims i and j
+    if (G.comp_i == -3) {
+        // legs +tau and -tau of tau ~ N(0, sigma^2 I)
+        const int mp = G.m0 + 2 * k, mm = mp + 1;
+        float* tp = a.tau + (size_t)mp * n;
+        float* tm = a.tau + (size_t)mm * n;
+        for (int d = 0; d < n; ++d) { tp[d] = (float)g[d]; tm[d] = (float)(-g[d]); }
+        if (a.meta) { a.meta[mp] = make_uint2(sub, (uint32_t)k); a.meta[mm] = make_uint2(sub, (uint32_t)k); }
+        if (a.w) { write_weights(a, G, mp, tp, 1.0); write_weights(a, G, mm, tm, -1.0); }
+        return;
+    } else if (G.lobe == 0) {
         const double r = sigma * sqrt(-2.0 * log(ua));
         pi_ = r; mi = -r; pj = pi_; mj = mi;
     } else if (i == j) {

@@ -222,7 +222,9 @@ void hr_server_s::setup(SrvReq* r) {
         gr.theta_row = 0;
         gr.pad = 0;
         if (o2.strategy == HR_AGGREGATE) { gr.comp_i = -1; gr.comp_j = -1; }
+        else if (o2.strategy == HR_PLAIN) { gr.comp_i = -3; gr.comp_j = -3; }
         else if (r->req.quantity == HR_GRAD) { gr.comp_i = g; gr.comp_j = g; }
+        else if (r->req.quantity == HR_HVP) { gr.comp_i = g; gr.comp_j = -2; gr.quantity = 4; }
         else {
             int row = 0, rem = g;
             while (rem >= n - row) { rem -= n - row; ++row; }
@@ -245,7 +247,7 @@ void hr_server_s::setup(SrvReq* r) {
     sa.Zd = 4.0 * std::exp(-0.5) / (std::sqrt(2.0 * M_PI) * s2);
     sa.Zo = sa.Zg * sa.Zg;
     sa.seed = o2.seed;
-    sa.v = r->req.quantity == HR_HVP ? r->vdev : nullptr;
+    sa.v = r->req.quantity == HR_HVP ? r->vdev : nullptr;   // also the row-mixture weights
     sa.tau = r->tau;
     sa.w = r->w;
     sa.invS = nullptr;
@@ -481,8 +483,8 @@ hr_status hr_server_submit(hr_server S, const hr_request* q, uint64_t* ticket) {
         if (q->quantity < HR_GRAD || q->quantity > HR_HVP) { delete r; return fail(HR_ERR_INVALID_ARG, "unknown quantity"); }
         if (!q->h_theta || (q->quantity == HR_HVP && !q->h_v)) { delete r; return fail(HR_ERR_INVALID_ARG, "theta/v missing"); }
         if (!(o->sigma > 0.0) || o->n_perturb < 2 || (o->n_perturb & 1) ||
-            (o->strategy != HR_ELEMENTWISE && o->strategy != HR_AGGREGATE) ||
-            (q->quantity == HR_HVP && o->strategy != HR_AGGREGATE) || o->n_perturb / 2 >= (1 << 24)) {
+            (o->strategy != HR_ELEMENTWISE && o->strategy != HR_AGGREGATE && o->strategy != HR_PLAIN) ||
+            o->n_perturb / 2 >= (1 << 24)) {
             delete r;
             return fail(HR_ERR_INVALID_ARG, "invalid estimate options");
         }

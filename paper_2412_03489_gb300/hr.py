@@ -19,7 +19,7 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(HERE, "_build", "libhr.so")
 
 HR_OK = 0
-HR_ELEMENTWISE, HR_AGGREGATE = 0, 1
+HR_ELEMENTWISE, HR_AGGREGATE, HR_PLAIN = 0, 1, 2
 HR_GRAD, HR_HESSIAN, HR_HVP = 0, 1, 2
 TAG_PATH, TAG_TARGET = 2, 3
 
@@ -99,6 +99,7 @@ def lib() -> ctypes.CDLL:
         L.hr_estimate_grad.argtypes = [vp, _f64p, ctypes.POINTER(hr_opts), _f64p]
         L.hr_estimate_hessian.argtypes = [vp, _f64p, ctypes.POINTER(hr_opts), _f64p]
         L.hr_estimate_hvp.argtypes = [vp, _f64p, _f64p, ctypes.POINTER(hr_opts), _f64p]
+        L.hr_estimate_hvp_fd.argtypes = [vp, _f64p, _f64p, ctypes.c_double, ctypes.POINTER(hr_opts), _f64p]
         L.hr_estimate_dev.argtypes = [vp, ctypes.c_int32, vp, vp, ctypes.POINTER(hr_opts), vp]
         L.hr_estimate_dev_noalloc.argtypes = [vp, ctypes.c_int32, vp, vp, ctypes.POINTER(hr_opts), vp]
         L.hr_render.argtypes = [vp, _f64p, ctypes.c_uint64, ctypes.c_uint32, ctypes.c_uint32, ctypes.c_uint32,
@@ -116,7 +117,8 @@ def lib() -> ctypes.CDLL:
         L.hr_last_error.argtypes = [ctypes.c_char_p, ctypes.c_size_t]
         L.hr_last_error.restype = ctypes.c_size_t
         for name in ("hr_create_scene", "hr_destroy_scene", "hr_estimate_grad", "hr_estimate_hessian",
-                     "hr_estimate_hvp", "hr_estimate_dev", "hr_estimate_dev_noalloc", "hr_render", "hr_optstate_create",
+                     "hr_estimate_hvp", "hr_estimate_hvp_fd", "hr_estimate_dev", "hr_estimate_dev_noalloc",
+                     "hr_render", "hr_optstate_create",
                      "hr_optstate_destroy", "hr_newton_cg_step", "hr_optstate_theta", "hr_profile_enable",
                      "hr_profile_last", "hr_server_create", "hr_server_destroy", "hr_server_submit",
                      "hr_server_wait"):
@@ -179,6 +181,11 @@ def hr_estimate_hessian(handle, theta, opts: hr_opts, out):
 def hr_estimate_hvp(handle, theta, v, opts: hr_opts, out):
     check(lib().hr_estimate_hvp(handle, _ptr(theta, _f64p), _ptr(v, _f64p), ctypes.byref(opts), _ptr(out, _f64p)),
           "hr_estimate_hvp")
+
+
+def hr_estimate_hvp_fd(handle, theta, v, eps, opts: hr_opts, out):
+    check(lib().hr_estimate_hvp_fd(handle, _ptr(theta, _f64p), _ptr(v, _f64p), float(eps), ctypes.byref(opts),
+                                   _ptr(out, _f64p)), "hr_estimate_hvp_fd")
 
 
 def hr_estimate_dev(handle, quantity: int, d_theta: int, d_v, opts: hr_opts, d_out: int):
@@ -245,6 +252,8 @@ class Scene:
         kind = int(sc["kind"])
         if kind == wl.SCENE_DISC2D:
             d.radius = float(sc["radius"])
+        elif kind == wl.SCENE_BOXES2D:
+            d.radius = float(sc["half_size"])
         elif kind == wl.SCENE_REVOLVE3D:
             keep["v"] = np.ascontiguousarray(sc["vertices"], np.float32)
             keep["t"] = np.ascontiguousarray(sc["triangles"], np.int32)

@@ -24,6 +24,7 @@ SCENE_DISC2D = 0
 SCENE_REVOLVE3D = 1
 SCENE_PTBOX = 2
 SCENE_TRIS2D = 3
+SCENE_BOXES2D = 4
 
 
 def _rng(seed: int) -> np.random.Generator:
@@ -42,6 +43,19 @@ def disc_scene(seed: int = 0xC0, width: int = 64, height: int = 64,
                 n_params=2, radius=np.float32(radius),
                 theta_target=target.astype(np.float64),
                 theta_query=query.astype(np.float64), sigma=0.05, seed=seed)
+
+
+# ---------------------------------------------------------------------------
+# Squares (Box2 / Box10 plateau tasks): K squares, 2K params (centres).
+# ---------------------------------------------------------------------------
+def boxes_scene(n_boxes: int = 1, seed: int = 0xB0, width: int = 64, height: int = 64,
+                half_size: float = 0.1, query_std: float = 0.15) -> dict:
+    g = _rng(seed + n_boxes)
+    target = g.uniform(0.2, 0.8, size=2 * n_boxes)
+    query = target + g.normal(0.0, query_std, size=2 * n_boxes)
+    return dict(kind=SCENE_BOXES2D, width=width, height=height, channels=1, n_params=2 * n_boxes,
+                half_size=np.float32(half_size), theta_target=target, theta_query=query,
+                sigma=0.05, seed=seed)
 
 
 # ---------------------------------------------------------------------------

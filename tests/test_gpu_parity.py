@@ -225,7 +225,65 @@ def test_invalid_arguments_are_rejected():
         with pytest.raises(hr.HRError):
             Sc.estimate(hr.HR_HESSIAN, theta, sigma, M, strat, 1, 1)
     with pytest.raises(hr.HRError):
-        Sc.estimate(hr.HR_HVP, theta, 0.05, 64, hr.HR_ELEMENTWISE, 1, 1, v=np.ones(2))
+        Sc.estimate(hr.HR_HVP, theta, 0.05, 64, 9, 1, 1, v=np.ones(2))
     # the scene still works afterwards
     Sc.estimate(hr.HR_HESSIAN, theta, 0.05, 64, hr.HR_AGGREGATE, 1, 1)
+    Sc.close()
+
+
+# ---------------------------------------------------------------------------
+# HVP forms: element-wise (row mixtures) and central difference of gradients
+# ---------------------------------------------------------------------------
+def test_elementwise_hvp_disc_and_tris():
+    sc = wl.disc_scene()
+    flat, dbg, ref = run_both(sc, O.DiscRenderer(sc), "hvp", 1024, "elementwise", v=np.array([0.7, -1.3]))
+    check_samples(dbg, ref)
+    assert np.array_equal(dbg["losses"].astype(np.float64), ref.losses)
+    assert_estimate_close(flat, ref, what="disc hvp elementwise")
+    st = wl.tris2d_scene(width=64, height=48, n_params=8)
+    v = st["v"].copy()
+    v[3] = 0.0
+    flat, dbg, ref = run_both(st, O.Tris2dRenderer(st), "hvp", 16, "elementwise", v=v)
+    check_samples(dbg, ref)
+    assert_estimate_close(flat, ref, what="tris hvp elementwise")
+
+
+@pytest.mark.parametrize("strategy", ["aggregate", "elementwise"])
+def test_fd_hvp_matches_oracle(strategy):
+    for sc, r, M in [(wl.disc_scene(), None, 1024), (wl.revolve_scene(width=64, height=48), None, 64)]:
+        r = O.renderer_for(sc)
+        theta = np.asarray(sc["theta_query"], np.float64)
+        v = np.array([0.6, -0.8])
+        eps = 0.2 * sc["sigma"]
+        S = hr.Scene(sc)
+        out = np.zeros(2)
+        hr.hr_estimate_hvp_fd(S.handle, theta, v, eps, hr.make_opts(sc["sigma"], M, S_[strategy], 21, 4), out)
+        S.close()
+        ref, gp, gm = O.estimate_hvp_fd(r, theta, v, eps, sc["sigma"], M, strategy, 21, 4)
+        scale = (gp.scale + gm.scale) / (2 * eps)
+        assert np.all(np.abs(out - ref) <= 1e-4 * np.maximum(np.abs(ref), scale)), (out, ref, scale)
+
+
+S_ = {"elementwise": hr.HR_ELEMENTWISE, "aggregate": hr.HR_AGGREGATE}
+
+
+# ---------------------------------------------------------------------------
+# squares (Box2 / Box10) and plain Gaussian sampling
+# ---------------------------------------------------------------------------
+@pytest.mark.parametrize("n_boxes", [1, 5])
+@pytest.mark.parametrize("strategy", ["elementwise", "aggregate", "plain"])
+def test_boxes_parity(n_boxes, strategy):
+    sc = wl.boxes_scene(n_boxes=n_boxes)
+    S_["plain"] = hr.HR_PLAIN
+    S["plain"] = hr.HR_PLAIN
+    r = O.BoxesRenderer(sc)
+    Sc = hr.Scene(sc)
+    assert np.array_equal(Sc.render(sc["theta_query"]), r.image(np.asarray(sc["theta_query"], np.float32)))
+    M = 256 if n_boxes == 5 and strategy == "elementwise" else 1024
+    for q in ("hessian", "grad", "hvp"):
+        v = np.linspace(-1, 1, sc["n_params"]) if q == "hvp" else None
+        flat, dbg, ref = run_both(sc, r, q, M, strategy, v=v, scene=Sc)
+        check_samples(dbg, ref)
+        assert np.array_equal(dbg["losses"].astype(np.float64), ref.losses)
+        assert_estimate_close(flat, ref, what=f"boxes{n_boxes} {q} {strategy}")
     Sc.close()

@@ -263,3 +263,100 @@ def test_negated_gaussian_error_report():
                 e.append(np.abs(est.value - neg_gauss_hessian(th, s1 * s1 + s2 * s2)).mean())
         errs[M] = float(np.mean(e))
     assert errs[6400] < errs[100] / 4
+
+
+# ---------------------------------------------------------------------------
+# HVP forms beyond the aggregate direct kernel
+# ---------------------------------------------------------------------------
+def test_elementwise_hvp_row_mixture_is_unbiased():
+    f, H = quad_task()
+    r = O.FunctionRenderer(f, 2)
+    theta = np.array([0.3, -0.4])
+    v = np.array([0.8, -0.6])
+    est = O.estimate(r, "hvp", theta, 0.5, 40000, "elementwise", seed=41, request=5, v=v)
+    assert len(est.losses) == 2 * 40000            # Tab. 1: n sample sets for the HVP
+    assert np.all(np.abs(est.flat - H @ v) < 4 * per_pair_stats(est) + 1e-12)
+    # 4D random quadratic, v with a zero entry (that component is never drawn)
+    g = np.random.default_rng(11)
+    B = g.normal(size=(4, 4))
+    A = B + B.T
+    f4 = lambda X: 0.5 * np.einsum("mi,ij,mj->m", X, A, X)
+    v4 = np.array([0.5, 0.0, -1.0, 2.0])
+    est = O.estimate(O.FunctionRenderer(f4, 4), "hvp", g.normal(size=4), 0.3, 40000, "elementwise", 42, 5, v=v4)
+    assert np.all(np.abs(est.flat - A @ v4) < 4 * per_pair_stats(est) + 1e-12)
+    assert np.all(est.tau[:, 1] != 0)
+
+
+def test_elementwise_hvp_on_disc_matches_exact():
+    sc = wl.disc_scene()
+    th = np.asarray(sc["theta_query"])
+    _, _, H = disc_closed_form(sc, th, sc["sigma"])
+    v = np.array([1.0, -2.0])
+    est = O.estimate(O.DiscRenderer(sc), "hvp", th, sc["sigma"], 1 << 14, "elementwise", 43, 0, v=v)
+    assert np.all(np.abs(est.flat - H @ v) < 4 * per_pair_stats(est))
+
+
+def test_finite_difference_hvp_of_gradients():
+    f, H = quad_task()
+    r = O.FunctionRenderer(f, 2)
+    theta = np.array([0.3, -0.4])
+    v = np.array([0.8, -0.6])
+    for strat in ("aggregate", "elementwise"):
+        hv, gp, gm = O.estimate_hvp_fd(r, theta, v, 1e-2, 0.5, 20000, strat, 44, 6)
+        assert np.array_equal(gp.tau, gm.tau)                # common random numbers
+        # per-pair differences: for a quadratic the difference has no eps bias
+        c = 0.5 * (gp.w[0::2] * (gp.losses[0::2] - gm.losses[0::2])[:, None]
+                   + gp.w[1::2] * (gp.losses[1::2] - gm.losses[1::2])[:, None]) / 2e-2
+        used = (np.abs(gp.w[0::2]) + np.abs(gp.w[1::2])) > 0
+        se = np.array([c[used[:, e], e].std(ddof=1) / math.sqrt(used[:, e].sum()) for e in range(2)])
+        assert np.all(np.abs(hv - H @ v) < 4 * se + 1e-9), (strat, hv, H @ v, se)
+    # disc: FD of the exact smoothed gradient equals H v up to O(eps^2)
+    sc = wl.disc_scene()
+    th = np.asarray(sc["theta_query"])
+    _, _, Hd = disc_closed_form(sc, th, sc["sigma"])
+    vd = np.array([0.6, 0.8])
+    hv, gp, gm = O.estimate_hvp_fd(O.DiscRenderer(sc), th, vd, 0.01, sc["sigma"], 1 << 14, "aggregate", 45, 0)
+    c = 0.5 * (gp.w[0::2] * (gp.losses[0::2] - gm.losses[0::2])[:, None]
+               + gp.w[1::2] * (gp.losses[1::2] - gm.losses[1::2])[:, None]) / 0.02
+    se = c.std(axis=0, ddof=1) / math.sqrt(c.shape[0])
+    assert np.all(np.abs(hv - Hd @ vd) < 4 * se + 0.02 * np.abs(Hd @ vd).max())
+
+
+# ---------------------------------------------------------------------------
+# plain (no importance sampling) estimator and the squares (Box2/Box10) scene
+# ---------------------------------------------------------------------------
+def test_plain_sampling_is_unbiased_on_quadratic():
+    f, H = quad_task()
+    r = O.FunctionRenderer(f, 2)
+    theta = np.array([0.3, -0.4])
+    est = O.estimate(r, "hessian", theta, 0.5, 40000, "plain", seed=51, request=1)
+    assert np.array_equal(est.tau[0::2], -est.tau[1::2])
+    assert np.all(np.abs(est.flat - upper(H)) < 4 * per_pair_stats(est) + 1e-12)
+    g = O.estimate(r, "grad", theta, 0.5, 40000, "plain", seed=52, request=1)
+    assert np.all(np.abs(g.flat - H @ theta) < 4 * per_pair_stats(g) + 1e-12)
+
+
+def test_boxes_renderer_matches_brute_force_and_box2_variance_ordering():
+    sc = wl.boxes_scene(n_boxes=5)
+    r = O.BoxesRenderer(sc)
+    p = np.asarray(sc["theta_query"], np.float32)
+    img = r.image(p).reshape(64, 64)
+    xs = (np.arange(64) + 0.5) / 64
+    X, Y = np.meshgrid(xs, xs)
+    ref = np.zeros((64, 64), bool)
+    for k in range(5):
+        ref |= (np.abs(X - p[2 * k]) < sc["half_size"]) & (np.abs(Y - p[2 * k + 1]) < sc["half_size"])
+    assert np.array_equal(img > 0, ref)
+    # Sec. "How much variance is reduced?": element-wise IS <= aggregate << plain,
+    # per render, on the Box2 task (diagonal entries)
+    b2 = wl.boxes_scene(n_boxes=1)
+    rb = O.BoxesRenderer(b2)
+    th = np.asarray(b2["theta_target"]) + 0.05
+    var = {}
+    for strat, M in (("elementwise", 4096), ("aggregate", 3 * 4096), ("plain", 3 * 4096)):
+        est = O.estimate(rb, "hessian", th, b2["sigma"], M, strat, 61, 1)
+        se = per_pair_stats(est)
+        renders = len(est.losses)
+        var[strat] = (se ** 2 * renders)[[0, 2]]      # variance per render, diagonal entries
+    assert np.all(var["elementwise"] < var["aggregate"])
+    assert np.all(var["aggregate"] < var["plain"])

@@ -190,6 +190,19 @@ hr_status hr_estimate_hvp(hr_scene scene, const double* h_theta, const double* h
 hr_status hr_estimate_hvp_fd(hr_scene scene, const double* h_theta, const double* h_v, double eps,
                              const hr_opts* opts, double* h_out_Hv);
 
+/* Grey-box composition (Suppl. "Grey-box differentials"): the loss is
+ * f(g(x)) with a white-box inner map g, whose Jacobian J = dg/dx at x the
+ * caller supplies (h_J [n][n_x] row-major, n = the scene's parameter count),
+ * and the black-box renderer loss f, estimated at y = g(x) (h_y [n]).
+ *   HR_GRAD:    h_out [n_x]       = J^T grad_y fbar(y)
+ *   HR_HESSIAN: h_out [n_x][n_x]  = J^T H_y J  (n_x <= 4096; drops the curvature
+ *                                   of g, exact when g is affine)
+ *   HR_HVP:     h_out [n_x]       = J^T H_y (J h_vx), h_vx [n_x]
+ * The products with J run on the device in FP64; opts as for the estimates
+ * (inspection outputs ignored).  1 <= n_x <= 2^24. */
+hr_status hr_estimate_greybox(hr_scene scene, int32_t quantity, const double* h_y, const double* h_J, int32_t n_x,
+                              const double* h_vx, const hr_opts* opts, double* h_out);
+
 /* Device-pointer form of the three estimates, asynchronous on opts->stream:
  * d_theta [n], d_v [n] (HVP only, else NULL), d_out [n], [n][n] or [n]
  * FP64 device memory.  Debug outputs in opts are ignored. */

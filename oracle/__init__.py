@@ -372,6 +372,20 @@ def estimate_hvp_fd(r: Renderer, theta, v, eps: float, sigma: float, M: int, str
     return (gp.flat - gm.flat) / (2.0 * eps), gp, gm
 
 
+def estimate_greybox(r: Renderer, quantity: str, y, J, sigma, M, strategy, seed, request, sub=0, vx=None):
+    """Grey-box derivatives of f(g(x)) (Suppl. "Grey-box differentials"):
+    the black-box estimate at y = g(x) composed with the inner Jacobian J:
+    J^T g, J^T H J, or J^T H (J v_x)."""
+    J = np.asarray(J, np.float64)
+    if quantity == "hvp":
+        est = estimate(r, "hvp", y, sigma, M, strategy, seed, request, sub, v=J @ np.asarray(vx, np.float64))
+        return J.T @ est.value, est
+    est = estimate(r, quantity, y, sigma, M, strategy, seed, request, sub)
+    if quantity == "grad":
+        return J.T @ est.value, est
+    return J.T @ est.value @ J, est
+
+
 def elements(quantity: str, n: int):
     """Unique elements estimated by element-wise importance sampling: the n
     gradient entries, or the upper triangle of the Hessian (symmetry, Sec. 3.3)."""

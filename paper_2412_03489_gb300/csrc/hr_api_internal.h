@@ -25,9 +25,10 @@ struct DevBuf {
 
 struct Workspace {
     DevBuf theta32, v, tau, w, meta, loss, flat, scale, full, groups, render_img, render_params;
+    DevBuf gb_J, gb_vx, gb_y, gb_vy, gb_out, gb_tmp, gb_hj;
     void release_all() {
         for (DevBuf* b : {&theta32, &v, &tau, &w, &meta, &loss, &flat, &scale, &full, &groups, &render_img,
-                          &render_params})
+                          &render_params, &gb_J, &gb_vx, &gb_y, &gb_vy, &gb_out, &gb_tmp, &gb_hj})
             b->release();
     }
 };

@@ -100,6 +100,8 @@ def lib() -> ctypes.CDLL:
         L.hr_estimate_hessian.argtypes = [vp, _f64p, ctypes.POINTER(hr_opts), _f64p]
         L.hr_estimate_hvp.argtypes = [vp, _f64p, _f64p, ctypes.POINTER(hr_opts), _f64p]
         L.hr_estimate_hvp_fd.argtypes = [vp, _f64p, _f64p, ctypes.c_double, ctypes.POINTER(hr_opts), _f64p]
+        L.hr_estimate_greybox.argtypes = [vp, ctypes.c_int32, _f64p, _f64p, ctypes.c_int32, _f64p,
+                                          ctypes.POINTER(hr_opts), _f64p]
         L.hr_estimate_dev.argtypes = [vp, ctypes.c_int32, vp, vp, ctypes.POINTER(hr_opts), vp]
         L.hr_estimate_dev_noalloc.argtypes = [vp, ctypes.c_int32, vp, vp, ctypes.POINTER(hr_opts), vp]
         L.hr_render.argtypes = [vp, _f64p, ctypes.c_uint64, ctypes.c_uint32, ctypes.c_uint32, ctypes.c_uint32,
@@ -117,7 +119,8 @@ def lib() -> ctypes.CDLL:
         L.hr_last_error.argtypes = [ctypes.c_char_p, ctypes.c_size_t]
         L.hr_last_error.restype = ctypes.c_size_t
         for name in ("hr_create_scene", "hr_destroy_scene", "hr_estimate_grad", "hr_estimate_hessian",
-                     "hr_estimate_hvp", "hr_estimate_hvp_fd", "hr_estimate_dev", "hr_estimate_dev_noalloc",
+                     "hr_estimate_hvp", "hr_estimate_hvp_fd", "hr_estimate_greybox", "hr_estimate_dev",
+                     "hr_estimate_dev_noalloc",
                      "hr_render", "hr_optstate_create",
                      "hr_optstate_destroy", "hr_newton_cg_step", "hr_optstate_theta", "hr_profile_enable",
                      "hr_profile_last", "hr_server_create", "hr_server_destroy", "hr_server_submit",
@@ -186,6 +189,14 @@ def hr_estimate_hvp(handle, theta, v, opts: hr_opts, out):
 def hr_estimate_hvp_fd(handle, theta, v, eps, opts: hr_opts, out):
     check(lib().hr_estimate_hvp_fd(handle, _ptr(theta, _f64p), _ptr(v, _f64p), float(eps), ctypes.byref(opts),
                                    _ptr(out, _f64p)), "hr_estimate_hvp_fd")
+
+
+def hr_estimate_greybox(handle, quantity, y, J, vx, opts: hr_opts, out):
+    J = np.ascontiguousarray(J, np.float64)
+    check(lib().hr_estimate_greybox(handle, int(quantity), _ptr(np.ascontiguousarray(y, np.float64), _f64p),
+                                    _ptr(J, _f64p), int(J.shape[1]),
+                                    None if vx is None else _ptr(np.ascontiguousarray(vx, np.float64), _f64p),
+                                    ctypes.byref(opts), _ptr(out, _f64p)), "hr_estimate_greybox")
 
 
 def hr_estimate_dev(handle, quantity: int, d_theta: int, d_v, opts: hr_opts, d_out: int):

@@ -287,3 +287,31 @@ def test_boxes_parity(n_boxes, strategy):
         assert np.array_equal(dbg["losses"].astype(np.float64), ref.losses)
         assert_estimate_close(flat, ref, what=f"boxes{n_boxes} {q} {strategy}")
     Sc.close()
+
+
+# ---------------------------------------------------------------------------
+# grey-box composition
+# ---------------------------------------------------------------------------
+@pytest.mark.parametrize("quantity", ["grad", "hessian", "hvp"])
+def test_greybox_matches_oracle(quantity):
+    sc = wl.disc_scene()
+    g = np.random.default_rng(5)
+    J = g.normal(size=(2, 7))
+    y = np.asarray(sc["theta_query"], np.float64)
+    vx = g.normal(size=7) if quantity == "hvp" else None
+    S = hr.Scene(sc)
+    out = np.zeros((7, 7) if quantity == "hessian" else 7)
+    hr.hr_estimate_greybox(S.handle, Q[quantity], y, J, vx, hr.make_opts(sc["sigma"], 1024, hr.HR_AGGREGATE, 9, 2), out)
+    S.close()
+    ref, est = O.estimate_greybox(O.DiscRenderer(sc), quantity, y, J, sc["sigma"], 1024, "aggregate", 9, 2, vx=vx)
+    aJ = np.abs(J)
+    if quantity == "hessian":
+        Sc = np.zeros((2, 2))
+        Sc[np.triu_indices(2)] = est.scale
+        Sc = Sc + np.triu(Sc, 1).T
+        scale = aJ.T @ Sc @ aJ
+    elif quantity == "hvp":
+        scale = aJ.T @ (est.scale)
+    else:
+        scale = aJ.T @ est.scale
+    assert np.all(np.abs(out - ref) <= 1e-4 * np.maximum(np.abs(ref), scale)), (out, ref)

@@ -10,10 +10,13 @@
 //      pixel bounding box, flat Lambert shade; surviving triangles are
 //      compacted into shared memory;
 //   4. binning into 8x8 pixel tiles (count, scan, fill; all in shared memory);
-//   5. warp-per-tile raster: each lane owns two pixels; nearest 1/Z wins,
-//      ties to the lower triangle index; (colour - target)^2 accumulated in
-//      registers; tiles with an empty bin add the precomputed sum of target^2;
-//   6. warp shuffle + block reduction to one FP32 loss per perturbation.
+//   5. warp-per-tile raster, tiles fetched dynamically: the two half-warps
+//      take alternate bin entries, each lane testing 4 pixels; nearest 1/Z
+//      wins, ties to the lower triangle index (half-warp winners merged by a
+//      shuffle); (colour - target)^2 per tile; tiles with an empty bin take
+//      the precomputed sum of target^2;
+//   6. per-tile losses summed in tile order, warp shuffle + block reduction to
+//      one FP32 loss per perturbation.
 // The FP32 sequences of steps 2-5 define the renderer (coverage and depth
 // decisions), so they use explicitly rounded intrinsics.
 #include <climits>
@@ -236,14 +239,20 @@ revolve_kernel(RvArgs P, RenderBatch b, const float* __restrict__ img_params, fl
         // again) and the slots are summed in tile order below, so the loss does
         // not depend on which warp took which tile
         float* tile_loss = reinterpret_cast<float*>(tcnt);
-        const int lx = lane & 7, ly = lane >> 3;
+        // Half-warp pairing: lanes 0-15 and 16-31 walk alternate entries of the
+        // bin, each lane covering 4 pixels (rows ly, ly+2, ly+4, ly+6), so the
+        // per-entry work (record loads, unpacking, thresholds) is paid once per
+        // pair of entries; the halves' per-pixel winners merge with a shuffle
+        // (largest 1/Z, lower index on ties: order-independent).
+        const int half = lane >> 4, hl = lane & 15;
+        const int lx = hl & 7, ly = hl >> 3;
         for (;;) {
             int t = 0;
             if (lane == 0) t = atomicAdd(&s_tile, 1);
             t = __shfl_sync(0xffffffffu, t, 0);
             if (t >= P.T) break;
             const int ty = t / P.TX, tx = t - ty * P.TX;
-            const int x = tx * kTile + lx, y0 = ty * kTile + ly, y1 = y0 + 4;
+            const int x = tx * kTile + lx, ybase = ty * kTile + ly;
             int beg, end;
             if (overflow) { beg = 0; end = count; }
             else { beg = toff[t]; end = (t + 1 < P.T) ? toff[t + 1] : total; }
@@ -251,69 +260,81 @@ revolve_kernel(RvArgs P, RenderBatch b, const float* __restrict__ img_params, fl
                 if (lane == 0) tile_loss[t] = P.tile_t2[t];
                 continue;
             }
-            const bool v0 = x < P.W && y0 < P.H, v1 = x < P.W && y1 < P.H;
-            float tg0[3] = {0.f, 0.f, 0.f}, tg1[3] = {0.f, 0.f, 0.f};
+            // loss pixels of this lane after the merge: rows 2*half and 2*half+1 of its four
+            const int ya = ybase + 4 * half, yb = ya + 2;
+            const bool va = x < P.W && ya < P.H, vb = x < P.W && yb < P.H;
+            float tga[3] = {0.f, 0.f, 0.f}, tgb[3] = {0.f, 0.f, 0.f};
             if (!kImage) {
-                if (v0) for (int c = 0; c < 3; ++c) tg0[c] = P.target[3 * ((size_t)y0 * P.W + x) + c];
-                if (v1) for (int c = 0; c < 3; ++c) tg1[c] = P.target[3 * ((size_t)y1 * P.W + x) + c];
+                if (va) for (int c = 0; c < 3; ++c) tga[c] = P.target[3 * ((size_t)ya * P.W + x) + c];
+                if (vb) for (int c = 0; c < 3; ++c) tgb[c] = P.target[3 * ((size_t)yb * P.W + x) + c];
             }
             const float fx = __fadd_rn((float)x, 0.5f);
-            const float fy0 = __fadd_rn((float)y0, 0.5f), fy1 = __fadd_rn((float)y1, 0.5f);
-            float bw0 = -INFINITY, bw1 = -INFINITY;
-            int bi0 = INT_MAX, bi1 = INT_MAX;
-            for (int j = beg; j < end; ++j) {
-                const int s = overflow ? j : (int)ent[j];
-                const float4* rp = reinterpret_cast<const float4*>(&rec[s]);
-                const float4 q0 = rp[0], q1 = rp[1], q2 = rp[2], q3 = rp[3];
-                const uint32_t key = __float_as_uint(q3.y);
-                const uint32_t xr = __float_as_uint(q3.z), yr = __float_as_uint(q3.w);
-                const int ti = (int)(key & 0x1FFFFFFFu);
-                const float th0 = tl_threshold(key, 0), th1 = tl_threshold(key, 1), th2 = tl_threshold(key, 2);
-                const int xlo = (int)(xr & 0xffffu), ylo = (int)(yr & 0xffffu);
-                const bool inx = (unsigned)(x - xlo) <= (xr >> 16) - (unsigned)xlo;
-                const unsigned yspan = (yr >> 16) - (unsigned)ylo;
-                {
-                    const float E0 = edge_eval(q0.x, q0.y, q0.z, fx, fy0);
-                    const float E1 = edge_eval(q0.w, q1.x, q1.y, fx, fy0);
-                    const float E2 = edge_eval(q1.z, q1.w, q2.x, fx, fy0);
-                    const float wz = edge_eval(q2.y, q2.z, q2.w, fx, fy0);
-                    const bool in = inx && ((unsigned)(y0 - ylo) <= yspan) && (E0 > th0) && (E1 > th1) && (E2 > th2);
-                    const bool better = in && (wz > bw0 || (wz == bw0 && ti < bi0));
-                    bw0 = better ? wz : bw0;
-                    bi0 = better ? ti : bi0;
-                }
-                {
-                    const float E0 = edge_eval(q0.x, q0.y, q0.z, fx, fy1);
-                    const float E1 = edge_eval(q0.w, q1.x, q1.y, fx, fy1);
-                    const float E2 = edge_eval(q1.z, q1.w, q2.x, fx, fy1);
-                    const float wz = edge_eval(q2.y, q2.z, q2.w, fx, fy1);
-                    const bool in = inx && ((unsigned)(y1 - ylo) <= yspan) && (E0 > th0) && (E1 > th1) && (E2 > th2);
-                    const bool better = in && (wz > bw1 || (wz == bw1 && ti < bi1));
-                    bw1 = better ? wz : bw1;
-                    bi1 = better ? ti : bi1;
+            float fy[4], bw[4];
+            int bi[4];
+#pragma unroll
+            for (int r = 0; r < 4; ++r) {
+                fy[r] = __fadd_rn((float)(ybase + 2 * r), 0.5f);
+                bw[r] = -INFINITY;
+                bi[r] = INT_MAX;
+            }
+            for (int jj = beg; jj < end; jj += 2) {
+                const int j = jj + half;
+                if (j < end) {
+                    const int s = overflow ? j : (int)ent[j];
+                    const float4* rp = reinterpret_cast<const float4*>(&rec[s]);
+                    const float4 q0 = rp[0], q1 = rp[1], q2 = rp[2], q3 = rp[3];
+                    const uint32_t key = __float_as_uint(q3.y);
+                    const uint32_t xr = __float_as_uint(q3.z), yr = __float_as_uint(q3.w);
+                    const int ti = (int)(key & 0x1FFFFFFFu);
+                    const float th0 = tl_threshold(key, 0), th1 = tl_threshold(key, 1), th2 = tl_threshold(key, 2);
+                    const int xlo = (int)(xr & 0xffffu), ylo = (int)(yr & 0xffffu);
+                    const bool inx = (unsigned)(x - xlo) <= (xr >> 16) - (unsigned)xlo;
+                    const unsigned yspan = (yr >> 16) - (unsigned)ylo;
+#pragma unroll
+                    for (int r = 0; r < 4; ++r) {
+                        const float E0 = edge_eval(q0.x, q0.y, q0.z, fx, fy[r]);
+                        const float E1 = edge_eval(q0.w, q1.x, q1.y, fx, fy[r]);
+                        const float E2 = edge_eval(q1.z, q1.w, q2.x, fx, fy[r]);
+                        const float wz = edge_eval(q2.y, q2.z, q2.w, fx, fy[r]);
+                        const bool in = inx && ((unsigned)(ybase + 2 * r - ylo) <= yspan) && (E0 > th0) &&
+                                        (E1 > th1) && (E2 > th2);
+                        const bool better = in && (wz > bw[r] || (wz == bw[r] && ti < bi[r]));
+                        bw[r] = better ? wz : bw[r];
+                        bi[r] = better ? ti : bi[r];
+                    }
                 }
             }
-            const float sh0 = bi0 != INT_MAX ? tshade[bi0] : 0.0f;
-            const float sh1 = bi1 != INT_MAX ? tshade[bi1] : 0.0f;
-            const float c00 = sh0 * P.alb0, c01 = sh0 * P.alb1, c02 = sh0 * P.alb2;
-            const float c10 = sh1 * P.alb0, c11 = sh1 * P.alb1, c12 = sh1 * P.alb2;
+#pragma unroll
+            for (int r = 0; r < 4; ++r) {
+                const float ow = __shfl_xor_sync(0xffffffffu, bw[r], 16);
+                const int oi = __shfl_xor_sync(0xffffffffu, bi[r], 16);
+                const bool take = ow > bw[r] || (ow == bw[r] && oi < bi[r]);
+                bw[r] = take ? ow : bw[r];
+                bi[r] = take ? oi : bi[r];
+            }
+            // this lane's two pixels: rows 2*half and 2*half+1 of its four
+            const int ia = half ? bi[2] : bi[0], ib = half ? bi[3] : bi[1];
+            const float sha = ia != INT_MAX ? tshade[ia] : 0.0f;
+            const float shb = ib != INT_MAX ? tshade[ib] : 0.0f;
+            const float ca0 = sha * P.alb0, ca1 = sha * P.alb1, ca2 = sha * P.alb2;
+            const float cb0 = shb * P.alb0, cb1 = shb * P.alb1, cb2 = shb * P.alb2;
             if (kImage) {
-                if (v0) {
-                    const size_t p = 3 * ((size_t)y0 * P.W + x);
-                    img[p] = c00; img[p + 1] = c01; img[p + 2] = c02;
+                if (va) {
+                    const size_t p = 3 * ((size_t)ya * P.W + x);
+                    img[p] = ca0; img[p + 1] = ca1; img[p + 2] = ca2;
                 }
-                if (v1) {
-                    const size_t p = 3 * ((size_t)y1 * P.W + x);
-                    img[p] = c10; img[p + 1] = c11; img[p + 2] = c12;
+                if (vb) {
+                    const size_t p = 3 * ((size_t)yb * P.W + x);
+                    img[p] = cb0; img[p + 1] = cb1; img[p + 2] = cb2;
                 }
             } else {
                 float acc = 0.0f;
-                if (v0) {
-                    const float d0 = c00 - tg0[0], d1 = c01 - tg0[1], d2 = c02 - tg0[2];
+                if (va) {
+                    const float d0 = ca0 - tga[0], d1 = ca1 - tga[1], d2 = ca2 - tga[2];
                     acc += d0 * d0 + d1 * d1 + d2 * d2;
                 }
-                if (v1) {
-                    const float d0 = c10 - tg1[0], d1 = c11 - tg1[1], d2 = c12 - tg1[2];
+                if (vb) {
+                    const float d0 = cb0 - tgb[0], d1 = cb1 - tgb[1], d2 = cb2 - tgb[2];
                     acc += d0 * d0 + d1 * d1 + d2 * d2;
                 }
                 acc = warp_sum(acc);

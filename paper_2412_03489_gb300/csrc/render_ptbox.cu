@@ -28,11 +28,18 @@ constexpr int kThreads = 256;
 constexpr int kLight = 12;
 constexpr float kInvPi = 0.318309886183790671538f;
 
+// quad q: {plane, lo_u, lo_v, hi_u} and {hi_v, axis, u, v} as two 16-byte
+// loads; sphere i: {centre xyz, r^2}
+struct __align__(16) QuadS {
+    float plane, lo_u, lo_v, hi_u;
+    float hi_v;
+    int axis, u, v;
+};
 struct PtShared {
-    int axis[13];
-    float plane[13], lo_u[13], lo_v[13], hi_u[13], hi_v[13];
+    QuadS q[13];
+    float4 sph[3];
     float alb[16][3];
-    float sc[3][3], sr[3], sr2[3], isr[3];
+    float sr[3], isr[3];
     float em[3];
 };
 
@@ -48,21 +55,27 @@ __device__ int intersect(const PtShared& S, const float o[3], const float d[3], 
     const float inv[3] = {__frcp_rn(d[0]), __frcp_rn(d[1]), __frcp_rn(d[2])};
 #pragma unroll 1
     for (int q = 0; q <= kLight; ++q) {
-        const int a = S.axis[q];
-        const int u = a == 0 ? 1 : 0, v = a == 2 ? 1 : 2;
-        if (d[a] == 0.0f) continue;
-        const float t = __fmul_rn(__fsub_rn(S.plane[q], o[a]), inv[a]);
+        const QuadS Q = S.q[q];
+        const int a = Q.axis;
+        const float da = a == 0 ? d[0] : (a == 1 ? d[1] : d[2]);
+        if (da == 0.0f) continue;
+        const float oa = a == 0 ? o[0] : (a == 1 ? o[1] : o[2]);
+        const float ia = a == 0 ? inv[0] : (a == 1 ? inv[1] : inv[2]);
+        const float t = __fmul_rn(__fsub_rn(Q.plane, oa), ia);
         if (!(t > 0.0f)) continue;
-        const float hu = __fmaf_rn(t, d[u], o[u]);
-        const float hv = __fmaf_rn(t, d[v], o[v]);
-        if (hu < S.lo_u[q] || hu > S.hi_u[q] || hv < S.lo_v[q] || hv > S.hi_v[q]) continue;
+        const float du = Q.u == 0 ? d[0] : d[1], ou = Q.u == 0 ? o[0] : o[1];
+        const float dv = Q.v == 1 ? d[1] : d[2], ov = Q.v == 1 ? o[1] : o[2];
+        const float hu = __fmaf_rn(t, du, ou);
+        const float hv = __fmaf_rn(t, dv, ov);
+        if (hu < Q.lo_u || hu > Q.hi_u || hv < Q.lo_v || hv > Q.hi_v) continue;
         if (t < best) { best = t; prim = q; }
     }
 #pragma unroll
     for (int i = 0; i < 3; ++i) {
-        const float oc[3] = {__fsub_rn(o[0], S.sc[i][0]), __fsub_rn(o[1], S.sc[i][1]), __fsub_rn(o[2], S.sc[i][2])};
+        const float4 sp = S.sph[i];
+        const float oc[3] = {__fsub_rn(o[0], sp.x), __fsub_rn(o[1], sp.y), __fsub_rn(o[2], sp.z)};
         const float b = dot3(oc, d);
-        const float cc = __fsub_rn(dot3(oc, oc), S.sr2[i]);
+        const float cc = __fsub_rn(dot3(oc, oc), sp.w);
         const float disc = __fmaf_rn(b, b, -cc);
         if (disc < 0.0f) continue;
         const float sq = __fsqrt_rn(disc);
@@ -87,20 +100,23 @@ __device__ void radiance(const PtShared& S, int depth, uint64_t seed, uint32_t r
         if (d[1] > 0.0f) { L[0] += S.em[0]; L[1] += S.em[1]; L[2] += S.em[2]; }
         return;
     }
-    const float area = __fmul_rn(__fsub_rn(S.hi_u[kLight], S.lo_u[kLight]), __fsub_rn(S.hi_v[kLight], S.lo_v[kLight]));
+    const QuadS& LQ = S.q[kLight];
+    const float area = __fmul_rn(__fsub_rn(LQ.hi_u, LQ.lo_u), __fsub_rn(LQ.hi_v, LQ.lo_v));
     for (int v = 1; v <= depth; ++v) {
         if (prim == kLight) return;
         float x[3], n[3], o2[3];
 #pragma unroll
         for (int c = 0; c < 3; ++c) x[c] = __fmaf_rn(t, d[c], o[c]);
         if (prim <= kLight) {
-            const int a = S.axis[prim];
+            const int a = S.q[prim].axis;
             n[0] = n[1] = n[2] = 0.0f;
             n[a] = d[a] > 0.0f ? -1.0f : 1.0f;
         } else {
             const int i = prim - 13;
-#pragma unroll
-            for (int c = 0; c < 3; ++c) n[c] = __fmul_rn(__fsub_rn(x[c], S.sc[i][c]), S.isr[i]);
+            const float4 sp = S.sph[i];
+            n[0] = __fmul_rn(__fsub_rn(x[0], sp.x), S.isr[i]);
+            n[1] = __fmul_rn(__fsub_rn(x[1], sp.y), S.isr[i]);
+            n[2] = __fmul_rn(__fsub_rn(x[2], sp.z), S.isr[i]);
             if (dot3(n, d) > 0.0f) { n[0] = -n[0]; n[1] = -n[1]; n[2] = -n[2]; }
         }
 #pragma unroll
@@ -110,9 +126,8 @@ __device__ void radiance(const PtShared& S, int depth, uint64_t seed, uint32_t r
         const u32x4 w0 = philox_seed(seed, idx, cbase, c2, request);
         // next-event estimation
         {
-            const float ly[3] = {__fmaf_rn(u24f(w0.x), __fsub_rn(S.hi_u[kLight], S.lo_u[kLight]), S.lo_u[kLight]),
-                                 S.plane[kLight],
-                                 __fmaf_rn(u24f(w0.y), __fsub_rn(S.hi_v[kLight], S.lo_v[kLight]), S.lo_v[kLight])};
+            const float ly[3] = {__fmaf_rn(u24f(w0.x), __fsub_rn(LQ.hi_u, LQ.lo_u), LQ.lo_u), LQ.plane,
+                                 __fmaf_rn(u24f(w0.y), __fsub_rn(LQ.hi_v, LQ.lo_v), LQ.lo_v)};
             const float wv[3] = {__fsub_rn(ly[0], o2[0]), __fsub_rn(ly[1], o2[1]), __fsub_rn(ly[2], o2[2])};
             const float dist2 = dot3(wv, wv);
             const float idist = __frcp_rn(__fsqrt_rn(dist2));
@@ -180,32 +195,37 @@ struct PtArgs {
 
 __device__ void load_scene(const PtArgs& A, const float* p, PtShared& S) {
     const int t = threadIdx.x;
-    if (t < 13) {
-        S.axis[t] = A.qaxis[t];
-        S.plane[t] = A.qgeom[t][0];
-        S.lo_u[t] = A.qgeom[t][1]; S.lo_v[t] = A.qgeom[t][2];
-        S.hi_u[t] = A.qgeom[t][3]; S.hi_v[t] = A.qgeom[t][4];
-        if (t < 12) { S.alb[t][0] = A.qalb[t][0]; S.alb[t][1] = A.qalb[t][1]; S.alb[t][2] = A.qalb[t][2]; }
-        else { S.alb[t][0] = S.alb[t][1] = S.alb[t][2] = 0.0f; }
-    } else if (t < 16) {
+    if (t < 12) {
+        QuadS& Q = S.q[t];
+        Q.axis = A.qaxis[t];
+        Q.u = Q.axis == 0 ? 1 : 0;
+        Q.v = Q.axis == 2 ? 1 : 2;
+        Q.plane = A.qgeom[t][0];
+        Q.lo_u = A.qgeom[t][1]; Q.lo_v = A.qgeom[t][2];
+        Q.hi_u = A.qgeom[t][3]; Q.hi_v = A.qgeom[t][4];
+        S.alb[t][0] = A.qalb[t][0]; S.alb[t][1] = A.qalb[t][1]; S.alb[t][2] = A.qalb[t][2];
+    } else if (t >= 13 && t < 16) {
         const int i = t - 13;
-        for (int c = 0; c < 3; ++c) { S.sc[i][c] = (i == 0) ? p[3 + c] : A.sc[i][c]; S.alb[t][c] = A.salb[i][c]; }
+        S.sph[i] = make_float4(i == 0 ? p[3] : A.sc[i][0], i == 0 ? p[4] : A.sc[i][1], i == 0 ? p[5] : A.sc[i][2],
+                               __fmul_rn(A.sr[i], A.sr[i]));
+        for (int c = 0; c < 3; ++c) S.alb[t][c] = A.salb[i][c];
         S.sr[i] = A.sr[i];
-        S.sr2[i] = __fmul_rn(A.sr[i], A.sr[i]);
         S.isr[i] = __frcp_rn(A.sr[i]);
     } else if (t == 16) {
-        S.axis[kLight] = 1;
-        S.plane[kLight] = p[1];
-        S.lo_u[kLight] = __fsub_rn(p[0], A.light_half);
-        S.hi_u[kLight] = __fadd_rn(p[0], A.light_half);
-        S.lo_v[kLight] = __fsub_rn(p[2], A.light_half);
-        S.hi_v[kLight] = __fadd_rn(p[2], A.light_half);
+        QuadS& Q = S.q[kLight];
+        Q.axis = 1; Q.u = 0; Q.v = 2;
+        Q.plane = p[1];
+        Q.lo_u = __fsub_rn(p[0], A.light_half);
+        Q.hi_u = __fadd_rn(p[0], A.light_half);
+        Q.lo_v = __fsub_rn(p[2], A.light_half);
+        Q.hi_v = __fadd_rn(p[2], A.light_half);
+        S.alb[kLight][0] = S.alb[kLight][1] = S.alb[kLight][2] = 0.0f;
         S.em[0] = A.em[0]; S.em[1] = A.em[1]; S.em[2] = A.em[2];
     }
 }
 
 template <bool kImage>
-__global__ void __launch_bounds__(kThreads)
+__global__ void __launch_bounds__(kThreads, 3)
 ptbox_kernel(PtArgs A, RenderBatch b, const float* __restrict__ img_params, uint64_t seed_img, uint32_t req_img,
              uint32_t sub_img, uint32_t k_img, uint32_t tag_img, int spp_img, float* __restrict__ img) {
     __shared__ PtShared S;

@@ -3,9 +3,9 @@
 // coordinates (x W, y H); both windings are drawn (edge coefficients negated
 // when the signed area is negative, skipped when it is zero); painter's
 // order: the highest covering triangle index wins.  One CTA renders one
-// perturbation: a warp sets up the triangles in shared memory, then every
-// thread walks its pixels and tests only the triangles whose bounding box
-// covers the pixel's 8-pixel row segment.
+// perturbation: the triangles are set up in shared memory, then each warp
+// walks 8x4-pixel tiles with one pixel per lane, testing (warp-uniformly, from
+// the highest index down) the triangles whose pixel box meets the tile.
 #include "hr_device.cuh"
 #include "hr_internal.h"
 
@@ -76,36 +76,41 @@ tris2d_kernel(RenderBatch b, const float* __restrict__ raw, const int32_t* __res
     __syncthreads();
     if (tid < n_tris) s_valid[tid] = setup_tri(&s_raw[9 * tid], W, H, s_rec[tid]) ? 1 : 0;
     __syncthreads();
+    // warp-uniform raster: each warp walks 8x4 tiles (one pixel per lane); a
+    // ballot gives the triangles whose pixel box meets the tile, tested from the
+    // highest index down (painter's order) until every lane is covered
     float acc = 0.0f;
     const int npx = W * H;
-    // each thread: 8 consecutive pixels of one row per step
-    const int segs_per_row = (W + 7) / 8;
-    const int nseg = segs_per_row * H;
-    for (int sidx = tid; sidx < nseg; sidx += kThreads) {
-        const int y = sidx / segs_per_row;
-        const int x0 = (sidx - y * segs_per_row) * 8;
-        const int x1 = min(x0 + 7, W - 1);
-        uint32_t mask = 0;
-        for (int t = 0; t < n_tris; ++t) {
-            if (!s_valid[t]) continue;
-            const T2Rec& r = s_rec[t];
-            if (y >= r.ylo && y <= r.yhi && x1 >= r.xlo && x0 <= r.xhi) mask |= 1u << t;
+    const int lane = tid & 31, warp = tid >> 5;
+    const int TXn = (W + 7) / 8, TYn = (H + 3) / 4;
+    for (int t = warp; t < TXn * TYn; t += kThreads / 32) {
+        const int ty = t / TXn, tx = t - ty * TXn;
+        const int x0 = tx * 8, y0 = ty * 4;
+        const int x = x0 + (lane & 7), y = y0 + (lane >> 3);
+        bool over = false;
+        if (lane < n_tris && s_valid[lane]) {
+            const T2Rec& r = s_rec[lane];
+            over = r.xlo <= x0 + 7 && r.xhi >= x0 && r.ylo <= y0 + 3 && r.yhi >= y0;
         }
-        const float fy = __fadd_rn((float)y, 0.5f);
-        for (int x = x0; x <= x1; ++x) {
-            const float fx = __fadd_rn((float)x, 0.5f);
-            int win = -1;
-            uint32_t mm = mask;
-            while (mm) {
-                const int t = 31 - __clz(mm);   // highest index first: first hit wins
-                mm &= ~(1u << t);
-                const T2Rec& r = s_rec[t];
-                if (x < r.xlo || x > r.xhi) continue;
-                const float E0 = edge_eval(r.A0, r.B0, r.C0, fx, fy);
-                const float E1 = edge_eval(r.A1, r.B1, r.C1, fx, fy);
-                const float E2 = edge_eval(r.A2, r.B2, r.C2, fx, fy);
-                if (edge_in(r.A0, r.B0, E0) && edge_in(r.A1, r.B1, E1) && edge_in(r.A2, r.B2, E2)) { win = t; break; }
+        uint32_t mm = __ballot_sync(0xffffffffu, over);
+        const bool inside_img = x < W && y < H;
+        const float fx = __fadd_rn((float)x, 0.5f), fy = __fadd_rn((float)y, 0.5f);
+        int win = -1;
+        while (mm) {
+            const int k = 31 - __clz(mm);
+            mm &= ~(1u << k);
+            if (win < 0 && inside_img) {
+                const T2Rec& r = s_rec[k];
+                if (x >= r.xlo && x <= r.xhi && y >= r.ylo && y <= r.yhi) {
+                    const float E0 = edge_eval(r.A0, r.B0, r.C0, fx, fy);
+                    const float E1 = edge_eval(r.A1, r.B1, r.C1, fx, fy);
+                    const float E2 = edge_eval(r.A2, r.B2, r.C2, fx, fy);
+                    if (edge_in(r.A0, r.B0, E0) && edge_in(r.A1, r.B1, E1) && edge_in(r.A2, r.B2, E2)) win = k;
+                }
             }
+            if (__all_sync(0xffffffffu, win >= 0 || !inside_img)) break;
+        }
+        if (inside_img) {
             const size_t p = (size_t)y * W + x;
             const float c0 = win >= 0 ? s_rec[win].r : 0.0f;
             const float c1 = win >= 0 ? s_rec[win].g : 0.0f;

@@ -36,6 +36,10 @@ ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
 METRIC = "Hessian/HVP estimates/s at oracle-matched error; perturbed renders/s; p50/p99 latency"
+# DRAM bytes (read + write) of one render+loss launch from the ncu capture of
+# the current mesh kernel (profiles/revolve_kernel_M4096.md); set to None when
+# the kernel changes until it is captured again.
+TRAFFIC_BYTES = 523008
 M_PERTURB = 4096
 SEED = 2024
 
@@ -504,7 +508,7 @@ def main():
                 "latency_ms": {"p50": float(np.percentile(times, 50)), "p99": float(np.percentile(times, 99))},
                 "roofline": {"bound": "alu", "kernel": "revolve_kernel (render + loss)",
                              "achieved": achieved / 1e12, "peak": peak_ops / 1e12, "unit": "TFLOP/s",
-                             "frac": achieved / peak_ops, "traffic": None,
+                             "frac": achieved / peak_ops, "traffic": TRAFFIC_BYTES,
                              "peak_source": f"{n_sm} SMs x 128 FP32 lanes x {peaks.get('sm_max_mhz', 2070.0)} MHz "
                                             f"({src} max SM clock); one FMA = one operation",
                              "ops_per_render": ops, "pixel_triangle_candidates_per_render": cand,

@@ -518,3 +518,133 @@ def newton_cg_step(r: Renderer, theta, sigma, M_grad, M_hvp, K, lam_rel, delta, 
         p = res + (rr_new / rr) * p
         rr = rr_new
     return theta + d, StepInfo(float(np.linalg.norm(g)), lam, it, exit_reason, float(np.linalg.norm(d)))
+
+
+# --------------------------------------------------------------------------
+# The published optimiser (Sec. 2 "Newton Conjugate Gradient" with the
+# point moved every iteration; Suppl. "Hyperparameters": linear sigma
+# annealing, line-search iterations and tolerance, "recompute" period,
+# trust region).  Readings:
+#  * line search = Newton-Raphson steps along the current direction d, each
+#    alpha = -g(x).d / d.H(x)d (Eq. pertubation) at the current point, at most
+#    ls_iters steps, ending early once |alpha| |d| <= ls_tol;
+#  * |alpha| <= Delta / |d| (trust-region truncation, Sec. 2); where
+#    d.H d <= 0 the step goes to that bound in the descent direction;
+#  * residual (residual_mode 0) follows the printed recurrence
+#    r <- r - alpha (H + lambda I) d at every step; every `recompute` outer
+#    iterations it is recomputed from a fresh gradient estimate and the
+#    direction restarts, r = d = -g; residual_mode 1 takes r = -g at every
+#    outer iteration (nonlinear CG);
+#  * Fletcher-Reeves beta = r'.r' / r.r; a direction with r.d <= 0 restarts;
+#  * sigma_i = start + (end - start) min(i, T-1) / (T-1) for outer iteration i.
+# One evaluation = one line-search step = one gradient estimate (sub 64 e)
+# and one aggregate Hessian-vector product (sub 64 e + 1) at the same point.
+# --------------------------------------------------------------------------
+@dataclass
+class NcgOpts:
+    sigma_start: float
+    sigma_end: float
+    anneal_iters: int
+    n_grad: int
+    n_hvp: int
+    ls_iters: int
+    ls_tol: float
+    recompute: int
+    trust_radius: float
+    residual_mode: int = 0
+    lambda_rel: float = 0.0
+
+
+def anneal_sigma(start: float, end: float, T: int, i: int) -> float:
+    """Linear bandwidth schedule over outer iterations (Suppl. Hyperparameters)."""
+    if T <= 1:
+        return float(start)
+    if i >= T - 1:
+        return float(end)
+    return float(start) + (float(end) - float(start)) * float(i) / float(T - 1)
+
+
+@dataclass
+class NcgState:
+    x: np.ndarray
+    d: np.ndarray
+    r: np.ndarray
+    rr: float = 0.0
+    it: int = 0          # outer iteration
+    j: int = 0           # line-search step within it
+    evals: int = 0
+    sigma: float = 0.0
+
+
+@dataclass
+class NcgInfo:
+    it: int
+    ls_step: int
+    restarted: bool
+    sigma: float
+    grad_norm: float
+    gd: float
+    dHd: float
+    alpha: float
+    step_norm: float
+
+
+def ncg_init(theta0, o: NcgOpts) -> NcgState:
+    x = np.asarray(theta0, np.float64).copy()
+    z = np.zeros_like(x)
+    return NcgState(x=x, d=z.copy(), r=z.copy(), sigma=anneal_sigma(o.sigma_start, o.sigma_end, o.anneal_iters, 0))
+
+
+def ncg_evaluate(r: Renderer, st: NcgState, o: NcgOpts, seed: int, request: int,
+                 grad_fn=None, hvp_fn=None) -> NcgInfo:
+    """One evaluation (one line-search step) of the optimiser; updates st."""
+    e, sigma = st.evals, st.sigma
+    if grad_fn is None:
+        def grad_fn(x, s, ev):
+            return estimate(r, "grad", x, s, o.n_grad, "aggregate", seed, request, sub=64 * ev).value
+    if hvp_fn is None:
+        def hvp_fn(x, s, ev, vec):
+            return estimate(r, "hvp", x, s, o.n_hvp, "aggregate", seed, request, sub=64 * ev + 1, v=vec).value
+    g = np.asarray(grad_fn(st.x, sigma, e), np.float64)
+    restarted = False
+    if st.j == 0:
+        if st.it % o.recompute == 0:
+            st.r = -g
+            st.d = st.r.copy()
+            st.rr = float(st.r @ st.r)
+            restarted = True
+        else:
+            r_new = -g if o.residual_mode == 1 else st.r
+            rr_new = float(r_new @ r_new)
+            beta = rr_new / st.rr if st.rr > 0.0 else 0.0
+            d = r_new + beta * st.d
+            if float(r_new @ d) <= 0.0:
+                d = r_new.copy()
+                restarted = True
+            st.r, st.d, st.rr = r_new.copy(), d, rr_new
+    lam = o.lambda_rel * float(np.linalg.norm(g))
+    q = np.asarray(hvp_fn(st.x, sigma, e, st.d), np.float64) + lam * st.d
+    gd = float(g @ st.d)
+    dHd = float(st.d @ q)
+    dn = float(np.linalg.norm(st.d))
+    alpha = 0.0
+    if dn > 0.0:
+        cap = o.trust_radius / dn
+        if dHd > 0.0:
+            alpha = -gd / dHd
+        elif gd < 0.0:
+            alpha = cap
+        elif gd > 0.0:
+            alpha = -cap
+        alpha = min(max(alpha, -cap), cap)
+    st.x = st.x + alpha * st.d
+    if o.residual_mode == 0:
+        st.r = st.r - alpha * q
+    info = NcgInfo(st.it, st.j, restarted, sigma, float(np.linalg.norm(g)), gd, dHd, alpha, abs(alpha) * dn)
+    st.j += 1
+    if st.j >= o.ls_iters or abs(alpha) * dn <= o.ls_tol:
+        st.j = 0
+        st.it += 1
+        st.sigma = anneal_sigma(o.sigma_start, o.sigma_end, o.anneal_iters, st.it)
+    st.evals += 1
+    return info

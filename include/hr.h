@@ -276,6 +276,77 @@ hr_status hr_newton_cg_step(hr_scene scene, hr_optstate st, hr_step_info* h_info
 /* Current parameters, h_theta [n_instances][n]. */
 hr_status hr_optstate_theta(hr_optstate st, double* h_theta);
 
+/* ---------------------------------------------------------------------------
+ * The optimiser as the paper runs it (Sec. 2 "Newton Conjugate Gradient" with
+ * the point moved at every iteration; Suppl. "Hyperparameters": linear sigma
+ * annealing, line-search iterations and tolerance, recompute period, trust
+ * region).  Per instance it keeps x, a direction d, a residual r and an outer
+ * iteration counter i.  One evaluation is one line-search step at the
+ * current x:
+ *   g = aggregate gradient estimate at x (n_grad perturbations, sub 64 e),
+ *   Hd = aggregate Hessian-vector product at x (n_hvp perturbations, sub
+ *        64 e + 1; the perturbations do not depend on d) plus lambda d,
+ *        lambda = lambda_rel |g|;
+ *   at the first step of outer iteration i the direction is updated:
+ *     i % recompute == 0: r = d = -g (recompute / restart),
+ *     else r' = r (residual_mode 0, the printed recurrence) or -g (mode 1),
+ *          d = r' + (r'.r' / r.r) d (Fletcher-Reeves), d = r' if r'.d <= 0;
+ *   alpha = -g.d / d.Hd (Eq. pertubation), or +-Delta/|d| downhill when
+ *   d.Hd <= 0; |alpha| <= Delta/|d| (trust region); x += alpha d; mode 0
+ *   also r -= alpha Hd;
+ *   the line search ends after ls_iters steps or once |alpha| |d| <= ls_tol;
+ *   then i += 1 and sigma_i = sigma_start + (sigma_end - sigma_start) i/(T-1)
+ *   (sigma_end from i >= T-1; T = anneal_iters, T = 1: sigma_start always).
+ * Each instance follows its own line search, so instances in one launch can
+ * be at different outer iterations and bandwidths.  Request id of instance b
+ * = request_base + b; evaluation e counts from 0 per state (at most 262,144).
+ * Limits: n <= 64, n_hvp <= 512, 1 <= n_instances <= 4096.
+ * ------------------------------------------------------------------------- */
+typedef struct hr_ncg_s* hr_ncg;
+
+typedef struct {
+    double sigma_start;
+    double sigma_end;
+    int32_t anneal_iters;  /* T >= 1 */
+    int32_t n_grad;        /* perturbations per gradient estimate (even, >= 2) */
+    int32_t n_hvp;         /* perturbations per Hessian product (even, 2..512) */
+    int32_t ls_iters;      /* J >= 1 */
+    double ls_tol;         /* line search ends once |alpha| |d| <= ls_tol */
+    int32_t recompute;     /* R >= 1 */
+    int32_t residual_mode; /* 0 recurrence r -= alpha Hd, 1 r = -g each outer iteration */
+    double trust_radius;   /* Delta > 0 */
+    double lambda_rel;     /* >= 0 */
+    uint64_t seed;
+    uint32_t request_base;
+    int32_t use_graph;     /* 1: capture one evaluation into a CUDA graph, replay it */
+    void* stream;          /* cudaStream_t or NULL (own stream) */
+} hr_ncg_opts;
+
+typedef struct {
+    int32_t iter;          /* outer iteration i of this evaluation */
+    int32_t ls_step;       /* line-search step within it (0: direction updated here) */
+    int32_t restarted;     /* 1: r and d were reset to -g here */
+    int32_t pad;
+    double sigma;          /* bandwidth the estimates used */
+    double grad_norm;      /* |g| */
+    double gd;             /* g.d */
+    double dHd;            /* d.(H + lambda I) d */
+    double alpha;          /* step along d after truncation */
+    double step_norm;      /* |alpha| |d| */
+} hr_ncg_info;
+
+/* Allocates the state (device memory for B instances) and copies h_theta0
+ * [n_instances][n]; returns HR_ERR_INVALID_ARG on bad options, HR_ERR_OOM if
+ * device memory runs out.  The state belongs to `scene`. */
+hr_status hr_ncg_create(hr_scene scene, int32_t n_instances, const double* h_theta0, const hr_ncg_opts* opts,
+                        hr_ncg* out);
+hr_status hr_ncg_destroy(hr_ncg st);
+/* Runs n_evals evaluations for all instances and waits for them.  h_info, if
+ * not NULL, receives [n_evals][n_instances] records. */
+hr_status hr_ncg_run(hr_scene scene, hr_ncg st, int32_t n_evals, hr_ncg_info* h_info);
+/* Current parameters, h_theta [n_instances][n] (waits for the state's stream). */
+hr_status hr_ncg_theta(hr_ncg st, double* h_theta);
+
 /* Render one image at h_params [n] (rounded to FP32) into h_img [H][W][C]
  * (host).  For PTBOX the path random numbers are those of (seed, request,
  * sub, pair k, tag) with spp samples per pixel (tag 2: perturbation renders,

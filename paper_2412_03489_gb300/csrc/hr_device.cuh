@@ -85,6 +85,20 @@ __device__ __forceinline__ int warp_sum_i(int v) {
     return v;
 }
 
+// FP64 dot product of two shared/global n-vectors over the whole block;
+// red holds one double per warp.  Every thread returns the same value.
+__device__ __forceinline__ double block_dot(const double* a, const double* b, int n, double* red) {
+    double v = 0.0;
+    for (int i = threadIdx.x; i < n; i += blockDim.x) v += a[i] * b[i];
+    v = warp_sum_d(v);
+    if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = v;
+    __syncthreads();
+    double s = 0.0;
+    for (int w = 0; w < (int)(blockDim.x >> 5); ++w) s += red[w];
+    __syncthreads();
+    return s;
+}
+
 // Kahan-compensated FP32 accumulator
 struct Kahan {
     float s = 0.0f, c = 0.0f;

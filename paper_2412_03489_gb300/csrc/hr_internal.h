@@ -35,9 +35,15 @@ struct SampleArgs {
     float* invS;          // [M] n^2 / S (Hessian mixture) or null
     uint2* meta;          // [M] (sub, pair k) or null
     const int32_t* step;  // optional device step index s: every group's sub += 64 s
+    const double* sigma_row;  // optional [rows]: group sigma = sigma_row[theta_row] (Z's derived in-kernel)
 };
 
 void launch_sample(const SampleArgs& a, int n_groups, int max_P, cudaStream_t s);
+
+// g[b][e] = 1/Mg sum of w[m][e] loss[m] over rows [b per_inst, b per_inst + Mg)
+// (Kahan FP32 chunks, FP64 tree); grid (n, B)
+void launch_grad_reduce(const float* w, const float* loss, int n, int per_inst, int Mg, int B, double* g,
+                        cudaStream_t s);
 
 struct FinalizeArgs {
     const float* w;       // [M][E]

@@ -52,18 +52,6 @@ __global__ void __launch_bounds__(256) grad_reduce_kernel(const float* w, const 
     if (threadIdx.x == 0) g[b * n + e] = sh[0] / (double)Mg;
 }
 
-__device__ double block_dot(const double* a, const double* b, int n, double* red) {
-    double v = 0.0;
-    for (int i = threadIdx.x; i < n; i += blockDim.x) v += a[i] * b[i];
-    v = warp_sum_d(v);
-    if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = v;
-    __syncthreads();
-    double s = 0.0;
-    for (int w = 0; w < (int)(blockDim.x >> 5); ++w) s += red[w];
-    __syncthreads();
-    return s;
-}
-
 struct CgArgs {
     int n, per_inst, Mg, Mh, K;
     double sigma, lambda_rel, delta;
@@ -146,6 +134,12 @@ __global__ void __launch_bounds__(kCgThreads) cg_kernel(CgArgs a) {
 __global__ void advance_step_kernel(int32_t* step) { *step += 1; }
 
 }  // namespace
+
+void launch_grad_reduce(const float* w, const float* loss, int n, int per_inst, int Mg, int B, double* g,
+                        cudaStream_t s) {
+    grad_reduce_kernel<<<dim3(n, B), 256, 0, s>>>(w, loss, n, per_inst, Mg, g);
+}
+
 }  // namespace hr
 
 using namespace hr;
@@ -197,8 +191,8 @@ hr_status enqueue_step(hr_optstate_s* st) {
     rb.request0 = st->opts.request_base;
     rb.seed = st->opts.seed;
     launch_render_loss(sc, rb, st->stream);
-    grad_reduce_kernel<<<dim3(n, B), 256, 0, st->stream>>>((const float*)st->w.ptr, (const float*)st->loss.ptr, n,
-                                                           st->per_inst, st->Mg, (double*)st->g.ptr);
+    launch_grad_reduce((const float*)st->w.ptr, (const float*)st->loss.ptr, n, st->per_inst, st->Mg, B,
+                       (double*)st->g.ptr, st->stream);
     CgArgs ca{};
     ca.n = n; ca.per_inst = st->per_inst; ca.Mg = st->Mg; ca.Mh = st->Mh; ca.K = st->K;
     ca.sigma = st->opts.sigma; ca.lambda_rel = st->opts.lambda_rel; ca.delta = st->opts.trust_radius;

@@ -98,11 +98,26 @@ __device__ double hess_mixture(const float* t, int n, double s2, double Zd, doub
     return (sd / s4 / Zd + (off > 0.0 ? off : 0.0) / s4 / Zo) / ((double)n * (double)n);
 }
 
-__device__ void write_weights(const SampleArgs& a, const SampleGroup& G, int m, const float* t, double sign) {
+// e^{-1/2}, rounded to double
+constexpr double kExpMinusHalf = 0.60653065971263342360;
+
+// bandwidth of a group and the masses of its lobes (Sec. 3.2-3.3):
+// Zg = sqrt(2/pi)/sigma, Zd = 4 e^{-1/2} / (sqrt(2 pi) sigma^2), Zo = Zg^2
+struct Lobes { double sigma, Zg, Zd, Zo; };
+
+__device__ __forceinline__ Lobes lobes_for(const SampleArgs& a, const SampleGroup& G) {
+    if (!a.sigma_row) return {a.sigma, a.Zg, a.Zd, a.Zo};
+    const double s = a.sigma_row[G.theta_row];
+    const double zg = sqrt(2.0 / kPi) / s;
+    return {s, zg, 4.0 * kExpMinusHalf / (sqrt(2.0 * kPi) * (s * s)), zg * zg};
+}
+
+__device__ void write_weights(const SampleArgs& a, const Lobes& L, const SampleGroup& G, int m, const float* t,
+                              double sign) {
     const int n = a.n;
-    const double s2 = a.sigma * a.sigma, s4 = s2 * s2;
+    const double s2 = L.sigma * L.sigma, s4 = s2 * s2;
     if (G.quantity == 3) {
-        const double S = hess_mixture(t, n, s2, a.Zd, a.Zo);
+        const double S = hess_mixture(t, n, s2, L.Zd, L.Zo);
         a.invS[m] = (float)(S > 0.0 ? 1.0 / S : 0.0);
         return;
     }
@@ -135,28 +150,28 @@ __device__ void write_weights(const SampleArgs& a, const SampleGroup& G, int m, 
             const double c = (b == i) ? (ti * ti - s2) / s4 : ti * (double)t[b] / s4;
             hv += c * a.v[b];
             den += fabs(a.v[b]) * fabs(c);
-            tot += fabs(a.v[b]) * (b == i ? a.Zd : a.Zo);
+            tot += fabs(a.v[b]) * (b == i ? L.Zd : L.Zo);
         }
         wm[i] = (float)(den > 0.0 ? hv * tot / den : 0.0);
         return;
     }
     if (G.comp_i >= 0) {
         if (G.quantity == 0) {
-            wm[G.comp_i] = (float)(sign * a.Zg);
+            wm[G.comp_i] = (float)(sign * L.Zg);
         } else {
             const int lo = min(G.comp_i, G.comp_j), hi = max(G.comp_i, G.comp_j);
-            wm[upper_index(lo, hi, n)] = (float)(sign * (lo == hi ? a.Zd : a.Zo));
+            wm[upper_index(lo, hi, n)] = (float)(sign * (lo == hi ? L.Zd : L.Zo));
         }
         return;
     }
     if (G.quantity == 0) {
         double S = 0.0;
         for (int d = 0; d < n; ++d) S += fabs((double)t[d] / s2);
-        S = S / a.Zg / (double)n;
+        S = S / L.Zg / (double)n;
         for (int d = 0; d < n; ++d) wm[d] = (float)(S > 0.0 ? ((double)t[d] / s2) / S : 0.0);
         return;
     }
-    const double S = hess_mixture(t, n, s2, a.Zd, a.Zo);
+    const double S = hess_mixture(t, n, s2, L.Zd, L.Zo);
     if (!(S > 0.0)) return;
     if (G.quantity == 1) {
         int e = 0;
@@ -184,7 +199,8 @@ __global__ void __launch_bounds__(kSampleThreads) sample_kernel(SampleArgs a) {
     const int k = blockIdx.x * blockDim.x + threadIdx.x;
     if (k >= G.P) return;
     const int n = a.n;
-    const double sigma = a.sigma;
+    const Lobes L = lobes_for(a, G);
+    const double sigma = L.sigma;
     const uint32_t sub = G.sub + (a.step ? 64u * (uint32_t)(*a.step) : 0u);
     const uint32_t c2 = (TAG_SAMPLE << 24) | (sub & 0xFFFFFFu);
     const u32x4 w0 = philox_seed(a.seed, (uint32_t)k, 0u, c2, G.request);
@@ -196,14 +212,14 @@ __global__ void __launch_bounds__(kSampleThreads) sample_kernel(SampleArgs a) {
         // |v_j| Z_ij / sum_l |v_l| Z_il (cumulative sums in index order)
         i = G.comp_i;
         double tot = 0.0;
-        for (int l = 0; l < n; ++l) tot += fabs(a.v[l]) * (l == i ? a.Zd : a.Zo);
+        for (int l = 0; l < n; ++l) tot += fabs(a.v[l]) * (l == i ? L.Zd : L.Zo);
         const double u = u01d(w0.x) * tot;
         double acc = 0.0;
         j = i;
         int last = i;
         bool found = false;
         for (int l = 0; l < n; ++l) {
-            const double p = fabs(a.v[l]) * (l == i ? a.Zd : a.Zo);
+            const double p = fabs(a.v[l]) * (l == i ? L.Zd : L.Zo);
             if (p > 0.0) last = l;
             acc += p;
             if (!found && p > 0.0 && u < acc) { j = l; found = true; }
@@ -247,7 +263,7 @@ __global__ void __launch_bounds__(kSampleThreads) sample_kernel(SampleArgs a) {
         float* tm = a.tau + (size_t)mm * n;
         for (int d = 0; d < n; ++d) { tp[d] = (float)g[d]; tm[d] = (float)(-g[d]); }
         if (a.meta) { a.meta[mp] = make_uint2(sub, (uint32_t)k); a.meta[mm] = make_uint2(sub, (uint32_t)k); }
-        if (a.w) { write_weights(a, G, mp, tp, 1.0); write_weights(a, G, mm, tm, -1.0); }
+        if (a.w) { write_weights(a, L, G, mp, tp, 1.0); write_weights(a, L, G, mm, tm, -1.0); }
         return;
     } else if (G.lobe == 0) {
         const double r = sigma * sqrt(-2.0 * log(ua));
@@ -281,8 +297,8 @@ __global__ void __launch_bounds__(kSampleThreads) sample_kernel(SampleArgs a) {
         a.meta[mm] = make_uint2(sub, (uint32_t)k);
     }
     if (a.w || a.invS) {
-        write_weights(a, G, mp, tp, 1.0);
-        write_weights(a, G, mm, tm, -1.0);
+        write_weights(a, L, G, mp, tp, 1.0);
+        write_weights(a, L, G, mm, tm, -1.0);
     }
 }
 

@@ -62,6 +62,21 @@ class hr_step_info(ctypes.Structure):
                 ("exit_reason", ctypes.c_int32), ("step_norm", ctypes.c_double)]
 
 
+class hr_ncg_opts(ctypes.Structure):
+    _fields_ = [("sigma_start", ctypes.c_double), ("sigma_end", ctypes.c_double), ("anneal_iters", ctypes.c_int32),
+                ("n_grad", ctypes.c_int32), ("n_hvp", ctypes.c_int32), ("ls_iters", ctypes.c_int32),
+                ("ls_tol", ctypes.c_double), ("recompute", ctypes.c_int32), ("residual_mode", ctypes.c_int32),
+                ("trust_radius", ctypes.c_double), ("lambda_rel", ctypes.c_double), ("seed", ctypes.c_uint64),
+                ("request_base", ctypes.c_uint32), ("use_graph", ctypes.c_int32), ("stream", ctypes.c_void_p)]
+
+
+class hr_ncg_info(ctypes.Structure):
+    _fields_ = [("iter", ctypes.c_int32), ("ls_step", ctypes.c_int32), ("restarted", ctypes.c_int32),
+                ("pad", ctypes.c_int32), ("sigma", ctypes.c_double), ("grad_norm", ctypes.c_double),
+                ("gd", ctypes.c_double), ("dHd", ctypes.c_double), ("alpha", ctypes.c_double),
+                ("step_norm", ctypes.c_double)]
+
+
 class hr_server_opts(ctypes.Structure):
     _fields_ = [("hbm_budget", ctypes.c_int64), ("max_active", ctypes.c_int32), ("chunk", ctypes.c_int32)]
 
@@ -110,6 +125,10 @@ def lib() -> ctypes.CDLL:
         L.hr_optstate_destroy.argtypes = [vp]
         L.hr_newton_cg_step.argtypes = [vp, vp, ctypes.POINTER(hr_step_info)]
         L.hr_optstate_theta.argtypes = [vp, _f64p]
+        L.hr_ncg_create.argtypes = [vp, ctypes.c_int32, _f64p, ctypes.POINTER(hr_ncg_opts), ctypes.POINTER(vp)]
+        L.hr_ncg_destroy.argtypes = [vp]
+        L.hr_ncg_run.argtypes = [vp, vp, ctypes.c_int32, ctypes.POINTER(hr_ncg_info)]
+        L.hr_ncg_theta.argtypes = [vp, _f64p]
         L.hr_profile_enable.argtypes = [vp, ctypes.c_int32]
         L.hr_profile_last.argtypes = [vp, _f32p]
         L.hr_server_create.argtypes = [ctypes.POINTER(hr_server_opts), ctypes.POINTER(vp)]
@@ -124,7 +143,7 @@ def lib() -> ctypes.CDLL:
                      "hr_render", "hr_optstate_create",
                      "hr_optstate_destroy", "hr_newton_cg_step", "hr_optstate_theta", "hr_profile_enable",
                      "hr_profile_last", "hr_server_create", "hr_server_destroy", "hr_server_submit",
-                     "hr_server_wait"):
+                     "hr_server_wait", "hr_ncg_create", "hr_ncg_destroy", "hr_ncg_run", "hr_ncg_theta"):
             getattr(L, name).restype = ctypes.c_int32
         L.hr_version.restype = ctypes.c_int32
         _lib = L
@@ -240,6 +259,26 @@ def hr_optstate_theta(st, out):
 
 def hr_optstate_destroy(st):
     check(lib().hr_optstate_destroy(st), "hr_optstate_destroy")
+
+
+def hr_ncg_create(handle, n_instances, theta0, opts: hr_ncg_opts) -> int:
+    h = ctypes.c_void_p()
+    check(lib().hr_ncg_create(handle, n_instances, _ptr(theta0, _f64p), ctypes.byref(opts), ctypes.byref(h)),
+          "hr_ncg_create")
+    return h.value
+
+
+def hr_ncg_run(handle, st, n_evals, info=None):
+    """n_evals evaluations; info: None or a (hr_ncg_info * (n_evals * n_instances)) array."""
+    check(lib().hr_ncg_run(handle, st, n_evals, info), "hr_ncg_run")
+
+
+def hr_ncg_theta(st, out):
+    check(lib().hr_ncg_theta(st, _ptr(out, _f64p)), "hr_ncg_theta")
+
+
+def hr_ncg_destroy(st):
+    check(lib().hr_ncg_destroy(st), "hr_ncg_destroy")
 
 
 # ---------------------------------------------------------------------------

@@ -1,0 +1,122 @@
+"""The published optimiser on the GPU (hr_ncg_*) against the oracle's
+ncg_evaluate: per evaluation the same outer iteration, line-search step,
+restart decision and bandwidth, the same gradient norm and step within the
+estimator tolerance, and the same iterates; option validation; and a run that
+approaches the target."""
+import numpy as np
+import pytest
+
+import oracle as O
+from paper_2412_03489_gb300 import build as hb
+from paper_2412_03489_gb300 import hr
+from paper_2412_03489_gb300 import workloads as wl
+
+pytestmark = pytest.mark.gpu
+
+hb.build()
+
+
+def _opts(**kw):
+    o = hr.hr_ncg_opts()
+    base = dict(sigma_start=0.02, sigma_end=0.01, anneal_iters=4, n_grad=16, n_hvp=8, ls_iters=2, ls_tol=1e-4,
+                recompute=3, residual_mode=0, trust_radius=0.05, lambda_rel=1e-3, seed=99, request_base=10,
+                use_graph=1)
+    base.update(kw)
+    for k, v in base.items():
+        setattr(o, k, v)
+    return o
+
+
+def _oracle_opts(o):
+    return O.NcgOpts(o.sigma_start, o.sigma_end, o.anneal_iters, o.n_grad, o.n_hvp, o.ls_iters, o.ls_tol,
+                     o.recompute, o.trust_radius, o.residual_mode, o.lambda_rel)
+
+
+def _compare(sc, r, B, o, n_evals, theta0):
+    Sc = hr.Scene(sc)
+    n = sc["n_params"]
+    st = hr.hr_ncg_create(Sc.handle, B, np.ascontiguousarray(theta0, np.float64), o)
+    info = (hr.hr_ncg_info * (n_evals * B))()
+    # two calls: the state carries over between runs
+    k1 = n_evals // 2
+    hr.hr_ncg_run(Sc.handle, st, k1, info)
+    rest = (hr.hr_ncg_info * ((n_evals - k1) * B))()
+    hr.hr_ncg_run(Sc.handle, st, n_evals - k1, rest)
+    recs = [info[i] for i in range(k1 * B)] + [rest[i] for i in range((n_evals - k1) * B)]
+    got = np.zeros((B, n))
+    hr.hr_ncg_theta(st, got)
+    hr.hr_ncg_destroy(st)
+    Sc.close()
+    oo = _oracle_opts(o)
+    for b in range(B):
+        ost = O.ncg_init(theta0[b], oo)
+        for e in range(n_evals):
+            ref = O.ncg_evaluate(r, ost, oo, o.seed, o.request_base + b)
+            g = recs[e * B + b]
+            assert (g.iter, g.ls_step, bool(g.restarted)) == (ref.it, ref.ls_step, ref.restarted), (b, e)
+            assert g.sigma == ref.sigma
+            assert abs(g.grad_norm - ref.grad_norm) <= 1e-4 * ref.grad_norm, (b, e)
+            assert abs(g.alpha - ref.alpha) <= 1e-3 * abs(ref.alpha) + 1e-12, (b, e, g.alpha, ref.alpha)
+        move = np.linalg.norm(ost.x - theta0[b])
+        assert np.allclose(got[b], ost.x, rtol=0, atol=1e-3 * move + 1e-12), b
+    return recs, got
+
+
+@pytest.mark.parametrize("mode,graph", [(0, 1), (1, 0)])
+def test_tris2d_matches_oracle(mode, graph):
+    sc = wl.tris2d_scene(width=48, height=40, n_instances=3)
+    r = O.Tris2dRenderer(sc)
+    recs, _ = _compare(sc, r, 3, _opts(residual_mode=mode, use_graph=graph), 10, sc["theta_init"][:3])
+    assert any(x.ls_step == 1 for x in recs)          # line searches of two steps occur
+    assert len({x.sigma for x in recs}) > 1            # the bandwidth anneals
+
+
+def test_disc_matches_oracle_with_negative_curvature_region():
+    sc = wl.disc_scene()
+    r = O.DiscRenderer(sc)
+    th0 = np.stack([sc["theta_query"], np.asarray(sc["theta_target"]) + [0.3, -0.25]])
+    o = _opts(sigma_start=0.05, sigma_end=0.02, anneal_iters=6, n_grad=64, n_hvp=64, ls_iters=3, ls_tol=1e-3,
+              recompute=2, trust_radius=0.03, lambda_rel=0.0)
+    _compare(sc, r, 2, o, 12, th0)
+
+
+def test_options_are_validated():
+    sc = wl.disc_scene()
+    Sc = hr.Scene(sc)
+    th = np.ascontiguousarray(sc["theta_query"][None, :], np.float64)
+    for bad in (dict(sigma_end=0.0), dict(anneal_iters=0), dict(n_grad=3), dict(n_hvp=1024), dict(ls_iters=0),
+                dict(recompute=0), dict(residual_mode=2), dict(trust_radius=0.0), dict(ls_tol=float("nan"))):
+        with pytest.raises(hr.HRError, match="status -1"):
+            hr.hr_ncg_create(Sc.handle, 1, th, _opts(**bad))
+    st = hr.hr_ncg_create(Sc.handle, 1, th, _opts())
+    with pytest.raises(hr.HRError, match="status -1"):
+        hr.hr_ncg_run(Sc.handle, st, -1)
+    with pytest.raises(hr.HRError, match="status -1"):
+        hr.hr_ncg_run(Sc.handle, st, (1 << 18) + 1)
+    hr.hr_ncg_run(Sc.handle, st, 0)
+    hr.hr_ncg_destroy(st)
+    Sc.close()
+
+
+def test_mesh_full_size_run_approaches_target():
+    """Bench-size mesh scene (256x256, 2048 triangles), 64 instances started
+    around the target: annealed sigma 0.1 -> 0.01, line search of 2 steps.
+    The second parameter turns the 32-slice mesh about its own axis, so the
+    loss repeats every 2 pi / 32 in it; starts more than half a period away
+    settle in a neighbouring copy, hence the median."""
+    sc = wl.revolve_scene()
+    S = hr.Scene(sc)
+    B = 64
+    tgt = np.asarray(sc["theta_target"])
+    th0 = np.ascontiguousarray(tgt + np.random.default_rng(0xC5).normal(0.0, 0.1, size=(B, 2)), np.float64)
+    o = _opts(sigma_start=0.1, sigma_end=0.01, anneal_iters=30, n_grad=256, n_hvp=256, ls_iters=2, ls_tol=1e-3,
+              recompute=1, trust_radius=0.02, lambda_rel=0.0, seed=5, request_base=0)
+    st = hr.hr_ncg_create(S.handle, B, th0, o)
+    hr.hr_ncg_run(S.handle, st, 80)
+    got = np.zeros_like(th0)
+    hr.hr_ncg_theta(st, got)
+    hr.hr_ncg_destroy(st)
+    S.close()
+    e0 = np.linalg.norm(th0 - tgt, axis=1)
+    e1 = np.linalg.norm(got - tgt, axis=1)
+    assert np.median(e1 / e0) < 0.2, (e0, e1)

@@ -4,14 +4,16 @@
 //
 // One CTA (1024 threads, one per SM, persistent over perturbations) renders a
 // whole perturbation:
-//   1. rotation R = Rx(p0) Ry(p1) from RN32 of FP64 cos / sin;
+//   1. rotation R = Rx(p0) Ry(p1) from RN32 of FP64 cos / sin (for every
+//      perturbation after a CTA's first, computed during the previous raster);
 //   2. vertex transform and projection (FP32, fixed operation order);
 //   3. triangle setup: edge functions, back-face cull, depth plane of 1/Z,
 //      pixel bounding box, flat Lambert shade; surviving triangles are
 //      compacted into shared memory;
-//   4. binning into 8x8 pixel tiles (count, scan, fill; all in shared memory);
+//   4. binning into 8x8 pixel tiles (count, scan, fill; all in shared memory),
+//      skipping tiles that a conservative edge test shows the triangle misses;
 //   5. warp-per-tile raster, tiles fetched dynamically: the two half-warps
-//      take alternate bin entries, each lane testing 4 pixels; nearest 1/Z
+//      take alternate bin entries, each lane testing 4 pixels of a row; nearest 1/Z
 //      wins, ties to the lower triangle index (half-warp winners merged by a
 //      shuffle); (colour - target)^2 per tile; tiles with an empty bin take
 //      the precomputed sum of target^2;
@@ -70,6 +72,27 @@ __device__ __forceinline__ bool pixel_range(float mn, float mx, int N, int& lo, 
     return lo <= hi;
 }
 
+// Does any pixel centre of tile (tx, ty) inside the triangle's bounding box
+// pass all three edge tests?  Conservative: false only when, for some edge,
+// the edge function at the corner of the (tile ∩ box) rectangle where it is
+// largest is below -1e-5 times its term magnitudes; the FP32 errors of the
+// exact per-pixel test and of this test are below 3e-7 of that magnitude, so
+// no rejected tile holds a covered pixel.
+__device__ __forceinline__ bool tile_hits(const TriRec& r, int tx, int ty) {
+    const int x0 = max(tx * kTile, (int)(r.xr & 0xffffu)), x1 = min(tx * kTile + kTile - 1, (int)(r.xr >> 16));
+    const int y0 = max(ty * kTile, (int)(r.yr & 0xffffu)), y1 = min(ty * kTile + kTile - 1, (int)(r.yr >> 16));
+    const float fx0 = (float)x0 + 0.5f, fx1 = (float)x1 + 0.5f, fy0 = (float)y0 + 0.5f, fy1 = (float)y1 + 0.5f;
+    const float A[3] = {r.A0, r.A1, r.A2}, B[3] = {r.B0, r.B1, r.B2}, C[3] = {r.C0, r.C1, r.C2};
+#pragma unroll
+    for (int i = 0; i < 3; ++i) {
+        const float x = A[i] > 0.0f ? fx1 : fx0, y = B[i] > 0.0f ? fy1 : fy0;
+        const float e = fmaf(A[i], x, fmaf(B[i], y, C[i]));
+        const float mag = fmaf(fabsf(A[i]), fx1, fmaf(fabsf(B[i]), fy1, fabsf(C[i])));
+        if (e < -1e-5f * mag) return false;
+    }
+    return true;
+}
+
 // exclusive scan of cnt[0..T) into off[0..T); returns the total (all threads)
 __device__ int block_scan(const int* cnt, int* off, int T, int* warp_tot) {
     const int per = (T + kThreads - 1) / kThreads;
@@ -106,6 +129,12 @@ __device__ int block_scan(const int* cnt, int* off, int T, int* warp_tot) {
     return total;
 }
 
+// rotation angle d of perturbation m: RN32(theta32 + tau)
+__device__ __forceinline__ float rotation_param(const RenderBatch& b, int m, int d) {
+    const Pert pt = resolve(b, m);
+    return __fadd_rn(pt.theta[d], pt.tau[d]);
+}
+
 template <bool kImage>
 __global__ void __launch_bounds__(kThreads, 1)
 revolve_kernel(RvArgs P, RenderBatch b, const float* __restrict__ img_params, float* __restrict__ img) {
@@ -118,7 +147,7 @@ revolve_kernel(RvArgs P, RenderBatch b, const float* __restrict__ img_params, fl
     int* toff = tcnt + P.T;
     uint16_t* ent = reinterpret_cast<uint16_t*>(toff + P.T);
 
-    __shared__ float s_cs[4];
+    __shared__ float s_cs[4], s_cs_next[4];
     __shared__ float sR[9];
     __shared__ float sL[3];
     __shared__ int s_count;
@@ -126,22 +155,20 @@ revolve_kernel(RvArgs P, RenderBatch b, const float* __restrict__ img_params, fl
     __shared__ float s_part[kWarps];
     __shared__ int s_tile;
     float* tshade = reinterpret_cast<float*>(ent + kEntryCap);   // [nt] shade by triangle index
+    uint32_t* tmask = reinterpret_cast<uint32_t*>(tshade + P.nt);  // [nt] tiles hit, by record slot
 
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     const int M = kImage ? 1 : b.M;
     for (int m = kImage ? 0 : (int)blockIdx.x; m < M; m += kImage ? 1 : (int)gridDim.x) {
         // ---- 1. parameters and rotation ----------------------------------
-        if (tid < 4) {
-            float p;
-            if (kImage) {
-                p = img_params[tid >> 1];
+        if (tid < 4) {   // ca, sa, cb, sb
+            if (kImage || m == (int)blockIdx.x) {
+                const float p = kImage ? img_params[tid >> 1] : rotation_param(b, m, tid >> 1);
+                const double a = (double)p;
+                s_cs[tid] = (float)((tid & 1) ? sin(a) : cos(a));
             } else {
-                const Pert pt = resolve(b, m);
-                const int d = tid >> 1;
-                p = __fadd_rn(pt.theta[d], pt.tau[d]);
+                s_cs[tid] = s_cs_next[tid];   // computed during the previous raster phase
             }
-            const double a = (double)p;
-            s_cs[tid] = (float)((tid & 1) ? sin(a) : cos(a));   // ca, sa, cb, sb
         }
         for (int i = tid; i < P.T; i += kThreads) tcnt[i] = 0;
         if (tid == 0) { s_count = 0; s_tile = 0; }
@@ -206,12 +233,23 @@ revolve_kernel(RvArgs P, RenderBatch b, const float* __restrict__ img_params, fl
         __syncthreads();
         const int count = s_count;
         // ---- 4. binning -----------------------------------------------------
+        // count pass: each record's tiles that pass the conservative edge test
+        // go into a bit mask (row-major over its tile rectangle; rectangles of
+        // more than 32 tiles skip the test), reused by the fill pass
         for (int s = tid; s < count; s += kThreads) {
-            const uint32_t xr = rec[s].xr, yr = rec[s].yr;
-            const int tx0 = (int)(xr & 0xffffu) / kTile, tx1 = (int)(xr >> 16) / kTile;
-            const int ty0 = (int)(yr & 0xffffu) / kTile, ty1 = (int)(yr >> 16) / kTile;
+            const TriRec r = rec[s];
+            const int tx0 = (int)(r.xr & 0xffffu) / kTile, tx1 = (int)(r.xr >> 16) / kTile;
+            const int ty0 = (int)(r.yr & 0xffffu) / kTile, ty1 = (int)(r.yr >> 16) / kTile;
+            const bool test = (tx1 - tx0 + 1) * (ty1 - ty0 + 1) <= 32;
+            uint32_t mask = 0;
+            int bit = 0;
             for (int ty = ty0; ty <= ty1; ++ty)
-                for (int tx = tx0; tx <= tx1; ++tx) atomicAdd(&tcnt[ty * P.TX + tx], 1);
+                for (int tx = tx0; tx <= tx1; ++tx, ++bit)
+                    if (!test || tile_hits(r, tx, ty)) {
+                        atomicAdd(&tcnt[ty * P.TX + tx], 1);
+                        if (test) mask |= 1u << bit;
+                    }
+            tmask[s] = test ? mask : 0xFFFFFFFFu;
         }
         __syncthreads();
         const int total = block_scan(tcnt, toff, P.T, s_wtot);
@@ -220,11 +258,13 @@ revolve_kernel(RvArgs P, RenderBatch b, const float* __restrict__ img_params, fl
         __syncthreads();
         if (!overflow) {
             for (int s = tid; s < count; s += kThreads) {
-                const uint32_t xr = rec[s].xr, yr = rec[s].yr;
+                const uint32_t xr = rec[s].xr, yr = rec[s].yr, mask = tmask[s];
                 const int tx0 = (int)(xr & 0xffffu) / kTile, tx1 = (int)(xr >> 16) / kTile;
                 const int ty0 = (int)(yr & 0xffffu) / kTile, ty1 = (int)(yr >> 16) / kTile;
+                int bit = 0;
                 for (int ty = ty0; ty <= ty1; ++ty)
-                    for (int tx = tx0; tx <= tx1; ++tx) {
+                    for (int tx = tx0; tx <= tx1; ++tx, ++bit) {
+                        if (mask != 0xFFFFFFFFu && !((mask >> bit) & 1u)) continue;
                         const int tile = ty * P.TX + tx;
                         const int pos = atomicAdd(&tcnt[tile], 1);
                         ent[toff[tile] + pos] = (uint16_t)s;
@@ -234,25 +274,35 @@ revolve_kernel(RvArgs P, RenderBatch b, const float* __restrict__ img_params, fl
         __syncthreads();
         // ---- 5. raster + loss ------------------------------------------------
         // warps fetch tiles dynamically (object tiles cost far more than
-        // background tiles); each lane owns pixels (x, y0) and (x, y0 + 4)
-        // each tile's loss goes to its own slot (the fill cursor array is free
+        // background tiles); each tile's loss goes to its own slot (the fill cursor array is free
         // again) and the slots are summed in tile order below, so the loss does
         // not depend on which warp took which tile
         float* tile_loss = reinterpret_cast<float*>(tcnt);
         // Half-warp pairing: lanes 0-15 and 16-31 walk alternate entries of the
-        // bin, each lane covering 4 pixels (rows ly, ly+2, ly+4, ly+6), so the
-        // per-entry work (record loads, unpacking, thresholds) is paid once per
-        // pair of entries; the halves' per-pixel winners merge with a shuffle
-        // (largest 1/Z, lower index on ties: order-independent).
+        // bin.  Lane (row ry, half-row hx) of a half covers the 4 pixels
+        // (x0 .. x0 + 3, y): the row term fma(B, y + 1/2, C) of each edge and of
+        // the depth plane is formed once per entry and shared by the 4 pixels.
+        // The per-entry work (record loads, unpacking, thresholds) is paid once
+        // per pair of entries; the halves' per-pixel winners merge with a
+        // shuffle (largest 1/Z, lower index on ties: order-independent).
         const int half = lane >> 4, hl = lane & 15;
-        const int lx = hl & 7, ly = hl >> 3;
+        const int ry = hl >> 1, hx = hl & 1;
+        // the FP64 cos / sin of this CTA's next perturbation, off the critical
+        // path: one warp computes them before it joins the tile loop
+        if (!kImage && warp == kWarps - 1 && lane < 4) {
+            const int mn = m + (int)gridDim.x;
+            if (mn < M) {
+                const double a = (double)rotation_param(b, mn, lane >> 1);
+                s_cs_next[lane] = (float)((lane & 1) ? sin(a) : cos(a));
+            }
+        }
         for (;;) {
             int t = 0;
             if (lane == 0) t = atomicAdd(&s_tile, 1);
             t = __shfl_sync(0xffffffffu, t, 0);
             if (t >= P.T) break;
             const int ty = t / P.TX, tx = t - ty * P.TX;
-            const int x = tx * kTile + lx, ybase = ty * kTile + ly;
+            const int x0 = tx * kTile + 4 * hx, y = ty * kTile + ry;
             int beg, end;
             if (overflow) { beg = 0; end = count; }
             else { beg = toff[t]; end = (t + 1 < P.T) ? toff[t + 1] : total; }
@@ -260,22 +310,22 @@ revolve_kernel(RvArgs P, RenderBatch b, const float* __restrict__ img_params, fl
                 if (lane == 0) tile_loss[t] = P.tile_t2[t];
                 continue;
             }
-            // loss pixels of this lane after the merge: rows 2*half and 2*half+1 of its four
-            const int ya = ybase + 4 * half, yb = ya + 2;
-            const bool va = x < P.W && ya < P.H, vb = x < P.W && yb < P.H;
+            // loss pixels of this lane after the merge: columns x0 + 2 half, x0 + 2 half + 1
+            const int xa = x0 + 2 * half, xb = xa + 1;
+            const bool va = xa < P.W && y < P.H, vb = xb < P.W && y < P.H;
             float tga[3] = {0.f, 0.f, 0.f}, tgb[3] = {0.f, 0.f, 0.f};
             if (!kImage) {
-                if (va) for (int c = 0; c < 3; ++c) tga[c] = P.target[3 * ((size_t)ya * P.W + x) + c];
-                if (vb) for (int c = 0; c < 3; ++c) tgb[c] = P.target[3 * ((size_t)yb * P.W + x) + c];
+                if (va) for (int c = 0; c < 3; ++c) tga[c] = P.target[3 * ((size_t)y * P.W + xa) + c];
+                if (vb) for (int c = 0; c < 3; ++c) tgb[c] = P.target[3 * ((size_t)y * P.W + xb) + c];
             }
-            const float fx = __fadd_rn((float)x, 0.5f);
-            float fy[4], bw[4];
+            const float fy = __fadd_rn((float)y, 0.5f);
+            float fx[4], bw[4];
             int bi[4];
 #pragma unroll
-            for (int r = 0; r < 4; ++r) {
-                fy[r] = __fadd_rn((float)(ybase + 2 * r), 0.5f);
-                bw[r] = -INFINITY;
-                bi[r] = INT_MAX;
+            for (int c = 0; c < 4; ++c) {
+                fx[c] = __fadd_rn((float)(x0 + c), 0.5f);
+                bw[c] = -INFINITY;
+                bi[c] = INT_MAX;
             }
             for (int jj = beg; jj < end; jj += 2) {
                 const int j = jj + half;
@@ -287,32 +337,35 @@ revolve_kernel(RvArgs P, RenderBatch b, const float* __restrict__ img_params, fl
                     const uint32_t xr = __float_as_uint(q3.z), yr = __float_as_uint(q3.w);
                     const int ti = (int)(key & 0x1FFFFFFFu);
                     const float th0 = tl_threshold(key, 0), th1 = tl_threshold(key, 1), th2 = tl_threshold(key, 2);
-                    const int xlo = (int)(xr & 0xffffu), ylo = (int)(yr & 0xffffu);
-                    const bool inx = (unsigned)(x - xlo) <= (xr >> 16) - (unsigned)xlo;
-                    const unsigned yspan = (yr >> 16) - (unsigned)ylo;
+                    const int lo = (int)(xr & 0xffffu) - x0, hi = (int)(xr >> 16) - x0;
+                    const int ylo = (int)(yr & 0xffffu);
+                    const bool yok = (unsigned)(y - ylo) <= (yr >> 16) - (unsigned)ylo;
+                    const float r0 = __fmaf_rn(q0.y, fy, q0.z);
+                    const float r1 = __fmaf_rn(q1.x, fy, q1.y);
+                    const float r2 = __fmaf_rn(q1.w, fy, q2.x);
+                    const float rw = __fmaf_rn(q2.z, fy, q2.w);
 #pragma unroll
-                    for (int r = 0; r < 4; ++r) {
-                        const float E0 = edge_eval(q0.x, q0.y, q0.z, fx, fy[r]);
-                        const float E1 = edge_eval(q0.w, q1.x, q1.y, fx, fy[r]);
-                        const float E2 = edge_eval(q1.z, q1.w, q2.x, fx, fy[r]);
-                        const float wz = edge_eval(q2.y, q2.z, q2.w, fx, fy[r]);
-                        const bool in = inx && ((unsigned)(ybase + 2 * r - ylo) <= yspan) && (E0 > th0) &&
-                                        (E1 > th1) && (E2 > th2);
-                        const bool better = in && (wz > bw[r] || (wz == bw[r] && ti < bi[r]));
-                        bw[r] = better ? wz : bw[r];
-                        bi[r] = better ? ti : bi[r];
+                    for (int c = 0; c < 4; ++c) {
+                        const float E0 = __fmaf_rn(q0.x, fx[c], r0);
+                        const float E1 = __fmaf_rn(q0.w, fx[c], r1);
+                        const float E2 = __fmaf_rn(q1.z, fx[c], r2);
+                        const float wz = __fmaf_rn(q2.y, fx[c], rw);
+                        const bool in = yok && c >= lo && c <= hi && (E0 > th0) && (E1 > th1) && (E2 > th2);
+                        const bool better = in && (wz > bw[c] || (wz == bw[c] && ti < bi[c]));
+                        bw[c] = better ? wz : bw[c];
+                        bi[c] = better ? ti : bi[c];
                     }
                 }
             }
 #pragma unroll
-            for (int r = 0; r < 4; ++r) {
-                const float ow = __shfl_xor_sync(0xffffffffu, bw[r], 16);
-                const int oi = __shfl_xor_sync(0xffffffffu, bi[r], 16);
-                const bool take = ow > bw[r] || (ow == bw[r] && oi < bi[r]);
-                bw[r] = take ? ow : bw[r];
-                bi[r] = take ? oi : bi[r];
+            for (int c = 0; c < 4; ++c) {
+                const float ow = __shfl_xor_sync(0xffffffffu, bw[c], 16);
+                const int oi = __shfl_xor_sync(0xffffffffu, bi[c], 16);
+                const bool take = ow > bw[c] || (ow == bw[c] && oi < bi[c]);
+                bw[c] = take ? ow : bw[c];
+                bi[c] = take ? oi : bi[c];
             }
-            // this lane's two pixels: rows 2*half and 2*half+1 of its four
+            // this lane's two pixels: columns 2 half and 2 half + 1 of its four
             const int ia = half ? bi[2] : bi[0], ib = half ? bi[3] : bi[1];
             const float sha = ia != INT_MAX ? tshade[ia] : 0.0f;
             const float shb = ib != INT_MAX ? tshade[ib] : 0.0f;
@@ -320,11 +373,11 @@ revolve_kernel(RvArgs P, RenderBatch b, const float* __restrict__ img_params, fl
             const float cb0 = shb * P.alb0, cb1 = shb * P.alb1, cb2 = shb * P.alb2;
             if (kImage) {
                 if (va) {
-                    const size_t p = 3 * ((size_t)ya * P.W + x);
+                    const size_t p = 3 * ((size_t)y * P.W + xa);
                     img[p] = ca0; img[p + 1] = ca1; img[p + 2] = ca2;
                 }
                 if (vb) {
-                    const size_t p = 3 * ((size_t)yb * P.W + x);
+                    const size_t p = 3 * ((size_t)y * P.W + xb);
                     img[p] = cb0; img[p + 1] = cb1; img[p + 2] = cb2;
                 }
             } else {
@@ -407,7 +460,7 @@ RvArgs make_args(const DevScene& sc) {
 size_t revolve_smem_bytes(int nv, int nt, int W, int H) {
     const int T = ((W + kTile - 1) / kTile) * ((H + kTile - 1) / kTile);
     return sizeof(TriRec) * (size_t)nt + 3 * sizeof(float) * (size_t)nv + 2 * sizeof(int) * (size_t)T +
-           sizeof(uint16_t) * kEntryCap + sizeof(float) * (size_t)nt;
+           sizeof(uint16_t) * kEntryCap + sizeof(float) * (size_t)nt + sizeof(uint32_t) * (size_t)nt;
 }
 
 void revolve_prepare(DevScene& sc, cudaStream_t s) {

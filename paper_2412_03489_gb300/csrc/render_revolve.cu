@@ -75,22 +75,22 @@ __device__ __forceinline__ bool pixel_range(float mn, float mx, int N, int& lo, 
 // Does any pixel centre of tile (tx, ty) inside the triangle's bounding box
 // pass all three edge tests?  Conservative: false only when, for some edge,
 // the edge function at the corner of the (tile ∩ box) rectangle where it is
-// largest is below -1e-5 times its term magnitudes; the FP32 errors of the
-// exact per-pixel test and of this test are below 3e-7 of that magnitude, so
-// no rejected tile holds a covered pixel.
-__device__ __forceinline__ bool tile_hits(const TriRec& r, int tx, int ty) {
+// largest lies below neg[i] = -1e-5 (|A| W + |B| H + |C|), minus 1e-5 times
+// a bound on its term magnitudes anywhere in the image; the FP32 errors of
+// the exact per-pixel test and of this test are below 3e-7 of that
+// magnitude, so no rejected tile holds a covered pixel.
+__device__ __forceinline__ bool tile_hits(const TriRec& r, const float neg[3], int tx, int ty) {
     const int x0 = max(tx * kTile, (int)(r.xr & 0xffffu)), x1 = min(tx * kTile + kTile - 1, (int)(r.xr >> 16));
     const int y0 = max(ty * kTile, (int)(r.yr & 0xffffu)), y1 = min(ty * kTile + kTile - 1, (int)(r.yr >> 16));
     const float fx0 = (float)x0 + 0.5f, fx1 = (float)x1 + 0.5f, fy0 = (float)y0 + 0.5f, fy1 = (float)y1 + 0.5f;
     const float A[3] = {r.A0, r.A1, r.A2}, B[3] = {r.B0, r.B1, r.B2}, C[3] = {r.C0, r.C1, r.C2};
+    bool hit = true;
 #pragma unroll
     for (int i = 0; i < 3; ++i) {
         const float x = A[i] > 0.0f ? fx1 : fx0, y = B[i] > 0.0f ? fy1 : fy0;
-        const float e = fmaf(A[i], x, fmaf(B[i], y, C[i]));
-        const float mag = fmaf(fabsf(A[i]), fx1, fmaf(fabsf(B[i]), fy1, fabsf(C[i])));
-        if (e < -1e-5f * mag) return false;
+        hit = hit && !(fmaf(A[i], x, fmaf(B[i], y, C[i])) < neg[i]);
     }
-    return true;
+    return hit;
 }
 
 // exclusive scan of cnt[0..T) into off[0..T); returns the total (all threads)
@@ -241,11 +241,15 @@ revolve_kernel(RvArgs P, RenderBatch b, const float* __restrict__ img_params, fl
             const int tx0 = (int)(r.xr & 0xffffu) / kTile, tx1 = (int)(r.xr >> 16) / kTile;
             const int ty0 = (int)(r.yr & 0xffffu) / kTile, ty1 = (int)(r.yr >> 16) / kTile;
             const bool test = (tx1 - tx0 + 1) * (ty1 - ty0 + 1) <= 32;
+            const float fW = (float)P.W, fH = (float)P.H;
+            const float neg[3] = {-1e-5f * fmaf(fabsf(r.A0), fW, fmaf(fabsf(r.B0), fH, fabsf(r.C0))),
+                                  -1e-5f * fmaf(fabsf(r.A1), fW, fmaf(fabsf(r.B1), fH, fabsf(r.C1))),
+                                  -1e-5f * fmaf(fabsf(r.A2), fW, fmaf(fabsf(r.B2), fH, fabsf(r.C2)))};
             uint32_t mask = 0;
             int bit = 0;
             for (int ty = ty0; ty <= ty1; ++ty)
                 for (int tx = tx0; tx <= tx1; ++tx, ++bit)
-                    if (!test || tile_hits(r, tx, ty)) {
+                    if (!test || tile_hits(r, neg, tx, ty)) {
                         atomicAdd(&tcnt[ty * P.TX + tx], 1);
                         if (test) mask |= 1u << bit;
                     }

@@ -39,7 +39,7 @@ METRIC = "Hessian/HVP estimates/s at oracle-matched error; perturbed renders/s; 
 # DRAM bytes (read + write) of one render+loss launch from the ncu capture of
 # the current mesh kernel (profiles/revolve_kernel_M4096.md); set to None when
 # the kernel changes until it is captured again.
-TRAFFIC_BYTES = None
+TRAFFIC_BYTES = 496896
 M_PERTURB = 4096
 SEED = 2024
 

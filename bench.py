@@ -13,8 +13,9 @@ events on the launching stream; `e2e` times the host-pointer entry point
 (hr_estimate_hessian: parameters up, Hessian down) with the host clock.
 The roofline line is for the render+loss kernel, timed per launch with the
 library's own events; its algorithmic work is an FP32-operation count (see
-`revolve_work`).  `cpu_baseline` runs the oracle (plain single-threaded C,
-FP64) on a bounded sample of the same estimate.
+`revolve_work`).  `cpu_baseline` runs the oracle (plain C renders, FP64
+sums) on the same estimate with its renders split over all host threads, and
+on a bounded sample with one thread (`single_thread`).
 
 Multi-GPU: estimates are independent, so N ranks run N replicas (weak
 scaling, no collective on the data path); `value` = all ranks' estimates /
@@ -128,23 +129,43 @@ def measured_peaks():
     return {"hbm_gbs": 6800.0, "sm_max_mhz": 2070.0}, "fallback"
 
 
-def cpu_baseline(sc, theta, sample=1024):
-    """The oracle, single-threaded, on the first `sample` perturbations of the
-    same estimate; scaled to estimates/s of the full M."""
+def cpu_baseline(sc, theta, sample=1024, threads=1):
+    """The oracle (plain C renders, FP64 sums) on the first `sample`
+    perturbations of the same estimate, the renders split over `threads`
+    host threads (contiguous slices; the C calls run without the GIL);
+    scaled to estimates/s of the full M."""
     import oracle as O
+    from concurrent.futures import ThreadPoolExecutor
     t0 = time.perf_counter()
     r = O.RevolveRenderer(sc)
     tau, _ = O.draw(1, 2, sc["sigma"], sample // 2, SEED, 0, 0)
     w = O.weights(1, 2, sc["sigma"], tau)
     t1 = time.perf_counter()
-    losses = np.array([r.loss(O.perturb(theta, tau[m])) for m in range(sample)])
+
+    def part(lo, hi):
+        return [r.loss(O.perturb(theta, tau[m])) for m in range(lo, hi)]
+    if threads <= 1:
+        losses = np.array(part(0, sample))
+    else:
+        cut = np.linspace(0, sample, threads + 1).astype(int)
+        with ThreadPoolExecutor(threads) as ex:
+            losses = np.concatenate(list(ex.map(lambda i: np.array(part(cut[i], cut[i + 1])), range(threads))))
     _ = (w * losses[:, None]).sum(0)
     t2 = time.perf_counter()
     per_render = (t2 - t1) / sample
     est_s = per_render * M_PERTURB + (t1 - t0) * M_PERTURB / sample
-    return {"value": 1.0 / est_s, "unit": "estimates/s", "cores": 1, "kind": "oracle",
-            "sample": f"{sample} of the {M_PERTURB} perturbations of one estimate (plain C, FP64 values), "
-                      f"scaled to one full estimate", "renders_per_s": 1.0 / per_render}
+    return {"value": 1.0 / est_s, "unit": "estimates/s", "cores": max(1, threads), "kind": "oracle",
+            "sample": f"{sample} of the {M_PERTURB} perturbations of one estimate (plain C renders, FP64 sums) "
+                      f"on {max(1, threads)} host thread(s), scaled to one full estimate",
+            "renders_per_s": 1.0 / per_render}
+
+
+def host_threads():
+    """Host cores this process may run on."""
+    try:
+        return len(os.sched_getaffinity(0))
+    except AttributeError:
+        return os.cpu_count() or 1
 
 
 def run_reference(args):
@@ -154,11 +175,11 @@ def run_reference(args):
     from paper_2412_03489_gb300 import workloads as wl
     sc = wl.revolve_scene()
     theta = np.asarray(sc["theta_query"], np.float64)
-    sample = 256
+    threads = host_threads()
+    sample = 64 * threads
     times = []
     for i in range(args.warmup + args.steps):
-        t0 = time.perf_counter()
-        cb = cpu_baseline(sc, theta, sample=sample)
+        cb = cpu_baseline(sc, theta, sample=sample, threads=threads)
         if i >= args.warmup:
             times.append(1.0 / cb["value"])
     est_s = float(np.mean(times))
@@ -167,8 +188,9 @@ def run_reference(args):
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": est_s * 1e3, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
             "config": workload_config(sc),
-            "cpu_baseline": {"value": val, "unit": "estimates/s", "cores": 1, "kind": "oracle",
-                             "sample": f"each step: {sample} of the {M_PERTURB} perturbations, scaled to one estimate"},
+            "cpu_baseline": {"value": val, "unit": "estimates/s", "cores": threads, "kind": "oracle",
+                             "sample": f"each step: {sample} of the {M_PERTURB} perturbations on {threads} host "
+                                       f"threads, scaled to one estimate"},
             "e2e": {"value": val, "unit": "estimates/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line))
     return 0
@@ -407,91 +429,126 @@ def boxes_variance_bench(hr, wl):
 
 def serving_bench(torch, hr, wl):
     """Poisson arrivals through the server versus the plain one-request-at-a-
-    time entry points on the same request list."""
+    time entry points on the same request list (estimates of every kind and
+    Newton-CG steps on resident optimizer states); the arrival rate swept from
+    a quarter of the saturated rate to past it."""
     import threading
     scenes = wl.serving_scenes()
     S = {k: hr.Scene(v) for k, v in scenes.items()}
-    reqs = wl.serving_requests(scenes, n_requests=240)
+    reqs = wl.serving_requests(scenes, n_requests=1200)
+    specs = wl.serving_newton_states(scenes)
 
-    def make(r):
-        o = hr.make_opts(r["sigma"], r["M"], r["strategy"], r["seed"], r["request"])
-        return hr.make_request(S[r["scene"]], r["quantity"], r["theta"], r["v"], o)
+    def new_states():
+        out = []
+        for sp in specs:
+            o = hr.hr_cg_opts()
+            o.sigma, o.n_grad, o.n_hvp, o.cg_iters = sp["sigma"], sp["n_grad"], sp["n_hvp"], sp["cg_iters"]
+            o.lambda_rel, o.trust_radius, o.seed, o.request_base, o.use_graph = 1e-3, sp["trust_radius"], 3, 0, 1
+            out.append(hr.hr_optstate_create(S[sp["scene"]].handle, sp["B"],
+                                             np.ascontiguousarray(sp["theta0"], np.float64), o))
+        return out
 
     def out_for(r):
+        if r["quantity"] == hr.HR_NEWTON_STEP:
+            return (hr.hr_step_info * specs[r["state"]]["B"])()
         n = S[r["scene"]].n
         return np.zeros((n, n) if r["quantity"] == hr.HR_HESSIAN else n)
 
-    # plain: one request at a time through hr_estimate_* (host pointers)
+    def as_array(o):
+        if isinstance(o, np.ndarray):
+            return o
+        return np.array([(x.grad_norm, x.step_norm, x.iters) for x in o])
+
+    def make(r, states):
+        if r["quantity"] == hr.HR_NEWTON_STEP:
+            return hr.make_request(S[r["scene"]], hr.HR_NEWTON_STEP, optstate=states[r["state"]])
+        o = hr.make_opts(r["sigma"], r["M"], r["strategy"], r["seed"], r["request"])
+        return hr.make_request(S[r["scene"]], r["quantity"], r["theta"], r["v"], o)
+
+    def plain_one(r, states):
+        if r["quantity"] == hr.HR_NEWTON_STEP:
+            o = out_for(r)
+            hr.hr_newton_cg_step(S[r["scene"]].handle, states[r["state"]], o)
+            return as_array(o)
+        return S[r["scene"]].estimate(r["quantity"], r["theta"], r["sigma"], r["M"], r["strategy"], r["seed"],
+                                      r["request"], v=r["v"])
+
+    # plain: one request at a time through hr_estimate_* / hr_newton_cg_step
+    st_plain = new_states()
     for r in reqs[:8]:
-        S[r["scene"]].estimate(r["quantity"], r["theta"], r["sigma"], r["M"], r["strategy"], r["seed"],
-                               r["request"], v=r["v"])
+        plain_one(r, st_plain)
     torch.cuda.synchronize()
     t0 = time.perf_counter()
-    plain = []
-    for r in reqs:
-        plain.append(S[r["scene"]].estimate(r["quantity"], r["theta"], r["sigma"], r["M"], r["strategy"],
-                                            r["seed"], r["request"], v=r["v"]))
+    plain = [plain_one(r, st_plain) for r in reqs]
     plain_s = time.perf_counter() - t0
 
     srv = hr.hr_server_create(4 << 30, max_active=32, chunk=2048)
-    # warm the lanes
-    for r in reqs[:8]:
-        req, keep = make(r)
+    st_srv = new_states()
+    for r in reqs[:8]:                                   # warm the lanes (same requests as the plain warm-up)
+        req, keep = make(r, st_srv)
         hr.hr_server_wait(srv, hr.hr_server_submit(srv, req), out_for(r), hr.hr_request_info())
     # saturation: everything submitted at once
     t0 = time.perf_counter()
     tk = []
     for r in reqs:
-        req, keep = make(r)
+        req, keep = make(r, st_srv)
         tk.append((hr.hr_server_submit(srv, req), keep, r))
     sat = []
     for t, keep, r in tk:
         o = out_for(r)
         hr.hr_server_wait(srv, t, o, hr.hr_request_info())
-        sat.append(o)
+        sat.append(as_array(o))
     sat_s = time.perf_counter() - t0
     same = all(np.array_equal(a, b) for a, b in zip(plain, sat))
+    sat_rate = len(reqs) / sat_s
 
-    # Poisson arrivals at 70 % of the saturated rate
-    rate = 0.7 * len(reqs) / sat_s
-    arrivals = np.cumsum(np.random.default_rng(0xC5).exponential(1.0 / rate, size=len(reqs)))
-    tickets = [None] * len(reqs)
-    ready = threading.Semaphore(0)
+    def poisson(frac, seed):
+        rate = frac * sat_rate
+        arrivals = np.cumsum(np.random.default_rng(seed).exponential(1.0 / rate, size=len(reqs)))
+        tickets = [None] * len(reqs)
+        ready = threading.Semaphore(0)
 
-    def submitter():
-        start = time.perf_counter()
+        def submitter():
+            start = time.perf_counter()
+            for i, r in enumerate(reqs):
+                d = arrivals[i] - (time.perf_counter() - start)
+                if d > 0:
+                    time.sleep(d)
+                req, keep = make(r, st_srv)
+                tickets[i] = (hr.hr_server_submit(srv, req), keep)
+                ready.release()
+        th = threading.Thread(target=submitter)
+        t1 = time.perf_counter()
+        th.start()
+        lat = []
         for i, r in enumerate(reqs):
-            d = arrivals[i] - (time.perf_counter() - start)
-            if d > 0:
-                time.sleep(d)
-            req, keep = make(r)
-            tickets[i] = (hr.hr_server_submit(srv, req), keep)
-            ready.release()
-    th = threading.Thread(target=submitter)
-    t0 = time.perf_counter()
-    th.start()
-    lat = []
-    for i, r in enumerate(reqs):
-        ready.acquire()
-        info = hr.hr_request_info()
-        hr.hr_server_wait(srv, tickets[i][0], out_for(r), info)
-        lat.append(info.done_ms - info.submit_ms)
-    th.join()
-    poisson_s = time.perf_counter() - t0
+            ready.acquire()
+            info = hr.hr_request_info()
+            hr.hr_server_wait(srv, tickets[i][0], out_for(r), info)
+            lat.append(info.done_ms - info.submit_ms)
+        th.join()
+        dt = time.perf_counter() - t1
+        return {"offered_fraction_of_saturated": frac, "arrival_rate_hz": rate,
+                "estimates_per_s": len(reqs) / dt,
+                "latency_ms": {"p50": float(np.percentile(lat, 50)), "p99": float(np.percentile(lat, 99))}}
+
+    sweep = [poisson(f, 0xC5 + k) for k, f in enumerate((0.25, 0.5, 0.7, 0.9, 1.1))]
     hr.hr_server_destroy(srv)
+    for st in st_plain + st_srv:
+        hr.hr_optstate_destroy(st)
     for v in S.values():
         v.close()
+    n_newton = sum(r["quantity"] == hr.HR_NEWTON_STEP for r in reqs)
     return {"metric": "estimates/s and p50/p99 latency, serving mix vs one request at a time",
-            "requests": len(reqs),
+            "requests": len(reqs), "newton_step_requests": int(n_newton),
             "plain_one_at_a_time": {"estimates_per_s": len(reqs) / plain_s},
-            "served_saturated": {"estimates_per_s": len(reqs) / sat_s,
+            "served_saturated": {"estimates_per_s": sat_rate,
                                  "speedup_vs_plain": plain_s / sat_s, "results_identical_to_plain": same},
-            "served_poisson": {"arrival_rate_hz": rate, "estimates_per_s": len(reqs) / poisson_s,
-                               "latency_ms": {"p50": float(np.percentile(lat, 50)),
-                                              "p99": float(np.percentile(lat, 99))}},
+            "served_poisson_sweep": sweep,
             "config": {"workload": "Poisson arrivals over 8 resident scenes (disc 64/512, mesh 128/256/512, "
                                    "path-traced box 64, triangles 128 (n 64) / 256 (n 16)), 256..16384 samples, "
-                                   "grad / Hessian / HVP, element-wise and aggregate"}}
+                                   "grad / Hessian / HVP, element-wise and aggregate, and Newton-CG steps on 2 "
+                                   "resident optimizer states (8 and 4 instances)"}}
 
 
 def main():
@@ -602,7 +659,9 @@ def main():
                 "gpu_launches": 3 * args.steps,
                 "clocks": clk}
         if not args.no_cpu_baseline:
-            line["cpu_baseline"] = cpu_baseline(sc, theta)
+            threads = host_threads()
+            line["cpu_baseline"] = cpu_baseline(sc, theta, sample=M_PERTURB, threads=threads)
+            line["cpu_baseline"]["single_thread"] = cpu_baseline(sc, theta, sample=256, threads=1)
         print(json.dumps(line))
     S.close()
     if world > 1:

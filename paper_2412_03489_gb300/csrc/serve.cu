@@ -133,6 +133,11 @@ struct hr_server_s {
     Arena arena;
     unsigned char* pinned = nullptr;
     std::vector<int> free_slots;
+    // optimizer states with a step in flight (worker thread only, like
+    // free_slots): a second step request on the same state waits in the
+    // queue, since both would copy their step records into the state's one
+    // pinned buffer
+    std::vector<hr_optstate> busy_states;
     std::unordered_map<hr_scene, Lane> lanes;
     cudaStream_t upload = nullptr;
     std::vector<cudaEvent_t> event_pool;
@@ -168,6 +173,8 @@ struct hr_server_s {
 bool hr_server_s::admit(SrvReq* r) {
     if (free_slots.empty()) return false;
     if (r->req.quantity == HR_NEWTON_STEP) {
+        if (std::find(busy_states.begin(), busy_states.end(), r->req.optstate) != busy_states.end()) return false;
+        busy_states.push_back(r->req.optstate);
         r->slot = free_slots.back();
         free_slots.pop_back();
         return true;
@@ -361,7 +368,11 @@ bool hr_server_s::retire() {
             // drain them before its arena block can be handed out again
             cudaStreamSynchronize(lane(r->req.scene).stream);
         }
-        if (r->req.quantity != HR_NEWTON_STEP) arena.release(r->off, r->bytes);
+        if (r->req.quantity != HR_NEWTON_STEP) {
+            arena.release(r->off, r->bytes);
+        } else {
+            busy_states.erase(std::find(busy_states.begin(), busy_states.end(), r->req.optstate));
+        }
         free_slots.push_back(r->slot);
         r->slot = -1;
         r->t_done = now_ms();

@@ -218,13 +218,29 @@ def serving_scenes() -> dict:
     }
 
 
-# (scene, quantity, strategy, samples); quantity 0 grad, 1 Hessian, 2 HVP;
+# (scene, quantity, strategy, samples); quantity 0 grad, 1 Hessian, 2 HVP,
+# 3 Newton-CG step (samples = index of the resident optimizer state);
 # strategy 0 element-wise, 1 aggregate
 SERVING_KINDS = [
     ("disc64", 1, 0, 1024), ("disc64", 1, 1, 16384), ("disc64", 0, 1, 4096), ("disc512", 1, 1, 256),
     ("revolve128", 1, 1, 2048), ("revolve256", 1, 1, 4096), ("revolve256", 2, 1, 1024), ("revolve512", 1, 1, 256),
     ("pt64", 2, 1, 256), ("tris128_n64", 2, 1, 512), ("tris128_n64", 0, 1, 1024), ("tris256_n16", 2, 1, 256),
+    ("tris128_n64", 3, 1, 0), ("tris256_n16", 3, 1, 1),
 ]
+
+
+def serving_newton_states(scenes: dict) -> list:
+    """Resident Newton-CG states of the serving mix: (scene, instances,
+    initial parameters [B][n], sigma, gradient / HVP samples, CG iterations,
+    trust radius)."""
+    g = _rng(0xC6)
+    out = []
+    for name, B in (("tris128_n64", 8), ("tris256_n16", 4)):
+        sc = scenes[name]
+        th0 = np.asarray(sc["theta_target"], np.float64)[None, :] + g.normal(0.0, 0.03, size=(B, sc["n_params"]))
+        out.append(dict(scene=name, B=B, theta0=th0, sigma=sc["sigma"], n_grad=32, n_hvp=32, cg_iters=4,
+                        trust_radius=0.05))
+    return out
 
 
 def serving_requests(scenes: dict, n_requests: int = 240, rate_hz: float = 1000.0, seed: int = 0xC4) -> list:
@@ -239,5 +255,6 @@ def serving_requests(scenes: dict, n_requests: int = 240, rate_hz: float = 1000.
         theta = np.asarray(sc["theta_query"], np.float64) + g.normal(0.0, 0.01, n)
         v = g.normal(size=n) if q == 2 else None
         reqs.append(dict(scene=name, quantity=q, strategy=strat, M=M, theta=theta, v=v,
-                         sigma=sc["sigma"], seed=1 + i, request=i, arrival_s=t))
+                         sigma=sc["sigma"], seed=1 + i, request=i, arrival_s=t,
+                         state=M if q == 3 else None))
     return reqs

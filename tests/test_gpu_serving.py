@@ -111,6 +111,40 @@ def test_newton_step_through_server_matches_direct_step():
     hr.hr_optstate_destroy(st_served)
 
 
+def test_overlapping_steps_on_one_state_run_in_order():
+    """Two step requests on the same state submitted back to back: the second
+    waits for the first, and each returns its own step record."""
+    sc = wl.tris2d_scene(width=48, height=40, n_instances=2)
+    Sd, Ss = hr.Scene(sc), hr.Scene(sc)
+    opts = hr.hr_cg_opts()
+    opts.sigma, opts.n_grad, opts.n_hvp, opts.cg_iters = sc["sigma"], 16, 8, 3
+    opts.lambda_rel, opts.trust_radius, opts.seed, opts.request_base, opts.use_graph = 1e-3, 0.05, 9, 0, 1
+    th0 = np.ascontiguousarray(sc["theta_init"][:2], np.float64)
+    st_direct = hr.hr_optstate_create(Sd.handle, 2, th0, opts)
+    st_served = hr.hr_optstate_create(Ss.handle, 2, th0, opts)
+    direct = []
+    for _ in range(3):
+        info = (hr.hr_step_info * 2)()
+        hr.hr_newton_cg_step(Sd.handle, st_direct, info)
+        direct.append([(info[b].iters, info[b].step_norm, info[b].grad_norm) for b in range(2)])
+    srv = hr.hr_server_create(16 << 20, max_active=4)
+    tickets = []
+    for _ in range(3):
+        r, keep = hr.make_request(Ss, hr.HR_NEWTON_STEP, optstate=st_served)
+        tickets.append((hr.hr_server_submit(srv, r), keep))
+    for (t, keep), ref in zip(tickets, direct):
+        info = (hr.hr_step_info * 2)()
+        hr.hr_server_wait(srv, t, info, hr.hr_request_info())
+        assert [(info[b].iters, info[b].step_norm, info[b].grad_norm) for b in range(2)] == ref
+    a, b = np.zeros((2, sc["n_params"])), np.zeros((2, sc["n_params"]))
+    hr.hr_optstate_theta(st_direct, a)
+    hr.hr_optstate_theta(st_served, b)
+    assert np.array_equal(a, b)
+    hr.hr_server_destroy(srv)
+    hr.hr_optstate_destroy(st_direct)
+    hr.hr_optstate_destroy(st_served)
+
+
 def test_budget_validation_timeout_and_shutdown():
     Sd = hr.Scene(wl.disc_scene())
     th = np.asarray(Sd.sc["theta_query"])

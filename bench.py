@@ -210,6 +210,16 @@ def whole_job_rate(local_ms, steps, world, device):
     return world * steps / (local_ms / 1e3), local_ms
 
 
+def tune_scene(hr, S, theta, n_probe):
+    """The library's autotuner on this scene (launch shapes that leave every
+    result bit-identical); returns the choice and the probe timings."""
+    i = hr.hr_autotune(S.handle, theta, n_probe)
+    return {"render_variant": i.render_variant, "sample_threads": i.sample_threads,
+            "render_ms": [round(i.render_ms[k], 4) for k in range(i.n_render_variants)],
+            "sample_ms": [round(i.sample_ms[k], 4) for k in range(i.n_sample_variants)],
+            "probe_perturbations": n_probe}
+
+
 def _timed_steps(torch, stream, flush, fn, warmup, steps):
     """CUDA-event time of `fn(i)` per step (L2 flushed before each, untimed)."""
     for i in range(warmup):
@@ -247,6 +257,7 @@ def run_secondary(args):
         d_theta = torch.tensor(sc["theta_query"], dtype=torch.float64, device="cuda")
         d_v = torch.tensor(sc.get("v", np.ones(n)), dtype=torch.float64, device="cuda")
         d_out = torch.zeros((n, n), dtype=torch.float64, device="cuda")
+        line["tuning"] = tune_scene(hr, S, sc["theta_query"], 1024 if args.workload == "disc" else 256)
         hr.hr_profile_enable(S.handle, True)
         variants = ([("hessian_elementwise_3x1024", hr.HR_HESSIAN, hr.HR_ELEMENTWISE, 1024, 3 * 1024),
                      ("hessian_aggregate_1024", hr.HR_HESSIAN, hr.HR_AGGREGATE, 1024, 1024)]
@@ -589,6 +600,7 @@ def main():
     d_theta = torch.tensor(theta, dtype=torch.float64, device="cuda")
     d_out = torch.zeros((2, 2), dtype=torch.float64, device="cuda")
     flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda")
+    tuning = tune_scene(hr, S, theta, 1024)
     hr.hr_profile_enable(S.handle, True)
 
     def step(i):
@@ -657,6 +669,7 @@ def main():
                         "d2h_bytes_per_step": 32},
                 "stage_ms": dict(zip(("sample", "render_loss", "sums"), np.mean(stage_ms, axis=0).tolist())),
                 "gpu_launches": 3 * args.steps,
+                "tuning": tuning,
                 "clocks": clk}
         if not args.no_cpu_baseline:
             threads = host_threads()

@@ -415,6 +415,32 @@ hr_status hr_server_wait(hr_server srv, uint64_t ticket, void* h_out, hr_request
 hr_status hr_profile_enable(hr_scene scene, int32_t on);
 hr_status hr_profile_last(hr_scene scene, float* ms3);
 
+/* ---------------------------------------------------------------------------
+ * Autotuning of launch shapes.  Each scene kind has render+loss launch-shape
+ * variants (path tracer: minimum resident CTAs per SM 3 / 2 / 4, i.e. register
+ * caps; disc and squares: 8 / 4 / 16 warps per CTA, one warp per
+ * perturbation; mesh and 2D triangles: one shape) and the sampler runs with
+ * 32, 64 or 128 threads per block.  Every variant computes the same values in
+ * the same order, so results are bit-identical whatever is chosen.
+ * hr_autotune times each variant on profiled aggregate HVP estimates of
+ * n_probe perturbations at h_theta [n] (v = ones, sigma 0.05; median of 3
+ * after a warm-up), keeps the fastest for the scene and, if info is not NULL,
+ * reports the choice and the timings (ms).  hr_set_tuning sets a choice
+ * directly (HR_ERR_INVALID_ARG when out of range).  Scenes start at variant 0
+ * and 32 sampler threads.
+ * ------------------------------------------------------------------------- */
+typedef struct {
+    int32_t render_variant;     /* chosen render variant */
+    int32_t sample_threads;     /* chosen sampler threads per block */
+    int32_t n_render_variants;
+    int32_t n_sample_variants;  /* 3: 32, 64, 128 threads */
+    float render_ms[4];         /* median render+loss time per variant */
+    float sample_ms[4];         /* median sampler time per shape */
+} hr_tune_info;
+
+hr_status hr_autotune(hr_scene scene, const double* h_theta, int32_t n_probe, hr_tune_info* info);
+hr_status hr_set_tuning(hr_scene scene, int32_t render_variant, int32_t sample_threads);
+
 /* Thread-local message of the last failure (empty if none); returns the
  * message length.  buf may be NULL to query the length. */
 size_t hr_last_error(char* buf, size_t len);

@@ -241,6 +241,7 @@ hr_status run_estimate(hr_scene_s* s, int quantity, const double* h_theta, const
     sa.w = (float*)ws.w.ptr;
     sa.invS = nullptr;
     sa.meta = (uint2*)ws.meta.ptr;
+    sa.threads = s->sc.sample_threads;
     if (s->profile) cudaEventRecord(s->ev[0], stream);
     launch_sample(sa, G, P, stream);
     if (s->profile) cudaEventRecord(s->ev[1], stream);
@@ -353,6 +354,7 @@ hr_status run_hvp_fd(hr_scene_s* s, const double* h_theta, const double* h_v, do
     sa.tau = (float*)ws.tau.ptr;
     sa.w = (float*)ws.w.ptr;
     sa.meta = (uint2*)ws.meta.ptr;
+    sa.threads = s->sc.sample_threads;
     launch_sample(sa, G, P, stream);
     RenderBatch rb{};
     rb.M = (int32_t)(2 * Mt);

@@ -36,6 +36,7 @@ struct SampleArgs {
     uint2* meta;          // [M] (sub, pair k) or null
     const int32_t* step;  // optional device step index s: every group's sub += 64 s
     const double* sigma_row;  // optional [rows]: group sigma = sigma_row[theta_row] (Z's derived in-kernel)
+    int32_t threads;          // threads per block: 32 (0 = 32), 64 or 128; no effect on the results
 };
 
 void launch_sample(const SampleArgs& a, int n_groups, int max_P, cudaStream_t s);
@@ -163,7 +164,13 @@ struct DevScene {
     float emission[3] = {0, 0, 0};
     int spp = 0, target_spp = 0, depth = 0;
     uint64_t scene_seed = 0;
+    // launch shapes picked by the autotuner; none of them changes a result
+    int render_variant = 0;       // index into render_variant_count(kind)
+    int sample_threads = 32;
 };
+
+// launch-shape variants of a scene kind's render+loss kernel (1 = none)
+int render_variant_count(int kind);
 
 void revolve_prepare(DevScene& sc, cudaStream_t s);   // normals, smem size
 void revolve_tile_t2(DevScene& sc, cudaStream_t s);   // after the target exists

@@ -201,6 +201,7 @@ hr_status enqueue_eval(hr_ncg_s* st) {
     sa.meta = (uint2*)st->meta.ptr;
     sa.step = (const int32_t*)st->evc.ptr;
     sa.sigma_row = (const double*)st->sigma.ptr;
+    sa.threads = sc.sample_threads;
     launch_sample(sa, 2 * B, (o.n_grad > o.n_hvp ? o.n_grad : o.n_hvp) / 2, st->stream);
     ncg_theta32_kernel<<<(B * n + 127) / 128, 128, 0, st->stream>>>((const double*)st->theta.ptr,
                                                                      (float*)st->theta32.ptr, B * n);

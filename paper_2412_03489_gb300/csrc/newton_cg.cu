@@ -177,6 +177,7 @@ hr_status enqueue_step(hr_optstate_s* st) {
     sa.meta = (uint2*)st->meta.ptr;
     sa.step = (const int32_t*)st->step.ptr;
     const int maxP = (st->Mg > st->Mh ? st->Mg : st->Mh) / 2;
+    sa.threads = sc.sample_threads;
     launch_sample(sa, B * (1 + st->K), maxP, st->stream);
     theta32_kernel<<<(B * n + 127) / 128, 128, 0, st->stream>>>((const double*)st->theta.ptr, (float*)st->theta32.ptr,
                                                                  B * n);

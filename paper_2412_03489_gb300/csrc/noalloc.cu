@@ -151,6 +151,7 @@ extern "C" hr_status hr_estimate_dev_noalloc(hr_scene s, int32_t quantity, const
     sa.invS = nullptr;
     sa.meta = reinterpret_cast<uint2*>(base + off_meta);
     sa.step = nullptr;
+    sa.threads = sc.sample_threads;
     launch_sample(sa, G, (int)(M / 2), stream);
 
     RenderBatch rb{};

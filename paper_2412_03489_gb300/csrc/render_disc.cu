@@ -9,7 +9,6 @@
 namespace hr {
 namespace {
 
-constexpr int kWarps = 8;
 
 __device__ __forceinline__ float disc_value(int x, int y, float invW_dummy, int W, int H, float cx, float cy, float r2) {
     (void)invW_dummy;
@@ -21,10 +20,11 @@ __device__ __forceinline__ float disc_value(int x, int y, float invW_dummy, int 
     return d2 < r2 ? 1.0f : 0.0f;
 }
 
-__global__ void __launch_bounds__(32 * kWarps) disc_loss_kernel(RenderBatch b, int W, int H, float radius,
-                                                                const float* __restrict__ target) {
+template <int kW>
+__global__ void __launch_bounds__(32 * kW) disc_loss_kernel(RenderBatch b, int W, int H, float radius,
+                                                            const float* __restrict__ target) {
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    const int m = blockIdx.x * kWarps + warp;
+    const int m = blockIdx.x * kW + warp;
     if (m >= b.M) return;
     const Pert pt = resolve(b, m);
     const float cx = __fadd_rn(pt.theta[0], pt.tau[0]);
@@ -60,11 +60,12 @@ __device__ __forceinline__ float boxes_value(int x, int y, int W, int H, const f
 
 constexpr int kMaxBoxParams = 64;
 
-__global__ void __launch_bounds__(32 * kWarps) boxes_loss_kernel(RenderBatch b, int W, int H, float h,
-                                                                 const float* __restrict__ target) {
-    __shared__ float s_c[kWarps][kMaxBoxParams];
+template <int kW>
+__global__ void __launch_bounds__(32 * kW) boxes_loss_kernel(RenderBatch b, int W, int H, float h,
+                                                             const float* __restrict__ target) {
+    __shared__ float s_c[kW][kMaxBoxParams];
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    const int m = blockIdx.x * kWarps + warp;
+    const int m = blockIdx.x * kW + warp;
     if (m >= b.M) return;
     const Pert pt = resolve(b, m);
     for (int d = lane; d < b.n; d += 32) s_c[warp][d] = __fadd_rn(pt.theta[d], pt.tau[d]);
@@ -90,9 +91,14 @@ __global__ void boxes_image_kernel(const float* params, int K, int W, int H, flo
 
 }  // namespace
 
+// Launch-shape variants (autotuner): 8, 4 or 16 warps per CTA; one warp
+// renders one perturbation in every shape, so the choice never changes a result.
 void launch_boxes_loss(const DevScene& sc, const RenderBatch& b, cudaStream_t s) {
-    const int blocks = (b.M + kWarps - 1) / kWarps;
-    boxes_loss_kernel<<<blocks, 32 * kWarps, 0, s>>>(b, sc.W, sc.H, sc.radius, sc.target);
+    switch (sc.render_variant) {
+        case 1: boxes_loss_kernel<4><<<(b.M + 3) / 4, 128, 0, s>>>(b, sc.W, sc.H, sc.radius, sc.target); break;
+        case 2: boxes_loss_kernel<16><<<(b.M + 15) / 16, 512, 0, s>>>(b, sc.W, sc.H, sc.radius, sc.target); break;
+        default: boxes_loss_kernel<8><<<(b.M + 7) / 8, 256, 0, s>>>(b, sc.W, sc.H, sc.radius, sc.target); break;
+    }
 }
 
 void launch_boxes_image(const DevScene& sc, const float* params, float* img, cudaStream_t s) {
@@ -101,8 +107,11 @@ void launch_boxes_image(const DevScene& sc, const float* params, float* img, cud
 }
 
 void launch_disc_loss(const DevScene& sc, const RenderBatch& b, cudaStream_t s) {
-    const int blocks = (b.M + kWarps - 1) / kWarps;
-    disc_loss_kernel<<<blocks, 32 * kWarps, 0, s>>>(b, sc.W, sc.H, sc.radius, sc.target);
+    switch (sc.render_variant) {
+        case 1: disc_loss_kernel<4><<<(b.M + 3) / 4, 128, 0, s>>>(b, sc.W, sc.H, sc.radius, sc.target); break;
+        case 2: disc_loss_kernel<16><<<(b.M + 15) / 16, 512, 0, s>>>(b, sc.W, sc.H, sc.radius, sc.target); break;
+        default: disc_loss_kernel<8><<<(b.M + 7) / 8, 256, 0, s>>>(b, sc.W, sc.H, sc.radius, sc.target); break;
+    }
 }
 
 void launch_disc_image(const DevScene& sc, const float* params, float* img, cudaStream_t s) {

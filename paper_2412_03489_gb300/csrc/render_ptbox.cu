@@ -224,8 +224,8 @@ __device__ void load_scene(const PtArgs& A, const float* p, PtShared& S) {
     }
 }
 
-template <bool kImage>
-__global__ void __launch_bounds__(kThreads, 3)
+template <bool kImage, int kMinBlocks>
+__global__ void __launch_bounds__(kThreads, kMinBlocks)
 ptbox_kernel(PtArgs A, RenderBatch b, const float* __restrict__ img_params, uint64_t seed_img, uint32_t req_img,
              uint32_t sub_img, uint32_t k_img, uint32_t tag_img, int spp_img, float* __restrict__ img) {
     __shared__ PtShared S;
@@ -310,14 +310,22 @@ PtArgs make_args(const DevScene& sc) {
 
 }  // namespace
 
+// Launch-shape variants (autotuner): the same 256-thread layout and
+// arithmetic, different register caps through the minimum number of resident
+// CTAs per SM (3, 2, 4), so the choice never changes a result.
 void launch_ptbox_loss(const DevScene& sc, const RenderBatch& b, cudaStream_t s) {
-    ptbox_kernel<false><<<b.M, kThreads, 0, s>>>(make_args(sc), b, nullptr, 0, 0, 0, 0, 0, 0, nullptr);
+    const PtArgs a = make_args(sc);
+    switch (sc.render_variant) {
+        case 1: ptbox_kernel<false, 2><<<b.M, kThreads, 0, s>>>(a, b, nullptr, 0, 0, 0, 0, 0, 0, nullptr); break;
+        case 2: ptbox_kernel<false, 4><<<b.M, kThreads, 0, s>>>(a, b, nullptr, 0, 0, 0, 0, 0, 0, nullptr); break;
+        default: ptbox_kernel<false, 3><<<b.M, kThreads, 0, s>>>(a, b, nullptr, 0, 0, 0, 0, 0, 0, nullptr); break;
+    }
 }
 
 void launch_ptbox_image(const DevScene& sc, const float* params, uint64_t seed, uint32_t request, uint32_t sub,
                         uint32_t k, uint32_t tag, int spp, float* img, cudaStream_t s) {
     RenderBatch b{};
-    ptbox_kernel<true><<<1, kThreads, 0, s>>>(make_args(sc), b, params, seed, request, sub, k, tag, spp, img);
+    ptbox_kernel<true, 3><<<1, kThreads, 0, s>>>(make_args(sc), b, params, seed, request, sub, k, tag, spp, img);
 }
 
 }  // namespace hr

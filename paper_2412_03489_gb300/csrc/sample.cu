@@ -192,9 +192,9 @@ __device__ void write_weights(const SampleArgs& a, const Lobes& L, const SampleG
     }
 }
 
-constexpr int kSampleThreads = 32;   // FP64-latency bound: spread pairs over many SMs
+constexpr int kSampleThreadsMax = 128;   // launch shapes 32 / 64 / 128 threads per block
 
-__global__ void __launch_bounds__(kSampleThreads) sample_kernel(SampleArgs a) {
+__global__ void __launch_bounds__(kSampleThreadsMax) sample_kernel(SampleArgs a) {
     const SampleGroup G = a.groups[blockIdx.y];
     const int k = blockIdx.x * blockDim.x + threadIdx.x;
     if (k >= G.P) return;
@@ -349,8 +349,10 @@ __global__ void __launch_bounds__(kFinThreads) finalize_kernel(FinalizeArgs a) {
 }  // namespace
 
 void launch_sample(const SampleArgs& a, int n_groups, int max_P, cudaStream_t s) {
-    dim3 grid((max_P + kSampleThreads - 1) / kSampleThreads, n_groups);
-    sample_kernel<<<grid, kSampleThreads, 0, s>>>(a);
+    // FP64-latency bound: few threads per block spread the pairs over many SMs
+    const int t = (a.threads == 64 || a.threads == 128) ? a.threads : 32;
+    dim3 grid((max_P + t - 1) / t, n_groups);
+    sample_kernel<<<grid, t, 0, s>>>(a);
 }
 
 void launch_finalize(const FinalizeArgs& a, cudaStream_t s) {

@@ -260,6 +260,7 @@ void hr_server_s::setup(SrvReq* r) {
     sa.invS = nullptr;
     sa.meta = r->meta;
     sa.step = nullptr;
+    sa.threads = r->req.scene->sc.sample_threads;
     launch_sample(sa, r->G, r->P, L.stream);
     // the upload event may be reused once the lane has consumed it
     cudaEventRecord(up_ev, L.stream);

@@ -77,6 +77,12 @@ class hr_ncg_info(ctypes.Structure):
                 ("step_norm", ctypes.c_double)]
 
 
+class hr_tune_info(ctypes.Structure):
+    _fields_ = [("render_variant", ctypes.c_int32), ("sample_threads", ctypes.c_int32),
+                ("n_render_variants", ctypes.c_int32), ("n_sample_variants", ctypes.c_int32),
+                ("render_ms", ctypes.c_float * 4), ("sample_ms", ctypes.c_float * 4)]
+
+
 class hr_server_opts(ctypes.Structure):
     _fields_ = [("hbm_budget", ctypes.c_int64), ("max_active", ctypes.c_int32), ("chunk", ctypes.c_int32)]
 
@@ -129,6 +135,8 @@ def lib() -> ctypes.CDLL:
         L.hr_ncg_destroy.argtypes = [vp]
         L.hr_ncg_run.argtypes = [vp, vp, ctypes.c_int32, ctypes.POINTER(hr_ncg_info)]
         L.hr_ncg_theta.argtypes = [vp, _f64p]
+        L.hr_autotune.argtypes = [vp, _f64p, ctypes.c_int32, ctypes.POINTER(hr_tune_info)]
+        L.hr_set_tuning.argtypes = [vp, ctypes.c_int32, ctypes.c_int32]
         L.hr_profile_enable.argtypes = [vp, ctypes.c_int32]
         L.hr_profile_last.argtypes = [vp, _f32p]
         L.hr_server_create.argtypes = [ctypes.POINTER(hr_server_opts), ctypes.POINTER(vp)]
@@ -143,7 +151,8 @@ def lib() -> ctypes.CDLL:
                      "hr_render", "hr_optstate_create",
                      "hr_optstate_destroy", "hr_newton_cg_step", "hr_optstate_theta", "hr_profile_enable",
                      "hr_profile_last", "hr_server_create", "hr_server_destroy", "hr_server_submit",
-                     "hr_server_wait", "hr_ncg_create", "hr_ncg_destroy", "hr_ncg_run", "hr_ncg_theta"):
+                     "hr_server_wait", "hr_ncg_create", "hr_ncg_destroy", "hr_ncg_run", "hr_ncg_theta",
+                     "hr_autotune", "hr_set_tuning"):
             getattr(L, name).restype = ctypes.c_int32
         L.hr_version.restype = ctypes.c_int32
         _lib = L
@@ -259,6 +268,17 @@ def hr_optstate_theta(st, out):
 
 def hr_optstate_destroy(st):
     check(lib().hr_optstate_destroy(st), "hr_optstate_destroy")
+
+
+def hr_autotune(handle, theta, n_probe=1024) -> hr_tune_info:
+    info = hr_tune_info()
+    th = np.ascontiguousarray(theta, np.float64)
+    check(lib().hr_autotune(handle, _ptr(th, _f64p), int(n_probe), ctypes.byref(info)), "hr_autotune")
+    return info
+
+
+def hr_set_tuning(handle, render_variant, sample_threads):
+    check(lib().hr_set_tuning(handle, int(render_variant), int(sample_threads)), "hr_set_tuning")
 
 
 def hr_ncg_create(handle, n_instances, theta0, opts: hr_ncg_opts) -> int:

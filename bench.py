@@ -129,7 +129,7 @@ def measured_peaks():
     return {"hbm_gbs": 6800.0, "sm_max_mhz": 2070.0}, "fallback"
 
 
-def cpu_baseline(sc, theta, sample=1024, threads=1):
+def cpu_baseline(sc, theta, sample=1024, threads=1, keep_estimate=False):
     """The oracle (plain C renders, FP64 sums) on the first `sample`
     perturbations of the same estimate, the renders split over `threads`
     host threads (contiguous slices; the C calls run without the GIL);
@@ -150,14 +150,32 @@ def cpu_baseline(sc, theta, sample=1024, threads=1):
         cut = np.linspace(0, sample, threads + 1).astype(int)
         with ThreadPoolExecutor(threads) as ex:
             losses = np.concatenate(list(ex.map(lambda i: np.array(part(cut[i], cut[i + 1])), range(threads))))
-    _ = (w * losses[:, None]).sum(0)
+    wl_ = w * losses[:, None]
+    flat = np.array([math.fsum(wl_[:, e]) for e in range(w.shape[1])]) / sample
     t2 = time.perf_counter()
     per_render = (t2 - t1) / sample
     est_s = per_render * M_PERTURB + (t1 - t0) * M_PERTURB / sample
-    return {"value": 1.0 / est_s, "unit": "estimates/s", "cores": max(1, threads), "kind": "oracle",
-            "sample": f"{sample} of the {M_PERTURB} perturbations of one estimate (plain C renders, FP64 sums) "
-                      f"on {max(1, threads)} host thread(s), scaled to one full estimate",
-            "renders_per_s": 1.0 / per_render}
+    out = {"value": 1.0 / est_s, "unit": "estimates/s", "cores": max(1, threads), "kind": "oracle",
+           "sample": f"{sample} of the {M_PERTURB} perturbations of one estimate (plain C renders, FP64 sums) "
+                     f"on {max(1, threads)} host thread(s), scaled to one full estimate",
+           "renders_per_s": 1.0 / per_render}
+    if keep_estimate and sample == M_PERTURB:
+        # the oracle's own estimate of request 0 (upper triangle) and the sums' scale
+        out["_estimate"] = flat
+        out["_scale"] = np.array([math.fsum(np.abs(wl_[:, e])) for e in range(w.shape[1])]) / sample
+    return out
+
+
+def oracle_match(hr, S, sc, theta, cb):
+    """Error of the GPU estimate of request 0 against the oracle's estimate of
+    the same request on the same perturbations: max over the Hessian's unique
+    entries of |gpu - oracle| / max(|oracle|, A_e), A_e = 1/(2P) sum |w f|."""
+    H = S.estimate(hr.HR_HESSIAN, theta, sc["sigma"], M_PERTURB, hr.HR_AGGREGATE, SEED, 0)
+    gpu = H[np.triu_indices(2)]
+    ref, scale = cb.pop("_estimate"), cb.pop("_scale")
+    rel = np.abs(gpu - ref) / np.maximum(np.abs(ref), scale)
+    return {"max_rel_err": float(rel.max()), "tolerance": 1e-4, "entries": int(rel.size),
+            "request": 0, "gpu": gpu.tolist(), "oracle": ref.tolist()}
 
 
 def host_threads():
@@ -217,7 +235,7 @@ def tune_scene(hr, S, theta, n_probe):
     return {"render_variant": i.render_variant, "sample_threads": i.sample_threads,
             "render_ms": [round(i.render_ms[k], 4) for k in range(i.n_render_variants)],
             "sample_ms": [round(i.sample_ms[k], 4) for k in range(i.n_sample_variants)],
-            "probe_perturbations": n_probe}
+            "probe_perturbations_requested": n_probe}
 
 
 def _timed_steps(torch, stream, flush, fn, warmup, steps):
@@ -257,7 +275,7 @@ def run_secondary(args):
         d_theta = torch.tensor(sc["theta_query"], dtype=torch.float64, device="cuda")
         d_v = torch.tensor(sc.get("v", np.ones(n)), dtype=torch.float64, device="cuda")
         d_out = torch.zeros((n, n), dtype=torch.float64, device="cuda")
-        line["tuning"] = tune_scene(hr, S, sc["theta_query"], 1024 if args.workload == "disc" else 256)
+        line["tuning"] = tune_scene(hr, S, sc["theta_query"], 2048)
         hr.hr_profile_enable(S.handle, True)
         variants = ([("hessian_elementwise_3x1024", hr.HR_HESSIAN, hr.HR_ELEMENTWISE, 1024, 3 * 1024),
                      ("hessian_aggregate_1024", hr.HR_HESSIAN, hr.HR_AGGREGATE, 1024, 1024)]
@@ -673,7 +691,8 @@ def main():
                 "clocks": clk}
         if not args.no_cpu_baseline:
             threads = host_threads()
-            line["cpu_baseline"] = cpu_baseline(sc, theta, sample=M_PERTURB, threads=threads)
+            line["cpu_baseline"] = cpu_baseline(sc, theta, sample=M_PERTURB, threads=threads, keep_estimate=True)
+            line["oracle_match"] = oracle_match(hr, S, sc, theta, line["cpu_baseline"])
             line["cpu_baseline"]["single_thread"] = cpu_baseline(sc, theta, sample=256, threads=1)
         print(json.dumps(line))
     S.close()

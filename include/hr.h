@@ -423,8 +423,9 @@ hr_status hr_profile_last(hr_scene scene, float* ms3);
  * 32, 64 or 128 threads per block.  Every variant computes the same values in
  * the same order, so results are bit-identical whatever is chosen.
  * hr_autotune times each variant on profiled aggregate HVP estimates of
- * n_probe perturbations at h_theta [n] (v = ones, sigma 0.05; median of 3
- * after a warm-up), keeps the fastest for the scene and, if info is not NULL,
+ * max(n_probe, 8 x the SM count) perturbations at h_theta [n] (v = ones,
+ * sigma 0.05; median of 3 after a warm-up; the floor keeps the GPU full so
+ * that occupancy shows), keeps the fastest for the scene and, if info is not NULL,
  * reports the choice and the timings (ms).  hr_set_tuning sets a choice
  * directly (HR_ERR_INVALID_ARG when out of range).  Scenes start at variant 0
  * and 32 sampler threads.

@@ -78,9 +78,13 @@ hr_status hr_autotune(hr_scene s, const double* h_theta, int32_t n_probe, hr_tun
     s->profile = true;
     const int n = s->sc.n;
     std::vector<double> v(n, 1.0);
+    // a probe that fills the GPU several times over, so that the shapes'
+    // occupancy shows in the timings (one render per CTA in the path tracer)
+    const int min_probe = 8 * num_sms();
+    const int probe_m = n_probe >= min_probe ? n_probe : (min_probe + 1) & ~1;
     hr_opts o{};
     o.sigma = 0.05;
-    o.n_perturb = n_probe;
+    o.n_perturb = probe_m;
     o.strategy = HR_AGGREGATE;
     o.seed = 0x7E57;
     o.request_id = 0;

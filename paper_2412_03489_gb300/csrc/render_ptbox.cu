@@ -90,11 +90,60 @@ __device__ int intersect(const PtShared& S, const float o[3], const float d[3], 
     return prim;
 }
 
+// The same closest-hit rule with the quad axes known at compile time: the
+// layout the procedural box always has (box walls and block faces two per
+// axis, x x y y z z, then the horizontal light).  Fully unrolled and
+// predicated: every quad is tested in index order with the same operation
+// sequence and the same acceptance (axis direction non-zero, t > 0, hit
+// inside the closed rectangle, t < best), so it returns what the general
+// loop returns.
+__device__ __noinline__ int intersect_canon(const PtShared& S, const float o[3], const float d[3], float& t_out) {
+    constexpr int kAxis[13] = {0, 0, 1, 1, 2, 2, 0, 0, 1, 1, 2, 2, 1};
+    float best = INFINITY;
+    int prim = -1;
+    const float inv[3] = {__frcp_rn(d[0]), __frcp_rn(d[1]), __frcp_rn(d[2])};
+#pragma unroll
+    for (int q = 0; q <= kLight; ++q) {
+        const int a = kAxis[q];
+        const int u = a == 0 ? 1 : 0, v = a == 2 ? 1 : 2;
+        const QuadS Q = S.q[q];
+        const float t = __fmul_rn(__fsub_rn(Q.plane, o[a]), inv[a]);
+        const float hu = __fmaf_rn(t, d[u], o[u]);
+        const float hv = __fmaf_rn(t, d[v], o[v]);
+        const bool ok = d[a] != 0.0f && t > 0.0f && !(hu < Q.lo_u || hu > Q.hi_u || hv < Q.lo_v || hv > Q.hi_v) &&
+                        t < best;
+        best = ok ? t : best;
+        prim = ok ? q : prim;
+    }
+#pragma unroll
+    for (int i = 0; i < 3; ++i) {
+        const float4 sp = S.sph[i];
+        const float oc[3] = {__fsub_rn(o[0], sp.x), __fsub_rn(o[1], sp.y), __fsub_rn(o[2], sp.z)};
+        const float b = dot3(oc, d);
+        const float cc = __fsub_rn(dot3(oc, oc), sp.w);
+        const float disc = __fmaf_rn(b, b, -cc);
+        const float sq = __fsqrt_rn(fmaxf(disc, 0.0f));
+        const float t0 = __fsub_rn(-b, sq), t1 = __fsub_rn(sq, b);
+        const float t = t0 > 0.0f ? t0 : t1;
+        const bool ok = disc >= 0.0f && t > 0.0f && t < best;   // NaN disc rejects, as in the loop
+        best = ok ? t : best;
+        prim = ok ? 13 + i : prim;
+    }
+    t_out = best;
+    return prim;
+}
+
+template <bool kCanon>
+__device__ __forceinline__ int closest_hit(const PtShared& S, const float o[3], const float d[3], float& t_out) {
+    return kCanon ? intersect_canon(S, o, d, t_out) : intersect(S, o, d, t_out);
+}
+
+template <bool kCanon>
 __device__ void radiance(const PtShared& S, int depth, uint64_t seed, uint32_t request, uint32_t c2, uint32_t k,
                          uint32_t idx, float o[3], float d[3], float L[3]) {
     float beta[3] = {1.0f, 1.0f, 1.0f};
     float t;
-    int prim = intersect(S, o, d, t);
+    int prim = closest_hit<kCanon>(S, o, d, t);
     if (prim < 0) return;
     if (prim == kLight) {
         if (d[1] > 0.0f) { L[0] += S.em[0]; L[1] += S.em[1]; L[2] += S.em[2]; }
@@ -136,7 +185,7 @@ __device__ void radiance(const PtShared& S, int depth, uint64_t seed, uint32_t r
             const float cosl = om[1];
             if (cosx > 0.0f && cosl > 0.0f) {
                 float ts;
-                if (intersect(S, o2, om, ts) == kLight) {
+                if (closest_hit<kCanon>(S, o2, om, ts) == kLight) {
                     const float geo = cosx * cosl / dist2 * area * kInvPi;
 #pragma unroll
                     for (int c = 0; c < 3; ++c) L[c] += beta[c] * rho[c] * S.em[c] * geo;
@@ -175,7 +224,7 @@ __device__ void radiance(const PtShared& S, int depth, uint64_t seed, uint32_t r
         for (int c = 0; c < 3; ++c) nd[c] = __fmaf_rn(cz, n[c], __fmaf_rn(b, t2[c], __fmul_rn(a, t1[c])));
 #pragma unroll
         for (int c = 0; c < 3; ++c) beta[c] *= rho[c];
-        prim = intersect(S, o2, nd, t);
+        prim = closest_hit<kCanon>(S, o2, nd, t);
         if (prim < 0) return;
 #pragma unroll
         for (int c = 0; c < 3; ++c) { o[c] = o2[c]; d[c] = nd[c]; }
@@ -224,7 +273,7 @@ __device__ void load_scene(const PtArgs& A, const float* p, PtShared& S) {
     }
 }
 
-template <bool kImage, int kMinBlocks>
+template <bool kImage, int kMinBlocks, bool kCanon>
 __global__ void __launch_bounds__(kThreads, kMinBlocks)
 ptbox_kernel(PtArgs A, RenderBatch b, const float* __restrict__ img_params, uint64_t seed_img, uint32_t req_img,
              uint32_t sub_img, uint32_t k_img, uint32_t tag_img, int spp_img, float* __restrict__ img) {
@@ -266,7 +315,7 @@ ptbox_kernel(PtArgs A, RenderBatch b, const float* __restrict__ img_params, uint
             const float il = __frcp_rn(__fsqrt_rn(dot3(d, d)));
             d[0] = __fmul_rn(d[0], il); d[1] = __fmul_rn(d[1], il); d[2] = __fmul_rn(d[2], il);
             float o[3] = {0.0f, 0.0f, A.cam_z};
-            radiance(S, A.depth, seed, request, c2, k, idx, o, d, L);
+            radiance<kCanon>(S, A.depth, seed, request, c2, k, idx, o, d, L);
         }
         const size_t p3 = 3 * (size_t)px;
         if (kImage) {
@@ -308,24 +357,42 @@ PtArgs make_args(const DevScene& sc) {
     return a;
 }
 
+// quad axes of the procedural box (walls, then block faces: x x y y z z)
+bool canonical_axes(const DevScene& sc) {
+    static const int kAxis[12] = {0, 0, 1, 1, 2, 2, 0, 0, 1, 1, 2, 2};
+    for (int q = 0; q < 12; ++q)
+        if (sc.qaxis[q] != kAxis[q]) return false;
+    return true;
+}
+
+template <bool kCanon>
+void launch_loss(const DevScene& sc, const RenderBatch& b, cudaStream_t s) {
+    const PtArgs a = make_args(sc);
+    switch (sc.render_variant) {
+        case 1: ptbox_kernel<false, 2, kCanon><<<b.M, kThreads, 0, s>>>(a, b, nullptr, 0, 0, 0, 0, 0, 0, nullptr); break;
+        case 2: ptbox_kernel<false, 4, kCanon><<<b.M, kThreads, 0, s>>>(a, b, nullptr, 0, 0, 0, 0, 0, 0, nullptr); break;
+        default: ptbox_kernel<false, 3, kCanon><<<b.M, kThreads, 0, s>>>(a, b, nullptr, 0, 0, 0, 0, 0, 0, nullptr); break;
+    }
+}
+
 }  // namespace
 
 // Launch-shape variants (autotuner): the same 256-thread layout and
 // arithmetic, different register caps through the minimum number of resident
-// CTAs per SM (3, 2, 4), so the choice never changes a result.
+// CTAs per SM (3, 2, 4), so the choice never changes a result.  Scenes with
+// the procedural box's quad layout use the compile-time-axis intersection.
 void launch_ptbox_loss(const DevScene& sc, const RenderBatch& b, cudaStream_t s) {
-    const PtArgs a = make_args(sc);
-    switch (sc.render_variant) {
-        case 1: ptbox_kernel<false, 2><<<b.M, kThreads, 0, s>>>(a, b, nullptr, 0, 0, 0, 0, 0, 0, nullptr); break;
-        case 2: ptbox_kernel<false, 4><<<b.M, kThreads, 0, s>>>(a, b, nullptr, 0, 0, 0, 0, 0, 0, nullptr); break;
-        default: ptbox_kernel<false, 3><<<b.M, kThreads, 0, s>>>(a, b, nullptr, 0, 0, 0, 0, 0, 0, nullptr); break;
-    }
+    if (canonical_axes(sc)) launch_loss<true>(sc, b, s);
+    else launch_loss<false>(sc, b, s);
 }
 
 void launch_ptbox_image(const DevScene& sc, const float* params, uint64_t seed, uint32_t request, uint32_t sub,
                         uint32_t k, uint32_t tag, int spp, float* img, cudaStream_t s) {
     RenderBatch b{};
-    ptbox_kernel<true, 3><<<1, kThreads, 0, s>>>(make_args(sc), b, params, seed, request, sub, k, tag, spp, img);
+    if (canonical_axes(sc))
+        ptbox_kernel<true, 3, true><<<1, kThreads, 0, s>>>(make_args(sc), b, params, seed, request, sub, k, tag, spp, img);
+    else
+        ptbox_kernel<true, 3, false><<<1, kThreads, 0, s>>>(make_args(sc), b, params, seed, request, sub, k, tag, spp, img);
 }
 
 }  // namespace hr

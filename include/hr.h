@@ -109,7 +109,11 @@ typedef struct {
     float radius;
     /* REVOLVE3D: model-space vertices [n_vertices][3], triangles [n_triangles][3]
        (outward winding), albedo RGB, unit light direction, camera distance on +z
-       and projection scale (pixels per unit of X/Z) */
+       and projection scale (pixels per unit of X/Z).  One render's triangle
+       records, projected vertices and tile bins live in shared memory
+       (72 B per triangle + 12 B per vertex + 8 B per 8x8 tile + 32 KB of bins,
+       within 227 KB): about 2,400 triangles at 256x256 on a GB300; larger
+       meshes are rejected with HR_ERR_UNSUPPORTED */
     const float* vertices;
     int32_t n_vertices;
     const int32_t* triangles;
@@ -118,7 +122,8 @@ typedef struct {
     float light[3];
     float eye_dist;
     float scale;
-    /* TRIS2D: raw params [n_tris][9], optimised subset param_index[n_params] */
+    /* TRIS2D: raw params [n_tris][9] (n_tris <= 32), optimised subset
+       param_index[n_params] (n_params <= 64) */
     const float* raw_params;
     int32_t n_tris;
     const int32_t* param_index;

@@ -231,6 +231,14 @@ def test_invalid_arguments_are_rejected():
     Sc.close()
 
 
+def test_mesh_beyond_shared_memory_is_rejected():
+    sc = wl.revolve_scene()
+    verts, tris = wl.revolve_mesh(np.linspace(0.3, 0.8, 8), rings=65, slices=64)   # 8,192 triangles
+    sc = dict(sc, vertices=verts, triangles=tris)
+    with pytest.raises(hr.HRError, match="status -6"):
+        hr.Scene(sc)
+
+
 # ---------------------------------------------------------------------------
 # HVP forms: element-wise (row mixtures) and central difference of gradients
 # ---------------------------------------------------------------------------

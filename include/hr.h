@@ -113,7 +113,8 @@ typedef struct {
        records, projected vertices and tile bins live in shared memory
        (72 B per triangle + 12 B per vertex + 8 B per 8x8 tile + 32 KB of bins,
        within 227 KB): about 2,400 triangles at 256x256 on a GB300; larger
-       meshes are rejected with HR_ERR_UNSUPPORTED */
+       meshes are rejected with HR_ERR_UNSUPPORTED.  At most HR_MAX_VERTICES
+       vertices and HR_MAX_TRIANGLES triangles (else HR_ERR_INVALID_ARG). */
     const float* vertices;
     int32_t n_vertices;
     const int32_t* triangles;

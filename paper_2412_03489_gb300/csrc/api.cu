@@ -433,8 +433,9 @@ hr_status hr_create_scene(const hr_scene_desc* d, hr_scene* out) {
             break;
         case HR_SCENE_REVOLVE3D: expect_n = 2;
             if (!d->vertices || !d->triangles || d->n_vertices < 3 || d->n_triangles < 1 ||
-                d->n_vertices > HR_MAX_VERTICES || d->n_triangles > 2048)
-                return fail(HR_ERR_INVALID_ARG, "mesh needs 3..%d vertices and 1..2048 triangles", HR_MAX_VERTICES);
+                d->n_vertices > HR_MAX_VERTICES || d->n_triangles > HR_MAX_TRIANGLES)
+                return fail(HR_ERR_INVALID_ARG, "mesh needs 3..%d vertices and 1..%d triangles", HR_MAX_VERTICES,
+                            HR_MAX_TRIANGLES);
             if (d->width > 512 || d->height > 512) return fail(HR_ERR_UNSUPPORTED, "mesh images are at most 512x512");
             for (int i = 0; i < 3 * d->n_triangles; ++i)
                 if (d->triangles[i] < 0 || d->triangles[i] >= d->n_vertices)

@@ -233,10 +233,13 @@ def test_invalid_arguments_are_rejected():
 
 def test_mesh_beyond_shared_memory_is_rejected():
     sc = wl.revolve_scene()
-    verts, tris = wl.revolve_mesh(np.linspace(0.3, 0.8, 8), rings=65, slices=64)   # 8,192 triangles
-    sc = dict(sc, vertices=verts, triangles=tris)
+    verts, tris = wl.revolve_mesh(np.linspace(0.3, 0.8, 8), rings=41, slices=40)   # 3,200 triangles
+    assert len(tris) == 3200
     with pytest.raises(hr.HRError, match="status -6"):
-        hr.Scene(sc)
+        hr.Scene(dict(sc, vertices=verts, triangles=tris))
+    verts, tris = wl.revolve_mesh(np.linspace(0.3, 0.8, 8), rings=65, slices=64)   # 8,192: over the format limit
+    with pytest.raises(hr.HRError, match="status -1"):
+        hr.Scene(dict(sc, vertices=verts, triangles=tris))
 
 
 # ---------------------------------------------------------------------------

@@ -704,7 +704,7 @@ def main():
                 "e2e": {"value": 1.0 / e2e_s, "unit": "estimates/s", "h2d_bytes_per_step": 8 + 40,
                         "d2h_bytes_per_step": 32},
                 "stage_ms": dict(zip(("sample", "render_loss", "sums"), np.mean(stage_ms, axis=0).tolist())),
-                "gpu_launches": 3 * args.steps,
+                "gpu_launches": 4 * args.steps,   # theta to FP32, sampler, render + loss, sums
                 "tuning": tuning,
                 "clocks": clk}
         if not args.no_cpu_baseline:

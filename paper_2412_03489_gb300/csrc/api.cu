@@ -117,6 +117,11 @@ __global__ void fd_combine_kernel(const double* gp, const double* gm, double inv
     if (i < n) out[i] = (gp[i] - gm[i]) * inv2eps;
 }
 
+struct ThetaArg { float v[64]; };
+__global__ void set_theta_kernel(ThetaArg a, float* out, int n) {
+    if ((int)threadIdx.x < n) out[threadIdx.x] = a.v[threadIdx.x];
+}
+
 __global__ void f64_to_f32_kernel(const double* in, float* out, int n) {
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i < n) out[i] = __double2float_rn(in[i]);
@@ -185,10 +190,10 @@ hr_status run_estimate(hr_scene_s* s, int quantity, const double* h_theta, const
     } while (0)
     float* theta32 = (float*)ws.theta32.ptr;
     if (h_theta) {
-        std::vector<float> t32(n);
-        for (int i = 0; i < n; ++i) t32[i] = (float)h_theta[i];
-        CU_TRY(cudaMemcpyAsync(theta32, t32.data(), sizeof(float) * n, cudaMemcpyHostToDevice, stream));
-        CU_TRY(cudaStreamSynchronize(stream));
+        // parameters by value (n <= 64): no host staging, no wait
+        ThetaArg ta{};
+        for (int i = 0; i < n; ++i) ta.v[i] = (float)h_theta[i];
+        set_theta_kernel<<<1, 64, 0, stream>>>(ta, theta32, n);
     } else {
         f64_to_f32_kernel<<<(n + 127) / 128, 128, 0, stream>>>(d_theta, theta32, n);
     }
@@ -222,9 +227,11 @@ hr_status run_estimate(hr_scene_s* s, int quantity, const double* h_theta, const
             gr.comp_i = r; gr.comp_j = r + rem;
         }
     }
-    CU_TRY(cudaMemcpyAsync(ws.groups.ptr, s->host_groups.data(), sizeof(SampleGroup) * G, cudaMemcpyHostToDevice,
-                           stream));
-    CU_TRY(cudaStreamSynchronize(stream));   // host group table may be reused by the next call
+    if (G > kInlineGroups) {
+        CU_TRY(cudaMemcpyAsync(ws.groups.ptr, s->host_groups.data(), sizeof(SampleGroup) * G, cudaMemcpyHostToDevice,
+                               stream));
+        CU_TRY(cudaStreamSynchronize(stream));   // host group table may be reused by the next call
+    }
 
     SampleArgs sa{};
     sa.groups = (const SampleGroup*)ws.groups.ptr;
@@ -242,6 +249,10 @@ hr_status run_estimate(hr_scene_s* s, int quantity, const double* h_theta, const
     sa.invS = nullptr;
     sa.meta = (uint2*)ws.meta.ptr;
     sa.threads = s->sc.sample_threads;
+    if (G <= kInlineGroups) {
+        sa.n_inline = G;
+        for (int g = 0; g < G; ++g) sa.inline_groups[g] = s->host_groups[g];
+    }
     if (s->profile) cudaEventRecord(s->ev[0], stream);
     launch_sample(sa, G, P, stream);
     if (s->profile) cudaEventRecord(s->ev[1], stream);

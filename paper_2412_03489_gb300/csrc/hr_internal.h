@@ -37,7 +37,11 @@ struct SampleArgs {
     const int32_t* step;  // optional device step index s: every group's sub += 64 s
     const double* sigma_row;  // optional [rows]: group sigma = sigma_row[theta_row] (Z's derived in-kernel)
     int32_t threads;          // threads per block: 32 (0 = 32), 64 or 128; no effect on the results
+    // up to kInlineGroups groups passed by value (n_inline > 0: groups[] is not read)
+    int32_t n_inline;
+    SampleGroup inline_groups[4];
 };
+constexpr int kInlineGroups = 4;
 
 void launch_sample(const SampleArgs& a, int n_groups, int max_P, cudaStream_t s);
 

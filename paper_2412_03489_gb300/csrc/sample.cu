@@ -195,7 +195,7 @@ __device__ void write_weights(const SampleArgs& a, const Lobes& L, const SampleG
 constexpr int kSampleThreadsMax = 128;   // launch shapes 32 / 64 / 128 threads per block
 
 __global__ void __launch_bounds__(kSampleThreadsMax) sample_kernel(SampleArgs a) {
-    const SampleGroup G = a.groups[blockIdx.y];
+    const SampleGroup G = a.n_inline > 0 ? a.inline_groups[blockIdx.y] : a.groups[blockIdx.y];
     const int k = blockIdx.x * blockDim.x + threadIdx.x;
     if (k >= G.P) return;
     const int n = a.n;

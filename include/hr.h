@@ -426,7 +426,7 @@ hr_status hr_profile_last(hr_scene scene, float* ms3);
  * variants (path tracer: minimum resident CTAs per SM 3 / 2 / 4, i.e. register
  * caps; disc and squares: 8 / 4 / 16 warps per CTA, one warp per
  * perturbation; mesh and 2D triangles: one shape) and the sampler runs with
- * 32, 64 or 128 threads per block.  Every variant computes the same values in
+ * 16, 32, 64 or 128 threads per block (16 spreads small requests over more SMs).  Every variant computes the same values in
  * the same order, so results are bit-identical whatever is chosen.
  * hr_autotune times each variant on profiled aggregate HVP estimates of
  * max(n_probe, 8 x the SM count) perturbations at h_theta [n] (v = ones,
@@ -440,7 +440,7 @@ typedef struct {
     int32_t render_variant;     /* chosen render variant */
     int32_t sample_threads;     /* chosen sampler threads per block */
     int32_t n_render_variants;
-    int32_t n_sample_variants;  /* 3: 32, 64, 128 threads */
+    int32_t n_sample_variants;  /* 4: 32, 64, 128, 16 threads */
     float render_ms[4];         /* median render+loss time per variant */
     float sample_ms[4];         /* median sampler time per shape */
 } hr_tune_info;

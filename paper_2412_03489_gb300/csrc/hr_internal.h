@@ -36,7 +36,7 @@ struct SampleArgs {
     uint2* meta;          // [M] (sub, pair k) or null
     const int32_t* step;  // optional device step index s: every group's sub += 64 s
     const double* sigma_row;  // optional [rows]: group sigma = sigma_row[theta_row] (Z's derived in-kernel)
-    int32_t threads;          // threads per block: 32 (0 = 32), 64 or 128; no effect on the results
+    int32_t threads;          // threads per block: 16, 32 (0 = 32), 64 or 128; no effect on the results
     // up to kInlineGroups groups passed by value (n_inline > 0: groups[] is not read)
     int32_t n_inline;
     SampleGroup inline_groups[4];

@@ -350,7 +350,7 @@ __global__ void __launch_bounds__(kFinThreads) finalize_kernel(FinalizeArgs a) {
 
 void launch_sample(const SampleArgs& a, int n_groups, int max_P, cudaStream_t s) {
     // FP64-latency bound: few threads per block spread the pairs over many SMs
-    const int t = (a.threads == 64 || a.threads == 128) ? a.threads : 32;
+    const int t = (a.threads == 16 || a.threads == 64 || a.threads == 128) ? a.threads : 32;
     dim3 grid((max_P + t - 1) / t, n_groups);
     sample_kernel<<<grid, t, 0, s>>>(a);
 }

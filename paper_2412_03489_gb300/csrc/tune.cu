@@ -24,7 +24,7 @@ int render_variant_count(int kind) {
 
 namespace {
 
-constexpr int kSampleShapes[3] = {32, 64, 128};
+constexpr int kSampleShapes[4] = {32, 64, 128, 16};
 
 // median over `reps` profiled estimates of stage `stage` (0 sampler, 1 render)
 hr_status probe(hr_scene_s* s, const double* h_theta, const double* h_v, const hr_opts& o, int stage, int reps,
@@ -58,8 +58,8 @@ hr_status hr_set_tuning(hr_scene s, int32_t render_variant, int32_t sample_threa
     if (!s) return fail(HR_ERR_INVALID_ARG, "scene is NULL");
     if (render_variant < 0 || render_variant >= render_variant_count(s->sc.kind))
         return fail(HR_ERR_INVALID_ARG, "render variant %d out of range", render_variant);
-    if (sample_threads != 32 && sample_threads != 64 && sample_threads != 128)
-        return fail(HR_ERR_INVALID_ARG, "sample_threads must be 32, 64 or 128");
+    if (sample_threads != 16 && sample_threads != 32 && sample_threads != 64 && sample_threads != 128)
+        return fail(HR_ERR_INVALID_ARG, "sample_threads must be 16, 32, 64 or 128");
     std::lock_guard<std::mutex> lk(s->mu);
     s->sc.render_variant = render_variant;
     s->sc.sample_threads = sample_threads;
@@ -91,7 +91,7 @@ hr_status hr_autotune(hr_scene s, const double* h_theta, int32_t n_probe, hr_tun
     hr_tune_info rep{};
     const int nv = render_variant_count(s->sc.kind);
     rep.n_render_variants = nv;
-    rep.n_sample_variants = 3;
+    rep.n_sample_variants = 4;
     hr_status st = HR_OK;
     int best_v = 0;
     for (int k = 0; k < nv && st == HR_OK; ++k) {
@@ -101,7 +101,7 @@ hr_status hr_autotune(hr_scene s, const double* h_theta, int32_t n_probe, hr_tun
     }
     int best_t = 0;
     if (st == HR_OK) s->sc.render_variant = best_v;
-    for (int k = 0; k < 3 && st == HR_OK; ++k) {
+    for (int k = 0; k < 4 && st == HR_OK; ++k) {
         s->sc.sample_threads = kSampleShapes[k];
         st = probe(s, h_theta, v.data(), o, 0, 3, &rep.sample_ms[k]);
         if (st == HR_OK && rep.sample_ms[k] < rep.sample_ms[best_t]) best_t = k;

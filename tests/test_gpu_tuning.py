@@ -36,14 +36,14 @@ def test_every_launch_shape_gives_identical_results(name):
     S = hr.Scene(sc)
     ref = _estimates(S, sc)
     info = hr.hr_autotune(S.handle, sc["theta_query"], 256)
-    assert 0 <= info.render_variant < info.n_render_variants and info.sample_threads in (32, 64, 128)
+    assert 0 <= info.render_variant < info.n_render_variants and info.sample_threads in (16, 32, 64, 128)
     assert all(info.render_ms[k] > 0 for k in range(info.n_render_variants))
-    assert all(info.sample_ms[k] > 0 for k in range(3))
+    assert all(info.sample_ms[k] > 0 for k in range(info.n_sample_variants))
     tuned = _estimates(S, sc)
     for x, y in zip(ref, tuned):
         assert np.array_equal(x, y)
     for rv in range(info.n_render_variants):
-        for t in (32, 64, 128):
+        for t in (16, 32, 64, 128):
             hr.hr_set_tuning(S.handle, rv, t)
             for x, y in zip(ref, _estimates(S, sc)):
                 assert np.array_equal(x, y), (rv, t)
@@ -53,7 +53,7 @@ def test_every_launch_shape_gives_identical_results(name):
 def test_out_of_range_settings_are_rejected():
     sc = wl.revolve_scene(width=64, height=64)
     S = hr.Scene(sc)
-    for rv, t in ((1, 32), (-1, 32), (0, 48), (0, 256)):
+    for rv, t in ((1, 32), (-1, 32), (0, 48), (0, 256), (0, 8)):
         with pytest.raises(hr.HRError, match="status -1"):
             hr.hr_set_tuning(S.handle, rv, t)
     with pytest.raises(hr.HRError, match="status -1"):

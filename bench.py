@@ -707,6 +707,13 @@ def main():
                 "gpu_launches": 4 * args.steps,   # theta to FP32, sampler, render + loss, sums
                 "tuning": tuning,
                 "clocks": clk}
+        # statistical error of one estimate against a converged reference: the
+        # same estimator at 2^20 perturbations (other seed), outside the timed region
+        Hc = S.estimate(hr.HR_HESSIAN, theta, sc["sigma"], 1 << 20, hr.HR_AGGREGATE, SEED + 1, 0)
+        He = S.estimate(hr.HR_HESSIAN, theta, sc["sigma"], M_PERTURB, hr.HR_AGGREGATE, SEED, 0)
+        line["converged_reference"] = {
+            "perturbations": 1 << 20, "reference": Hc.tolist(), "estimate": He.tolist(),
+            "max_abs_err_over_max_entry": float(np.max(np.abs(He - Hc)) / np.max(np.abs(Hc)))}
         if not args.no_cpu_baseline:
             threads = host_threads()
             line["cpu_baseline"] = cpu_baseline(sc, theta, sample=M_PERTURB, threads=threads, keep_estimate=True)

@@ -64,12 +64,24 @@ typedef int32_t hr_status;
  *            (x0 y0 x1 y1 x2 y2 r g b);
  * BOXES2D    K = n_params / 2 axis-aligned squares (the Box2 / Box10 plateau
  *            tasks), params = square centres, grayscale; a pixel centre is 1
- *            inside any square (|dx| < h and |dy| < h in FP32). */
+ *            inside any square (|dx| < h and |dy| < h in FP32);
+ * analytic test functions in place of a renderer (the "loss" is f(p) itself,
+ * evaluated in FP64 at the FP32 perturbed parameters and stored in FP32; the
+ * image is 1 x 1 x 1 holding f; no target):
+ * QUADRATIC  f = 1/2 p^T A p + b^T p (quad_A [n][n] row-major, quad_b [n]);
+ *            its smoothed gradient is A theta + b and Hessian (A + A^T)/2
+ *            exactly;
+ * STEP1D     f = 1 if p_0 > 0 else 0 (n = 1), the 1D hard edge;
+ * NEGGAUSS   f = -exp(-|p|^2 / (2 s^2)) / (2 pi s^2)^(n/2), s = gauss_sigma;
+ *            smoothing gives -N(0, (s^2 + sigma^2) I). */
 #define HR_SCENE_DISC2D 0
 #define HR_SCENE_REVOLVE3D 1
 #define HR_SCENE_PTBOX 2
 #define HR_SCENE_TRIS2D 3
 #define HR_SCENE_BOXES2D 4
+#define HR_SCENE_QUADRATIC 5
+#define HR_SCENE_STEP1D 6
+#define HR_SCENE_NEGGAUSS 7
 
 /* Sampling strategy: element-wise importance sampling (one sample set of M
  * perturbations per unique element: n for the gradient, n(n+1)/2 for the
@@ -143,6 +155,11 @@ typedef struct {
     float emission[3];
     int32_t spp, target_spp, depth;
     uint64_t seed;
+    /* QUADRATIC: A [n][n] row-major and b [n] (FP64); NEGGAUSS: s.  The
+       analytic kinds need neither theta_target nor target_image. */
+    const double* quad_A;
+    const double* quad_b;
+    double gauss_sigma;
 } hr_scene_desc;
 
 /* Options of one estimate. */

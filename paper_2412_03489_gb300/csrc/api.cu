@@ -26,6 +26,8 @@ int revolve_tiles(int W, int H);
 void launch_tris2d_loss(const DevScene&, const RenderBatch&, cudaStream_t);
 void launch_tris2d_image(const DevScene&, const float*, float*, cudaStream_t);
 void launch_ptbox_loss(const DevScene&, const RenderBatch&, cudaStream_t);
+void launch_analytic_loss(const DevScene&, const RenderBatch&, cudaStream_t);
+void launch_analytic_image(const DevScene&, const float*, float*, cudaStream_t);
 void launch_ptbox_image(const DevScene&, const float*, uint64_t, uint32_t, uint32_t, uint32_t, uint32_t, int, float*,
                         cudaStream_t);
 
@@ -47,6 +49,9 @@ void launch_render_loss(const DevScene& sc, const RenderBatch& b, cudaStream_t s
         case HR_SCENE_TRIS2D: launch_tris2d_loss(sc, b, s); break;
         case HR_SCENE_PTBOX: launch_ptbox_loss(sc, b, s); break;
         case HR_SCENE_BOXES2D: launch_boxes_loss(sc, b, s); break;
+        case HR_SCENE_QUADRATIC:
+        case HR_SCENE_STEP1D:
+        case HR_SCENE_NEGGAUSS: launch_analytic_loss(sc, b, s); break;
     }
 }
 
@@ -58,6 +63,9 @@ void launch_render_image(const DevScene& sc, const float* d_params, uint64_t see
         case HR_SCENE_TRIS2D: launch_tris2d_image(sc, d_params, d_img, s); break;
         case HR_SCENE_PTBOX: launch_ptbox_image(sc, d_params, seed, request, sub, k, tag, spp, d_img, s); break;
         case HR_SCENE_BOXES2D: launch_boxes_image(sc, d_params, d_img, s); break;
+        case HR_SCENE_QUADRATIC:
+        case HR_SCENE_STEP1D:
+        case HR_SCENE_NEGGAUSS: launch_analytic_image(sc, d_params, d_img, s); break;
     }
 }
 
@@ -471,11 +479,23 @@ hr_status hr_create_scene(const hr_scene_desc* d, hr_scene* out) {
                 if (d->param_index[j] < 0 || d->param_index[j] >= 9 * d->n_tris)
                     return fail(HR_ERR_INVALID_ARG, "param_index out of range");
             break;
+        case HR_SCENE_QUADRATIC: C = 1; expect_n = d->n_params;
+            if (!d->quad_A || !d->quad_b) return fail(HR_ERR_INVALID_ARG, "quadratic needs A and b");
+            break;
+        case HR_SCENE_STEP1D: C = 1; expect_n = 1; break;
+        case HR_SCENE_NEGGAUSS: C = 1; expect_n = d->n_params;
+            if (!(d->gauss_sigma > 0.0) || !std::isfinite(d->gauss_sigma))
+                return fail(HR_ERR_INVALID_ARG, "gauss_sigma must be finite and > 0");
+            break;
         default: return fail(HR_ERR_INVALID_ARG, "unknown scene kind %d", d->kind);
     }
+    const bool analytic = d->kind == HR_SCENE_QUADRATIC || d->kind == HR_SCENE_STEP1D || d->kind == HR_SCENE_NEGGAUSS;
     if (d->n_params != expect_n || d->n_params < 1 || d->n_params > HR_MAX_PARAMS)
         return fail(HR_ERR_INVALID_ARG, "n_params %d invalid for this scene", d->n_params);
-    if (!d->theta_target && !d->target_image) return fail(HR_ERR_INVALID_ARG, "need theta_target or target_image");
+    if (analytic && (d->width != 1 || d->height != 1))
+        return fail(HR_ERR_INVALID_ARG, "analytic scenes have a 1 x 1 image");
+    if (!analytic && !d->theta_target && !d->target_image)
+        return fail(HR_ERR_INVALID_ARG, "need theta_target or target_image");
 
     hr_scene_s* s = new hr_scene_s();
     DevScene& sc = s->sc;
@@ -530,8 +550,18 @@ hr_status hr_create_scene(const hr_scene_desc* d, hr_scene* out) {
             for (int c = 0; c < 3; ++c) sc.emission[c] = d->emission[c];
             sc.spp = d->spp; sc.target_spp = d->target_spp; sc.depth = d->depth; sc.scene_seed = d->seed;
             break;
+        case HR_SCENE_QUADRATIC:
+            if ((e = upload(&sc.qA, d->quad_A, (size_t)sc.n * sc.n)) != cudaSuccess) return bail(e, "A");
+            if ((e = upload(&sc.qb, d->quad_b, (size_t)sc.n)) != cudaSuccess) return bail(e, "b");
+            break;
+        case HR_SCENE_NEGGAUSS:
+            sc.gauss_sigma = d->gauss_sigma;
+            break;
     }
-    if (d->target_image) {
+    if (analytic) {
+        // no target: the loss is f itself
+        if ((e = cudaMemset(sc.target, 0, sizeof(float) * npx)) != cudaSuccess) return bail(e, "target");
+    } else if (d->target_image) {
         if ((e = cudaMemcpy(sc.target, d->target_image, sizeof(float) * npx, cudaMemcpyHostToDevice)) != cudaSuccess)
             return bail(e, "target upload");
     } else {
@@ -556,7 +586,7 @@ hr_status hr_destroy_scene(hr_scene s) {
     DevScene& sc = s->sc;
     if (s->stream) cudaStreamSynchronize(s->stream);
     cudaFree(sc.target); cudaFree(sc.verts); cudaFree(sc.tris); cudaFree(sc.tnrm); cudaFree(sc.tile_t2);
-    cudaFree(sc.raw); cudaFree(sc.pidx);
+    cudaFree(sc.raw); cudaFree(sc.pidx); cudaFree(sc.qA); cudaFree(sc.qb);
     s->ws.release_all();
     for (cudaEvent_t& e : s->ev)
         if (e) cudaEventDestroy(e);

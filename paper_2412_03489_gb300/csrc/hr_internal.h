@@ -168,6 +168,10 @@ struct DevScene {
     float emission[3] = {0, 0, 0};
     int spp = 0, target_spp = 0, depth = 0;
     uint64_t scene_seed = 0;
+    // analytic test functions
+    double* qA = nullptr;         // [n][n] FP64 (QUADRATIC)
+    double* qb = nullptr;         // [n] FP64
+    double gauss_sigma = 0.0;     // NEGGAUSS
     // launch shapes picked by the autotuner; none of them changes a result
     int render_variant = 0;       // index into render_variant_count(kind)
     int sample_threads = 32;

@@ -40,7 +40,8 @@ class hr_scene_desc(ctypes.Structure):
                 ("sph_radius", _f32p), ("sph_albedo", _f32p), ("light_half", ctypes.c_float),
                 ("cam_z", ctypes.c_float), ("tan_half", ctypes.c_float), ("pix_scale", ctypes.c_float),
                 ("emission", ctypes.c_float * 3), ("spp", ctypes.c_int32), ("target_spp", ctypes.c_int32),
-                ("depth", ctypes.c_int32), ("seed", ctypes.c_uint64)]
+                ("depth", ctypes.c_int32), ("seed", ctypes.c_uint64),
+                ("quad_A", _f64p), ("quad_b", _f64p), ("gauss_sigma", ctypes.c_double)]
 
 
 class hr_opts(ctypes.Structure):
@@ -314,8 +315,9 @@ class Scene:
         keep = {}
         d = hr_scene_desc()
         d.kind, d.width, d.height, d.n_params = int(sc["kind"]), self.W, self.H, self.n
-        keep["theta"] = np.ascontiguousarray(sc["theta_target"], np.float64)
-        d.theta_target = _ptr(keep["theta"], _f64p)
+        if sc.get("theta_target") is not None:
+            keep["theta"] = np.ascontiguousarray(sc["theta_target"], np.float64)
+            d.theta_target = _ptr(keep["theta"], _f64p)
         if target_image is not None:
             keep["target"] = np.ascontiguousarray(target_image, np.float32)
             d.target_image = _ptr(keep["target"], _f32p)
@@ -349,6 +351,12 @@ class Scene:
             d.emission[:] = [float(x) for x in sc["light_emission"]]
             d.spp, d.target_spp, d.depth = int(sc["spp"]), int(sc["target_spp"]), int(sc.get("depth", 3))
             d.seed = int(sc["seed"])
+        elif kind == wl.SCENE_QUADRATIC:
+            keep["A"] = np.ascontiguousarray(sc["A"], np.float64)
+            keep["b"] = np.ascontiguousarray(sc["b"], np.float64)
+            d.quad_A, d.quad_b = _ptr(keep["A"], _f64p), _ptr(keep["b"], _f64p)
+        elif kind == wl.SCENE_NEGGAUSS:
+            d.gauss_sigma = float(sc["gauss_sigma"])
         self._keep = keep
         self.handle = hr_create_scene(d)
 

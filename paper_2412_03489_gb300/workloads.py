@@ -25,6 +25,9 @@ SCENE_REVOLVE3D = 1
 SCENE_PTBOX = 2
 SCENE_TRIS2D = 3
 SCENE_BOXES2D = 4
+SCENE_QUADRATIC = 5
+SCENE_STEP1D = 6
+SCENE_NEGGAUSS = 7
 
 
 def _rng(seed: int) -> np.random.Generator:
@@ -56,6 +59,30 @@ def boxes_scene(n_boxes: int = 1, seed: int = 0xB0, width: int = 64, height: int
     return dict(kind=SCENE_BOXES2D, width=width, height=height, channels=1, n_params=2 * n_boxes,
                 half_size=np.float32(half_size), theta_target=target, theta_query=query,
                 sigma=0.05, seed=seed)
+
+
+# ---------------------------------------------------------------------------
+# Analytic test functions (no renderer): the Quad task's quadratic, the 1D
+# hard edge, the negated Gaussian.  1 x 1 x 1 "images".
+# ---------------------------------------------------------------------------
+def quadratic_scene(A=None, b=None, theta=None, sigma: float = 0.1) -> dict:
+    A = np.array([[10.0, 7.5], [7.5, 10.0]]) if A is None else np.asarray(A, np.float64)
+    n = A.shape[0]
+    b = np.zeros(n) if b is None else np.asarray(b, np.float64)
+    theta = np.full(n, 0.5) if theta is None else np.asarray(theta, np.float64)
+    return dict(kind=SCENE_QUADRATIC, width=1, height=1, channels=1, n_params=n, A=A, b=b,
+                theta_target=None, theta_query=theta, sigma=sigma, seed=0)
+
+
+def step1d_scene(theta: float = 0.03, sigma: float = 0.05) -> dict:
+    return dict(kind=SCENE_STEP1D, width=1, height=1, channels=1, n_params=1,
+                theta_target=None, theta_query=np.array([theta]), sigma=sigma, seed=0)
+
+
+def neggauss_scene(gauss_sigma: float = 1.0, theta=(0.7, -0.4), sigma: float = 0.5) -> dict:
+    return dict(kind=SCENE_NEGGAUSS, width=1, height=1, channels=1, n_params=len(theta),
+                gauss_sigma=gauss_sigma, theta_target=None, theta_query=np.asarray(theta, np.float64),
+                sigma=sigma, seed=0)
 
 
 # ---------------------------------------------------------------------------

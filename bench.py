@@ -679,7 +679,8 @@ def main():
     for i in range(ne):
         o = hr.make_opts(sc["sigma"], M_PERTURB, hr.HR_AGGREGATE, SEED, 600000 + i)
         hr.hr_estimate_hessian(S.handle, theta, o, Hh)
-    e2e_s = (time.perf_counter() - t0) / ne
+    # whole job, like `value`: all ranks' estimates over the slowest rank's time
+    e2e_rate, _ = whole_job_rate((time.perf_counter() - t0) * 1e3, ne, world, "cuda")
 
     if rank == 0:
         peaks, src = measured_peaks()
@@ -701,7 +702,7 @@ def main():
                                             f"({src} max SM clock); one FMA = one operation",
                              "ops_per_render": ops, "pixel_triangle_candidates_per_render": cand,
                              "render_ms_per_launch": render_avg_s * 1e3},
-                "e2e": {"value": 1.0 / e2e_s, "unit": "estimates/s", "h2d_bytes_per_step": 8 + 40,
+                "e2e": {"value": e2e_rate, "unit": "estimates/s", "h2d_bytes_per_step": 8 + 40,
                         "d2h_bytes_per_step": 32},
                 "stage_ms": dict(zip(("sample", "render_loss", "sums"), np.mean(stage_ms, axis=0).tolist())),
                 "gpu_launches": 4 * args.steps,   # theta to FP32, sampler, render + loss, sums

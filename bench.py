@@ -37,10 +37,13 @@ ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
 METRIC = "Hessian/HVP estimates/s at oracle-matched error; perturbed renders/s; p50/p99 latency"
-# DRAM bytes (read + write) of one render+loss launch from the ncu capture of
-# the current mesh kernel (profiles/revolve_kernel_M4096.md); set to None when
-# the kernel changes until it is captured again.
+# From the ncu capture of the current mesh kernel (profiles/revolve_kernel_M4096.md);
+# set to None when the kernel changes until it is captured again: DRAM bytes
+# (read + write) of one render+loss launch, and the fraction of instruction
+# issue slots busy (smsp__issue_active) — the kernel is bound by compare /
+# select issue on the ALU pipe rather than by FP32 arithmetic.
 TRAFFIC_BYTES = 496896
+ISSUE_ACTIVE_NCU = 0.765
 M_PERTURB = 4096
 SEED = 2024
 
@@ -701,7 +704,8 @@ def main():
                              "peak_source": f"{n_sm} SMs x 128 FP32 lanes x {peaks.get('sm_max_mhz', 2070.0)} MHz "
                                             f"({src} max SM clock); one FMA = one operation",
                              "ops_per_render": ops, "pixel_triangle_candidates_per_render": cand,
-                             "render_ms_per_launch": render_avg_s * 1e3},
+                             "render_ms_per_launch": render_avg_s * 1e3,
+                             "issue_slots_busy_ncu": ISSUE_ACTIVE_NCU},
                 "e2e": {"value": e2e_rate, "unit": "estimates/s", "h2d_bytes_per_step": 8 + 40,
                         "d2h_bytes_per_step": 32},
                 "stage_ms": dict(zip(("sample", "render_loss", "sums"), np.mean(stage_ms, axis=0).tolist())),

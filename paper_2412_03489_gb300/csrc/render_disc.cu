@@ -10,8 +10,7 @@ namespace hr {
 namespace {
 
 
-__device__ __forceinline__ float disc_value(int x, int y, float invW_dummy, int W, int H, float cx, float cy, float r2) {
-    (void)invW_dummy;
+__device__ __forceinline__ float disc_value(int x, int y, int W, int H, float cx, float cy, float r2) {
     const float px = __fdiv_rn(__fadd_rn((float)x, 0.5f), (float)W);
     const float py = __fdiv_rn(__fadd_rn((float)y, 0.5f), (float)H);
     const float dx = __fsub_rn(px, cx);
@@ -34,7 +33,7 @@ __global__ void __launch_bounds__(32 * kW) disc_loss_kernel(RenderBatch b, int W
     const int npx = W * H;
     for (int i = lane; i < npx; i += 32) {
         const int y = i / W, x = i - y * W;
-        const float d = __fsub_rn(disc_value(x, y, 0.f, W, H, cx, cy, r2), target[i]);
+        const float d = __fsub_rn(disc_value(x, y, W, H, cx, cy, r2), target[i]);
         acc = __fmaf_rn(d, d, acc);
     }
     acc = warp_sum(acc);
@@ -45,7 +44,7 @@ __global__ void disc_image_kernel(const float* params, int W, int H, float radiu
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= W * H) return;
     const int y = i / W, x = i - y * W;
-    img[i] = disc_value(x, y, 0.f, W, H, params[0], params[1], __fmul_rn(radius, radius));
+    img[i] = disc_value(x, y, W, H, params[0], params[1], __fmul_rn(radius, radius));
 }
 
 // Squares (Box2 / Box10): K axis-aligned squares of half-size h; a pixel

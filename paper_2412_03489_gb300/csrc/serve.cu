@@ -13,8 +13,10 @@
 //           slot and the arena block, wake the waiter.
 // Lanes keep at most two batched launches in flight, so new requests join
 // within a chunk's time.  Newton-CG step requests replay the state's step on
-// the state's own stream.  Waits on the device are event queries; the worker
-// sleeps briefly when nothing progressed.
+// the state's own stream; a step request waits in the queue while its state
+// has a step in flight, so steps on one state run in submission order.
+// Waits on the device are event queries; the worker sleeps briefly when
+// nothing progressed.
 #include <algorithm>
 #include <chrono>
 #include <cmath>

@@ -228,7 +228,11 @@ hr_status hr_estimate_greybox(hr_scene scene, int32_t quantity, const double* h_
 
 /* Device-pointer form of the three estimates, asynchronous on opts->stream:
  * d_theta [n], d_v [n] (HVP only, else NULL), d_out [n], [n][n] or [n]
- * FP64 device memory.  Debug outputs in opts are ignored. */
+ * FP64 device memory.  Debug outputs in opts are ignored.  Every estimate on
+ * a scene works in that scene's one workspace: calls are serialised on the
+ * host, but on the device two calls on the same scene must not overlap, so
+ * issue them on one stream (or order the streams).  Independent estimates run
+ * concurrently on separate scenes or through the server. */
 hr_status hr_estimate_dev(hr_scene scene, int32_t quantity, const double* d_theta, const double* d_v,
                           const hr_opts* opts, double* d_out);
 

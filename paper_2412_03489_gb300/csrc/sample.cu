@@ -1,6 +1,6 @@
 // K1: perturbation sampler and kernel weights (Sec. 3.2-3.5).
 //
-// One thread draws one antithetic pair k of one sample group: a + leg from
+// Two threads draw one antithetic pair k of one sample group: a + leg from
 // the positive lobe and a - leg from the negative lobe of the chosen kernel,
 // every other dimension N(0, sigma^2) shared by both legs (Sec. 3.2,
 // separability; Suppl. "Smooth Gradient Marginalization").  Lobe samples are
@@ -36,6 +36,28 @@ __device__ double lobe_root(double L, bool upper) {
         const double y = exp(-1.0 - L);
         s = (u < 1.0) ? 1.0 - u + u * u / 3.0 : y * (1.0 + y);
     }
+    // Away from the branch point the same Halley iteration first runs in
+    // FP32 (an FP64 log costs thousands of cycles on this GPU, an FP32 one
+    // tens), so the FP64 iteration below starts within a few FP32 ulps of the
+    // root and stops after about two steps.  Near s = 1 (small u) FP32 cannot
+    // resolve g, and the FP64 iteration starts from the series as before.
+    if (u > 0.05) {
+        float sf = (float)s;
+        const float Lf = (float)L;
+        for (int it = 0; it < 8; ++it) {
+            const float g = __logf(sf) - sf + 1.0f + Lf;
+            const float r = 1.0f / sf;
+            const float g1 = r - 1.0f;
+            float sn = sf - 2.0f * g * g1 / (2.0f * g1 * g1 + g * r * r);
+            if (!(sn > 0.0f)) sn = 0.5f * sf;
+            if (upper && sn < 1.0f) sn = 0.5f * (sf + 1.0f);
+            if (!upper && sn > 1.0f) sn = 0.5f * (sf + 1.0f);
+            const bool done = fabsf(sn - sf) <= 2e-6f * sn;
+            sf = sn;
+            if (done) break;
+        }
+        if (sf > 0.0f && (upper ? sf >= 1.0f : sf <= 1.0f)) s = (double)sf;
+    }
     // Stops at a relative step of 4e-16, or once a step fails to halve the
     // previous one: the residual log(s) - s + 1 + L carries rounding noise of
     // about 1e-16 max(|log s|, s, L), which for small s (the middle of the
@@ -44,9 +66,9 @@ __device__ double lobe_root(double L, bool upper) {
     double prev = INFINITY;
     for (int it = 0; it < 16; ++it) {
         const double g = log(s) - s + 1.0 + L;
-        const double g1 = 1.0 / s - 1.0;
-        const double g2 = -1.0 / (s * s);
-        double sn = s - 2.0 * g * g1 / (2.0 * g1 * g1 - g * g2);
+        const double r = 1.0 / s;
+        const double g1 = r - 1.0;
+        double sn = s - 2.0 * g * g1 / (2.0 * g1 * g1 + g * (r * r));
         if (!(sn > 0.0)) sn = 0.5 * s;
         if (upper && sn < 1.0) sn = 0.5 * (s + 1.0);
         if (!upper && sn > 1.0) sn = 0.5 * (s + 1.0);
@@ -196,7 +218,12 @@ constexpr int kSampleThreadsMax = 128;   // launch shapes 32 / 64 / 128 threads 
 
 __global__ void __launch_bounds__(kSampleThreadsMax) sample_kernel(SampleArgs a) {
     const SampleGroup G = a.n_inline > 0 ? a.inline_groups[blockIdx.y] : a.groups[blockIdx.y];
-    const int k = blockIdx.x * blockDim.x + threadIdx.x;
+    // two threads per pair: leg 0 writes the + perturbation, leg 1 the -
+    // one; both derive the pair's component and shared dims from the same
+    // Philox words, so the FP64-heavy lobe inverse and weights of the two
+    // legs run side by side (FP64 latency dominates this kernel)
+    const int tk = blockIdx.x * blockDim.x + threadIdx.x;
+    const int k = tk >> 1, leg = tk & 1;
     if (k >= G.P) return;
     const int n = a.n;
     const Lobes L = lobes_for(a, G);
@@ -255,51 +282,42 @@ __global__ void __launch_bounds__(kSampleThreadsMax) sample_kernel(SampleArgs a)
         }
     }
     const double ua = u01d(w0.y), ub = u01d(w0.z);
-    double pi_ = 0.0, pj = 0.0, mi = 0.0, mj = 0.0;   // + / - leg values in dims i and j
+    const double sign = leg ? -1.0 : 1.0;
+    const int m = G.m0 + 2 * k + leg;
+    float* tm = a.tau + (size_t)m * n;
     if (G.comp_i == -3) {
         // legs +tau and -tau of tau ~ N(0, sigma^2 I)
-        const int mp = G.m0 + 2 * k, mm = mp + 1;
-        float* tp = a.tau + (size_t)mp * n;
-        float* tm = a.tau + (size_t)mm * n;
-        for (int d = 0; d < n; ++d) { tp[d] = (float)g[d]; tm[d] = (float)(-g[d]); }
-        if (a.meta) { a.meta[mp] = make_uint2(sub, (uint32_t)k); a.meta[mm] = make_uint2(sub, (uint32_t)k); }
-        if (a.w) { write_weights(a, L, G, mp, tp, 1.0); write_weights(a, L, G, mm, tm, -1.0); }
+        for (int d = 0; d < n; ++d) tm[d] = leg ? (float)(-g[d]) : (float)g[d];
+        if (a.meta) a.meta[m] = make_uint2(sub, (uint32_t)k);
+        if (a.w) write_weights(a, L, G, m, tm, sign);
         return;
-    } else if (G.lobe == 0) {
+    }
+    double vi, vj;   // this leg's values in dims i and j
+    if (G.lobe == 0) {
         const double r = sigma * sqrt(-2.0 * log(ua));
-        pi_ = r; mi = -r; pj = pi_; mj = mi;
+        vi = leg ? -r : r;
+        vj = vi;
     } else if (i == j) {
-        const double cp = ua < 0.5 ? 0.5 * ua : 0.5 + 0.5 * ua;
-        const double cm = 0.25 + 0.5 * ua;
-        pi_ = sigma * diag_inverse(cp);
-        mi = sigma * diag_inverse(cm);
-        pj = pi_; mj = mi;
+        // + leg: the tails (c in (0, 1/4) or (3/4, 1)); - leg: the middle
+        const double c = leg ? 0.25 + 0.5 * ua : (ua < 0.5 ? 0.5 * ua : 0.5 + 0.5 * ua);
+        vi = sigma * diag_inverse(c);
+        vj = vi;
     } else {
         const double ri = sigma * sqrt(-2.0 * log(ua));
         const double rj = sigma * sqrt(-2.0 * log(ub));
         const double sg = (w0.w & 1u) ? -1.0 : 1.0;
-        pi_ = sg * ri; pj = sg * rj;
-        mi = sg * ri; mj = -sg * rj;
+        vi = sg * ri;
+        vj = leg ? -sg * rj : sg * rj;
     }
-    const int mp = G.m0 + 2 * k, mm = mp + 1;
-    float* tp = a.tau + (size_t)mp * n;
-    float* tm = a.tau + (size_t)mm * n;
     for (int d = 0; d < n; ++d) {
-        double vp, vm;
-        if (d == i) { vp = pi_; vm = mi; }
-        else if (d == j) { vp = pj; vm = mj; }
-        else { vp = g[d]; vm = g[d]; }
-        tp[d] = (float)vp;
-        tm[d] = (float)vm;
+        double vv;
+        if (d == i) vv = vi;
+        else if (d == j) vv = vj;
+        else vv = g[d];
+        tm[d] = (float)vv;
     }
-    if (a.meta) {
-        a.meta[mp] = make_uint2(sub, (uint32_t)k);
-        a.meta[mm] = make_uint2(sub, (uint32_t)k);
-    }
-    if (a.w || a.invS) {
-        write_weights(a, L, G, mp, tp, 1.0);
-        write_weights(a, L, G, mm, tm, -1.0);
-    }
+    if (a.meta) a.meta[m] = make_uint2(sub, (uint32_t)k);
+    if (a.w || a.invS) write_weights(a, L, G, m, tm, sign);
 }
 
 // K6: estimator sums.  Element e sums w[m][e] * loss[m] over its row range in
@@ -351,7 +369,7 @@ __global__ void __launch_bounds__(kFinThreads) finalize_kernel(FinalizeArgs a) {
 void launch_sample(const SampleArgs& a, int n_groups, int max_P, cudaStream_t s) {
     // FP64-latency bound: few threads per block spread the pairs over many SMs
     const int t = (a.threads == 16 || a.threads == 64 || a.threads == 128) ? a.threads : 32;
-    dim3 grid((max_P + t - 1) / t, n_groups);
+    dim3 grid((2 * max_P + t - 1) / t, n_groups);   // one thread per perturbation (pair leg)
     sample_kernel<<<grid, t, 0, s>>>(a);
 }
 

@@ -98,7 +98,7 @@ __global__ void __launch_bounds__(kNcgThreads) ncg_kernel(NcgArgs a) {
     const double gn = sqrt(block_dot(g, g, n, red));
     const double lam = a.lambda_rel * gn;
     // Hd = 1/Mh sum_m loss_m (tau_m (tau_m.d)/s^4 - d/s^2) n^2/S(tau_m) + lambda d
-    const double s2 = sigma * sigma, s4 = s2 * s2;
+    const double s2 = sigma * sigma, is2 = 1.0 / s2, is4 = is2 * is2;   // reciprocals: FP64 division is slow here
     const int m0 = b * a.per_inst + a.Mg;
     for (int k = threadIdx.x; k < a.Mh; k += blockDim.x) {
         const float* t = a.tau + (size_t)(m0 + k) * n;
@@ -111,7 +111,7 @@ __global__ void __launch_bounds__(kNcgThreads) ncg_kernel(NcgArgs a) {
         Kahan acc;
         for (int k = 0; k < a.Mh; ++k) {
             const int m = m0 + k;
-            const double w = ((double)a.tau[(size_t)m * n + c] * tp[k] / s4 - d[c] / s2) * (double)a.invS[m];
+            const double w = ((double)a.tau[(size_t)m * n + c] * tp[k] * is4 - d[c] * is2) * (double)a.invS[m];
             acc.add(__fmul_rn((float)w, a.loss[m]));
         }
         q[c] = ((double)acc.s - (double)acc.c) / (double)a.Mh + lam * d[c];

@@ -68,7 +68,7 @@ __global__ void __launch_bounds__(kCgThreads) cg_kernel(CgArgs a) {
     __shared__ double d[kMaxN], r[kMaxN], p[kMaxN], Hp[kMaxN], red[kCgThreads / 32];
     __shared__ double tp[512];
     const int b = blockIdx.x, n = a.n;
-    const double s2 = a.sigma * a.sigma, s4 = s2 * s2;
+    const double s2 = a.sigma * a.sigma, is2 = 1.0 / s2, is4 = is2 * is2;   // reciprocals: FP64 division is slow here
     const double* g = a.g + (size_t)b * n;
     for (int i = threadIdx.x; i < n; i += blockDim.x) { d[i] = 0.0; r[i] = -g[i]; p[i] = r[i]; }
     __syncthreads();
@@ -93,7 +93,7 @@ __global__ void __launch_bounds__(kCgThreads) cg_kernel(CgArgs a) {
             for (int q = 0; q < a.Mh; ++q) {
                 const int m = m0 + q;
                 const double tq = tp[q];
-                const double w = ((double)a.tau[(size_t)m * n + k] * tq / s4 - p[k] / s2) * (double)a.invS[m];
+                const double w = ((double)a.tau[(size_t)m * n + k] * tq * is4 - p[k] * is2) * (double)a.invS[m];
                 acc.add(__fmul_rn((float)w, a.loss[m]));
             }
             Hp[k] = ((double)acc.s - (double)acc.c) / (double)a.Mh + lam * p[k];

@@ -105,41 +105,56 @@ __device__ __forceinline__ int upper_index(int a, int b, int n) {
     return a * n - a * (a - 1) / 2 + (b - a);
 }
 
+// e^{-1/2}, rounded to double
+constexpr double kExpMinusHalf = 0.60653065971263342360;
+
+// Bandwidth of a group and the masses of its lobes (Sec. 3.2-3.3):
+// Zg = sqrt(2/pi)/sigma, Zd = 4 e^{-1/2} / (sqrt(2 pi) sigma^2), Zo = Zg^2,
+// with the reciprocals the weights use.  A dependent FP64 operation costs
+// tens of cycles on this GPU and a division hundreds, so the weights below
+// multiply by these reciprocals (within an FP64 ulp or two of dividing).
+struct Lobes {
+    double sigma, Zg, Zd, Zo;
+    double s2, is2, is4, iZg, iZd, iZo;
+};
+
+__device__ __forceinline__ Lobes make_lobes(double s, double zg, double zd, double zo) {
+    Lobes L;
+    L.sigma = s; L.Zg = zg; L.Zd = zd; L.Zo = zo;
+    L.s2 = s * s;
+    L.is2 = 1.0 / L.s2;
+    L.is4 = L.is2 * L.is2;
+    L.iZg = 1.0 / zg; L.iZd = 1.0 / zd; L.iZo = 1.0 / zo;
+    return L;
+}
+
+__device__ __forceinline__ Lobes lobes_for(const SampleArgs& a, const SampleGroup& G) {
+    if (!a.sigma_row) return make_lobes(a.sigma, a.Zg, a.Zd, a.Zo);
+    const double s = a.sigma_row[G.theta_row];
+    const double zg = sqrt(2.0 / kPi) / s;
+    return make_lobes(s, zg, 4.0 * kExpMinusHalf / (sqrt(2.0 * kPi) * (s * s)), zg * zg);
+}
+
 // S(tau): n^2 q(tau) / N(tau) for the Hessian mixture, O(n) via
 // sum_{i != j} |t_i t_j| = (sum |t_i|)^2 - sum t_i^2.
-__device__ double hess_mixture(const float* t, int n, double s2, double Zd, double Zo) {
-    const double s4 = s2 * s2;
+__device__ double hess_mixture(const float* t, int n, const Lobes& L) {
     double sd = 0.0, sa = 0.0, sq = 0.0;
     for (int d = 0; d < n; ++d) {
         const double x = (double)t[d];
-        sd += fabs(x * x - s2);
+        sd += fabs(x * x - L.s2);
         sa += fabs(x);
         sq += x * x;
     }
     const double off = sa * sa - sq;
-    return (sd / s4 / Zd + (off > 0.0 ? off : 0.0) / s4 / Zo) / ((double)n * (double)n);
-}
-
-// e^{-1/2}, rounded to double
-constexpr double kExpMinusHalf = 0.60653065971263342360;
-
-// bandwidth of a group and the masses of its lobes (Sec. 3.2-3.3):
-// Zg = sqrt(2/pi)/sigma, Zd = 4 e^{-1/2} / (sqrt(2 pi) sigma^2), Zo = Zg^2
-struct Lobes { double sigma, Zg, Zd, Zo; };
-
-__device__ __forceinline__ Lobes lobes_for(const SampleArgs& a, const SampleGroup& G) {
-    if (!a.sigma_row) return {a.sigma, a.Zg, a.Zd, a.Zo};
-    const double s = a.sigma_row[G.theta_row];
-    const double zg = sqrt(2.0 / kPi) / s;
-    return {s, zg, 4.0 * kExpMinusHalf / (sqrt(2.0 * kPi) * (s * s)), zg * zg};
+    return (sd * L.is4 * L.iZd + (off > 0.0 ? off : 0.0) * L.is4 * L.iZo) / ((double)n * (double)n);
 }
 
 __device__ void write_weights(const SampleArgs& a, const Lobes& L, const SampleGroup& G, int m, const float* t,
                               double sign) {
     const int n = a.n;
-    const double s2 = L.sigma * L.sigma, s4 = s2 * s2;
+    const double s2 = L.s2, is2 = L.is2, is4 = L.is4;
     if (G.quantity == 3) {
-        const double S = hess_mixture(t, n, s2, L.Zd, L.Zo);
+        const double S = hess_mixture(t, n, L);
         a.invS[m] = (float)(S > 0.0 ? 1.0 / S : 0.0);
         return;
     }
@@ -148,18 +163,18 @@ __device__ void write_weights(const SampleArgs& a, const Lobes& L, const SampleG
     if (G.comp_i == -3) {
         // plain Gaussian sampling: the weight is the kernel factor c(tau)
         if (G.quantity == 0) {
-            for (int d = 0; d < n; ++d) wm[d] = (float)((double)t[d] / s2);
+            for (int d = 0; d < n; ++d) wm[d] = (float)((double)t[d] * is2);
         } else if (G.quantity == 1) {
             int e = 0;
             for (int i = 0; i < n; ++i) {
                 const double ti = (double)t[i];
                 for (int jj = i; jj < n; ++jj, ++e)
-                    wm[e] = (float)((i == jj) ? (ti * ti - s2) / s4 : ti * (double)t[jj] / s4);
+                    wm[e] = (float)((i == jj) ? (ti * ti - s2) * is4 : ti * (double)t[jj] * is4);
             }
         } else {
             double tv = 0.0;
             for (int d = 0; d < n; ++d) tv += (double)t[d] * a.v[d];
-            for (int kk = 0; kk < n; ++kk) wm[kk] = (float)((double)t[kk] * tv / s4 - a.v[kk] / s2);
+            for (int kk = 0; kk < n; ++kk) wm[kk] = (float)((double)t[kk] * tv * is4 - a.v[kk] * is2);
         }
         return;
     }
@@ -169,7 +184,7 @@ __device__ void write_weights(const SampleArgs& a, const Lobes& L, const SampleG
         const double ti = (double)t[i];
         double hv = 0.0, den = 0.0, tot = 0.0;
         for (int b = 0; b < n; ++b) {
-            const double c = (b == i) ? (ti * ti - s2) / s4 : ti * (double)t[b] / s4;
+            const double c = (b == i) ? (ti * ti - s2) * is4 : ti * (double)t[b] * is4;
             hv += c * a.v[b];
             den += fabs(a.v[b]) * fabs(c);
             tot += fabs(a.v[b]) * (b == i ? L.Zd : L.Zo);
@@ -188,28 +203,30 @@ __device__ void write_weights(const SampleArgs& a, const Lobes& L, const SampleG
     }
     if (G.quantity == 0) {
         double S = 0.0;
-        for (int d = 0; d < n; ++d) S += fabs((double)t[d] / s2);
-        S = S / L.Zg / (double)n;
-        for (int d = 0; d < n; ++d) wm[d] = (float)(S > 0.0 ? ((double)t[d] / s2) / S : 0.0);
+        for (int d = 0; d < n; ++d) S += fabs((double)t[d] * is2);
+        S = S * L.iZg / (double)n;
+        const double iS = S > 0.0 ? 1.0 / S : 0.0;
+        for (int d = 0; d < n; ++d) wm[d] = (float)(((double)t[d] * is2) * iS);
         return;
     }
-    const double S = hess_mixture(t, n, s2, L.Zd, L.Zo);
+    const double S = hess_mixture(t, n, L);
     if (!(S > 0.0)) return;
+    const double iS = 1.0 / S;
     if (G.quantity == 1) {
         int e = 0;
         for (int i = 0; i < n; ++i) {
             const double ti = (double)t[i];
             for (int j = i; j < n; ++j, ++e) {
-                const double c = (i == j) ? (ti * ti - s2) / s4 : ti * (double)t[j] / s4;
-                wm[e] = (float)(c / S);
+                const double c = (i == j) ? (ti * ti - s2) * is4 : ti * (double)t[j] * is4;
+                wm[e] = (float)(c * iS);
             }
         }
     } else {
         double tv = 0.0;
         for (int d = 0; d < n; ++d) tv += (double)t[d] * a.v[d];
         for (int k = 0; k < n; ++k) {
-            const double hv = (double)t[k] * tv / s4 - a.v[k] / s2;
-            wm[k] = (float)(hv / S);
+            const double hv = (double)t[k] * tv * is4 - a.v[k] * is2;
+            wm[k] = (float)(hv * iS);
         }
     }
 }

@@ -22,33 +22,52 @@ namespace {
 constexpr int kMaxN = 64;
 constexpr double kPi = 3.141592653589793238462643383279502884;
 
+// 1/x for x in the normal FP32 range by the Newton-Raphson iteration for the
+// reciprocal, r' = r + r (1 - x r), started from the FP32 reciprocal (relative
+// error ~1e-7): one step leaves ~1e-14, two leave FP64 rounding.  An FP64
+// division costs hundreds of cycles on this GPU, a step two dependent FMAs.
+__device__ __forceinline__ double recip_nr(double x) {
+    const double r = (double)__frcp_rn((float)x);
+    return fma(r, fma(-x, r, 1.0), r);
+}
+__device__ __forceinline__ double recip_nr2(double x) {
+    const double r = recip_nr(x);
+    return fma(r, fma(-x, r, 1.0), r);
+}
+
 // Root s > 0 of  log(s) - s + 1 + L = 0  for L >= 0, i.e. s e^{-s} = e^{-1-L}.
 // upper: the root s >= 1 (tails of the diagonal lobe, |t| > 1), else s <= 1.
-// Halley's method on the log form, started from the branch-point expansion
-// s = 1 +- u + u^2/3 (u = sqrt(2L)) or from the asymptotics of each branch.
+// Halley's method on the log form.  A dependent FP64 operation costs tens of
+// cycles on this GPU, an FP64 log thousands, so:
+//   1. away from the branch point (u = sqrt(2L) > 0.05) the start comes from
+//      the same iteration in FP32, begun at the branch-point expansion
+//      s = 1 +- u + u^2/3 or at the asymptotics of each branch; near it
+//      (u <= 0.05) FP32 cannot resolve g and the start is the expansion in FP64;
+//   2. the FP64 iteration takes one log, of the start s0, and evaluates
+//      log s = log s0 + log1p(d), d = (s - s0)/s0, by the series of log1p
+//      (|d| <= 1e-4 on this path: the start is within ~1e-5 of the root;
+//      otherwise it falls back to log(s)); its divisions are Newton-refined
+//      reciprocals (a step needs ~1e-14 relative, not a rounded quotient);
+//   3. it stops by the cubic convergence of Halley's method: after a step of
+//      relative size D the error is about D^3 / (4 (1 - s)^2), below 1e-17
+//      once D <= 1e-7 min(1, |1 - s|).
 __device__ double lobe_root(double L, bool upper) {
-    const double u = sqrt(2.0 * L);
-    if (u < 1e-9) return upper ? 1.0 + u : 1.0 - u;
-    double s;
-    if (upper) {
-        s = (u < 2.0) ? 1.0 + u + u * u / 3.0 : (1.0 + L) + log(1.0 + L);
-    } else {
-        const double y = exp(-1.0 - L);
-        s = (u < 1.0) ? 1.0 - u + u * u / 3.0 : y * (1.0 + y);
-    }
-    // Away from the branch point the same Halley iteration first runs in
-    // FP32 (an FP64 log costs thousands of cycles on this GPU, an FP32 one
-    // tens), so the FP64 iteration below starts within a few FP32 ulps of the
-    // root and stops after about two steps.  Near s = 1 (small u) FP32 cannot
-    // resolve g, and the FP64 iteration starts from the series as before.
-    if (u > 0.05) {
-        float sf = (float)s;
-        const float Lf = (float)L;
+    const float Lf = (float)L;
+    const float uf = sqrtf(2.0f * Lf);
+    double s0 = -1.0;
+    if (uf > 0.05f) {
+        float sf;
+        if (upper) {
+            sf = (uf < 2.0f) ? 1.0f + uf + uf * uf * (1.0f / 3.0f) : (1.0f + Lf) + __logf(1.0f + Lf);
+        } else {
+            const float y = __expf(-1.0f - Lf);
+            sf = (uf < 1.0f) ? 1.0f - uf + uf * uf * (1.0f / 3.0f) : y * (1.0f + y);
+        }
         for (int it = 0; it < 8; ++it) {
             const float g = __logf(sf) - sf + 1.0f + Lf;
-            const float r = 1.0f / sf;
+            const float r = __frcp_rn(sf);
             const float g1 = r - 1.0f;
-            float sn = sf - 2.0f * g * g1 / (2.0f * g1 * g1 + g * r * r);
+            float sn = sf - __fdividef(2.0f * g * g1, 2.0f * g1 * g1 + g * r * r);
             if (!(sn > 0.0f)) sn = 0.5f * sf;
             if (upper && sn < 1.0f) sn = 0.5f * (sf + 1.0f);
             if (!upper && sn > 1.0f) sn = 0.5f * (sf + 1.0f);
@@ -56,49 +75,69 @@ __device__ double lobe_root(double L, bool upper) {
             sf = sn;
             if (done) break;
         }
-        if (sf > 0.0f && (upper ? sf >= 1.0f : sf <= 1.0f)) s = (double)sf;
+        if (sf > 0.0f && (upper ? sf >= 1.0f : sf <= 1.0f)) s0 = (double)sf;
     }
-    // Stops at a relative step of 4e-16, or once a step fails to halve the
-    // previous one: the residual log(s) - s + 1 + L carries rounding noise of
-    // about 1e-16 max(|log s|, s, L), which for small s (the middle of the
-    // lobe near c = 1/2) sits far above 4e-16 s, so the step can stall at
-    // that noise level without meeting the relative test.
-    double prev = INFINITY;
+    if (s0 < 0.0) {
+        const double u = sqrt(2.0 * L);
+        if (u < 1e-9) return upper ? 1.0 + u : 1.0 - u;
+        if (u < (upper ? 2.0 : 1.0)) {
+            s0 = 1.0 + (upper ? u : -u) + u * u * (1.0 / 3.0);
+        } else if (upper) {
+            s0 = (1.0 + L) + log(1.0 + L);
+        } else {
+            const double y = exp(-1.0 - L);
+            s0 = y * (1.0 + y);
+        }
+    }
+    const double lg0 = log(s0);
+    const double r0 = recip_nr(s0);
+    double s = s0;
     for (int it = 0; it < 16; ++it) {
-        const double g = log(s) - s + 1.0 + L;
-        const double r = 1.0 / s;
-        const double g1 = r - 1.0;
-        double sn = s - 2.0 * g * g1 / (2.0 * g1 * g1 + g * (r * r));
+        const double d = (s - s0) * r0;
+        const double ls = fabs(d) <= 1e-4 ? lg0 + d * (1.0 - d * (0.5 - d * (1.0 / 3.0 - 0.25 * d))) : log(s);
+        const double g = ls - s + 1.0 + L;
+        const double om = 1.0 - s;
+        // Halley: s - 2 g g' / (2 g'^2 - g g''), g' = (1 - s)/s, g'' = -1/s^2
+        double sn = s - 2.0 * g * om * s * recip_nr(2.0 * om * om + g);
         if (!(sn > 0.0)) sn = 0.5 * s;
         if (upper && sn < 1.0) sn = 0.5 * (s + 1.0);
         if (!upper && sn > 1.0) sn = 0.5 * (s + 1.0);
         const double step = fabs(sn - s);
         s = sn;
-        if (step <= 4e-16 * s) break;
-        if (it >= 2 && step >= 0.5 * prev) break;
-        prev = step;
+        if (step <= 1e-7 * s * fmin(1.0, fabs(om))) break;
     }
     return s;
 }
 
+// L = -log(16 m^2) for m in (0, 1/4], with one log either way: below
+// 16 m^2 = 1/2 the log of 16 m^2 itself; above it -log1p(y), y = -(1 - 4m)(1 + 4m)
+// (16 m^2 - 1 without cancellation), by Goldberg's identity
+// log1p(y) = y log(w) / (w - 1), w = 1 + y, where w - 1 is exact for w in
+// [1/2, 1] (D. Goldberg, "What every computer scientist should know about
+// floating-point arithmetic", ACM Computing Surveys 1991, Theorem 4).  The
+// lanes of a warp then share one log call instead of running a log and a log1p.
+__device__ __forceinline__ double neg_log16(double m) {
+    const double x = 16.0 * m * m;
+    const double y = -((1.0 - 4.0 * m) * (1.0 + 4.0 * m));
+    const bool direct = x < 0.5;
+    const double w = 1.0 + y;
+    const double lg = log(direct ? x : w);
+    if (direct) return -lg;
+    return w == 1.0 ? -y : -(y * (lg * recip_nr2(w - 1.0)));
+}
+
 // Inverse of the diagonal-lobe CDF (standardised t = tau / sigma): with tail
 // mass m (or middle offset a = |c - 1/2|), t^2 e^{-t^2} = 16 m^2 / e, i.e.
-// s = t^2 solves s e^{-s} = e^{-1-L}, L = -log(16 m^2).
+// s = t^2 solves s e^{-s} = e^{-1-L}, L = -log(16 m^2).  Tails and middle go
+// through one call of the root solve (the two legs of a pair sit in adjacent
+// lanes, so separate calls would run the solve twice per warp).
 __device__ double diag_inverse(double c) {
-    if (c < 0.25 || c > 0.75) {
-        const double m = c < 0.25 ? c : 1.0 - c;
-        const double m16 = 16.0 * m * m;
-        const double L = m16 < 0.5 ? -log(m16) : -log1p(-((1.0 - 4.0 * m) * (1.0 + 4.0 * m)));
-        const double t = sqrt(lobe_root(L, true));
-        return c < 0.25 ? -t : t;
-    }
+    const bool tail = c < 0.25 || c > 0.75;
     const double d = c - 0.5;
-    if (d == 0.0) return 0.0;
-    const double a = fabs(d);
-    const double a16 = 16.0 * a * a;
-    const double L = a16 < 0.5 ? -log(a16) : -log1p(-((1.0 - 4.0 * a) * (1.0 + 4.0 * a)));
-    const double t = sqrt(lobe_root(L, false));
-    return d < 0.0 ? -t : t;
+    if (!tail && d == 0.0) return 0.0;
+    const double m = tail ? (c < 0.25 ? c : 1.0 - c) : fabs(d);
+    const double t = sqrt(lobe_root(neg_log16(m), tail));
+    return (tail ? c < 0.25 : d < 0.0) ? -t : t;
 }
 
 __device__ __forceinline__ int upper_index(int a, int b, int n) {
@@ -113,26 +152,37 @@ constexpr double kExpMinusHalf = 0.60653065971263342360;
 // with the reciprocals the weights use.  A dependent FP64 operation costs
 // tens of cycles on this GPU and a division hundreds, so the weights below
 // multiply by these reciprocals (within an FP64 ulp or two of dividing).
+// With a single bandwidth per launch the host computes them once and passes
+// them in; per-instance bandwidths (sigma_row) are expanded in the kernel.
 struct Lobes {
     double sigma, Zg, Zd, Zo;
     double s2, is2, is4, iZg, iZd, iZo;
+    double inv_n, inv_n2;   // 1/n, 1/n^2 of the mixture densities
 };
 
-__device__ __forceinline__ Lobes make_lobes(double s, double zg, double zd, double zo) {
+__host__ __device__ inline Lobes make_lobes(double s, double zg, double zd, double zo, int n) {
     Lobes L;
     L.sigma = s; L.Zg = zg; L.Zd = zd; L.Zo = zo;
     L.s2 = s * s;
     L.is2 = 1.0 / L.s2;
     L.is4 = L.is2 * L.is2;
     L.iZg = 1.0 / zg; L.iZd = 1.0 / zd; L.iZo = 1.0 / zo;
+    L.inv_n = 1.0 / (double)n;
+    L.inv_n2 = 1.0 / ((double)n * (double)n);
     return L;
 }
 
-__device__ __forceinline__ Lobes lobes_for(const SampleArgs& a, const SampleGroup& G) {
-    if (!a.sigma_row) return make_lobes(a.sigma, a.Zg, a.Zd, a.Zo);
+__device__ __forceinline__ Lobes lobes_for(const SampleArgs& a, const SampleGroup& G, const Lobes& host) {
+    if (!a.sigma_row) return host;
     const double s = a.sigma_row[G.theta_row];
     const double zg = sqrt(2.0 / kPi) / s;
-    return make_lobes(s, zg, 4.0 * kExpMinusHalf / (sqrt(2.0 * kPi) * (s * s)), zg * zg);
+    return make_lobes(s, zg, 4.0 * kExpMinusHalf / (sqrt(2.0 * kPi) * (s * s)), zg * zg, a.n);
+}
+
+// 1/S for the mixture densities: S > 0 is far inside the FP32 range except in
+// degenerate draws, which take the division
+__device__ __forceinline__ double recip_mixture(double S) {
+    return (S > 1e-30 && S < 1e30) ? recip_nr2(S) : 1.0 / S;
 }
 
 // S(tau): n^2 q(tau) / N(tau) for the Hessian mixture, O(n) via
@@ -146,7 +196,7 @@ __device__ double hess_mixture(const float* t, int n, const Lobes& L) {
         sq += x * x;
     }
     const double off = sa * sa - sq;
-    return (sd * L.is4 * L.iZd + (off > 0.0 ? off : 0.0) * L.is4 * L.iZo) / ((double)n * (double)n);
+    return (sd * L.is4 * L.iZd + (off > 0.0 ? off : 0.0) * L.is4 * L.iZo) * L.inv_n2;
 }
 
 __device__ void write_weights(const SampleArgs& a, const Lobes& L, const SampleGroup& G, int m, const float* t,
@@ -155,7 +205,7 @@ __device__ void write_weights(const SampleArgs& a, const Lobes& L, const SampleG
     const double s2 = L.s2, is2 = L.is2, is4 = L.is4;
     if (G.quantity == 3) {
         const double S = hess_mixture(t, n, L);
-        a.invS[m] = (float)(S > 0.0 ? 1.0 / S : 0.0);
+        a.invS[m] = (float)(S > 0.0 ? recip_mixture(S) : 0.0);
         return;
     }
     float* wm = a.w + (size_t)m * a.E;
@@ -204,14 +254,14 @@ __device__ void write_weights(const SampleArgs& a, const Lobes& L, const SampleG
     if (G.quantity == 0) {
         double S = 0.0;
         for (int d = 0; d < n; ++d) S += fabs((double)t[d] * is2);
-        S = S * L.iZg / (double)n;
-        const double iS = S > 0.0 ? 1.0 / S : 0.0;
+        S = S * L.iZg * L.inv_n;
+        const double iS = S > 0.0 ? recip_mixture(S) : 0.0;
         for (int d = 0; d < n; ++d) wm[d] = (float)(((double)t[d] * is2) * iS);
         return;
     }
     const double S = hess_mixture(t, n, L);
     if (!(S > 0.0)) return;
-    const double iS = 1.0 / S;
+    const double iS = recip_mixture(S);
     if (G.quantity == 1) {
         int e = 0;
         for (int i = 0; i < n; ++i) {
@@ -233,7 +283,7 @@ __device__ void write_weights(const SampleArgs& a, const Lobes& L, const SampleG
 
 constexpr int kSampleThreadsMax = 128;   // launch shapes 32 / 64 / 128 threads per block
 
-__global__ void __launch_bounds__(kSampleThreadsMax) sample_kernel(SampleArgs a) {
+__global__ void __launch_bounds__(kSampleThreadsMax) sample_kernel(SampleArgs a, Lobes host_lobes) {
     const SampleGroup G = a.n_inline > 0 ? a.inline_groups[blockIdx.y] : a.groups[blockIdx.y];
     // two threads per pair: leg 0 writes the + perturbation, leg 1 the -
     // one; both derive the pair's component and shared dims from the same
@@ -243,7 +293,7 @@ __global__ void __launch_bounds__(kSampleThreadsMax) sample_kernel(SampleArgs a)
     const int k = tk >> 1, leg = tk & 1;
     if (k >= G.P) return;
     const int n = a.n;
-    const Lobes L = lobes_for(a, G);
+    const Lobes L = lobes_for(a, G, host_lobes);
     const double sigma = L.sigma;
     const uint32_t sub = G.sub + (a.step ? 64u * (uint32_t)(*a.step) : 0u);
     const uint32_t c2 = (TAG_SAMPLE << 24) | (sub & 0xFFFFFFu);
@@ -387,7 +437,7 @@ void launch_sample(const SampleArgs& a, int n_groups, int max_P, cudaStream_t s)
     // FP64-latency bound: few threads per block spread the pairs over many SMs
     const int t = (a.threads == 16 || a.threads == 64 || a.threads == 128) ? a.threads : 32;
     dim3 grid((2 * max_P + t - 1) / t, n_groups);   // one thread per perturbation (pair leg)
-    sample_kernel<<<grid, t, 0, s>>>(a);
+    sample_kernel<<<grid, t, 0, s>>>(a, make_lobes(a.sigma, a.Zg, a.Zd, a.Zo, a.n));
 }
 
 void launch_finalize(const FinalizeArgs& a, cudaStream_t s) {

@@ -3,6 +3,7 @@
 // ((x + 1/2)/W, (y + 1/2)/H) is inside when fma(dx, dx, dy*dy) < r*r in FP32,
 // value 1 inside, 0 outside.  With a 0/1 target every (v - t)^2 is 0 or 1 and
 // the FP32 sum is an exact integer count.
+#include "hr.h"
 #include "hr_device.cuh"
 #include "hr_internal.h"
 
@@ -19,9 +20,61 @@ __device__ __forceinline__ float disc_value(int x, int y, int W, int H, float cx
     return d2 < r2 ? 1.0f : 0.0f;
 }
 
+// The pixel-centre coordinates (c + 1/2)/W of the columns and (r + 1/2)/H of
+// the rows, rounded exactly as disc_value and boxes_value form them, filled
+// once per CTA: a pixel then costs no division.  Lane l of a warp visits
+// pixels i = l, l + 32, ... in row-major order (the order of its FP32 loss
+// sum); (x, y) follow i by increments.
+__device__ __forceinline__ void centre_tables(float* px, float* py, int W, int H) {
+    for (int x = threadIdx.x; x < W; x += blockDim.x) px[x] = __fdiv_rn(__fadd_rn((float)x, 0.5f), (float)W);
+    for (int y = threadIdx.x; y < H; y += blockDim.x) py[y] = __fdiv_rn(__fadd_rn((float)y, 0.5f), (float)H);
+}
+
+// kWide: W >= 32, so a step of 32 pixels wraps a row at most once
+template <bool kWide>
+__device__ __forceinline__ void next_pixel(int& x, int& y, int W) {
+    x += 32;
+    if (kWide) {
+        if (x >= W) { x -= W; ++y; }
+    } else {
+        while (x >= W) { x -= W; ++y; }
+    }
+}
+
+// Sum over this lane's pixels of (value(px, py) - target)^2, in pixel order;
+// the target values of four pixels are loaded ahead of their arithmetic so
+// that the loads overlap (one at a time, the loop waits on each load).
+template <bool kWide, class Value>
+__device__ __forceinline__ float lane_l2(const float* __restrict__ target, int W, int npx, int lane,
+                                        const float* px, const float* py, Value value) {
+    float acc = 0.0f;
+    int y = lane / W, x = lane - y * W;
+    int i = lane;
+    for (; i + 96 < npx; i += 128) {
+        float t[4];
+#pragma unroll
+        for (int u = 0; u < 4; ++u) t[u] = __ldg(target + i + 32 * u);
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+            const float d = __fsub_rn(value(px[x], py[y]), t[u]);
+            acc = __fmaf_rn(d, d, acc);
+            next_pixel<kWide>(x, y, W);
+        }
+    }
+    for (; i < npx; i += 32) {
+        const float d = __fsub_rn(value(px[x], py[y]), __ldg(target + i));
+        acc = __fmaf_rn(d, d, acc);
+        next_pixel<kWide>(x, y, W);
+    }
+    return acc;
+}
+
 template <int kW>
 __global__ void __launch_bounds__(32 * kW) disc_loss_kernel(RenderBatch b, int W, int H, float radius,
                                                             const float* __restrict__ target) {
+    __shared__ float s_px[HR_MAX_IMAGE_SIDE], s_py[HR_MAX_IMAGE_SIDE];
+    centre_tables(s_px, s_py, W, H);
+    __syncthreads();
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int m = blockIdx.x * kW + warp;
     if (m >= b.M) return;
@@ -29,13 +82,14 @@ __global__ void __launch_bounds__(32 * kW) disc_loss_kernel(RenderBatch b, int W
     const float cx = __fadd_rn(pt.theta[0], pt.tau[0]);
     const float cy = __fadd_rn(pt.theta[1], pt.tau[1]);
     const float r2 = __fmul_rn(radius, radius);
-    float acc = 0.0f;
     const int npx = W * H;
-    for (int i = lane; i < npx; i += 32) {
-        const int y = i / W, x = i - y * W;
-        const float d = __fsub_rn(disc_value(x, y, W, H, cx, cy, r2), target[i]);
-        acc = __fmaf_rn(d, d, acc);
-    }
+    auto value = [cx, cy, r2](float px, float py) {
+        const float dx = __fsub_rn(px, cx);
+        const float dy = __fsub_rn(py, cy);
+        return __fmaf_rn(dx, dx, __fmul_rn(dy, dy)) < r2 ? 1.0f : 0.0f;
+    };
+    float acc = W >= 32 ? lane_l2<true>(target, W, npx, lane, s_px, s_py, value)
+                        : lane_l2<false>(target, W, npx, lane, s_px, s_py, value);
     acc = warp_sum(acc);
     if (lane == 0) *pt.loss = __fdiv_rn(acc, (float)npx);
 }
@@ -63,6 +117,9 @@ template <int kW>
 __global__ void __launch_bounds__(32 * kW) boxes_loss_kernel(RenderBatch b, int W, int H, float h,
                                                              const float* __restrict__ target) {
     __shared__ float s_c[kW][kMaxBoxParams];
+    __shared__ float s_px[HR_MAX_IMAGE_SIDE], s_py[HR_MAX_IMAGE_SIDE];
+    centre_tables(s_px, s_py, W, H);
+    __syncthreads();
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int m = blockIdx.x * kW + warp;
     if (m >= b.M) return;
@@ -70,13 +127,15 @@ __global__ void __launch_bounds__(32 * kW) boxes_loss_kernel(RenderBatch b, int 
     for (int d = lane; d < b.n; d += 32) s_c[warp][d] = __fadd_rn(pt.theta[d], pt.tau[d]);
     __syncwarp();
     const int K = b.n / 2;
-    float acc = 0.0f;
+    const float* c = s_c[warp];
     const int npx = W * H;
-    for (int i = lane; i < npx; i += 32) {
-        const int y = i / W, x = i - y * W;
-        const float d = __fsub_rn(boxes_value(x, y, W, H, s_c[warp], K, h), target[i]);
-        acc = __fmaf_rn(d, d, acc);
-    }
+    auto value = [c, K, h](float px, float py) {
+        for (int k = 0; k < K; ++k)
+            if (fabsf(__fsub_rn(px, c[2 * k])) < h && fabsf(__fsub_rn(py, c[2 * k + 1])) < h) return 1.0f;
+        return 0.0f;
+    };
+    float acc = W >= 32 ? lane_l2<true>(target, W, npx, lane, s_px, s_py, value)
+                        : lane_l2<false>(target, W, npx, lane, s_px, s_py, value);
     acc = warp_sum(acc);
     if (lane == 0) *pt.loss = __fdiv_rn(acc, (float)npx);
 }

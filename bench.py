@@ -296,7 +296,6 @@ def run_secondary(args):
         d_v = torch.tensor(sc.get("v", np.ones(n)), dtype=torch.float64, device="cuda")
         d_out = torch.zeros((n, n), dtype=torch.float64, device="cuda")
         line["tuning"] = tune_scene(hr, S, sc["theta_query"], 2048)
-        hr.hr_profile_enable(S.handle, True)
         variants = ([("hessian_elementwise_3x1024", hr.HR_HESSIAN, hr.HR_ELEMENTWISE, 1024, 3 * 1024),
                      ("hessian_aggregate_1024", hr.HR_HESSIAN, hr.HR_AGGREGATE, 1024, 1024)]
                     if args.workload == "disc" else [("hvp_aggregate_8192", hr.HR_HVP, hr.HR_AGGREGATE, 8192, 8192)])
@@ -307,17 +306,24 @@ def run_secondary(args):
                 o = hr.make_opts(sc["sigma"], M, strat, SEED, i, stream=stream.cuda_stream)
                 hr.hr_estimate_dev(S.handle, q, d_theta.data_ptr(), d_v.data_ptr() if q == hr.HR_HVP else None,
                                    o, d_out.data_ptr())
+            # the rate is timed without the library's stage events (they add
+            # about 10 us per estimate, a fifth of a small estimate); a second
+            # pass with them gives the stage breakdown
             times = []
-            for i in range(args.warmup + args.steps):
-                flush.fill_(float(i))
-                ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-                ev0.record(stream)
-                fn(i)
-                ev1.record(stream)
-                ev1.synchronize()
-                if i >= args.warmup:
-                    times.append(ev0.elapsed_time(ev1))
-                    stage.append(hr.hr_profile_last(S.handle).astype(np.float64))
+            for profiled in (False, True):
+                hr.hr_profile_enable(S.handle, profiled)
+                for i in range(args.warmup + args.steps):
+                    flush.fill_(float(i))
+                    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                    ev0.record(stream)
+                    fn(i)
+                    ev1.record(stream)
+                    ev1.synchronize()
+                    if i >= args.warmup:
+                        if profiled:
+                            stage.append(hr.hr_profile_last(S.handle).astype(np.float64))
+                        else:
+                            times.append(ev0.elapsed_time(ev1))
             t = float(np.mean(times))
             line[name] = {"estimates_per_s": 1e3 / t, "renders_per_s": renders * 1e3 / t, "ms_per_estimate": t,
                           "latency_ms": {"p50": float(np.percentile(times, 50)),

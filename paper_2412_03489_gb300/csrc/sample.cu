@@ -401,25 +401,46 @@ __global__ void __launch_bounds__(kFinThreads) finalize_kernel(FinalizeArgs a) {
     const int b = m0 + threadIdx.x * chunk;
     const int end = min(m0 + cnt, b + chunk);
     Kahan ks, ka;
-    for (int m = b; m < end; ++m) {
+    int m = b;
+    // four items' loads go out before their sums, which stay in item order
+    for (; m + 3 < end; m += 4) {
+        float x[4];
+#pragma unroll
+        for (int u = 0; u < 4; ++u) x[u] = __fmul_rn(__ldg(a.w + (size_t)(m + u) * a.E + e), __ldg(a.loss + m + u));
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+            ks.add(x[u]);
+            ka.add(fabsf(x[u]));
+        }
+    }
+    for (; m < end; ++m) {
         const float x = __fmul_rn(a.w[(size_t)m * a.E + e], a.loss[m]);
         ks.add(x);
         ka.add(fabsf(x));
     }
-    sh[threadIdx.x] = (double)ks.s - (double)ks.c;
-    sa[threadIdx.x] = (double)ka.s - (double)ka.c;
+    const int t = threadIdx.x;
+    sh[t] = (double)ks.s - (double)ks.c;
+    sa[t] = (double)ka.s - (double)ka.c;
     __syncthreads();
-    for (int o = kFinThreads / 2; o > 0; o >>= 1) {
-        if (threadIdx.x < o) {
-            sh[threadIdx.x] += sh[threadIdx.x + o];
-            sa[threadIdx.x] += sa[threadIdx.x + o];
+    // pairwise tree (t, t + o); its last five levels by warp shuffles
+    for (int o = kFinThreads / 2; o >= 32; o >>= 1) {
+        if (t < o) {
+            sh[t] += sh[t + o];
+            sa[t] += sa[t + o];
         }
         __syncthreads();
     }
-    if (threadIdx.x == 0) {
-        const double val = sh[0] * a.inv2P;
+    if (t >= 32) return;
+    double vs = sh[t], va = sa[t];
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        vs += __shfl_down_sync(0xffffffffu, vs, o);
+        va += __shfl_down_sync(0xffffffffu, va, o);
+    }
+    if (t == 0) {
+        const double val = vs * a.inv2P;
         a.out_flat[e] = val;
-        if (a.out_scale) a.out_scale[e] = sa[0] * a.inv2P;
+        if (a.out_scale) a.out_scale[e] = va * a.inv2P;
         if (a.hessian && a.out_full) {
             // e -> (row, col) of the upper triangle
             int r = 0, rem = e;

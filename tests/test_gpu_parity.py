@@ -7,6 +7,9 @@ seeded inputs and the same Philox samples.
   within FP32 rounding;
 * estimates: |gpu - oracle| <= 1e-4 max(|oracle|, A_e) (see tests/parity.py).
 """
+import math
+from types import SimpleNamespace
+
 import numpy as np
 import pytest
 
@@ -168,6 +171,33 @@ def test_ptbox_hvp_small():
     assert_estimate_close(flat, ref, what="ptbox hvp")
 
 
+def test_ptbox_full_size_bench_configuration_sampled():
+    """128 x 128, 4 spp, depth 3, aggregate HVP with 8192 perturbations in the
+    launch shape the autotuner picks (the bench workload): every perturbation
+    and weight against the oracle's sampler, a spread of renders against the
+    oracle's path tracer one by one (a full oracle estimate would take
+    minutes), and the estimate against the oracle's FP64 sum of its own
+    weights times the GPU's losses."""
+    sc = wl.ptbox_scene()
+    Sc = hr.Scene(sc)
+    hr.hr_autotune(Sc.handle, sc["theta_query"], 2048)
+    theta, v, M, seed, request = np.asarray(sc["theta_query"]), sc["v"], 8192, 11, 3
+    out, dbg = Sc.estimate(hr.HR_HVP, theta, sc["sigma"], M, hr.HR_AGGREGATE, seed, request, 0, v=v, debug=True)
+    Sc.close()
+    tau, _ = O.draw(1, 6, sc["sigma"], M // 2, seed, request, 0)
+    w = O.weights(2, 6, sc["sigma"], tau, v=v)
+    check_samples(dbg, SimpleNamespace(tau=tau, w=w))
+    r = O.PtboxRenderer(sc)
+    picks = [0, 1, 2046, 2047, 4096, 6001, 8190, 8191]
+    ref = np.array([r.loss(O.perturb(theta, tau[m]), dict(seed=seed, request=request, sub=0, k=m // 2))
+                    for m in picks])
+    assert_losses_close(dbg["losses"][picks], ref, 1e-4, "ptbox full-size losses")
+    losses = dbg["losses"].astype(np.float64)
+    flat = np.array([math.fsum(w[:, e] * losses) for e in range(6)]) / M
+    scale = np.array([math.fsum(np.abs(w[:, e] * losses)) for e in range(6)]) / M
+    assert_estimate_close(out, SimpleNamespace(flat=flat, scale=scale), what="ptbox full-size hvp")
+
+
 # ---------------------------------------------------------------------------
 # Newton-CG
 # ---------------------------------------------------------------------------
@@ -197,6 +227,34 @@ def test_newton_cg_step_matches_oracle(use_graph):
             ref_th[b] = got[b]          # continue both from the GPU iterate
     hr.hr_optstate_destroy(st)
     Sc.close()
+
+
+def test_newton_cg_full_size_bench_configuration_sampled():
+    """256 x 256, 16 triangles, 64 parameters, 64 instances, 32 gradient and
+    10 x 32 HVP renders, graph-captured (the bench workload in its launch
+    configuration): one step of three instances against the oracle's
+    Newton-CG, which renders every one of their perturbations."""
+    sc = wl.tris2d_scene()
+    Sc = hr.Scene(sc)
+    r = O.Tris2dRenderer(sc)
+    B, n = 64, sc["n_params"]
+    opts = hr.hr_cg_opts()
+    opts.sigma, opts.n_grad, opts.n_hvp, opts.cg_iters = sc["sigma"], 32, 32, 10
+    opts.lambda_rel, opts.trust_radius, opts.seed, opts.request_base, opts.use_graph = 1e-3, 0.05, 2024, 0, 1
+    th0 = np.ascontiguousarray(sc["theta_init"], np.float64)
+    st = hr.hr_optstate_create(Sc.handle, B, th0, opts)
+    info = (hr.hr_step_info * B)()
+    hr.hr_newton_cg_step(Sc.handle, st, info)
+    got = np.zeros((B, n))
+    hr.hr_optstate_theta(st, got)
+    hr.hr_optstate_destroy(st)
+    Sc.close()
+    for b in (0, 37, 63):
+        new, inf = O.newton_cg_step(r, th0[b], sc["sigma"], 32, 32, 10, 1e-3, 0.05, 2024, b, 0)
+        d_ref, d_gpu = new - th0[b], got[b] - th0[b]
+        assert info[b].iters == inf.iters, b
+        assert np.allclose(d_gpu, d_ref, rtol=1e-3, atol=1e-4 * np.linalg.norm(d_ref)), b
+        assert abs(info[b].grad_norm - inf.grad_norm) <= 1e-4 * inf.grad_norm, b
 
 
 # ---------------------------------------------------------------------------

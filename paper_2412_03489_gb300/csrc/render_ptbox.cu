@@ -41,7 +41,16 @@ struct PtShared {
     float alb[16][3];
     float sr[3], isr[3];
     float em[3];
+    float box_lo[3], box_hi[3];   // wall planes per axis (procedural box layout)
+    int light_inside;             // light at least kWallMargin inside every wall plane
 };
+
+// Shadow rays may skip the six walls when the light quad lies at least this
+// far inside every wall plane and the ray starts inside the box: a wall is
+// then hit only behind the origin (t <= 0) or beyond the light (t above the
+// light's t by at least the margin over |d_a| <= 1, far above FP32 rounding),
+// so the closest primitive is the light exactly when it is without the skip.
+constexpr float kWallMargin = 1e-3f;
 
 __device__ __forceinline__ float dot3(const float* a, const float* b) {
     return __fmaf_rn(a[2], b[2], __fmaf_rn(a[1], b[1], __fmul_rn(a[0], b[0])));
@@ -97,13 +106,18 @@ __device__ int intersect(const PtShared& S, const float o[3], const float d[3], 
 // sequence and the same acceptance (axis direction non-zero, t > 0, hit
 // inside the closed rectangle, t < best), so it returns what the general
 // loop returns.
-__device__ __noinline__ int intersect_canon(const PtShared& S, const float o[3], const float d[3], float& t_out) {
+// skip_walls: leave out quads 0..5 (see kWallMargin; shadow rays only).  A
+// sphere's square root and roots are formed only when some lane of the warp
+// has a non-negative discriminant (a lane with a negative one rejects it).
+__device__ __noinline__ int intersect_canon(const PtShared& S, const float o[3], const float d[3], float& t_out,
+                                            bool skip_walls) {
     constexpr int kAxis[13] = {0, 0, 1, 1, 2, 2, 0, 0, 1, 1, 2, 2, 1};
     float best = INFINITY;
     int prim = -1;
     const float inv[3] = {__frcp_rn(d[0]), __frcp_rn(d[1]), __frcp_rn(d[2])};
 #pragma unroll
     for (int q = 0; q <= kLight; ++q) {
+        if (q < 6 && skip_walls) continue;
         const int a = kAxis[q];
         const int u = a == 0 ? 1 : 0, v = a == 2 ? 1 : 2;
         const QuadS Q = S.q[q];
@@ -122,6 +136,7 @@ __device__ __noinline__ int intersect_canon(const PtShared& S, const float o[3],
         const float b = dot3(oc, d);
         const float cc = __fsub_rn(dot3(oc, oc), sp.w);
         const float disc = __fmaf_rn(b, b, -cc);
+        if (!__any_sync(__activemask(), disc >= 0.0f)) continue;
         const float sq = __fsqrt_rn(fmaxf(disc, 0.0f));
         const float t0 = __fsub_rn(-b, sq), t1 = __fsub_rn(sq, b);
         const float t = t0 > 0.0f ? t0 : t1;
@@ -135,7 +150,17 @@ __device__ __noinline__ int intersect_canon(const PtShared& S, const float o[3],
 
 template <bool kCanon>
 __device__ __forceinline__ int closest_hit(const PtShared& S, const float o[3], const float d[3], float& t_out) {
-    return kCanon ? intersect_canon(S, o, d, t_out) : intersect(S, o, d, t_out);
+    return kCanon ? intersect_canon(S, o, d, t_out, false) : intersect(S, o, d, t_out);
+}
+
+// Is the light the closest primitive along a shadow ray?
+template <bool kCanon>
+__device__ __forceinline__ bool sees_light(const PtShared& S, const float o[3], const float d[3]) {
+    float t;
+    if (!kCanon) return intersect(S, o, d, t) == kLight;
+    const bool inside = S.light_inside && o[0] >= S.box_lo[0] && o[0] <= S.box_hi[0] && o[1] >= S.box_lo[1] &&
+                        o[1] <= S.box_hi[1] && o[2] >= S.box_lo[2] && o[2] <= S.box_hi[2];
+    return intersect_canon(S, o, d, t, inside) == kLight;
 }
 
 template <bool kCanon>
@@ -184,8 +209,7 @@ __device__ void radiance(const PtShared& S, int depth, uint64_t seed, uint32_t r
             const float cosx = dot3(n, om);
             const float cosl = om[1];
             if (cosx > 0.0f && cosl > 0.0f) {
-                float ts;
-                if (closest_hit<kCanon>(S, o2, om, ts) == kLight) {
+                if (sees_light<kCanon>(S, o2, om)) {
                     const float geo = cosx * cosl / dist2 * area * kInvPi;
 #pragma unroll
                     for (int c = 0; c < 3; ++c) L[c] += beta[c] * rho[c] * S.em[c] * geo;
@@ -270,6 +294,17 @@ __device__ void load_scene(const PtArgs& A, const float* p, PtShared& S) {
         Q.hi_v = __fadd_rn(p[2], A.light_half);
         S.alb[kLight][0] = S.alb[kLight][1] = S.alb[kLight][2] = 0.0f;
         S.em[0] = A.em[0]; S.em[1] = A.em[1]; S.em[2] = A.em[2];
+        // wall planes (quads 2a, 2a + 1 for axis a in the procedural box layout)
+        // and whether the light quad lies kWallMargin inside all of them
+        const float lmin[3] = {Q.lo_u, Q.plane, Q.lo_v}, lmax[3] = {Q.hi_u, Q.plane, Q.hi_v};
+        bool in = true;
+        for (int a = 0; a < 3; ++a) {
+            const float p0 = A.qgeom[2 * a][0], p1 = A.qgeom[2 * a + 1][0];
+            S.box_lo[a] = fminf(p0, p1);
+            S.box_hi[a] = fmaxf(p0, p1);
+            in = in && lmin[a] >= S.box_lo[a] + kWallMargin && lmax[a] <= S.box_hi[a] - kWallMargin;
+        }
+        S.light_inside = in ? 1 : 0;
     }
 }
 

@@ -42,14 +42,21 @@ struct PtShared {
     float sr[3], isr[3];
     float em[3];
     float box_lo[3], box_hi[3];   // wall planes per axis (procedural box layout)
+    int wall_lo[3], wall_hi[3];   // index of the wall quad at box_lo[a] / box_hi[a]
     int light_inside;             // light at least kWallMargin inside every wall plane
 };
 
-// Shadow rays may skip the six walls when the light quad lies at least this
-// far inside every wall plane and the ray starts inside the box: a wall is
-// then hit only behind the origin (t <= 0) or beyond the light (t above the
-// light's t by at least the margin over |d_a| <= 1, far above FP32 rounding),
-// so the closest primitive is the light exactly when it is without the skip.
+// Walls (quads 0..5, two per axis) from a ray origin inside the box, i.e.
+// box_lo[a] <= o_a <= box_hi[a] on every axis:
+//  * the wall behind the ray on axis a (at box_lo[a] when d_a > 0, at
+//    box_hi[a] when d_a < 0) has RN(plane - o_a) of the other sign than
+//    1/d_a, so t <= 0 and the closest-hit test rejects it: only the forward
+//    wall of each axis is tested (still in increasing quad index);
+//  * a shadow ray toward a light quad that lies at least kWallMargin inside
+//    every wall plane meets a forward wall only beyond the light (its t
+//    exceeds the light's by at least the margin over |d_a| <= 1, far above
+//    FP32 rounding), so the light is the closest primitive exactly when it
+//    is with the walls tested: shadow rays then test no wall.
 constexpr float kWallMargin = 1e-3f;
 
 __device__ __forceinline__ float dot3(const float* a, const float* b) {
@@ -106,29 +113,40 @@ __device__ int intersect(const PtShared& S, const float o[3], const float d[3], 
 // sequence and the same acceptance (axis direction non-zero, t > 0, hit
 // inside the closed rectangle, t < best), so it returns what the general
 // loop returns.
-// skip_walls: leave out quads 0..5 (see kWallMargin; shadow rays only).  A
-// sphere's square root and roots are formed only when some lane of the warp
-// has a non-negative discriminant (a lane with a negative one rejects it).
+// One quad of axis a: accepted when d_a != 0, t > 0, the hit lies in the
+// closed rectangle and t < best.
+__device__ __forceinline__ void quad_test(const PtShared& S, int q, int a, const float o[3], const float d[3],
+                                          const float inv[3], float& best, int& prim) {
+    const int u = a == 0 ? 1 : 0, v = a == 2 ? 1 : 2;
+    const QuadS Q = S.q[q];
+    const float t = __fmul_rn(__fsub_rn(Q.plane, o[a]), inv[a]);
+    const float hu = __fmaf_rn(t, d[u], o[u]);
+    const float hv = __fmaf_rn(t, d[v], o[v]);
+    const bool ok = d[a] != 0.0f && t > 0.0f && !(hu < Q.lo_u || hu > Q.hi_u || hv < Q.lo_v || hv > Q.hi_v) &&
+                    t < best;
+    best = ok ? t : best;
+    prim = ok ? q : prim;
+}
+
+// walls: 0 tests all six wall quads, 1 the forward wall of each axis, 2 none
+// (see kWallMargin for when 1 and 2 give the result of 0).  A sphere's square
+// root and roots are formed only when some lane of the warp has a
+// non-negative discriminant (a lane with a negative one rejects it).
 __device__ __noinline__ int intersect_canon(const PtShared& S, const float o[3], const float d[3], float& t_out,
-                                            bool skip_walls) {
+                                            int walls) {
     constexpr int kAxis[13] = {0, 0, 1, 1, 2, 2, 0, 0, 1, 1, 2, 2, 1};
     float best = INFINITY;
     int prim = -1;
     const float inv[3] = {__frcp_rn(d[0]), __frcp_rn(d[1]), __frcp_rn(d[2])};
+    if (walls == 0) {
 #pragma unroll
-    for (int q = 0; q <= kLight; ++q) {
-        if (q < 6 && skip_walls) continue;
-        const int a = kAxis[q];
-        const int u = a == 0 ? 1 : 0, v = a == 2 ? 1 : 2;
-        const QuadS Q = S.q[q];
-        const float t = __fmul_rn(__fsub_rn(Q.plane, o[a]), inv[a]);
-        const float hu = __fmaf_rn(t, d[u], o[u]);
-        const float hv = __fmaf_rn(t, d[v], o[v]);
-        const bool ok = d[a] != 0.0f && t > 0.0f && !(hu < Q.lo_u || hu > Q.hi_u || hv < Q.lo_v || hv > Q.hi_v) &&
-                        t < best;
-        best = ok ? t : best;
-        prim = ok ? q : prim;
+        for (int q = 0; q < 6; ++q) quad_test(S, q, kAxis[q], o, d, inv, best, prim);
+    } else if (walls == 1) {
+#pragma unroll
+        for (int a = 0; a < 3; ++a) quad_test(S, d[a] > 0.0f ? S.wall_hi[a] : S.wall_lo[a], a, o, d, inv, best, prim);
     }
+#pragma unroll
+    for (int q = 6; q <= kLight; ++q) quad_test(S, q, kAxis[q], o, d, inv, best, prim);
 #pragma unroll
     for (int i = 0; i < 3; ++i) {
         const float4 sp = S.sph[i];
@@ -148,9 +166,14 @@ __device__ __noinline__ int intersect_canon(const PtShared& S, const float o[3],
     return prim;
 }
 
+__device__ __forceinline__ bool inside_box(const PtShared& S, const float o[3]) {
+    return o[0] >= S.box_lo[0] && o[0] <= S.box_hi[0] && o[1] >= S.box_lo[1] && o[1] <= S.box_hi[1] &&
+           o[2] >= S.box_lo[2] && o[2] <= S.box_hi[2];
+}
+
 template <bool kCanon>
 __device__ __forceinline__ int closest_hit(const PtShared& S, const float o[3], const float d[3], float& t_out) {
-    return kCanon ? intersect_canon(S, o, d, t_out, false) : intersect(S, o, d, t_out);
+    return kCanon ? intersect_canon(S, o, d, t_out, inside_box(S, o) ? 1 : 0) : intersect(S, o, d, t_out);
 }
 
 // Is the light the closest primitive along a shadow ray?
@@ -158,9 +181,8 @@ template <bool kCanon>
 __device__ __forceinline__ bool sees_light(const PtShared& S, const float o[3], const float d[3]) {
     float t;
     if (!kCanon) return intersect(S, o, d, t) == kLight;
-    const bool inside = S.light_inside && o[0] >= S.box_lo[0] && o[0] <= S.box_hi[0] && o[1] >= S.box_lo[1] &&
-                        o[1] <= S.box_hi[1] && o[2] >= S.box_lo[2] && o[2] <= S.box_hi[2];
-    return intersect_canon(S, o, d, t, inside) == kLight;
+    const int walls = inside_box(S, o) ? (S.light_inside ? 2 : 1) : 0;
+    return intersect_canon(S, o, d, t, walls) == kLight;
 }
 
 template <bool kCanon>
@@ -302,6 +324,8 @@ __device__ void load_scene(const PtArgs& A, const float* p, PtShared& S) {
             const float p0 = A.qgeom[2 * a][0], p1 = A.qgeom[2 * a + 1][0];
             S.box_lo[a] = fminf(p0, p1);
             S.box_hi[a] = fmaxf(p0, p1);
+            S.wall_lo[a] = p0 <= p1 ? 2 * a : 2 * a + 1;
+            S.wall_hi[a] = p0 <= p1 ? 2 * a + 1 : 2 * a;
             in = in && lmin[a] >= S.box_lo[a] + kWallMargin && lmax[a] <= S.box_hi[a] - kWallMargin;
         }
         S.light_inside = in ? 1 : 0;

@@ -20,7 +20,15 @@ struct __align__(16) T2Rec {
     float B1, C1, A2, B2;
     float C2, r, g, bl;
     int xlo, xhi, ylo, yhi;
+    float th0, th1, th2, pad;   // edge i passes when E_i > th_i (see tl_thr)
 };
+
+// E > 0, or E == 0 on a top-left edge (A > 0, or A == 0 and B > 0), is one
+// compare E > th: th = 0, or th = -(smallest subnormal), no float lying
+// strictly between the two
+__device__ __forceinline__ float tl_thr(float A, float B) {
+    return (A > 0.0f || (A == 0.0f && B > 0.0f)) ? -0x1p-149f : 0.0f;
+}
 
 __device__ __forceinline__ bool pixel_range2(float mn, float mx, int N, int& lo, int& hi) {
     if (!(mx >= 0.5f) || !(mn <= (float)N - 0.5f)) return false;
@@ -50,6 +58,8 @@ __device__ bool setup_tri(const float* q, int W, int H, T2Rec& r) {
     r.A1 = e1.A; r.B1 = e1.B; r.C1 = e1.C;
     r.A2 = e2.A; r.B2 = e2.B; r.C2 = e2.C;
     r.r = q[6]; r.g = q[7]; r.bl = q[8];
+    r.th0 = tl_thr(e0.A, e0.B); r.th1 = tl_thr(e1.A, e1.B); r.th2 = tl_thr(e2.A, e2.B);
+    r.pad = 0.0f;
     return true;
 }
 
@@ -83,9 +93,13 @@ tris2d_kernel(RenderBatch b, const float* __restrict__ raw, const int32_t* __res
     const int npx = W * H;
     const int lane = tid & 31, warp = tid >> 5;
     const int TXn = (W + 7) / 8, TYn = (H + 3) / 4;
-    for (int t = warp; t < TXn * TYn; t += kThreads / 32) {
-        const int ty = t / TXn, tx = t - ty * TXn;
+    constexpr int kWarps = kThreads / 32;
+    // tile t = ty TXn + tx, stepped by kWarps without a division per tile
+    int ty = warp / TXn, tx = warp - ty * TXn;
+    for (int t = warp; t < TXn * TYn; t += kWarps) {
         const int x0 = tx * 8, y0 = ty * 4;
+        tx += kWarps;
+        while (tx >= TXn) { tx -= TXn; ++ty; }
         const int x = x0 + (lane & 7), y = y0 + (lane >> 3);
         bool over = false;
         if (lane < n_tris && s_valid[lane]) {
@@ -105,7 +119,7 @@ tris2d_kernel(RenderBatch b, const float* __restrict__ raw, const int32_t* __res
                     const float E0 = edge_eval(r.A0, r.B0, r.C0, fx, fy);
                     const float E1 = edge_eval(r.A1, r.B1, r.C1, fx, fy);
                     const float E2 = edge_eval(r.A2, r.B2, r.C2, fx, fy);
-                    if (edge_in(r.A0, r.B0, E0) && edge_in(r.A1, r.B1, E1) && edge_in(r.A2, r.B2, E2)) win = k;
+                    if (E0 > r.th0 && E1 > r.th1 && E2 > r.th2) win = k;
                 }
             }
             if (__all_sync(0xffffffffu, win >= 0 || !inside_img)) break;

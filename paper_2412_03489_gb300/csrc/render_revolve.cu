@@ -61,6 +61,7 @@ struct RvArgs {
     const float* target;
     const float* tile_t2;
     int nv, nt, W, H, TX, TY, T;
+    uint64_t tx_recip;   // ceil(2^32 / TX): t / TX = (t tx_recip) >> 32 exactly for t, TX < 2^16
     float alb0, alb1, alb2, l0, l1, l2, eye_dist, scale;
 };
 
@@ -305,8 +306,6 @@ revolve_kernel(RvArgs P, RenderBatch b, const float* __restrict__ img_params, fl
             if (lane == 0) t = atomicAdd(&s_tile, 1);
             t = __shfl_sync(0xffffffffu, t, 0);
             if (t >= P.T) break;
-            const int ty = t / P.TX, tx = t - ty * P.TX;
-            const int x0 = tx * kTile + 4 * hx, y = ty * kTile + ry;
             int beg, end;
             if (overflow) { beg = 0; end = count; }
             else { beg = toff[t]; end = (t + 1 < P.T) ? toff[t + 1] : total; }
@@ -314,6 +313,10 @@ revolve_kernel(RvArgs P, RenderBatch b, const float* __restrict__ img_params, fl
                 if (lane == 0) tile_loss[t] = P.tile_t2[t];
                 continue;
             }
+            // division by multiplication with the rounded-up reciprocal
+            // (Granlund and Montgomery, PLDI 1994): exact for t, TX < 2^16
+            const int ty = (int)(((uint64_t)(uint32_t)t * P.tx_recip) >> 32), tx = t - ty * P.TX;
+            const int x0 = tx * kTile + 4 * hx, y = ty * kTile + ry;
             // loss pixels of this lane after the merge: columns x0 + 2 half, x0 + 2 half + 1
             const int xa = x0 + 2 * half, xb = xa + 1;
             const bool va = xa < P.W && y < P.H, vb = xb < P.W && y < P.H;
@@ -453,6 +456,7 @@ RvArgs make_args(const DevScene& sc) {
     a.verts = sc.verts; a.tris = sc.tris; a.tnrm = sc.tnrm; a.target = sc.target; a.tile_t2 = sc.tile_t2;
     a.nv = sc.nv; a.nt = sc.nt; a.W = sc.W; a.H = sc.H;
     a.TX = (sc.W + kTile - 1) / kTile; a.TY = (sc.H + kTile - 1) / kTile; a.T = a.TX * a.TY;
+    a.tx_recip = ((uint64_t(1) << 32) + (uint64_t)a.TX - 1) / (uint64_t)a.TX;
     a.alb0 = sc.albedo[0]; a.alb1 = sc.albedo[1]; a.alb2 = sc.albedo[2];
     a.l0 = sc.light[0]; a.l1 = sc.light[1]; a.l2 = sc.light[2];
     a.eye_dist = sc.eye_dist; a.scale = sc.scale;

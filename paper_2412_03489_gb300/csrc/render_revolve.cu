@@ -301,11 +301,12 @@ revolve_kernel(RvArgs P, RenderBatch b, const float* __restrict__ img_params, fl
                 s_cs_next[lane] = (float)((lane & 1) ? sin(a) : cos(a));
             }
         }
-        for (;;) {
-            int t = 0;
-            if (lane == 0) t = atomicAdd(&s_tile, 1);
-            t = __shfl_sync(0xffffffffu, t, 0);
-            if (t >= P.T) break;
+        // each warp reserves its next tile when it starts the current one, so
+        // the shared atomic's latency overlaps the tile's work
+        int t_next = 0;
+        if (lane == 0) t_next = atomicAdd(&s_tile, 1);
+        for (int t = __shfl_sync(0xffffffffu, t_next, 0); t < P.T; t = __shfl_sync(0xffffffffu, t_next, 0)) {
+            if (lane == 0) t_next = atomicAdd(&s_tile, 1);
             int beg, end;
             if (overflow) { beg = 0; end = count; }
             else { beg = toff[t]; end = (t + 1 < P.T) ? toff[t + 1] : total; }

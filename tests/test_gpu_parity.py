@@ -163,6 +163,28 @@ def test_ptbox_images_match():
     Sc.close()
 
 
+@pytest.mark.parametrize("case", ["light_within_margin", "light_above_ceiling", "camera_outside"])
+def test_ptbox_wall_cut_fallbacks(case):
+    """The closest-hit test skips walls only when that cannot change a result
+    (origin inside the box; for shadow rays also the light 1e-3 inside every
+    wall plane).  Scenes where those conditions fail take the full tests and
+    still match the oracle's brute-force path tracer."""
+    sc = wl.ptbox_scene(width=24, height=20, spp=2, target_spp=4)
+    p = np.asarray(sc["theta_query"], np.float64).copy()
+    if case == "light_within_margin":
+        p[1] = 0.9995
+    elif case == "light_above_ceiling":
+        p[1] = 1.02
+    else:
+        sc["cam_z"] = np.float32(1.4)
+    Sc = hr.Scene(sc)
+    r = O.PtboxRenderer(sc)
+    gi = Sc.render(p, seed=5, request=2, sub=1, k=3, tag=hr.TAG_PATH, spp=2)
+    oi = r.image(p.astype(np.float32), 2, 5, 2, 1, 3, O.TAG_PATH)
+    assert np.allclose(gi, oi, rtol=2e-5, atol=2e-5 * max(oi.max(), 1e-6)), case
+    Sc.close()
+
+
 def test_ptbox_hvp_small():
     sc = wl.ptbox_scene(width=20, height=16, spp=2, target_spp=4)
     flat, dbg, ref = run_both(sc, O.PtboxRenderer(sc), "hvp", 16, "aggregate", v=sc["v"])

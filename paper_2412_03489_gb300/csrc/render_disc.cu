@@ -69,6 +69,50 @@ __device__ __forceinline__ float lane_l2(const float* __restrict__ target, int W
     return acc;
 }
 
+// Disc loss of one lane for W = 32 kCpr: the lane's kCpr columns are fixed,
+// so dx = px - cx is formed once per render and dy^2 once per row; a pixel is
+// then the test fma(dx, dx, dy^2) < r^2 of disc_value.  Rows go in order and
+// columns in order within a row: the pixel order of lane_l2, so the same sum.
+template <int kCpr>
+__device__ __forceinline__ float disc_rows(const float* __restrict__ target, int H, int lane, const float* px,
+                                           const float* py, float cx, float cy, float r2) {
+    constexpr int kRows = kCpr >= 4 ? 1 : 4 / kCpr;   // target loads of kRows rows in flight
+    constexpr int W = 32 * kCpr;
+    float dx[kCpr];
+#pragma unroll
+    for (int c = 0; c < kCpr; ++c) dx[c] = __fsub_rn(px[lane + 32 * c], cx);
+    float acc = 0.0f;
+    int y = 0;
+    for (; y + kRows <= H; y += kRows) {
+        float t[kRows][kCpr];
+#pragma unroll
+        for (int r = 0; r < kRows; ++r)
+#pragma unroll
+            for (int c = 0; c < kCpr; ++c) t[r][c] = __ldg(target + (size_t)(y + r) * W + lane + 32 * c);
+#pragma unroll
+        for (int r = 0; r < kRows; ++r) {
+            const float dy = __fsub_rn(py[y + r], cy);
+            const float dy2 = __fmul_rn(dy, dy);
+#pragma unroll
+            for (int c = 0; c < kCpr; ++c) {
+                const float d = __fsub_rn(__fmaf_rn(dx[c], dx[c], dy2) < r2 ? 1.0f : 0.0f, t[r][c]);
+                acc = __fmaf_rn(d, d, acc);
+            }
+        }
+    }
+    for (; y < H; ++y) {
+        const float dy = __fsub_rn(py[y], cy);
+        const float dy2 = __fmul_rn(dy, dy);
+#pragma unroll
+        for (int c = 0; c < kCpr; ++c) {
+            const float d = __fsub_rn(__fmaf_rn(dx[c], dx[c], dy2) < r2 ? 1.0f : 0.0f,
+                                      __ldg(target + (size_t)y * W + lane + 32 * c));
+            acc = __fmaf_rn(d, d, acc);
+        }
+    }
+    return acc;
+}
+
 template <int kW>
 __global__ void __launch_bounds__(32 * kW) disc_loss_kernel(RenderBatch b, int W, int H, float radius,
                                                             const float* __restrict__ target) {
@@ -88,8 +132,15 @@ __global__ void __launch_bounds__(32 * kW) disc_loss_kernel(RenderBatch b, int W
         const float dy = __fsub_rn(py, cy);
         return __fmaf_rn(dx, dx, __fmul_rn(dy, dy)) < r2 ? 1.0f : 0.0f;
     };
-    float acc = W >= 32 ? lane_l2<true>(target, W, npx, lane, s_px, s_py, value)
-                        : lane_l2<false>(target, W, npx, lane, s_px, s_py, value);
+    float acc;
+    switch (W) {
+        case 32: acc = disc_rows<1>(target, H, lane, s_px, s_py, cx, cy, r2); break;
+        case 64: acc = disc_rows<2>(target, H, lane, s_px, s_py, cx, cy, r2); break;
+        case 128: acc = disc_rows<4>(target, H, lane, s_px, s_py, cx, cy, r2); break;
+        default:
+            acc = W >= 32 ? lane_l2<true>(target, W, npx, lane, s_px, s_py, value)
+                          : lane_l2<false>(target, W, npx, lane, s_px, s_py, value);
+    }
     acc = warp_sum(acc);
     if (lane == 0) *pt.loss = __fdiv_rn(acc, (float)npx);
 }

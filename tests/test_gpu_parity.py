@@ -72,7 +72,7 @@ def test_disc_hvp_and_identity():
     assert np.allclose(H @ v, flat, rtol=1e-5, atol=1e-5 * np.abs(ref.scale).max())
 
 
-@pytest.mark.parametrize("W,H,M", [(37, 23, 2), (1, 1, 6), (64, 64, 2)])
+@pytest.mark.parametrize("W,H,M", [(37, 23, 2), (1, 1, 6), (64, 64, 2), (32, 17, 4), (128, 9, 4), (64, 33, 2)])
 def test_disc_ragged_and_minimum(W, H, M):
     sc = wl.disc_scene(width=W, height=H)
     flat, dbg, ref = run_both(sc, O.DiscRenderer(sc), "hessian", M, "aggregate")
@@ -82,6 +82,22 @@ def test_disc_ragged_and_minimum(W, H, M):
     assert np.array_equal(np.rint(dbg["losses"].astype(np.float64) * npx), np.rint(ref.losses * npx))
     assert np.all(np.abs(dbg["losses"] - ref.losses) <= np.spacing(np.float32(ref.losses)))
     assert_estimate_close(flat, ref, what="disc ragged")
+
+
+@pytest.mark.parametrize("W,H", [(64, 21), (96, 10), (128, 7)])
+def test_disc_grey_target(W, H):
+    """A caller's target image with grey levels (the renderer's own targets are
+    0/1, whose sums are exact in any order): every loss within FP32 rounding of
+    the oracle's FP64 loss, on both pixel loops (fixed columns per lane for
+    W = 64 and 128, the general loop for W = 96)."""
+    sc = wl.disc_scene(width=W, height=H)
+    tgt = np.random.default_rng(W * 1000 + H).uniform(0.0, 1.0, size=W * H).astype(np.float32)
+    Sc = hr.Scene(sc, target_image=tgt)
+    flat, dbg, ref = run_both(sc, O.DiscRenderer(sc, target=tgt), "hessian", 64, "aggregate", scene=Sc)
+    Sc.close()
+    check_samples(dbg, ref)
+    assert_losses_close(dbg["losses"], ref.losses, 2e-6, "disc grey-target losses")
+    assert_estimate_close(flat, ref, what="disc grey target")
 
 
 # ---------------------------------------------------------------------------

@@ -715,7 +715,7 @@ def main():
                 "e2e": {"value": e2e_rate, "unit": "estimates/s", "h2d_bytes_per_step": 8 + 40,
                         "d2h_bytes_per_step": 32},
                 "stage_ms": dict(zip(("sample", "render_loss", "sums"), np.mean(stage_ms, axis=0).tolist())),
-                "gpu_launches": 4 * args.steps,   # theta to FP32, sampler, render + loss, sums
+                "gpu_launches": 3 * args.steps,   # sampler (also writes theta in FP32), render + loss, sums
                 "tuning": tuning,
                 "clocks": clk}
         # statistical error of one estimate against a converged reference: the

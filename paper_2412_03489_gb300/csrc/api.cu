@@ -125,16 +125,6 @@ __global__ void fd_combine_kernel(const double* gp, const double* gm, double inv
     if (i < n) out[i] = (gp[i] - gm[i]) * inv2eps;
 }
 
-struct ThetaArg { float v[64]; };
-__global__ void set_theta_kernel(ThetaArg a, float* out, int n) {
-    if ((int)threadIdx.x < n) out[threadIdx.x] = a.v[threadIdx.x];
-}
-
-__global__ void f64_to_f32_kernel(const double* in, float* out, int n) {
-    const int i = blockIdx.x * blockDim.x + threadIdx.x;
-    if (i < n) out[i] = __double2float_rn(in[i]);
-}
-
 int n_elements(int quantity, int n) { return quantity == HR_HESSIAN ? n * (n + 1) / 2 : n; }
 
 hr_status validate_opts(const hr_scene_s* s, int quantity, const hr_opts* o) {
@@ -196,15 +186,10 @@ hr_status run_estimate(hr_scene_s* s, int quantity, const double* h_theta, const
         cudaError_t e_ = (x);                                                                   \
         if (e_ != cudaSuccess) return fail(HR_ERR_CUDA, "%s: %s", #x, cudaGetErrorString(e_));  \
     } while (0)
+    // theta in FP32 is written by the sampler launch (its first block): from
+    // the device array, or from values passed by value (n <= 64: no host
+    // staging, no wait)
     float* theta32 = (float*)ws.theta32.ptr;
-    if (h_theta) {
-        // parameters by value (n <= 64): no host staging, no wait
-        ThetaArg ta{};
-        for (int i = 0; i < n; ++i) ta.v[i] = (float)h_theta[i];
-        set_theta_kernel<<<1, 64, 0, stream>>>(ta, theta32, n);
-    } else {
-        f64_to_f32_kernel<<<(n + 127) / 128, 128, 0, stream>>>(d_theta, theta32, n);
-    }
     const double* vdev = d_v;
     if (quantity == HR_HVP && h_v) {
         CU_TRY(cudaMemcpyAsync(ws.v.ptr, h_v, sizeof(double) * n, cudaMemcpyHostToDevice, stream));
@@ -242,6 +227,11 @@ hr_status run_estimate(hr_scene_s* s, int quantity, const double* h_theta, const
     }
 
     SampleArgs sa{};
+    sa.theta_out = theta32;
+    sa.theta_n = n;
+    sa.theta_in = h_theta ? nullptr : d_theta;
+    if (h_theta)
+        for (int i = 0; i < n; ++i) sa.theta_vals[i] = (float)h_theta[i];
     sa.groups = (const SampleGroup*)ws.groups.ptr;
     sa.n = n;
     sa.E = E;

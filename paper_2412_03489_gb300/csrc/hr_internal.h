@@ -40,6 +40,12 @@ struct SampleArgs {
     // up to kInlineGroups groups passed by value (n_inline > 0: groups[] is not read)
     int32_t n_inline;
     SampleGroup inline_groups[4];
+    // optional: the first block also writes theta in FP32 (RN) to theta_out[theta_n],
+    // from theta_in (device, FP64) or, when theta_in is null, from theta_vals
+    const double* theta_in;
+    float* theta_out;
+    int32_t theta_n;
+    float theta_vals[64];
 };
 constexpr int kInlineGroups = 4;
 

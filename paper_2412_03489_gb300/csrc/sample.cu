@@ -289,6 +289,10 @@ __global__ void __launch_bounds__(kSampleThreadsMax) sample_kernel(SampleArgs a,
     // one; both derive the pair's component and shared dims from the same
     // Philox words, so the FP64-heavy lobe inverse and weights of the two
     // legs run side by side (FP64 latency dominates this kernel)
+    if (a.theta_out && blockIdx.x == 0 && blockIdx.y == 0) {
+        for (int d = threadIdx.x; d < a.theta_n; d += blockDim.x)
+            a.theta_out[d] = a.theta_in ? __double2float_rn(a.theta_in[d]) : a.theta_vals[d];
+    }
     const int tk = blockIdx.x * blockDim.x + threadIdx.x;
     const int k = tk >> 1, leg = tk & 1;
     if (k >= G.P) return;

@@ -293,14 +293,49 @@ __global__ void __launch_bounds__(kSampleThreadsMax) sample_kernel(SampleArgs a,
         for (int d = threadIdx.x; d < a.theta_n; d += blockDim.x)
             a.theta_out[d] = a.theta_in ? __double2float_rn(a.theta_in[d]) : a.theta_vals[d];
     }
-    const int tk = blockIdx.x * blockDim.x + threadIdx.x;
-    const int k = tk >> 1, leg = tk & 1;
-    if (k >= G.P) return;
     const int n = a.n;
-    const Lobes L = lobes_for(a, G, host_lobes);
-    const double sigma = L.sigma;
     const uint32_t sub = G.sub + (a.step ? 64u * (uint32_t)(*a.step) : 0u);
     const uint32_t c2 = (TAG_SAMPLE << 24) | (sub & 0xFFFFFFu);
+    const int leg = threadIdx.x & 1;
+    const int kb = blockIdx.x * (blockDim.x >> 1);   // first pair of this block
+    int k = kb + (threadIdx.x >> 1);
+    if (G.comp_i == -1 && G.lobe == 1 && blockDim.x >= 64 && n > 1) {
+        // Aggregate Hessian lobes: a pair's component is diagonal (the long
+        // Lambert-W root) or off-diagonal (two half-Rayleigh radii).  With two
+        // or more warps per block, the block's pairs are taken diagonal ones
+        // first, so that most warps run one of the two paths instead of both;
+        // every pair is computed by the same code either way.
+        __shared__ int s_order[kSampleThreadsMax / 2];
+        __shared__ int s_cnt[2][2];
+        const int np = blockDim.x >> 1, p = threadIdx.x, lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+        bool valid = false, diag = false;
+        if (p < np && kb + p < G.P) {
+            valid = true;
+            const u32x4 wq = philox_seed(a.seed, (uint32_t)(kb + p), 0u, c2, G.request);
+            const int e = (int)(((uint64_t)wq.x * (uint64_t)(n * n)) >> 32);
+            diag = e / n == e - (e / n) * n;
+        }
+        unsigned bd = 0u, bo = 0u;
+        if (w < 2) {
+            bd = __ballot_sync(0xffffffffu, valid && diag);
+            bo = __ballot_sync(0xffffffffu, valid && !diag);
+            if (lane == 0) { s_cnt[0][w] = __popc(bd); s_cnt[1][w] = __popc(bo); }
+        }
+        __syncthreads();
+        if (w < 2 && p < np) {
+            const unsigned lt = (1u << lane) - 1u;
+            const int nd = s_cnt[0][0] + s_cnt[0][1];
+            int pos = p;   // pairs past the end of the group keep their place (after all valid ones)
+            if (valid && diag) pos = __popc(bd & lt) + (w ? s_cnt[0][0] : 0);
+            else if (valid) pos = nd + __popc(bo & lt) + (w ? s_cnt[1][0] : 0);
+            s_order[pos] = p;
+        }
+        __syncthreads();
+        k = kb + s_order[threadIdx.x >> 1];
+    }
+    if (k >= G.P) return;
+    const Lobes L = lobes_for(a, G, host_lobes);
+    const double sigma = L.sigma;
     const u32x4 w0 = philox_seed(a.seed, (uint32_t)k, 0u, c2, G.request);
     int i, j;
     if (G.comp_i == -3) {

@@ -447,8 +447,11 @@ hr_status hr_profile_last(hr_scene scene, float* ms3);
  * variants (path tracer: minimum resident CTAs per SM 3 / 2 / 4, i.e. register
  * caps; disc and squares: 8 / 4 / 16 warps per CTA, one warp per
  * perturbation; mesh and 2D triangles: one shape) and the sampler runs with
- * 16, 32, 64 or 128 threads per block (16 spreads small requests over more SMs).  Every variant computes the same values in
- * the same order, so results are bit-identical whatever is chosen.
+ * 16, 32, 64 or 128 threads per block (16 spreads small requests over more
+ * SMs; with 64 or 128, a block takes its aggregate Hessian pairs diagonal-lobe
+ * ones first so that most warps run one lobe path).  Every variant computes
+ * each value with the same operations in the same order, so results are
+ * bit-identical whatever is chosen.
  * hr_autotune times each variant on profiled aggregate HVP estimates of
  * max(n_probe, 8 x the SM count) perturbations at h_theta [n] (v = ones,
  * sigma 0.05; median of 3 after a warm-up; the floor keeps the GPU full so

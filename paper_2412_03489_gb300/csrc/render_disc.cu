@@ -76,7 +76,7 @@ __device__ __forceinline__ float lane_l2(const float* __restrict__ target, int W
 template <int kCpr>
 __device__ __forceinline__ float disc_rows(const float* __restrict__ target, int H, int lane, const float* px,
                                            const float* py, float cx, float cy, float r2) {
-    constexpr int kRows = kCpr >= 4 ? 1 : 4 / kCpr;   // target loads of kRows rows in flight
+    constexpr int kRows = 16 / kCpr;   // target loads of kRows rows (16 loads) in flight
     constexpr int W = 32 * kCpr;
     float dx[kCpr];
 #pragma unroll

@@ -69,7 +69,7 @@ __device__ __forceinline__ float lane_l2(const float* __restrict__ target, int W
     return acc;
 }
 
-// Disc loss of one lane for W = 32 kCpr: the lane's kCpr columns are fixed,
+// Disc loss of one lane for W = 32 kCpr (32 to 512): the lane's kCpr columns are fixed,
 // so dx = px - cx is formed once per render and dy^2 once per row; a pixel is
 // then the test fma(dx, dx, dy^2) < r^2 of disc_value.  Rows go in order and
 // columns in order within a row: the pixel order of lane_l2, so the same sum.
@@ -133,10 +133,12 @@ __global__ void __launch_bounds__(32 * kW) disc_loss_kernel(RenderBatch b, int W
         return __fmaf_rn(dx, dx, __fmul_rn(dy, dy)) < r2 ? 1.0f : 0.0f;
     };
     float acc;
-    switch (W) {
+    switch (W) {   // the widths with a fixed-column loop; any other takes lane_l2
         case 32: acc = disc_rows<1>(target, H, lane, s_px, s_py, cx, cy, r2); break;
         case 64: acc = disc_rows<2>(target, H, lane, s_px, s_py, cx, cy, r2); break;
         case 128: acc = disc_rows<4>(target, H, lane, s_px, s_py, cx, cy, r2); break;
+        case 256: acc = disc_rows<8>(target, H, lane, s_px, s_py, cx, cy, r2); break;
+        case 512: acc = disc_rows<16>(target, H, lane, s_px, s_py, cx, cy, r2); break;
         default:
             acc = W >= 32 ? lane_l2<true>(target, W, npx, lane, s_px, s_py, value)
                           : lane_l2<false>(target, W, npx, lane, s_px, s_py, value);

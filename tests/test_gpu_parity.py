@@ -72,7 +72,8 @@ def test_disc_hvp_and_identity():
     assert np.allclose(H @ v, flat, rtol=1e-5, atol=1e-5 * np.abs(ref.scale).max())
 
 
-@pytest.mark.parametrize("W,H,M", [(37, 23, 2), (1, 1, 6), (64, 64, 2), (32, 17, 4), (128, 9, 4), (64, 33, 2)])
+@pytest.mark.parametrize("W,H,M", [(37, 23, 2), (1, 1, 6), (64, 64, 2), (32, 17, 4), (128, 9, 4), (64, 33, 2),
+                                   (256, 5, 2), (512, 3, 2)])
 def test_disc_ragged_and_minimum(W, H, M):
     sc = wl.disc_scene(width=W, height=H)
     flat, dbg, ref = run_both(sc, O.DiscRenderer(sc), "hessian", M, "aggregate")
@@ -84,12 +85,12 @@ def test_disc_ragged_and_minimum(W, H, M):
     assert_estimate_close(flat, ref, what="disc ragged")
 
 
-@pytest.mark.parametrize("W,H", [(64, 21), (96, 10), (128, 7)])
+@pytest.mark.parametrize("W,H", [(64, 21), (96, 10), (128, 7), (512, 3)])
 def test_disc_grey_target(W, H):
     """A caller's target image with grey levels (the renderer's own targets are
     0/1, whose sums are exact in any order): every loss within FP32 rounding of
     the oracle's FP64 loss, on both pixel loops (fixed columns per lane for
-    W = 64 and 128, the general loop for W = 96)."""
+    W = 64, 128 and 512, the general loop for W = 96)."""
     sc = wl.disc_scene(width=W, height=H)
     tgt = np.random.default_rng(W * 1000 + H).uniform(0.0, 1.0, size=W * H).astype(np.float32)
     Sc = hr.Scene(sc, target_image=tgt)

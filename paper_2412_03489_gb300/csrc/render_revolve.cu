@@ -94,40 +94,51 @@ __device__ __forceinline__ bool tile_hits(const TriRec& r, const float neg[3], i
     return hit;
 }
 
-// exclusive scan of cnt[0..T) into off[0..T); returns the total (all threads)
-__device__ int block_scan(const int* cnt, int* off, int T, int* warp_tot) {
+// Exclusive scan of cnt[0..T) into off[0..T) and, in the same pass, the
+// list of tiles with entries (olist[0..n_obj), in tile order): each tile
+// contributes cnt + (cnt > 0) 2^32 to one 64-bit scan.  Returns the total
+// entry count (all threads) and sets n_obj.
+__device__ int bin_scan(const int* cnt, int* off, uint16_t* olist, int T, unsigned long long* warp_tot,
+                        int* n_obj) {
     const int per = (T + kThreads - 1) / kThreads;
     const int b = threadIdx.x * per;
-    int local = 0;
+    auto packed = [](int c) { return (unsigned long long)c + ((unsigned long long)(c > 0) << 32); };
+    unsigned long long local = 0ull;
     for (int i = 0; i < per; ++i)
-        if (b + i < T) local += cnt[b + i];
+        if (b + i < T) local += packed(cnt[b + i]);
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    int incl = local;
+    unsigned long long incl = local;
 #pragma unroll
     for (int o = 1; o < 32; o <<= 1) {
-        const int v = __shfl_up_sync(0xffffffffu, incl, o);
+        const unsigned long long v = __shfl_up_sync(0xffffffffu, incl, o);
         if (lane >= o) incl += v;
     }
     if (lane == 31) warp_tot[warp] = incl;
     __syncthreads();
     if (warp == 0) {
-        int wv = warp_tot[lane];
-        int wi = wv;
+        const unsigned long long wv = warp_tot[lane];
+        unsigned long long wi = wv;
 #pragma unroll
         for (int o = 1; o < 32; o <<= 1) {
-            const int v = __shfl_up_sync(0xffffffffu, wi, o);
+            const unsigned long long v = __shfl_up_sync(0xffffffffu, wi, o);
             if (lane >= o) wi += v;
         }
         warp_tot[lane] = wi - wv;       // exclusive warp offsets
         if (lane == 31) warp_tot[32] = wi;
     }
     __syncthreads();
-    int run = warp_tot[warp] + incl - local;
+    unsigned long long run = warp_tot[warp] + incl - local;
     for (int i = 0; i < per; ++i)
-        if (b + i < T) { off[b + i] = run; run += cnt[b + i]; }
-    const int total = warp_tot[32];
+        if (b + i < T) {
+            const int c = cnt[b + i];
+            off[b + i] = (int)(run & 0xffffffffull);
+            if (c > 0) olist[run >> 32] = (uint16_t)(b + i);
+            run += packed(c);
+        }
+    const unsigned long long total = warp_tot[32];
     __syncthreads();
-    return total;
+    *n_obj = (int)(total >> 32);
+    return (int)(total & 0xffffffffull);
 }
 
 // rotation angle d of perturbation m: RN32(theta32 + tau)
@@ -144,7 +155,7 @@ revolve_kernel(RvArgs P, RenderBatch b, const float* __restrict__ img_params, fl
     float* vx = reinterpret_cast<float*>(rec + P.nt);
     float* vy = vx + P.nv;
     float* viz = vy + P.nv;
-    int* tcnt = reinterpret_cast<int*>(viz + P.nv);
+    int* tcnt = reinterpret_cast<int*>(vx + max(3 * P.nv, (P.T + 1) / 2));
     int* toff = tcnt + P.T;
     uint16_t* ent = reinterpret_cast<uint16_t*>(toff + P.T);
 
@@ -152,11 +163,14 @@ revolve_kernel(RvArgs P, RenderBatch b, const float* __restrict__ img_params, fl
     __shared__ float sR[9];
     __shared__ float sL[3];
     __shared__ int s_count;
-    __shared__ int s_wtot[33];
+    __shared__ unsigned long long s_wtot[33];
     __shared__ float s_part[kWarps];
     __shared__ int s_tile;
     float* tshade = reinterpret_cast<float*>(ent + kEntryCap);   // [nt] shade by triangle index
     uint32_t* tmask = reinterpret_cast<uint32_t*>(tshade + P.nt);  // [nt] tiles hit, by record slot
+    // [T] tiles with entries, in tile order: in the vertex arrays, free once
+    // the triangles are set up (the region holds max(3 nv, T / 2) floats)
+    uint16_t* olist = reinterpret_cast<uint16_t*>(vx);
 
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     const int M = kImage ? 1 : b.M;
@@ -257,7 +271,8 @@ revolve_kernel(RvArgs P, RenderBatch b, const float* __restrict__ img_params, fl
             tmask[s] = test ? mask : 0xFFFFFFFFu;
         }
         __syncthreads();
-        const int total = block_scan(tcnt, toff, P.T, s_wtot);
+        int n_obj = 0;
+        const int total = bin_scan(tcnt, toff, olist, P.T, s_wtot, &n_obj);
         const bool overflow = total > kEntryCap;
         for (int i = tid; i < P.T; i += kThreads) tcnt[i] = 0;   // becomes the fill cursor
         __syncthreads();
@@ -303,17 +318,18 @@ revolve_kernel(RvArgs P, RenderBatch b, const float* __restrict__ img_params, fl
         }
         // each warp reserves its next tile when it starts the current one, so
         // the shared atomic's latency overlaps the tile's work
+        // tiles without entries are not visited: their loss, the sum of
+        // target^2, is taken in the reduction (an image visits every tile)
+        const bool all_tiles = kImage || overflow;
+        const int n_iter = all_tiles ? P.T : n_obj;
         int t_next = 0;
         if (lane == 0) t_next = atomicAdd(&s_tile, 1);
-        for (int t = __shfl_sync(0xffffffffu, t_next, 0); t < P.T; t = __shfl_sync(0xffffffffu, t_next, 0)) {
+        for (int it = __shfl_sync(0xffffffffu, t_next, 0); it < n_iter; it = __shfl_sync(0xffffffffu, t_next, 0)) {
             if (lane == 0) t_next = atomicAdd(&s_tile, 1);
+            const int t = all_tiles ? it : (int)olist[it];
             int beg, end;
             if (overflow) { beg = 0; end = count; }
             else { beg = toff[t]; end = (t + 1 < P.T) ? toff[t + 1] : total; }
-            if (!kImage && !overflow && beg == end) {
-                if (lane == 0) tile_loss[t] = P.tile_t2[t];
-                continue;
-            }
             // division by multiplication with the rounded-up reciprocal
             // (Granlund and Montgomery, PLDI 1994): exact for t, TX < 2^16
             const int ty = (int)(((uint64_t)(uint32_t)t * P.tx_recip) >> 32), tx = t - ty * P.TX;
@@ -407,7 +423,10 @@ revolve_kernel(RvArgs P, RenderBatch b, const float* __restrict__ img_params, fl
             __syncthreads();
             // thread i sums tiles i, i + 1024, ...; then a fixed shuffle tree
             float acc = 0.0f;
-            for (int t = tid; t < P.T; t += kThreads) acc += tile_loss[t];
+            for (int t = tid; t < P.T; t += kThreads) {
+                const bool has = overflow || ((t + 1 < P.T) ? toff[t + 1] : total) > toff[t];
+                acc += has ? tile_loss[t] : P.tile_t2[t];
+            }
             acc = warp_sum(acc);
             if (lane == 0) s_part[warp] = acc;
             __syncthreads();
@@ -468,7 +487,8 @@ RvArgs make_args(const DevScene& sc) {
 
 size_t revolve_smem_bytes(int nv, int nt, int W, int H) {
     const int T = ((W + kTile - 1) / kTile) * ((H + kTile - 1) / kTile);
-    return sizeof(TriRec) * (size_t)nt + 3 * sizeof(float) * (size_t)nv + 2 * sizeof(int) * (size_t)T +
+    const size_t vreg = 3 * (size_t)nv > (size_t)(T + 1) / 2 ? 3 * (size_t)nv : (size_t)(T + 1) / 2;
+    return sizeof(TriRec) * (size_t)nt + sizeof(float) * vreg + 2 * sizeof(int) * (size_t)T +
            sizeof(uint16_t) * kEntryCap + sizeof(float) * (size_t)nt + sizeof(uint32_t) * (size_t)nt;
 }
 

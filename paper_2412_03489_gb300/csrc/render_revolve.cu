@@ -34,6 +34,7 @@ constexpr int kThreads = 1024;
 constexpr int kWarps = kThreads / 32;
 constexpr int kTile = 8;
 constexpr int kEntryCap = 16384;
+constexpr int kHeavy = 8;   // tiles with at least this many entries are fetched first
 
 struct __align__(16) TriRec {
     float A0, B0, C0, A1;
@@ -95,14 +96,20 @@ __device__ __forceinline__ bool tile_hits(const TriRec& r, const float neg[3], i
 }
 
 // Exclusive scan of cnt[0..T) into off[0..T) and, in the same pass, the
-// list of tiles with entries (olist[0..n_obj), in tile order): each tile
-// contributes cnt + (cnt > 0) 2^32 to one 64-bit scan.  Returns the total
-// entry count (all threads) and sets n_obj.
+// list of tiles with entries (olist[0..n_obj)): tiles with at least kHeavy
+// entries first, then the others, each group in tile order, so that the
+// dynamic fetch hands out the long tiles first and the raster ends on short
+// ones.  Each tile contributes cnt + heavy 2^32 + light 2^48 to one 64-bit
+// scan (cnt < 2^32, tile counts < 2^16).  Returns the total entry count (all
+// threads) and sets n_obj.
 __device__ int bin_scan(const int* cnt, int* off, uint16_t* olist, int T, unsigned long long* warp_tot,
                         int* n_obj) {
     const int per = (T + kThreads - 1) / kThreads;
     const int b = threadIdx.x * per;
-    auto packed = [](int c) { return (unsigned long long)c + ((unsigned long long)(c > 0) << 32); };
+    auto packed = [](int c) {
+        return (unsigned long long)c + ((unsigned long long)(c >= kHeavy) << 32) +
+               ((unsigned long long)(c > 0 && c < kHeavy) << 48);
+    };
     unsigned long long local = 0ull;
     for (int i = 0; i < per; ++i)
         if (b + i < T) local += packed(cnt[b + i]);
@@ -128,16 +135,18 @@ __device__ int bin_scan(const int* cnt, int* off, uint16_t* olist, int T, unsign
     }
     __syncthreads();
     unsigned long long run = warp_tot[warp] + incl - local;
+    const unsigned long long total = warp_tot[32];
+    const int n_heavy = (int)((total >> 32) & 0xffffull);
     for (int i = 0; i < per; ++i)
         if (b + i < T) {
             const int c = cnt[b + i];
             off[b + i] = (int)(run & 0xffffffffull);
-            if (c > 0) olist[run >> 32] = (uint16_t)(b + i);
+            if (c >= kHeavy) olist[(run >> 32) & 0xffffull] = (uint16_t)(b + i);
+            else if (c > 0) olist[n_heavy + (int)(run >> 48)] = (uint16_t)(b + i);
             run += packed(c);
         }
-    const unsigned long long total = warp_tot[32];
     __syncthreads();
-    *n_obj = (int)(total >> 32);
+    *n_obj = n_heavy + (int)(total >> 48);
     return (int)(total & 0xffffffffull);
 }
 

@@ -34,7 +34,7 @@ constexpr int kThreads = 1024;
 constexpr int kWarps = kThreads / 32;
 constexpr int kTile = 8;
 constexpr int kEntryCap = 16384;
-constexpr int kHeavy = 8;   // tiles with at least this many entries are fetched first
+constexpr int kHeavy = 6;   // tiles with at least this many entries are fetched first
 
 struct __align__(16) TriRec {
     float A0, B0, C0, A1;

@@ -37,8 +37,8 @@ ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
 METRIC = "Hessian/HVP estimates/s at oracle-matched error; perturbed renders/s; p50/p99 latency"
-# From the ncu capture of the current mesh kernel (profiles/revolve_kernel_M4096.md);
-# set to None when the kernel changes until it is captured again: DRAM bytes
+# From the ncu capture of the current mesh kernel; set to None when the
+# kernel changes until it is captured again: DRAM bytes
 # (read + write) of one render+loss launch, and the fraction of instruction
 # issue slots busy (smsp__issue_active) — the kernel is bound by compare /
 # select issue on the ALU pipe rather than by FP32 arithmetic.
@@ -213,7 +213,9 @@ def run_reference(args):
     sc = wl.revolve_scene()
     theta = np.asarray(sc["theta_query"], np.float64)
     threads = host_threads()
-    sample = 64 * threads
+    # every step is one whole estimate: all M perturbations rendered by the
+    # oracle on every host thread, FP64 sums (nothing extrapolated)
+    sample = M_PERTURB
     times = []
     for i in range(args.warmup + args.steps):
         cb = cpu_baseline(sc, theta, sample=sample, threads=threads)
@@ -226,8 +228,8 @@ def run_reference(args):
             "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
             "config": workload_config(sc),
             "cpu_baseline": {"value": val, "unit": "estimates/s", "cores": threads, "kind": "oracle",
-                             "sample": f"each step: {sample} of the {M_PERTURB} perturbations on {threads} host "
-                                       f"threads, scaled to one estimate"},
+                             "sample": f"each step: one whole estimate, all {M_PERTURB} perturbations rendered "
+                                       f"on {threads} host threads, FP64 sums"},
             "e2e": {"value": val, "unit": "estimates/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line))
     return 0

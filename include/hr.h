@@ -237,14 +237,16 @@ hr_status hr_estimate_dev(hr_scene scene, int32_t quantity, const double* d_thet
                           const hr_opts* opts, double* d_out);
 
 /* Device-pointer estimate that allocates nothing.  Same arguments, results
- * and stream behaviour as hr_estimate_dev; the paper has no counterpart.
+ * and stream behaviour as hr_estimate_dev (bit-identical outputs: the same
+ * kernels run in the same order on the same values); the paper has no
+ * counterpart.  Inspection outputs in opts are ignored.
  *
- * For callers that cannot allocate device memory while they run: code that is
- * being captured into a CUDA graph (cudaMalloc is not allowed during capture),
- * real-time loops that must not take allocator locks or pay the device-wide
- * synchronisation that cudaFree implies, and hosts that hand the library a
- * fixed memory budget up front.  Its working memory is one fixed 4 MiB array
- * of device memory inside the library, present on every GPU that loads the
+ * For callers that cannot allocate device memory while they run: real-time
+ * or latency-bound loops that must not take the allocator's locks or pay the
+ * device-wide synchronisation that cudaFree implies, and host applications
+ * that hand the library a fixed device-memory budget up front and forbid
+ * allocations outside it.  Its working memory is one fixed 4 MiB array of
+ * device memory inside the library, present on every GPU that loads the
  * library until the process exits; a request needing more than that (about
  * 130,000 perturbations for a 2 x 2 aggregate Hessian, fewer for larger n)
  * fails with HR_ERR_INVALID_ARG before anything is launched, and
@@ -256,7 +258,9 @@ hr_status hr_estimate_dev(hr_scene scene, int32_t quantity, const double* d_thet
  * last call's contents (every call overwrites all of it that it reads, so
  * nothing needs clearing): two calls that can run at the same time on the GPU
  * (different streams, or work not ordered one after the other) race and
- * corrupt each other's results, so issue them in order on one stream. */
+ * corrupt each other's results, so issue them in order on one stream.  On
+ * the host the call takes the scene's lock like every other call on the
+ * scene. */
 hr_status hr_estimate_dev_noalloc(hr_scene scene, int32_t quantity, const double* d_theta, const double* d_v,
                                   const hr_opts* opts, double* d_out);
 
@@ -302,6 +306,13 @@ hr_status hr_optstate_destroy(hr_optstate st);
 hr_status hr_newton_cg_step(hr_scene scene, hr_optstate st, hr_step_info* h_info);
 /* Current parameters, h_theta [n_instances][n]. */
 hr_status hr_optstate_theta(hr_optstate st, double* h_theta);
+/* What the last step computed, for inspection (waits for the state's
+ * stream): h_g [n_instances][n] the gradient estimates, h_p
+ * [n_instances][cg_iters][n] the CG directions p_i and h_Hp (same shape) the
+ * aggregate HVP estimates of H p_i (without the lambda p_i term), all at the
+ * step's starting parameters; rows i >= hr_step_info.iters are unspecified.
+ * Any pointer may be NULL. */
+hr_status hr_optstate_trace(hr_optstate st, double* h_g, double* h_p, double* h_Hp);
 
 /* ---------------------------------------------------------------------------
  * The optimiser as the paper runs it (Sec. 2 "Newton Conjugate Gradient" with
@@ -373,6 +384,12 @@ hr_status hr_ncg_destroy(hr_ncg st);
 hr_status hr_ncg_run(hr_scene scene, hr_ncg st, int32_t n_evals, hr_ncg_info* h_info);
 /* Current parameters, h_theta [n_instances][n] (waits for the state's stream). */
 hr_status hr_ncg_theta(hr_ncg st, double* h_theta);
+/* What the last evaluation computed, for inspection (waits for the state's
+ * stream): h_g [n_instances][n] the gradient estimates, h_d the direction d
+ * the evaluation stepped along and h_Hd the aggregate HVP estimates of H d
+ * (without the lambda d term), all at the evaluation's starting point.  Any
+ * pointer may be NULL. */
+hr_status hr_ncg_trace(hr_ncg st, double* h_g, double* h_d, double* h_Hd);
 
 /* Render one image at h_params [n] (rounded to FP32) into h_img [H][W][C]
  * (host).  For PTBOX the path random numbers are those of (seed, request,
@@ -433,6 +450,16 @@ hr_status hr_server_submit(hr_server srv, const hr_request* req, uint64_t* ticke
  * NULL.  timeout_ms < 0 waits without limit; on timeout HR_ERR_TIMEOUT is
  * returned and the ticket stays valid.  A ticket can be waited for once. */
 hr_status hr_server_wait(hr_server srv, uint64_t ticket, void* h_out, hr_request_info* info, int32_t timeout_ms);
+
+/* Diagnostics of a scene since its creation (waits for the scene's own
+ * stream).  mesh_overflow_renders: REVOLVE3D renders whose 8x8-tile bins
+ * held more than 16,384 (triangle, tile) entries, so that the render took the
+ * rasteriser's fallback in which every tile walks every surviving triangle
+ * (same pixels, same decisions, slower); 0 for other kinds. */
+typedef struct {
+    int64_t mesh_overflow_renders;
+} hr_scene_stats;
+hr_status hr_scene_get_stats(hr_scene scene, hr_scene_stats* out);
 
 /* Stage timing: when enabled (on != 0), every estimate records CUDA events
  * on its stream around its three launches (sampler, render + loss, sums) and

@@ -421,9 +421,12 @@ class Estimate:
 
 
 def estimate(r: Renderer, quantity: str, theta, sigma: float, M: int, strategy: str, seed: int,
-             request: int, sub: int = 0, v=None) -> Estimate:
+             request: int, sub: int = 0, v=None, threads: int = 1) -> Estimate:
     """One estimate: M perturbations (renders) for the aggregate strategy, M
-    per unique element for element-wise sampling (Tab. 1 render counts)."""
+    per unique element for element-wise sampling (Tab. 1 render counts).
+    threads > 1 runs the per-perturbation renders of renderers without a
+    batch form on that many host threads (the C renders release the GIL);
+    the losses, and everything computed from them, are the same."""
     n = r.n
     q = QUANTITY[quantity]
     lobe = 0 if quantity == "grad" else 1
@@ -453,8 +456,14 @@ def estimate(r: Renderer, quantity: str, theta, sigma: float, M: int, strategy: 
             # RN32(RN32(theta) + tau) row by row (IEEE single-precision add)
             losses = r.loss_batch(np.asarray(theta, np.float64).astype(np.float32)[None, :] + tau)
         else:
-            losses = np.array([r.loss(perturb(theta, tau[m]), dict(seed=seed, request=request, sub=s, k=m // 2))
-                               for m in range(2 * P)])
+            def one(m, tau=tau, s=s):
+                return r.loss(perturb(theta, tau[m]), dict(seed=seed, request=request, sub=s, k=m // 2))
+            if threads > 1:
+                from concurrent.futures import ThreadPoolExecutor
+                with ThreadPoolExecutor(threads) as ex:
+                    losses = np.array(list(ex.map(one, range(2 * P))))
+            else:
+                losses = np.array([one(m) for m in range(2 * P)])
         taus.append(tau); ws.append(w); ls.append(losses); comps.append(comp)
     tau = np.concatenate(taus); w = np.concatenate(ws); losses = np.concatenate(ls)
     E = w.shape[1]

@@ -125,6 +125,13 @@ __global__ void fd_combine_kernel(const double* gp, const double* gm, double inv
     if (i < n) out[i] = (gp[i] - gm[i]) * inv2eps;
 }
 
+}  // namespace
+
+// ---------------------------------------------------------------------------
+// estimator pipeline shared by the host- and device-pointer entry points
+// ---------------------------------------------------------------------------
+namespace hr {
+
 int n_elements(int quantity, int n) { return quantity == HR_HESSIAN ? n * (n + 1) / 2 : n; }
 
 hr_status validate_opts(const hr_scene_s* s, int quantity, const hr_opts* o) {
@@ -142,13 +149,6 @@ hr_status validate_opts(const hr_scene_s* s, int quantity, const hr_opts* o) {
     if ((uint64_t)o->sub + (uint64_t)G > (1u << 24)) return fail(HR_ERR_INVALID_ARG, "sub-stream out of range");
     return HR_OK;
 }
-
-}  // namespace
-
-// ---------------------------------------------------------------------------
-// estimator pipeline shared by the host- and device-pointer entry points
-// ---------------------------------------------------------------------------
-namespace hr {
 
 hr_status run_estimate(hr_scene_s* s, int quantity, const double* h_theta, const double* d_theta,
                        const double* h_v, const double* d_v, const hr_opts* o, double* h_out, double* d_out) {
@@ -518,6 +518,8 @@ hr_status hr_create_scene(const hr_scene_desc* d, hr_scene* out) {
             if ((e = cudaMalloc(&sc.tnrm, sizeof(float) * 3 * sc.nt)) != cudaSuccess) return bail(e, "normals");
             if ((e = cudaMalloc(&sc.tile_t2, sizeof(float) * revolve_tiles(sc.W, sc.H))) != cudaSuccess)
                 return bail(e, "tiles");
+            if ((e = cudaMalloc(&sc.rv_stats, sizeof(unsigned long long))) != cudaSuccess) return bail(e, "stats");
+            if ((e = cudaMemset(sc.rv_stats, 0, sizeof(unsigned long long))) != cudaSuccess) return bail(e, "stats");
             revolve_prepare(sc, s->stream);
             break;
         }
@@ -576,7 +578,7 @@ hr_status hr_destroy_scene(hr_scene s) {
     DevScene& sc = s->sc;
     if (s->stream) cudaStreamSynchronize(s->stream);
     cudaFree(sc.target); cudaFree(sc.verts); cudaFree(sc.tris); cudaFree(sc.tnrm); cudaFree(sc.tile_t2);
-    cudaFree(sc.raw); cudaFree(sc.pidx); cudaFree(sc.qA); cudaFree(sc.qb);
+    cudaFree(sc.raw); cudaFree(sc.pidx); cudaFree(sc.qA); cudaFree(sc.qb); cudaFree(sc.rv_stats);
     s->ws.release_all();
     for (cudaEvent_t& e : s->ev)
         if (e) cudaEventDestroy(e);
@@ -617,6 +619,21 @@ hr_status hr_estimate_dev(hr_scene s, int32_t quantity, const double* d_theta, c
     if (!d_theta || !d_out || (quantity == HR_HVP && !d_v)) return fail(HR_ERR_INVALID_ARG, "NULL device pointer");
     std::lock_guard<std::mutex> lk(s->mu);
     return run_estimate(s, quantity, nullptr, d_theta, nullptr, d_v, o, nullptr, d_out);
+}
+
+hr_status hr_scene_get_stats(hr_scene s, hr_scene_stats* out) {
+    clear_error();
+    if (!s || !out) return fail(HR_ERR_INVALID_ARG, "NULL argument");
+    std::lock_guard<std::mutex> lk(s->mu);
+    memset(out, 0, sizeof(*out));
+    if (s->sc.rv_stats) {
+        unsigned long long v = 0;
+        cudaError_t e = cudaStreamSynchronize(s->stream);
+        if (e == cudaSuccess) e = cudaMemcpy(&v, s->sc.rv_stats, sizeof v, cudaMemcpyDeviceToHost);
+        if (e != cudaSuccess) return fail(HR_ERR_CUDA, "stats: %s", cudaGetErrorString(e));
+        out->mesh_overflow_renders = (int64_t)v;
+    }
+    return HR_OK;
 }
 
 hr_status hr_profile_enable(hr_scene s, int32_t on) {

@@ -53,6 +53,13 @@ int optstate_instances(hr_optstate st);
 hr_scene optstate_scene(hr_optstate st);
 void optstate_copy_info(hr_optstate st, hr_step_info* out);
 
+// Checks of an estimate's options shared by every estimate entry point:
+// sigma > 0, M even and >= 2, a known strategy, pair / perturbation /
+// sub-stream counts within range; HR_ERR_INVALID_ARG (with a message)
+// otherwise.
+int n_elements(int quantity, int n);
+hr_status validate_opts(const hr_scene_s* s, int quantity, const hr_opts* o);
+
 hr_status run_hvp_fd(hr_scene_s* s, const double* h_theta, const double* h_v, double eps, const hr_opts* o,
                      double* h_out);
 hr_status run_estimate(hr_scene_s* s, int quantity, const double* h_theta, const double* d_theta, const double* h_v,

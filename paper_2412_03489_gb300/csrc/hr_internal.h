@@ -161,6 +161,7 @@ struct DevScene {
     float albedo[3] = {0, 0, 0}, light[3] = {0, 0, 0};
     float eye_dist = 0.f, scale = 0.f;
     size_t rv_smem = 0;
+    unsigned long long* rv_stats = nullptr;   // [1] renders that took the bin-overflow path
     // tris2d
     float* raw = nullptr;         // [n_tris][9]
     int32_t* pidx = nullptr;      // [n]

@@ -57,6 +57,7 @@ struct NcgArgs {
     int32_t* ls;          // [B]
     double* sigma;        // [B]
     hr_ncg_info* info;    // [B]
+    double* tr_q;         // [B][n] HVP estimate H d of the evaluation (without lambda d)
 };
 
 __global__ void __launch_bounds__(kNcgThreads) ncg_kernel(NcgArgs a) {
@@ -114,7 +115,9 @@ __global__ void __launch_bounds__(kNcgThreads) ncg_kernel(NcgArgs a) {
             const double w = ((double)a.tau[(size_t)m * n + c] * tp[k] * is4 - d[c] * is2) * (double)a.invS[m];
             acc.add(__fmul_rn((float)w, a.loss[m]));
         }
-        q[c] = ((double)acc.s - (double)acc.c) / (double)a.Mh + lam * d[c];
+        const double hv = ((double)acc.s - (double)acc.c) / (double)a.Mh;
+        q[c] = hv + lam * d[c];
+        a.tr_q[(size_t)b * n + c] = hv;
     }
     __syncthreads();
     const double gdv = block_dot(g, d, n, red);
@@ -176,7 +179,7 @@ struct hr_ncg_s {
     hr_ncg_opts opts{};
     cudaStream_t stream = nullptr;
     bool own_stream = false;
-    DevBuf theta, theta32, tau, w, invS, meta, loss, groups, g, d, r, rr, it, ls, sigma, info, evc;
+    DevBuf theta, theta32, tau, w, invS, meta, loss, groups, g, d, r, rr, it, ls, sigma, info, evc, tr_q;
     hr_ncg_info* h_info = nullptr;     // pinned [cap][B]
     int h_cap = 0;
     cudaGraph_t graph = nullptr;
@@ -235,6 +238,7 @@ hr_status enqueue_eval(hr_ncg_s* st) {
     a.ls = (int32_t*)st->ls.ptr;
     a.sigma = (double*)st->sigma.ptr;
     a.info = (hr_ncg_info*)st->info.ptr;
+    a.tr_q = (double*)st->tr_q.ptr;
     ncg_kernel<<<B, kNcgThreads, 0, st->stream>>>(a);
     ncg_advance_kernel<<<1, 1, 0, st->stream>>>((int32_t*)st->evc.ptr);
     const cudaError_t e = cudaGetLastError();
@@ -303,7 +307,7 @@ hr_status hr_ncg_create(hr_scene scene, int32_t B, const double* theta0, const h
                     std::make_pair(&st->r, sizeof(double) * Bn), std::make_pair(&st->rr, sizeof(double) * B),
                     std::make_pair(&st->it, sizeof(int32_t) * B), std::make_pair(&st->ls, sizeof(int32_t) * B),
                     std::make_pair(&st->sigma, sizeof(double) * B), std::make_pair(&st->info, sizeof(hr_ncg_info) * B),
-                    std::make_pair(&st->evc, sizeof(int32_t))}) {
+                    std::make_pair(&st->evc, sizeof(int32_t)), std::make_pair(&st->tr_q, sizeof(double) * Bn)}) {
         if (e == cudaSuccess) e = pr.first->reserve(pr.second);
     }
     if (e != cudaSuccess) {
@@ -351,7 +355,8 @@ hr_status hr_ncg_destroy(hr_ncg st) {
     if (st->exec) cudaGraphExecDestroy(st->exec);
     if (st->graph) cudaGraphDestroy(st->graph);
     for (DevBuf* b : {&st->theta, &st->theta32, &st->tau, &st->w, &st->invS, &st->meta, &st->loss, &st->groups,
-                      &st->g, &st->d, &st->r, &st->rr, &st->it, &st->ls, &st->sigma, &st->info, &st->evc})
+                      &st->g, &st->d, &st->r, &st->rr, &st->it, &st->ls, &st->sigma, &st->info, &st->evc,
+                      &st->tr_q})
         b->release();
     if (st->h_info) cudaFreeHost(st->h_info);
     if (st->own_stream && st->stream) cudaStreamDestroy(st->stream);
@@ -386,6 +391,18 @@ hr_status hr_ncg_run(hr_scene scene, hr_ncg st, int32_t n_evals, hr_ncg_info* h_
     if ((e = cudaStreamSynchronize(st->stream)) != cudaSuccess)
         return fail(HR_ERR_CUDA, "optimiser: %s", cudaGetErrorString(e));
     if (h_info) memcpy(h_info, st->h_info, sizeof(hr_ncg_info) * (size_t)n_evals * st->B);
+    return HR_OK;
+}
+
+hr_status hr_ncg_trace(hr_ncg st, double* h_g, double* h_d, double* h_Hd) {
+    clear_error();
+    if (!st) return fail(HR_ERR_INVALID_ARG, "NULL state");
+    const size_t bytes = sizeof(double) * st->B * st->n;
+    cudaError_t e = cudaStreamSynchronize(st->stream);
+    if (e == cudaSuccess && h_g) e = cudaMemcpy(h_g, st->g.ptr, bytes, cudaMemcpyDeviceToHost);
+    if (e == cudaSuccess && h_d) e = cudaMemcpy(h_d, st->d.ptr, bytes, cudaMemcpyDeviceToHost);
+    if (e == cudaSuccess && h_Hd) e = cudaMemcpy(h_Hd, st->tr_q.ptr, bytes, cudaMemcpyDeviceToHost);
+    if (e != cudaSuccess) return fail(HR_ERR_CUDA, "trace: %s", cudaGetErrorString(e));
     return HR_OK;
 }
 

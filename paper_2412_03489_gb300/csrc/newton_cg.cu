@@ -62,6 +62,8 @@ struct CgArgs {
     double* theta;
     hr_step_info* info;
     int32_t* step;
+    double* tr_p;     // [B][K][n] CG directions of the step
+    double* tr_Hp;    // [B][K][n] their HVP estimates (without lambda p)
 };
 
 __global__ void __launch_bounds__(kCgThreads) cg_kernel(CgArgs a) {
@@ -96,7 +98,11 @@ __global__ void __launch_bounds__(kCgThreads) cg_kernel(CgArgs a) {
                 const double w = ((double)a.tau[(size_t)m * n + k] * tq * is4 - p[k] * is2) * (double)a.invS[m];
                 acc.add(__fmul_rn((float)w, a.loss[m]));
             }
-            Hp[k] = ((double)acc.s - (double)acc.c) / (double)a.Mh + lam * p[k];
+            const double hv = ((double)acc.s - (double)acc.c) / (double)a.Mh;
+            Hp[k] = hv + lam * p[k];
+            const size_t tr = ((size_t)b * a.K + it) * n + k;
+            a.tr_p[tr] = p[k];
+            a.tr_Hp[tr] = hv;
         }
         __syncthreads();
         const double pHp = block_dot(p, Hp, n, red);
@@ -150,7 +156,7 @@ struct hr_optstate_s {
     hr_cg_opts opts{};
     cudaStream_t stream = nullptr;
     bool own_stream = false;
-    DevBuf theta, theta32, tau, w, invS, meta, loss, groups, g, info, step;
+    DevBuf theta, theta32, tau, w, invS, meta, loss, groups, g, info, step, tr_p, tr_Hp;
     hr_step_info* h_info = nullptr;   // pinned
     cudaGraph_t graph = nullptr;
     cudaGraphExec_t exec = nullptr;
@@ -204,6 +210,8 @@ hr_status enqueue_step(hr_optstate_s* st) {
     ca.theta = (double*)st->theta.ptr;
     ca.info = (hr_step_info*)st->info.ptr;
     ca.step = (int32_t*)st->step.ptr;
+    ca.tr_p = (double*)st->tr_p.ptr;
+    ca.tr_Hp = (double*)st->tr_Hp.ptr;
     cg_kernel<<<B, kCgThreads, 0, st->stream>>>(ca);
     advance_step_kernel<<<1, 1, 0, st->stream>>>((int32_t*)st->step.ptr);
     const cudaError_t e = cudaGetLastError();
@@ -244,7 +252,9 @@ hr_status hr_optstate_create(hr_scene scene, int32_t B, const double* theta0, co
                     std::make_pair(&st->loss, sizeof(float) * Mt),
                     std::make_pair(&st->groups, sizeof(SampleGroup) * B * (1 + st->K)),
                     std::make_pair(&st->g, sizeof(double) * B * n), std::make_pair(&st->info, sizeof(hr_step_info) * B),
-                    std::make_pair(&st->step, sizeof(int32_t))}) {
+                    std::make_pair(&st->step, sizeof(int32_t)),
+                    std::make_pair(&st->tr_p, sizeof(double) * B * st->K * n),
+                    std::make_pair(&st->tr_Hp, sizeof(double) * B * st->K * n)}) {
         if (e == cudaSuccess) e = pr.first->reserve(pr.second);
     }
     if (e == cudaSuccess) e = cudaMallocHost((void**)&st->h_info, sizeof(hr_step_info) * B);
@@ -285,7 +295,7 @@ hr_status hr_optstate_destroy(hr_optstate st) {
     if (st->exec) cudaGraphExecDestroy(st->exec);
     if (st->graph) cudaGraphDestroy(st->graph);
     for (DevBuf* b : {&st->theta, &st->theta32, &st->tau, &st->w, &st->invS, &st->meta, &st->loss, &st->groups, &st->g,
-                      &st->info, &st->step})
+                      &st->info, &st->step, &st->tr_p, &st->tr_Hp})
         b->release();
     if (st->h_info) cudaFreeHost(st->h_info);
     if (st->own_stream && st->stream) cudaStreamDestroy(st->stream);
@@ -349,6 +359,18 @@ void optstate_copy_info(hr_optstate st, hr_step_info* out) { memcpy(out, st->h_i
 }  // namespace hr
 
 extern "C" {
+
+hr_status hr_optstate_trace(hr_optstate st, double* h_g, double* h_p, double* h_Hp) {
+    clear_error();
+    if (!st) return fail(HR_ERR_INVALID_ARG, "NULL state");
+    cudaError_t e = cudaStreamSynchronize(st->stream);
+    const size_t nk = (size_t)st->B * st->K * st->n;
+    if (e == cudaSuccess && h_g) e = cudaMemcpy(h_g, st->g.ptr, sizeof(double) * st->B * st->n, cudaMemcpyDeviceToHost);
+    if (e == cudaSuccess && h_p) e = cudaMemcpy(h_p, st->tr_p.ptr, sizeof(double) * nk, cudaMemcpyDeviceToHost);
+    if (e == cudaSuccess && h_Hp) e = cudaMemcpy(h_Hp, st->tr_Hp.ptr, sizeof(double) * nk, cudaMemcpyDeviceToHost);
+    if (e != cudaSuccess) return fail(HR_ERR_CUDA, "trace: %s", cudaGetErrorString(e));
+    return HR_OK;
+}
 
 hr_status hr_optstate_theta(hr_optstate st, double* h_theta) {
     clear_error();

@@ -97,17 +97,16 @@ extern "C" hr_status hr_estimate_dev_noalloc(hr_scene s, int32_t quantity, const
     if (!s || !o) return fail(HR_ERR_INVALID_ARG, "scene/opts is NULL");
     if (quantity < HR_GRAD || quantity > HR_HVP) return fail(HR_ERR_INVALID_ARG, "unknown quantity %d", quantity);
     if (!d_theta || !d_out || (quantity == HR_HVP && !d_v)) return fail(HR_ERR_INVALID_ARG, "NULL device pointer");
-    if (!(o->sigma > 0.0) || !std::isfinite(o->sigma)) return fail(HR_ERR_INVALID_ARG, "sigma must be > 0");
-    if (o->n_perturb < 2 || (o->n_perturb & 1)) return fail(HR_ERR_INVALID_ARG, "n_perturb must be even and >= 2");
-    if (o->strategy != HR_ELEMENTWISE && o->strategy != HR_AGGREGATE && o->strategy != HR_PLAIN)
-        return fail(HR_ERR_INVALID_ARG, "unknown strategy %d", o->strategy);
+    // the scene's launch shapes and device pointers are read under its lock,
+    // as in hr_estimate_dev (the autotuner and scene teardown take it too)
+    std::lock_guard<std::mutex> lk(s->mu);
+    const hr_status valid = validate_opts(s, quantity, o);
+    if (valid != HR_OK) return valid;
     const DevScene& sc = s->sc;
     const int n = sc.n;
-    const int E = quantity == HR_HESSIAN ? n * (n + 1) / 2 : n;
+    const int E = n_elements(quantity, n);
     const int G = o->strategy == HR_ELEMENTWISE ? E : 1;
     const int64_t M = o->n_perturb;
-    if (M / 2 >= (1 << 24) || (uint64_t)o->sub + (uint64_t)G > (1u << 24))
-        return fail(HR_ERR_INVALID_ARG, "pairs or sub-streams out of range");
     const int64_t Mt = (int64_t)G * M;
 
     // carve the fixed array: theta32 | groups | tau | weights | keys | losses | sums | scale

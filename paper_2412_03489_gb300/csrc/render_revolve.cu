@@ -63,6 +63,7 @@ struct RvArgs {
     const float* tile_t2;
     int nv, nt, W, H, TX, TY, T;
     uint64_t tx_recip;   // ceil(2^32 / TX): t / TX = (t tx_recip) >> 32 exactly for t, TX < 2^16
+    unsigned long long* stats;   // [0]: renders whose bins overflowed (diagnostics)
     float alb0, alb1, alb2, l0, l1, l2, eye_dist, scale;
 };
 
@@ -283,6 +284,7 @@ revolve_kernel(RvArgs P, RenderBatch b, const float* __restrict__ img_params, fl
         int n_obj = 0;
         const int total = bin_scan(tcnt, toff, olist, P.T, s_wtot, &n_obj);
         const bool overflow = total > kEntryCap;
+        if (overflow && tid == 0 && P.stats) atomicAdd(P.stats, 1ull);
         for (int i = tid; i < P.T; i += kThreads) tcnt[i] = 0;   // becomes the fill cursor
         __syncthreads();
         if (!overflow) {
@@ -489,6 +491,7 @@ RvArgs make_args(const DevScene& sc) {
     a.alb0 = sc.albedo[0]; a.alb1 = sc.albedo[1]; a.alb2 = sc.albedo[2];
     a.l0 = sc.light[0]; a.l1 = sc.light[1]; a.l2 = sc.light[2];
     a.eye_dist = sc.eye_dist; a.scale = sc.scale;
+    a.stats = sc.rv_stats;
     return a;
 }
 

@@ -78,6 +78,10 @@ class hr_ncg_info(ctypes.Structure):
                 ("step_norm", ctypes.c_double)]
 
 
+class hr_scene_stats(ctypes.Structure):
+    _fields_ = [("mesh_overflow_renders", ctypes.c_int64)]
+
+
 class hr_tune_info(ctypes.Structure):
     _fields_ = [("render_variant", ctypes.c_int32), ("sample_threads", ctypes.c_int32),
                 ("n_render_variants", ctypes.c_int32), ("n_sample_variants", ctypes.c_int32),
@@ -132,10 +136,13 @@ def lib() -> ctypes.CDLL:
         L.hr_optstate_destroy.argtypes = [vp]
         L.hr_newton_cg_step.argtypes = [vp, vp, ctypes.POINTER(hr_step_info)]
         L.hr_optstate_theta.argtypes = [vp, _f64p]
+        L.hr_optstate_trace.argtypes = [vp, _f64p, _f64p, _f64p]
         L.hr_ncg_create.argtypes = [vp, ctypes.c_int32, _f64p, ctypes.POINTER(hr_ncg_opts), ctypes.POINTER(vp)]
         L.hr_ncg_destroy.argtypes = [vp]
         L.hr_ncg_run.argtypes = [vp, vp, ctypes.c_int32, ctypes.POINTER(hr_ncg_info)]
         L.hr_ncg_theta.argtypes = [vp, _f64p]
+        L.hr_ncg_trace.argtypes = [vp, _f64p, _f64p, _f64p]
+        L.hr_scene_get_stats.argtypes = [vp, ctypes.POINTER(hr_scene_stats)]
         L.hr_autotune.argtypes = [vp, _f64p, ctypes.c_int32, ctypes.POINTER(hr_tune_info)]
         L.hr_set_tuning.argtypes = [vp, ctypes.c_int32, ctypes.c_int32]
         L.hr_profile_enable.argtypes = [vp, ctypes.c_int32]
@@ -153,7 +160,7 @@ def lib() -> ctypes.CDLL:
                      "hr_optstate_destroy", "hr_newton_cg_step", "hr_optstate_theta", "hr_profile_enable",
                      "hr_profile_last", "hr_server_create", "hr_server_destroy", "hr_server_submit",
                      "hr_server_wait", "hr_ncg_create", "hr_ncg_destroy", "hr_ncg_run", "hr_ncg_theta",
-                     "hr_autotune", "hr_set_tuning"):
+                     "hr_autotune", "hr_set_tuning", "hr_scene_get_stats", "hr_optstate_trace", "hr_ncg_trace"):
             getattr(L, name).restype = ctypes.c_int32
         L.hr_version.restype = ctypes.c_int32
         _lib = L
@@ -242,6 +249,12 @@ def hr_render(handle, params, seed, request, sub, k, tag, spp, out):
           "hr_render")
 
 
+def hr_scene_get_stats(handle) -> hr_scene_stats:
+    st = hr_scene_stats()
+    check(lib().hr_scene_get_stats(handle, ctypes.byref(st)), "hr_scene_get_stats")
+    return st
+
+
 def hr_profile_enable(handle, on: bool):
     check(lib().hr_profile_enable(handle, int(on)), "hr_profile_enable")
 
@@ -265,6 +278,13 @@ def hr_newton_cg_step(handle, st, info):
 
 def hr_optstate_theta(st, out):
     check(lib().hr_optstate_theta(st, _ptr(out, _f64p)), "hr_optstate_theta")
+
+
+def hr_optstate_trace(st, B, K, n):
+    """(g [B][n], p [B][K][n], Hp [B][K][n]) of the state's last step."""
+    g, p, hp = np.zeros((B, n)), np.zeros((B, K, n)), np.zeros((B, K, n))
+    check(lib().hr_optstate_trace(st, _ptr(g, _f64p), _ptr(p, _f64p), _ptr(hp, _f64p)), "hr_optstate_trace")
+    return g, p, hp
 
 
 def hr_optstate_destroy(st):
@@ -296,6 +316,13 @@ def hr_ncg_run(handle, st, n_evals, info=None):
 
 def hr_ncg_theta(st, out):
     check(lib().hr_ncg_theta(st, _ptr(out, _f64p)), "hr_ncg_theta")
+
+
+def hr_ncg_trace(st, B, n):
+    """(g, d, Hd), each [B][n], of the state's last evaluation."""
+    g, d, hd = np.zeros((B, n)), np.zeros((B, n)), np.zeros((B, n))
+    check(lib().hr_ncg_trace(st, _ptr(g, _f64p), _ptr(d, _f64p), _ptr(hd, _f64p)), "hr_ncg_trace")
+    return g, d, hd
 
 
 def hr_ncg_destroy(st):

@@ -130,6 +130,35 @@ def revolve_mesh(radii: np.ndarray, rings: int = 33, slices: int = 32):
     return verts, np.asarray(tris, np.int32)
 
 
+def sheets_mesh(layers: int = 8, grid: int = 8, seed: int = 0xC6, half: float = 1.0):
+    """Stacked, slightly tilted square sheets facing the camera (+z), for the
+    rasteriser's stress cases: `layers` sheets of grid x grid quads (two
+    triangles each), sheet k at depth z_k in [-0.6, 0.6] with seeded
+    vertex jitter, so that every pixel is covered by several triangles at
+    different depths and every triangle spans many 8x8 tiles.  Triangles are
+    wound so that (v1 - v0) x (v2 - v0) points towards +z (front-facing).
+    Returns (vertices float32 [V,3], triangles int32 [T,3])."""
+    g = _rng(seed)
+    verts, tris = [], []
+    xs = np.linspace(-half, half, grid + 1)
+    for k in range(layers):
+        z0 = -0.6 + 1.2 * k / max(1, layers - 1)
+        tilt = g.uniform(-0.15, 0.15, size=2)
+        base = len(verts)
+        for iy in range(grid + 1):
+            for ix in range(grid + 1):
+                x = xs[ix] + g.uniform(-0.02, 0.02)
+                y = xs[iy] + g.uniform(-0.02, 0.02)
+                verts.append((x, y, z0 + tilt[0] * x + tilt[1] * y))
+        for iy in range(grid):
+            for ix in range(grid):
+                a = base + iy * (grid + 1) + ix
+                b, c, d = a + 1, a + grid + 1, a + grid + 2
+                tris.append((a, b, d))
+                tris.append((a, d, c))
+    return np.asarray(verts, np.float32), np.asarray(tris, np.int32)
+
+
 def revolve_scene(seed: int = 0xC1, width: int = 256, height: int = 256,
                   fov_deg: float = 30.0, eye_dist: float = 4.0,
                   query_std: float = 0.1) -> dict:

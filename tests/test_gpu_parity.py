@@ -8,6 +8,7 @@ seeded inputs and the same Philox samples.
 * estimates: |gpu - oracle| <= 1e-4 max(|oracle|, A_e) (see tests/parity.py).
 """
 import math
+import os
 from types import SimpleNamespace
 
 import numpy as np
@@ -142,6 +143,45 @@ def test_revolve_full_size_bench_configuration():
     assert_estimate_close(flat, ref, what="revolve full")
 
 
+def _sheets_scene(W):
+    sc = wl.revolve_scene(width=W, height=W)
+    sc["vertices"], sc["triangles"] = wl.sheets_mesh(layers=8, grid=8)
+    return sc
+
+
+@pytest.mark.parametrize("W,overflow", [(128, False), (512, True)])
+def test_revolve_stacked_sheets_and_bin_overflow(W, overflow):
+    """Eight stacked, tilted sheets of 128 triangles each: every pixel is
+    covered at several depths, and every triangle spans many tiles.  At 128^2
+    the tile bins hold about 6,000 entries (the binned raster); at 512^2 more
+    than 40,000, beyond the 16,384-entry bin capacity, so every render takes
+    the fallback in which each tile walks every surviving triangle.  The
+    scene's overflow counter shows which path ran.  Both paths against the
+    oracle: images pixel by pixel (the depth winner decides each pixel's
+    shade), then an aggregate Hessian on identical samples."""
+    sc = _sheets_scene(W)
+    Sc = hr.Scene(sc)
+    r = O.RevolveRenderer(sc)
+    before = hr.hr_scene_get_stats(Sc.handle).mesh_overflow_renders
+    g = np.random.default_rng(7)
+    for _ in range(3):
+        p = np.asarray(sc["theta_query"]) + g.normal(0, 0.2, 2)
+        gi = Sc.render(p).reshape(W, W, 3)
+        oi = r.image(p.astype(np.float32)).reshape(W, W, 3)
+        assert np.array_equal(gi.sum(-1) > 0, oi.sum(-1) > 0), "coverage differs"
+        assert np.allclose(gi, oi, rtol=1e-5, atol=1e-6), "a different triangle won some pixel"
+    flat, dbg, ref = run_both(sc, r, "hessian", 16, "aggregate", scene=Sc)
+    check_samples(dbg, ref)
+    assert_losses_close(dbg["losses"], ref.losses, 2e-5, "sheets losses")
+    assert_estimate_close(flat, ref, what=f"sheets {W}")
+    after = hr.hr_scene_get_stats(Sc.handle).mesh_overflow_renders
+    Sc.close()
+    if overflow:
+        assert after - before >= 3 + 16, (before, after)
+    else:
+        assert after == before == 0, (before, after)
+
+
 # ---------------------------------------------------------------------------
 # coloured triangles
 # ---------------------------------------------------------------------------
@@ -210,60 +250,124 @@ def test_ptbox_hvp_small():
     assert_estimate_close(flat, ref, what="ptbox hvp")
 
 
+def _host_threads():
+    try:
+        return len(os.sched_getaffinity(0))
+    except AttributeError:
+        return os.cpu_count() or 1
+
+
 def test_ptbox_full_size_bench_configuration_sampled():
     """128 x 128, 4 spp, depth 3, aggregate HVP with 8192 perturbations in the
     launch shape the autotuner picks (the bench workload): every perturbation
-    and weight against the oracle's sampler, a spread of renders against the
-    oracle's path tracer one by one (a full oracle estimate would take
-    minutes), and the estimate against the oracle's FP64 sum of its own
-    weights times the GPU's losses."""
+    and weight against the oracle's sampler, and 64 renders spread over the
+    launch against the oracle's path tracer one by one."""
     sc = wl.ptbox_scene()
     Sc = hr.Scene(sc)
     hr.hr_autotune(Sc.handle, sc["theta_query"], 2048)
     theta, v, M, seed, request = np.asarray(sc["theta_query"]), sc["v"], 8192, 11, 3
     out, dbg = Sc.estimate(hr.HR_HVP, theta, sc["sigma"], M, hr.HR_AGGREGATE, seed, request, 0, v=v, debug=True)
     Sc.close()
+    assert np.all(np.isfinite(out))
     tau, _ = O.draw(1, 6, sc["sigma"], M // 2, seed, request, 0)
     w = O.weights(2, 6, sc["sigma"], tau, v=v)
     check_samples(dbg, SimpleNamespace(tau=tau, w=w))
     r = O.PtboxRenderer(sc)
-    picks = [0, 1, 2046, 2047, 4096, 6001, 8190, 8191]
-    ref = np.array([r.loss(O.perturb(theta, tau[m]), dict(seed=seed, request=request, sub=0, k=m // 2))
-                    for m in picks])
+    picks = sorted(set([0, 1, M - 2, M - 1] + np.linspace(2, M - 3, 60).astype(int).tolist()))
+    assert len(picks) == 64
+
+    def one(m):
+        return r.loss(O.perturb(theta, tau[m]), dict(seed=seed, request=request, sub=0, k=m // 2))
+    from concurrent.futures import ThreadPoolExecutor
+    with ThreadPoolExecutor(_host_threads()) as ex:
+        ref = np.array(list(ex.map(one, picks)))
     assert_losses_close(dbg["losses"][picks], ref, 1e-4, "ptbox full-size losses")
-    losses = dbg["losses"].astype(np.float64)
-    flat = np.array([math.fsum(w[:, e] * losses) for e in range(6)]) / M
-    scale = np.array([math.fsum(np.abs(w[:, e] * losses)) for e in range(6)]) / M
-    assert_estimate_close(out, SimpleNamespace(flat=flat, scale=scale), what="ptbox full-size hvp")
+
+
+def test_ptbox_full_size_estimate_against_oracle_estimate():
+    """The path-traced HVP at the bench image size (128 x 128, 4 spp, depth 3,
+    the autotuned launch shape) against the oracle's own full estimate of the
+    same request: the oracle samples, renders every one of the 256
+    perturbations with its own path tracer and sums in FP64."""
+    sc = wl.ptbox_scene()
+    Sc = hr.Scene(sc)
+    hr.hr_autotune(Sc.handle, sc["theta_query"], 2048)
+    theta, v = np.asarray(sc["theta_query"]), sc["v"]
+    flat, dbg, ref = run_both_threads(sc, O.PtboxRenderer(sc), "hvp", 256, "aggregate", 17, 9, v, Sc)
+    Sc.close()
+    check_samples(dbg, ref)
+    assert_losses_close(dbg["losses"], ref.losses, 1e-4, "ptbox estimate losses")
+    assert_estimate_close(flat, ref, what="ptbox full-size hvp against the oracle's estimate")
+
+
+def run_both_threads(sc, renderer, quantity, M, strategy, seed, request, v, scene):
+    theta = np.asarray(sc["theta_query"], np.float64)
+    out, dbg = scene.estimate(Q[quantity], theta, sc["sigma"], M, S[strategy], seed, request, 0, v=v, debug=True)
+    ref = O.estimate(renderer, quantity, theta, sc["sigma"], M, strategy, seed, request, 0, v=v,
+                     threads=_host_threads())
+    return flat_of(quantity, out, sc["n_params"]), dbg, ref
 
 
 # ---------------------------------------------------------------------------
 # Newton-CG
 # ---------------------------------------------------------------------------
+def _check_cg_step(r, sc, th_b, got_b, info_b, g_b, p_b, hp_b, M_g, M_h, K, seed, request, step, what):
+    """One instance's Newton-CG step, piece by piece:
+    * the gradient estimate and every Hessian-vector product inside the CG
+      loop against the oracle's estimate of the same request on the same
+      samples, at the GPU's own direction p_i: 1e-4 per entry (the estimate
+      tolerance of every other parity test);
+    * the FP64 CG recurrence: the oracle's Newton-CG fed with the GPU's
+      gradient and products takes the same number of iterations and the
+      same step to 1e-9 (FP64 sums in another order);
+    * the step against the oracle's Newton-CG on its own estimates within
+      1e-3: the CG step is a non-linear function of K products, each within
+      1e-4, and a product error e moves the step by up to about
+      e |p| / lambda_min(H + lambda I)."""
+    sigma = sc["sigma"]
+    ref_g = O.estimate(r, "grad", th_b, sigma, M_g, "aggregate", seed, request, sub=64 * step)
+    assert_estimate_close(g_b, ref_g, what=f"{what}: gradient")
+    for i in range(info_b.iters):
+        ref = O.estimate(r, "hvp", th_b, sigma, M_h, "aggregate", seed, request, sub=64 * step + 1 + i, v=p_b[i])
+        assert_estimate_close(hp_b[i], ref, what=f"{what}: product {i}")
+
+    def hvp_gpu(th, i, vec):
+        assert np.allclose(vec, p_b[i], rtol=1e-12, atol=1e-12 * np.abs(p_b[i]).max()), (what, i)
+        return hp_b[i]
+    new, inf = O.newton_cg_step(r, th_b, sigma, M_g, M_h, K, 1e-3, 0.05, seed, request, step,
+                                grad_fn=lambda th: g_b, hvp_fn=hvp_gpu)
+    assert inf.iters == info_b.iters, what
+    d_gpu = got_b - th_b
+    assert np.allclose(d_gpu, new - th_b, rtol=1e-9, atol=1e-9 * np.linalg.norm(d_gpu)), what
+    new_o, inf_o = O.newton_cg_step(r, th_b, sigma, M_g, M_h, K, 1e-3, 0.05, seed, request, step)
+    assert inf_o.iters == info_b.iters, what
+    d_ref = new_o - th_b
+    assert np.allclose(d_gpu, d_ref, rtol=1e-3, atol=1e-4 * np.linalg.norm(d_ref)), what
+    assert abs(info_b.grad_norm - inf_o.grad_norm) <= 1e-4 * inf_o.grad_norm, what
+
+
 @pytest.mark.parametrize("use_graph", [0, 1])
 def test_newton_cg_step_matches_oracle(use_graph):
     sc = wl.tris2d_scene(width=48, height=40, n_instances=3)
     Sc = hr.Scene(sc)
     r = O.Tris2dRenderer(sc)
-    B, n = 3, sc["n_params"]
+    B, n, K = 3, sc["n_params"], 4
     opts = hr.hr_cg_opts()
-    opts.sigma, opts.n_grad, opts.n_hvp, opts.cg_iters = sc["sigma"], 16, 8, 4
+    opts.sigma, opts.n_grad, opts.n_hvp, opts.cg_iters = sc["sigma"], 16, 8, K
     opts.lambda_rel, opts.trust_radius, opts.seed, opts.request_base, opts.use_graph = 1e-3, 0.05, 99, 10, use_graph
     th0 = np.ascontiguousarray(sc["theta_init"][:B], np.float64)
     st = hr.hr_optstate_create(Sc.handle, B, th0, opts)
     info = (hr.hr_step_info * B)()
-    ref_th = th0.copy()
+    th = th0.copy()
     for step in range(2):
         hr.hr_newton_cg_step(Sc.handle, st, info)
         got = np.zeros((B, n))
         hr.hr_optstate_theta(st, got)
+        g, p, hp = hr.hr_optstate_trace(st, B, K, n)
         for b in range(B):
-            new, inf = O.newton_cg_step(r, ref_th[b], sc["sigma"], 16, 8, 4, 1e-3, 0.05, 99, 10 + b, step)
-            d_ref, d_gpu = new - ref_th[b], got[b] - ref_th[b]
-            assert info[b].iters == inf.iters
-            assert np.allclose(d_gpu, d_ref, rtol=1e-3, atol=1e-4 * np.linalg.norm(d_ref)), (step, b)
-            assert abs(info[b].grad_norm - inf.grad_norm) <= 1e-4 * inf.grad_norm
-            ref_th[b] = got[b]          # continue both from the GPU iterate
+            _check_cg_step(r, sc, th[b], got[b], info[b], g[b], p[b], hp[b], 16, 8, K, 99, 10 + b, step,
+                           f"step {step} instance {b}")
+        th = got.copy()            # continue both from the GPU iterate
     hr.hr_optstate_destroy(st)
     Sc.close()
 
@@ -271,14 +375,15 @@ def test_newton_cg_step_matches_oracle(use_graph):
 def test_newton_cg_full_size_bench_configuration_sampled():
     """256 x 256, 16 triangles, 64 parameters, 64 instances, 32 gradient and
     10 x 32 HVP renders, graph-captured (the bench workload in its launch
-    configuration): one step of three instances against the oracle's
-    Newton-CG, which renders every one of their perturbations."""
+    configuration): one step; for three instances every product inside the
+    CG loop, the gradient, the CG recurrence and the step against the
+    oracle, which renders every one of their perturbations."""
     sc = wl.tris2d_scene()
     Sc = hr.Scene(sc)
     r = O.Tris2dRenderer(sc)
-    B, n = 64, sc["n_params"]
+    B, n, K = 64, sc["n_params"], 10
     opts = hr.hr_cg_opts()
-    opts.sigma, opts.n_grad, opts.n_hvp, opts.cg_iters = sc["sigma"], 32, 32, 10
+    opts.sigma, opts.n_grad, opts.n_hvp, opts.cg_iters = sc["sigma"], 32, 32, K
     opts.lambda_rel, opts.trust_radius, opts.seed, opts.request_base, opts.use_graph = 1e-3, 0.05, 2024, 0, 1
     th0 = np.ascontiguousarray(sc["theta_init"], np.float64)
     st = hr.hr_optstate_create(Sc.handle, B, th0, opts)
@@ -286,14 +391,11 @@ def test_newton_cg_full_size_bench_configuration_sampled():
     hr.hr_newton_cg_step(Sc.handle, st, info)
     got = np.zeros((B, n))
     hr.hr_optstate_theta(st, got)
+    g, p, hp = hr.hr_optstate_trace(st, B, K, n)
     hr.hr_optstate_destroy(st)
     Sc.close()
     for b in (0, 37, 63):
-        new, inf = O.newton_cg_step(r, th0[b], sc["sigma"], 32, 32, 10, 1e-3, 0.05, 2024, b, 0)
-        d_ref, d_gpu = new - th0[b], got[b] - th0[b]
-        assert info[b].iters == inf.iters, b
-        assert np.allclose(d_gpu, d_ref, rtol=1e-3, atol=1e-4 * np.linalg.norm(d_ref)), b
-        assert abs(info[b].grad_norm - inf.grad_norm) <= 1e-4 * inf.grad_norm, b
+        _check_cg_step(r, sc, th0[b], got[b], info[b], g[b], p[b], hp[b], 32, 32, K, 2024, b, 0, f"instance {b}")
 
 
 # ---------------------------------------------------------------------------

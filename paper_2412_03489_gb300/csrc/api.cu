@@ -21,7 +21,6 @@ void launch_boxes_loss(const DevScene&, const RenderBatch&, cudaStream_t);
 void launch_boxes_image(const DevScene&, const float*, float*, cudaStream_t);
 void launch_revolve_loss(const DevScene&, const RenderBatch&, cudaStream_t);
 void launch_revolve_image(const DevScene&, const float*, float*, cudaStream_t);
-size_t revolve_smem_bytes(int nv, int nt, int W, int H);
 int revolve_tiles(int W, int H);
 void launch_tris2d_loss(const DevScene&, const RenderBatch&, cudaStream_t);
 void launch_tris2d_image(const DevScene&, const float*, float*, cudaStream_t);
@@ -508,10 +507,10 @@ hr_status hr_create_scene(const hr_scene_desc* d, hr_scene* out) {
             int dev = 0, maxsm = 0;
             cudaGetDevice(&dev);
             cudaDeviceGetAttribute(&maxsm, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
-            const size_t need = revolve_smem_bytes(sc.nv, sc.nt, sc.W, sc.H);
-            if (need + 1024 > (size_t)maxsm) {
+            if (!revolve_layout(sc.nv, sc.nt, sc.W, sc.H, maxsm, &sc.rv_smem, &sc.rv_cap, &sc.rv_vreg)) {
                 hr_destroy_scene(s);
-                return fail(HR_ERR_UNSUPPORTED, "mesh needs %zu B of shared memory (device max %d)", need, maxsm);
+                return fail(HR_ERR_UNSUPPORTED, "mesh of %d triangles at %dx%d does not fit in %d B of shared memory",
+                            sc.nt, sc.W, sc.H, maxsm);
             }
             if ((e = upload(&sc.verts, d->vertices, 3 * (size_t)sc.nv)) != cudaSuccess) return bail(e, "vertices");
             if ((e = upload(&sc.tris, d->triangles, 3 * (size_t)sc.nt)) != cudaSuccess) return bail(e, "triangles");

@@ -160,7 +160,8 @@ struct DevScene {
     int nv = 0, nt = 0;
     float albedo[3] = {0, 0, 0}, light[3] = {0, 0, 0};
     float eye_dist = 0.f, scale = 0.f;
-    size_t rv_smem = 0;
+    size_t rv_smem = 0;           // dynamic shared memory of one render
+    int rv_cap = 0, rv_vreg = 0;  // bin entry capacity, vertex-region floats
     unsigned long long* rv_stats = nullptr;   // [1] renders that took the bin-overflow path
     // tris2d
     float* raw = nullptr;         // [n_tris][9]
@@ -187,7 +188,10 @@ struct DevScene {
 // launch-shape variants of a scene kind's render+loss kernel (1 = none)
 int render_variant_count(int kind);
 
-void revolve_prepare(DevScene& sc, cudaStream_t s);   // normals, smem size
+// shared-memory layout of one mesh render on a device with max_smem bytes of
+// opt-in shared memory per block; false if the mesh does not fit
+bool revolve_layout(int nv, int nt, int W, int H, int max_smem, size_t* bytes, int* cap, int* vreg);
+void revolve_prepare(DevScene& sc, cudaStream_t s);   // normals, kernel attributes
 void revolve_tile_t2(DevScene& sc, cudaStream_t s);   // after the target exists
 
 int num_sms();

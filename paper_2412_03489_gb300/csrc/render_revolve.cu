@@ -7,16 +7,20 @@
 //   1. rotation R = Rx(p0) Ry(p1) from RN32 of FP64 cos / sin (for every
 //      perturbation after a CTA's first, computed during the previous raster);
 //   2. vertex transform and projection (FP32, fixed operation order);
-//   3. triangle setup: edge functions, back-face cull, depth plane of 1/Z,
-//      pixel bounding box, flat Lambert shade; surviving triangles are
-//      compacted into shared memory;
+//   3. triangle setup: edge functions with their top-left thresholds, back-face
+//      cull, depth plane of 1/Z, pixel bounding box, flat Lambert shade; each
+//      record stays at its triangle's index in shared memory;
 //   4. binning into 8x8 pixel tiles (count, scan, fill; all in shared memory),
 //      skipping tiles that a conservative edge test shows the triangle misses;
+//      each bin entry carries the triangle index and the rows / columns of its
+//      tile that lie inside the triangle's bounding box; each bin is then
+//      sorted (triangle order);
 //   5. warp-per-tile raster, tiles fetched dynamically: the two half-warps
-//      take alternate bin entries, each lane testing 4 pixels of a row; nearest 1/Z
-//      wins, ties to the lower triangle index (half-warp winners merged by a
-//      shuffle); (colour - target)^2 per tile; tiles with an empty bin take
-//      the precomputed sum of target^2;
+//      take alternate bin entries, each lane testing 4 pixels of a row; nearest
+//      1/Z wins with a strict compare, which in triangle order gives ties to
+//      the lower index (half-warp winners merged by a shuffle with the
+//      explicit tie rule); (colour - target)^2 per tile; tiles with an empty
+//      bin take the precomputed sum of target^2;
 //   6. per-tile losses summed in tile order, warp shuffle + block reduction to
 //      one FP32 loss per perturbation.
 // The FP32 sequences of steps 2-5 define the renderer (coverage and depth
@@ -33,26 +37,33 @@ namespace {
 constexpr int kThreads = 1024;
 constexpr int kWarps = kThreads / 32;
 constexpr int kTile = 8;
-constexpr int kEntryCap = 16384;
-constexpr int kHeavy = 6;   // tiles with at least this many entries are fetched first
+constexpr int kEntryCapMax = 16384;  // bin entries per render (less where shared memory is short)
+constexpr int kEntryCapMin = 2048;
+constexpr int kStaticSmem = 1024;    // the kernel's static shared memory, rounded up
 
+// One surviving triangle.  E > 0, or E == 0 on a top-left edge, is one
+// compare: E > th with th = 0 or th = -(smallest subnormal) (no float lies
+// strictly between the two).
 struct __align__(16) TriRec {
-    float A0, B0, C0, A1;
-    float B1, C1, A2, B2;
-    float C2, Aw, Bw, Cw;
-    float shade;
-    uint32_t key;  // triangle index | top-left flag of edge i at bit 29 + i
-    uint32_t xr;   // x_lo | x_hi << 16 (pixel columns whose centre is inside the bbox)
-    uint32_t yr;
+    float A0, B0, C0, th0;
+    float A1, B1, C1, th1;
+    float A2, B2, C2, th2;
+    float Aw, Bw, Cw, shade;
 };
 
-// E > 0, or E == 0 on a top-left edge, is one compare: E > thr with thr = 0
-// or thr = -(smallest subnormal) (no float lies strictly between the two)
-__device__ __forceinline__ float tl_threshold(uint32_t key, int i) {
-    return ((key >> (29 + i)) & 1u) ? -0x1p-149f : 0.0f;
+// bin entry: triangle << 16 | (tile rows inside the bounding box) << 8 |
+// (tile columns inside it); sorting entries sorts their triangles
+__device__ __forceinline__ uint32_t entry_word(int tri, uint32_t rows, uint32_t cols) {
+    return ((uint32_t)tri << 16) | (rows << 8) | cols;
 }
-__device__ __forceinline__ uint32_t tl_bit(float A, float B) {
-    return (A > 0.0f || (A == 0.0f && B > 0.0f)) ? 1u : 0u;
+// bits lo..hi (clamped to 0..7) of a byte
+__device__ __forceinline__ uint32_t span_bits(int lo, int hi) {
+    lo = max(lo, 0);
+    hi = min(hi, kTile - 1);
+    return lo > hi ? 0u : ((0xFFu >> (kTile - 1 - hi)) & (0xFFu << lo));
+}
+__device__ __forceinline__ float tl_threshold(float A, float B) {
+    return (A > 0.0f || (A == 0.0f && B > 0.0f)) ? -0x1p-149f : 0.0f;
 }
 
 struct RvArgs {
@@ -62,6 +73,8 @@ struct RvArgs {
     const float* target;
     const float* tile_t2;
     int nv, nt, W, H, TX, TY, T;
+    int cap;             // bin entry capacity
+    int vreg;            // floats in the vertex region
     uint64_t tx_recip;   // ceil(2^32 / TX): t / TX = (t tx_recip) >> 32 exactly for t, TX < 2^16
     unsigned long long* stats;   // [0]: renders whose bins overflowed (diagnostics)
     float alb0, alb1, alb2, l0, l1, l2, eye_dist, scale;
@@ -82,11 +95,11 @@ __device__ __forceinline__ bool pixel_range(float mn, float mx, int N, int& lo, 
 // a bound on its term magnitudes anywhere in the image; the FP32 errors of
 // the exact per-pixel test and of this test are below 3e-7 of that
 // magnitude, so no rejected tile holds a covered pixel.
-__device__ __forceinline__ bool tile_hits(const TriRec& r, const float neg[3], int tx, int ty) {
-    const int x0 = max(tx * kTile, (int)(r.xr & 0xffffu)), x1 = min(tx * kTile + kTile - 1, (int)(r.xr >> 16));
-    const int y0 = max(ty * kTile, (int)(r.yr & 0xffffu)), y1 = min(ty * kTile + kTile - 1, (int)(r.yr >> 16));
+__device__ __forceinline__ bool tile_hits(const float A[3], const float B[3], const float C[3], uint2 bb,
+                                          const float neg[3], int tx, int ty) {
+    const int x0 = max(tx * kTile, (int)(bb.x & 0xffffu)), x1 = min(tx * kTile + kTile - 1, (int)(bb.x >> 16));
+    const int y0 = max(ty * kTile, (int)(bb.y & 0xffffu)), y1 = min(ty * kTile + kTile - 1, (int)(bb.y >> 16));
     const float fx0 = (float)x0 + 0.5f, fx1 = (float)x1 + 0.5f, fy0 = (float)y0 + 0.5f, fy1 = (float)y1 + 0.5f;
-    const float A[3] = {r.A0, r.A1, r.A2}, B[3] = {r.B0, r.B1, r.B2}, C[3] = {r.C0, r.C1, r.C2};
     bool hit = true;
 #pragma unroll
     for (int i = 0; i < 3; ++i) {
@@ -96,59 +109,79 @@ __device__ __forceinline__ bool tile_hits(const TriRec& r, const float neg[3], i
     return hit;
 }
 
-// Exclusive scan of cnt[0..T) into off[0..T) and, in the same pass, the
-// list of tiles with entries (olist[0..n_obj)): tiles with at least kHeavy
-// entries first, then the others, each group in tile order, so that the
-// dynamic fetch hands out the long tiles first and the raster ends on short
-// ones.  Each tile contributes cnt + heavy 2^32 + light 2^48 to one 64-bit
-// scan (cnt < 2^32, tile counts < 2^16).  Returns the total entry count (all
+// Batcher's odd-even merge sort of 16 values held in registers: the 63
+// compare-exchanges of the network, in its stage order
+__device__ __forceinline__ void sort16(uint32_t v[16]) {
+#define X(a, b)                                   \
+    do {                                          \
+        const uint32_t lo_ = min(v[a], v[b]);     \
+        v[b] = max(v[a], v[b]);                   \
+        v[a] = lo_;                               \
+    } while (0)
+    X(0, 1); X(2, 3); X(4, 5); X(6, 7); X(8, 9); X(10, 11); X(12, 13); X(14, 15);
+    X(0, 2); X(1, 3); X(4, 6); X(5, 7); X(8, 10); X(9, 11); X(12, 14); X(13, 15);
+    X(1, 2); X(5, 6); X(9, 10); X(13, 14); X(0, 4); X(1, 5); X(2, 6); X(3, 7);
+    X(8, 12); X(9, 13); X(10, 14); X(11, 15); X(2, 4); X(3, 5); X(10, 12); X(11, 13);
+    X(1, 2); X(3, 4); X(5, 6); X(9, 10); X(11, 12); X(13, 14); X(0, 8); X(1, 9);
+    X(2, 10); X(3, 11); X(4, 12); X(5, 13); X(6, 14); X(7, 15); X(4, 8); X(5, 9);
+    X(6, 10); X(7, 11); X(2, 4); X(3, 5); X(6, 8); X(7, 9); X(10, 12); X(11, 13);
+    X(1, 2); X(3, 4); X(5, 6); X(7, 8); X(9, 10); X(11, 12); X(13, 14);
+#undef X
+}
+
+constexpr int kCountClasses = 32;   // tiles ordered by entry count, counts >= 31 share a class
+
+// Exclusive scan of cnt[0..T) into off[0..T) and, in the same barriers, the
+// list of tiles with entries (olist[0..n_obj)) ordered by entry count,
+// largest first (a counting sort over count classes; the order within a
+// class is arbitrary, which only affects which warp takes which tile).  The
+// raster fetches tiles in pairs, one per half-warp, so pairs of nearly equal
+// counts waste few iterations, and the long tiles go first.  hist
+// [kCountClasses] must be zero on entry.  Returns the total entry count (all
 // threads) and sets n_obj.
-__device__ int bin_scan(const int* cnt, int* off, uint16_t* olist, int T, unsigned long long* warp_tot,
-                        int* n_obj) {
+__device__ int bin_scan(const int* cnt, int* off, uint16_t* olist, int T, int* warp_tot, int* hist, int* n_obj) {
     const int per = (T + kThreads - 1) / kThreads;
     const int b = threadIdx.x * per;
-    auto packed = [](int c) {
-        return (unsigned long long)c + ((unsigned long long)(c >= kHeavy) << 32) +
-               ((unsigned long long)(c > 0 && c < kHeavy) << 48);
-    };
-    unsigned long long local = 0ull;
+    int local = 0;
     for (int i = 0; i < per; ++i)
-        if (b + i < T) local += packed(cnt[b + i]);
+        if (b + i < T) {
+            const int c = cnt[b + i];
+            local += c;
+            if (c > 0) atomicAdd(&hist[kCountClasses - 1 - min(c, kCountClasses - 1)], 1);
+        }
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    unsigned long long incl = local;
+    int incl = local;
 #pragma unroll
     for (int o = 1; o < 32; o <<= 1) {
-        const unsigned long long v = __shfl_up_sync(0xffffffffu, incl, o);
+        const int v = __shfl_up_sync(0xffffffffu, incl, o);
         if (lane >= o) incl += v;
     }
     if (lane == 31) warp_tot[warp] = incl;
     __syncthreads();
-    if (warp == 0) {
-        const unsigned long long wv = warp_tot[lane];
-        unsigned long long wi = wv;
+    if (warp < 2) {   // warp 0: offsets of the warps' tile ranges; warp 1: the count classes
+        int* arr = warp == 0 ? warp_tot : hist;
+        const int wv = arr[lane];
+        int wi = wv;
 #pragma unroll
         for (int o = 1; o < 32; o <<= 1) {
-            const unsigned long long v = __shfl_up_sync(0xffffffffu, wi, o);
+            const int v = __shfl_up_sync(0xffffffffu, wi, o);
             if (lane >= o) wi += v;
         }
-        warp_tot[lane] = wi - wv;       // exclusive warp offsets
-        if (lane == 31) warp_tot[32] = wi;
+        arr[lane] = wi - wv;
+        if (lane == 31) arr[32] = wi;
     }
     __syncthreads();
-    unsigned long long run = warp_tot[warp] + incl - local;
-    const unsigned long long total = warp_tot[32];
-    const int n_heavy = (int)((total >> 32) & 0xffffull);
+    int run = warp_tot[warp] + incl - local;
     for (int i = 0; i < per; ++i)
         if (b + i < T) {
             const int c = cnt[b + i];
-            off[b + i] = (int)(run & 0xffffffffull);
-            if (c >= kHeavy) olist[(run >> 32) & 0xffffull] = (uint16_t)(b + i);
-            else if (c > 0) olist[n_heavy + (int)(run >> 48)] = (uint16_t)(b + i);
-            run += packed(c);
+            off[b + i] = run;
+            if (c > 0) olist[atomicAdd(&hist[kCountClasses - 1 - min(c, kCountClasses - 1)], 1)] = (uint16_t)(b + i);
+            run += c;
         }
     __syncthreads();
-    *n_obj = n_heavy + (int)(total >> 48);
-    return (int)(total & 0xffffffffull);
+    *n_obj = hist[32];
+    return warp_tot[32];
 }
 
 // rotation angle d of perturbation m: RN32(theta32 + tau)
@@ -157,30 +190,63 @@ __device__ __forceinline__ float rotation_param(const RenderBatch& b, int m, int
     return __fadd_rn(pt.theta[d], pt.tau[d]);
 }
 
+// one triangle's setup; false if it is clipped, culled or outside the image
+__device__ __forceinline__ bool setup_triangle(const RvArgs& P, int t, const float* vx, const float* vy,
+                                               const float* viz, const float sL[3], TriRec& r, uint2& bb) {
+    const int ia = P.tris[3 * t], ib = P.tris[3 * t + 1], ic = P.tris[3 * t + 2];
+    const float iza = viz[ia], izb = viz[ib], izc = viz[ic];
+    if (!(iza > 0.0f && izb > 0.0f && izc > 0.0f)) return false;
+    const float ax = vx[ia], ay = vy[ia], bx = vx[ib], by = vy[ib], cx = vx[ic], cy = vy[ic];
+    const Edge e0 = edge_of(bx, by, cx, cy);
+    const Edge e1 = edge_of(cx, cy, ax, ay);
+    const Edge e2 = edge_of(ax, ay, bx, by);
+    const float D2 = edge_eval(e2.A, e2.B, e2.C, cx, cy);
+    if (!(D2 > 0.0f)) return false;
+    int xlo, xhi, ylo, yhi;
+    const float mnx = fminf(fminf(ax, bx), cx), mxx = fmaxf(fmaxf(ax, bx), cx);
+    const float mny = fminf(fminf(ay, by), cy), mxy = fmaxf(fmaxf(ay, by), cy);
+    if (!pixel_range(mnx, mxx, P.W, xlo, xhi) || !pixel_range(mny, mxy, P.H, ylo, yhi)) return false;
+    const float invD = __fdiv_rn(1.0f, D2);
+    r.A0 = e0.A; r.B0 = e0.B; r.C0 = e0.C; r.th0 = tl_threshold(e0.A, e0.B);
+    r.A1 = e1.A; r.B1 = e1.B; r.C1 = e1.C; r.th1 = tl_threshold(e1.A, e1.B);
+    r.A2 = e2.A; r.B2 = e2.B; r.C2 = e2.C; r.th2 = tl_threshold(e2.A, e2.B);
+    r.Aw = __fmul_rn(__fmaf_rn(e2.A, izc, __fmaf_rn(e1.A, izb, __fmul_rn(e0.A, iza))), invD);
+    r.Bw = __fmul_rn(__fmaf_rn(e2.B, izc, __fmaf_rn(e1.B, izb, __fmul_rn(e0.B, iza))), invD);
+    r.Cw = __fmul_rn(__fmaf_rn(e2.C, izc, __fmaf_rn(e1.C, izb, __fmul_rn(e0.C, iza))), invD);
+    const float sh = P.tnrm[3 * t] * sL[0] + P.tnrm[3 * t + 1] * sL[1] + P.tnrm[3 * t + 2] * sL[2];
+    r.shade = fmaxf(sh, 0.0f);
+    bb.x = (uint32_t)xlo | ((uint32_t)xhi << 16);
+    bb.y = (uint32_t)ylo | ((uint32_t)yhi << 16);
+    return true;
+}
+
 template <bool kImage>
 __global__ void __launch_bounds__(kThreads, 1)
 revolve_kernel(RvArgs P, RenderBatch b, const float* __restrict__ img_params, float* __restrict__ img) {
     extern __shared__ __align__(16) unsigned char smem[];
-    TriRec* rec = reinterpret_cast<TriRec*>(smem);
-    float* vx = reinterpret_cast<float*>(rec + P.nt);
+    TriRec* rec = reinterpret_cast<TriRec*>(smem);                // [nt] by triangle
+    uint2* bbx = reinterpret_cast<uint2*>(rec + P.nt);           // [nt] pixel bounding box by triangle
+    float* tshade = reinterpret_cast<float*>(bbx + P.nt);        // [nt] flat shade by triangle
+    float* vx = tshade + P.nt;                                   // vertex region, P.vreg floats
     float* vy = vx + P.nv;
     float* viz = vy + P.nv;
-    int* tcnt = reinterpret_cast<int*>(vx + max(3 * P.nv, (P.T + 1) / 2));
+    int* tcnt = reinterpret_cast<int*>(vx + P.vreg);
     int* toff = tcnt + P.T;
-    uint16_t* ent = reinterpret_cast<uint16_t*>(toff + P.T);
+    uint16_t* surv = reinterpret_cast<uint16_t*>(toff + P.T);   // [nt] surviving triangles (any order)
+    uint32_t* ent = reinterpret_cast<uint32_t*>(surv + ((P.nt + 1) & ~1));   // [cap] bin entries
+    // after the triangle setup the vertex region holds the count pass's tile
+    // masks [nt] (by survivor) and the list of tiles with entries [T]
+    uint32_t* tmask = reinterpret_cast<uint32_t*>(vx);
+    uint16_t* olist = reinterpret_cast<uint16_t*>(tmask + P.nt);
 
     __shared__ float s_cs[4], s_cs_next[4];
     __shared__ float sR[9];
     __shared__ float sL[3];
     __shared__ int s_count;
-    __shared__ unsigned long long s_wtot[33];
+    __shared__ int s_wtot[33];
+    __shared__ int s_hist[33];
     __shared__ float s_part[kWarps];
     __shared__ int s_tile;
-    float* tshade = reinterpret_cast<float*>(ent + kEntryCap);   // [nt] shade by triangle index
-    uint32_t* tmask = reinterpret_cast<uint32_t*>(tshade + P.nt);  // [nt] tiles hit, by record slot
-    // [T] tiles with entries, in tile order: in the vertex arrays, free once
-    // the triangles are set up (the region holds max(3 nv, T / 2) floats)
-    uint16_t* olist = reinterpret_cast<uint16_t*>(vx);
 
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     const int M = kImage ? 1 : b.M;
@@ -196,6 +262,7 @@ revolve_kernel(RvArgs P, RenderBatch b, const float* __restrict__ img_params, fl
             }
         }
         for (int i = tid; i < P.T; i += kThreads) tcnt[i] = 0;
+        if (tid < 33) s_hist[tid] = 0;
         if (tid == 0) { s_count = 0; s_tile = 0; }
         __syncthreads();
         if (tid == 0) {
@@ -223,99 +290,115 @@ revolve_kernel(RvArgs P, RenderBatch b, const float* __restrict__ img_params, fl
             viz[v] = (Z > 0.0f) ? __fdiv_rn(1.0f, Z) : -1.0f;
         }
         __syncthreads();
-        // ---- 3. triangle setup ----------------------------------------------
+        // ---- 3. triangle setup ------------------------------------------------
+        // records stay at their triangle's index (bin entries sorted by index
+        // are in triangle order); the survivors are listed for the binning,
+        // and a clipped, culled or off-image triangle gets an empty bounding
+        // box (lo > hi), which the all-triangles fallback of the raster skips
         for (int t = tid; t < P.nt; t += kThreads) {
-            const int ia = P.tris[3 * t], ib = P.tris[3 * t + 1], ic = P.tris[3 * t + 2];
-            const float iza = viz[ia], izb = viz[ib], izc = viz[ic];
-            if (!(iza > 0.0f && izb > 0.0f && izc > 0.0f)) continue;
-            const float ax = vx[ia], ay = vy[ia], bx = vx[ib], by = vy[ib], cx = vx[ic], cy = vy[ic];
-            const Edge e0 = edge_of(bx, by, cx, cy);
-            const Edge e1 = edge_of(cx, cy, ax, ay);
-            const Edge e2 = edge_of(ax, ay, bx, by);
-            const float D2 = edge_eval(e2.A, e2.B, e2.C, cx, cy);
-            if (!(D2 > 0.0f)) continue;
-            int xlo, xhi, ylo, yhi;
-            const float mnx = fminf(fminf(ax, bx), cx), mxx = fmaxf(fmaxf(ax, bx), cx);
-            const float mny = fminf(fminf(ay, by), cy), mxy = fmaxf(fmaxf(ay, by), cy);
-            if (!pixel_range(mnx, mxx, P.W, xlo, xhi) || !pixel_range(mny, mxy, P.H, ylo, yhi)) continue;
-            const float invD = __fdiv_rn(1.0f, D2);
             TriRec r;
-            r.A0 = e0.A; r.B0 = e0.B; r.C0 = e0.C;
-            r.A1 = e1.A; r.B1 = e1.B; r.C1 = e1.C;
-            r.A2 = e2.A; r.B2 = e2.B; r.C2 = e2.C;
-            r.Aw = __fmul_rn(__fmaf_rn(e2.A, izc, __fmaf_rn(e1.A, izb, __fmul_rn(e0.A, iza))), invD);
-            r.Bw = __fmul_rn(__fmaf_rn(e2.B, izc, __fmaf_rn(e1.B, izb, __fmul_rn(e0.B, iza))), invD);
-            r.Cw = __fmul_rn(__fmaf_rn(e2.C, izc, __fmaf_rn(e1.C, izb, __fmul_rn(e0.C, iza))), invD);
-            const float sh = P.tnrm[3 * t] * sL[0] + P.tnrm[3 * t + 1] * sL[1] + P.tnrm[3 * t + 2] * sL[2];
-            r.shade = fmaxf(sh, 0.0f);
-            tshade[t] = r.shade;
-            r.key = (uint32_t)t | (tl_bit(e0.A, e0.B) << 29) | (tl_bit(e1.A, e1.B) << 30) | (tl_bit(e2.A, e2.B) << 31);
-            r.xr = (uint32_t)xlo | ((uint32_t)xhi << 16);
-            r.yr = (uint32_t)ylo | ((uint32_t)yhi << 16);
-            const int slot = atomicAdd(&s_count, 1);
-            rec[slot] = r;
+            uint2 bb;
+            if (setup_triangle(P, t, vx, vy, viz, sL, r, bb)) {
+                rec[t] = r;
+                tshade[t] = r.shade;
+                surv[atomicAdd(&s_count, 1)] = (uint16_t)t;
+            } else {
+                bb = make_uint2(1u, 1u);
+            }
+            bbx[t] = bb;
         }
         __syncthreads();
         const int count = s_count;
         // ---- 4. binning -----------------------------------------------------
-        // count pass: each record's tiles that pass the conservative edge test
-        // go into a bit mask (row-major over its tile rectangle; rectangles of
-        // more than 32 tiles skip the test), reused by the fill pass
-        for (int s = tid; s < count; s += kThreads) {
-            const TriRec r = rec[s];
-            const int tx0 = (int)(r.xr & 0xffffu) / kTile, tx1 = (int)(r.xr >> 16) / kTile;
-            const int ty0 = (int)(r.yr & 0xffffu) / kTile, ty1 = (int)(r.yr >> 16) / kTile;
+        // count pass: each survivor's tiles that pass the conservative edge
+        // test go into a bit mask (row-major over its tile rectangle;
+        // rectangles of more than 32 tiles skip the test), reused by the fill
+        for (int k = tid; k < count; k += kThreads) {
+            const int s = surv[k];
+            const uint2 bb = bbx[s];
+            const float4* rp = reinterpret_cast<const float4*>(&rec[s]);
+            const float4 q0 = rp[0], q1 = rp[1], q2 = rp[2];
+            const float A[3] = {q0.x, q1.x, q2.x}, B[3] = {q0.y, q1.y, q2.y}, C[3] = {q0.z, q1.z, q2.z};
+            const int tx0 = (int)(bb.x & 0xffffu) / kTile, tx1 = (int)(bb.x >> 16) / kTile;
+            const int ty0 = (int)(bb.y & 0xffffu) / kTile, ty1 = (int)(bb.y >> 16) / kTile;
             const bool test = (tx1 - tx0 + 1) * (ty1 - ty0 + 1) <= 32;
             const float fW = (float)P.W, fH = (float)P.H;
-            const float neg[3] = {-1e-5f * fmaf(fabsf(r.A0), fW, fmaf(fabsf(r.B0), fH, fabsf(r.C0))),
-                                  -1e-5f * fmaf(fabsf(r.A1), fW, fmaf(fabsf(r.B1), fH, fabsf(r.C1))),
-                                  -1e-5f * fmaf(fabsf(r.A2), fW, fmaf(fabsf(r.B2), fH, fabsf(r.C2)))};
+            float neg[3];
+#pragma unroll
+            for (int i = 0; i < 3; ++i) neg[i] = -1e-5f * fmaf(fabsf(A[i]), fW, fmaf(fabsf(B[i]), fH, fabsf(C[i])));
             uint32_t mask = 0;
             int bit = 0;
             for (int ty = ty0; ty <= ty1; ++ty)
                 for (int tx = tx0; tx <= tx1; ++tx, ++bit)
-                    if (!test || tile_hits(r, neg, tx, ty)) {
+                    if (!test || tile_hits(A, B, C, bb, neg, tx, ty)) {
                         atomicAdd(&tcnt[ty * P.TX + tx], 1);
                         if (test) mask |= 1u << bit;
                     }
-            tmask[s] = test ? mask : 0xFFFFFFFFu;
+            tmask[k] = test ? mask : 0xFFFFFFFFu;
         }
         __syncthreads();
         int n_obj = 0;
-        const int total = bin_scan(tcnt, toff, olist, P.T, s_wtot, &n_obj);
-        const bool overflow = total > kEntryCap;
+        const int total = bin_scan(tcnt, toff, olist, P.T, s_wtot, s_hist, &n_obj);
+        const bool overflow = total > P.cap;
         if (overflow && tid == 0 && P.stats) atomicAdd(P.stats, 1ull);
         for (int i = tid; i < P.T; i += kThreads) tcnt[i] = 0;   // becomes the fill cursor
         __syncthreads();
         if (!overflow) {
-            for (int s = tid; s < count; s += kThreads) {
-                const uint32_t xr = rec[s].xr, yr = rec[s].yr, mask = tmask[s];
-                const int tx0 = (int)(xr & 0xffffu) / kTile, tx1 = (int)(xr >> 16) / kTile;
-                const int ty0 = (int)(yr & 0xffffu) / kTile, ty1 = (int)(yr >> 16) / kTile;
+            for (int k = tid; k < count; k += kThreads) {
+                const int s = surv[k];
+                const uint2 bb = bbx[s];
+                const uint32_t mask = tmask[k];
+                const int xlo = (int)(bb.x & 0xffffu), xhi = (int)(bb.x >> 16);
+                const int ylo = (int)(bb.y & 0xffffu), yhi = (int)(bb.y >> 16);
+                const int tx0 = xlo / kTile, tx1 = xhi / kTile, ty0 = ylo / kTile, ty1 = yhi / kTile;
                 int bit = 0;
-                for (int ty = ty0; ty <= ty1; ++ty)
+                for (int ty = ty0; ty <= ty1; ++ty) {
+                    const uint32_t rows = span_bits(ylo - ty * kTile, yhi - ty * kTile);
                     for (int tx = tx0; tx <= tx1; ++tx, ++bit) {
                         if (mask != 0xFFFFFFFFu && !((mask >> bit) & 1u)) continue;
                         const int tile = ty * P.TX + tx;
                         const int pos = atomicAdd(&tcnt[tile], 1);
-                        ent[toff[tile] + pos] = (uint16_t)s;
+                        ent[toff[tile] + pos] = entry_word(s, rows, span_bits(xlo - tx * kTile, xhi - tx * kTile));
                     }
+                }
+            }
+            __syncthreads();
+            // each bin in triangle order: a sorting network in registers for
+            // bins of up to 16 entries, insertion sort beyond
+            for (int t = tid; t < P.T; t += kThreads) {
+                const int n = tcnt[t];
+                if (n < 2) continue;
+                uint32_t* e = ent + toff[t];
+                if (n <= 16) {
+                    uint32_t v[16];
+#pragma unroll
+                    for (int i = 0; i < 16; ++i) v[i] = i < n ? e[i] : 0xFFFFFFFFu;
+                    sort16(v);
+#pragma unroll
+                    for (int i = 0; i < 16; ++i)
+                        if (i < n) e[i] = v[i];
+                } else {
+                    for (int i = 1; i < n; ++i) {
+                        const uint32_t v = e[i];
+                        int j = i - 1;
+                        while (j >= 0 && e[j] > v) { e[j + 1] = e[j]; --j; }
+                        e[j + 1] = v;
+                    }
+                }
             }
         }
         __syncthreads();
         // ---- 5. raster + loss ------------------------------------------------
-        // warps fetch tiles dynamically (object tiles cost far more than
-        // background tiles); each tile's loss goes to its own slot (the fill cursor array is free
-        // again) and the slots are summed in tile order below, so the loss does
-        // not depend on which warp took which tile
-        float* tile_loss = reinterpret_cast<float*>(tcnt);
-        // Half-warp pairing: lanes 0-15 and 16-31 walk alternate entries of the
-        // bin.  Lane (row ry, half-row hx) of a half covers the 4 pixels
-        // (x0 .. x0 + 3, y): the row term fma(B, y + 1/2, C) of each edge and of
-        // the depth plane is formed once per entry and shared by the 4 pixels.
-        // The per-entry work (record loads, unpacking, thresholds) is paid once
-        // per pair of entries; the halves' per-pixel winners merge with a
-        // shuffle (largest 1/Z, lower index on ties: order-independent).
+        // Warps fetch tiles dynamically in pairs from the count-ordered list,
+        // one tile per half-warp; each tile's loss goes to its own slot (the
+        // fill cursor array is free again) and the slots are summed in tile
+        // order below, so the loss does not depend on which warp took which
+        // tile.  Lane (row ry, half-row hx) of a half owns the 4 pixels
+        // (x0 .. x0 + 3, y) of its tile and walks the tile's whole bin in
+        // triangle order: the row term fma(B, y + 1/2, C) of each edge and of
+        // the depth plane is formed once per entry and shared by the 4
+        // pixels, and the strict depth compare keeps the lower triangle index
+        // on ties.
         const int half = lane >> 4, hl = lane & 15;
         const int ry = hl >> 1, hx = hl & 1;
         // the FP64 cos / sin of this CTA's next perturbation, off the critical
@@ -327,106 +410,116 @@ revolve_kernel(RvArgs P, RenderBatch b, const float* __restrict__ img_params, fl
                 s_cs_next[lane] = (float)((lane & 1) ? sin(a) : cos(a));
             }
         }
-        // each warp reserves its next tile when it starts the current one, so
-        // the shared atomic's latency overlaps the tile's work
         // tiles without entries are not visited: their loss, the sum of
         // target^2, is taken in the reduction (an image visits every tile)
+        float* tile_loss = reinterpret_cast<float*>(tcnt);
         const bool all_tiles = kImage || overflow;
         const int n_iter = all_tiles ? P.T : n_obj;
+        const uint32_t row_bit = 1u << (8 + ry);
+        const int col_shift = 4 * hx;
+        const bool vec_target = (P.W & 3) == 0;
+        // each warp reserves its next pair of tiles when it starts the current
+        // one, so the shared atomic's latency overlaps the tiles' work
         int t_next = 0;
-        if (lane == 0) t_next = atomicAdd(&s_tile, 1);
+        if (lane == 0) t_next = atomicAdd(&s_tile, 2);
         for (int it = __shfl_sync(0xffffffffu, t_next, 0); it < n_iter; it = __shfl_sync(0xffffffffu, t_next, 0)) {
-            if (lane == 0) t_next = atomicAdd(&s_tile, 1);
-            const int t = all_tiles ? it : (int)olist[it];
-            int beg, end;
-            if (overflow) { beg = 0; end = count; }
-            else { beg = toff[t]; end = (t + 1 < P.T) ? toff[t + 1] : total; }
+            if (lane == 0) t_next = atomicAdd(&s_tile, 2);
+            const int my = it + half;
+            const bool has_tile = my < n_iter;
+            const int t = !has_tile ? 0 : (all_tiles ? my : (int)olist[my]);
+            const int beg = has_tile && !overflow ? toff[t] : 0;
+            const int n_mine = has_tile && !overflow ? ((t + 1 < P.T) ? toff[t + 1] : total) - beg : 0;
             // division by multiplication with the rounded-up reciprocal
             // (Granlund and Montgomery, PLDI 1994): exact for t, TX < 2^16
             const int ty = (int)(((uint64_t)(uint32_t)t * P.tx_recip) >> 32), tx = t - ty * P.TX;
             const int x0 = tx * kTile + 4 * hx, y = ty * kTile + ry;
-            // loss pixels of this lane after the merge: columns x0 + 2 half, x0 + 2 half + 1
-            const int xa = x0 + 2 * half, xb = xa + 1;
-            const bool va = xa < P.W && y < P.H, vb = xb < P.W && y < P.H;
-            float tga[3] = {0.f, 0.f, 0.f}, tgb[3] = {0.f, 0.f, 0.f};
-            if (!kImage) {
-                if (va) for (int c = 0; c < 3; ++c) tga[c] = P.target[3 * ((size_t)y * P.W + xa) + c];
-                if (vb) for (int c = 0; c < 3; ++c) tgb[c] = P.target[3 * ((size_t)y * P.W + xb) + c];
-            }
             const float fy = __fadd_rn((float)y, 0.5f);
             float fx[4], bw[4];
-            int bi[4];
+            int bs[4];
 #pragma unroll
             for (int c = 0; c < 4; ++c) {
                 fx[c] = __fadd_rn((float)(x0 + c), 0.5f);
                 bw[c] = -INFINITY;
-                bi[c] = INT_MAX;
+                bs[c] = INT_MAX;
             }
-            for (int jj = beg; jj < end; jj += 2) {
-                const int j = jj + half;
-                if (j < end) {
-                    const int s = overflow ? j : (int)ent[j];
-                    const float4* rp = reinterpret_cast<const float4*>(&rec[s]);
-                    const float4 q0 = rp[0], q1 = rp[1], q2 = rp[2], q3 = rp[3];
-                    const uint32_t key = __float_as_uint(q3.y);
-                    const uint32_t xr = __float_as_uint(q3.z), yr = __float_as_uint(q3.w);
-                    const int ti = (int)(key & 0x1FFFFFFFu);
-                    const float th0 = tl_threshold(key, 0), th1 = tl_threshold(key, 1), th2 = tl_threshold(key, 2);
-                    const int lo = (int)(xr & 0xffffu) - x0, hi = (int)(xr >> 16) - x0;
-                    const int ylo = (int)(yr & 0xffffu);
-                    const bool yok = (unsigned)(y - ylo) <= (yr >> 16) - (unsigned)ylo;
-                    const float r0 = __fmaf_rn(q0.y, fy, q0.z);
-                    const float r1 = __fmaf_rn(q1.x, fy, q1.y);
-                    const float r2 = __fmaf_rn(q1.w, fy, q2.x);
-                    const float rw = __fmaf_rn(q2.z, fy, q2.w);
+            // one bin entry against this lane's 4 pixels
+            auto raster_entry = [&](int s, uint32_t nib) {
+                const float4* rp = reinterpret_cast<const float4*>(&rec[s]);
+                const float4 q0 = rp[0], q1 = rp[1], q2 = rp[2], q3 = rp[3];
+                const float r0 = __fmaf_rn(q0.y, fy, q0.z);
+                const float r1 = __fmaf_rn(q1.y, fy, q1.z);
+                const float r2 = __fmaf_rn(q2.y, fy, q2.z);
+                const float rw = __fmaf_rn(q3.y, fy, q3.z);
 #pragma unroll
-                    for (int c = 0; c < 4; ++c) {
-                        const float E0 = __fmaf_rn(q0.x, fx[c], r0);
-                        const float E1 = __fmaf_rn(q0.w, fx[c], r1);
-                        const float E2 = __fmaf_rn(q1.z, fx[c], r2);
-                        const float wz = __fmaf_rn(q2.y, fx[c], rw);
-                        const bool in = yok && c >= lo && c <= hi && (E0 > th0) && (E1 > th1) && (E2 > th2);
-                        const bool better = in && (wz > bw[c] || (wz == bw[c] && ti < bi[c]));
-                        bw[c] = better ? wz : bw[c];
-                        bi[c] = better ? ti : bi[c];
+                for (int c = 0; c < 4; ++c) {
+                    const float E0 = __fmaf_rn(q0.x, fx[c], r0);
+                    const float E1 = __fmaf_rn(q1.x, fx[c], r1);
+                    const float E2 = __fmaf_rn(q2.x, fx[c], r2);
+                    const float wz = __fmaf_rn(q3.x, fx[c], rw);
+                    const bool better =
+                        ((nib >> c) & 1u) && (E0 > q0.w) && (E1 > q1.w) && (E2 > q2.w) && (wz > bw[c]);
+                    bw[c] = better ? wz : bw[c];
+                    bs[c] = better ? s : bs[c];
+                }
+            };
+            if (!overflow) {
+                const int n_max = max(n_mine, __shfl_xor_sync(0xffffffffu, n_mine, 16));
+                for (int k = 0; k < n_max; ++k) {
+                    if (k < n_mine) {
+                        const uint32_t e = ent[beg + k];
+                        // this lane's 4 columns inside the bounding box (none if its row is not)
+                        raster_entry((int)(e >> 16), (e & row_bit) ? (e >> col_shift) & 0xFu : 0u);
                     }
                 }
-            }
-#pragma unroll
-            for (int c = 0; c < 4; ++c) {
-                const float ow = __shfl_xor_sync(0xffffffffu, bw[c], 16);
-                const int oi = __shfl_xor_sync(0xffffffffu, bi[c], 16);
-                const bool take = ow > bw[c] || (ow == bw[c] && oi < bi[c]);
-                bw[c] = take ? ow : bw[c];
-                bi[c] = take ? oi : bi[c];
-            }
-            // this lane's two pixels: columns 2 half and 2 half + 1 of its four
-            const int ia = half ? bi[2] : bi[0], ib = half ? bi[3] : bi[1];
-            const float sha = ia != INT_MAX ? tshade[ia] : 0.0f;
-            const float shb = ib != INT_MAX ? tshade[ib] : 0.0f;
-            const float ca0 = sha * P.alb0, ca1 = sha * P.alb1, ca2 = sha * P.alb2;
-            const float cb0 = shb * P.alb0, cb1 = shb * P.alb1, cb2 = shb * P.alb2;
-            if (kImage) {
-                if (va) {
-                    const size_t p = 3 * ((size_t)y * P.W + xa);
-                    img[p] = ca0; img[p + 1] = ca1; img[p + 2] = ca2;
-                }
-                if (vb) {
-                    const size_t p = 3 * ((size_t)y * P.W + xb);
-                    img[p] = cb0; img[p + 1] = cb1; img[p + 2] = cb2;
-                }
             } else {
+                // every triangle in index order (culled ones have an empty box)
+                for (int s = 0; s < P.nt; ++s) {
+                    const uint2 bb = bbx[s];
+                    const int xlo = (int)(bb.x & 0xffffu), xhi = (int)(bb.x >> 16);
+                    const int ylo = (int)(bb.y & 0xffffu), yhi = (int)(bb.y >> 16);
+                    if (has_tile && xlo <= xhi && y >= ylo && y <= yhi)
+                        raster_entry(s, (span_bits(xlo - tx * kTile, xhi - tx * kTile) >> col_shift) & 0xFu);
+                }
+            }
+            // (both halves run the shuffles below, a half without a tile too)
+            float sh[4];
+#pragma unroll
+            for (int c = 0; c < 4; ++c) sh[c] = bs[c] != INT_MAX ? tshade[bs[c]] : 0.0f;
+            const bool rowv = has_tile && y < P.H;
+            if (kImage) {
+#pragma unroll
+                for (int c = 0; c < 4; ++c)
+                    if (rowv && x0 + c < P.W) {
+                        const size_t p = 3 * ((size_t)y * P.W + x0 + c);
+                        img[p] = sh[c] * P.alb0; img[p + 1] = sh[c] * P.alb1; img[p + 2] = sh[c] * P.alb2;
+                    }
+            } else {
+                float tg[12];
+                if (rowv && vec_target && x0 + 3 < P.W) {
+                    const float4* tp = reinterpret_cast<const float4*>(P.target + 3 * ((size_t)y * P.W + x0));
+                    const float4 a0 = tp[0], a1 = tp[1], a2 = tp[2];
+                    tg[0] = a0.x; tg[1] = a0.y; tg[2] = a0.z; tg[3] = a0.w;
+                    tg[4] = a1.x; tg[5] = a1.y; tg[6] = a1.z; tg[7] = a1.w;
+                    tg[8] = a2.x; tg[9] = a2.y; tg[10] = a2.z; tg[11] = a2.w;
+                } else {
+#pragma unroll
+                    for (int c = 0; c < 4; ++c)
+#pragma unroll
+                        for (int ch = 0; ch < 3; ++ch)
+                            tg[3 * c + ch] = (rowv && x0 + c < P.W) ? P.target[3 * ((size_t)y * P.W + x0 + c) + ch] : 0.0f;
+                }
                 float acc = 0.0f;
-                if (va) {
-                    const float d0 = ca0 - tga[0], d1 = ca1 - tga[1], d2 = ca2 - tga[2];
-                    acc += d0 * d0 + d1 * d1 + d2 * d2;
-                }
-                if (vb) {
-                    const float d0 = cb0 - tgb[0], d1 = cb1 - tgb[1], d2 = cb2 - tgb[2];
-                    acc += d0 * d0 + d1 * d1 + d2 * d2;
-                }
-                acc = warp_sum(acc);
-                if (lane == 0) tile_loss[t] = acc;
+#pragma unroll
+                for (int c = 0; c < 4; ++c)
+                    if (rowv && x0 + c < P.W) {
+                        const float d0 = sh[c] * P.alb0 - tg[3 * c], d1 = sh[c] * P.alb1 - tg[3 * c + 1];
+                        const float d2 = sh[c] * P.alb2 - tg[3 * c + 2];
+                        acc += d0 * d0 + d1 * d1 + d2 * d2;
+                    }
+                // sum over the half's 16 lanes
+#pragma unroll
+                for (int o = 8; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
+                if (hl == 0 && has_tile) tile_loss[t] = acc;
             }
         }
         // ---- 6. reduction -----------------------------------------------------
@@ -491,22 +584,36 @@ RvArgs make_args(const DevScene& sc) {
     a.alb0 = sc.albedo[0]; a.alb1 = sc.albedo[1]; a.alb2 = sc.albedo[2];
     a.l0 = sc.light[0]; a.l1 = sc.light[1]; a.l2 = sc.light[2];
     a.eye_dist = sc.eye_dist; a.scale = sc.scale;
+    a.cap = sc.rv_cap; a.vreg = sc.rv_vreg;
     a.stats = sc.rv_stats;
     return a;
 }
 
 }  // namespace
 
-size_t revolve_smem_bytes(int nv, int nt, int W, int H) {
+// Shared-memory layout of one render: records (64 B), bounding boxes (8 B)
+// and shades (4 B) by triangle, the vertex region (the projected vertices,
+// later the tile masks and the list of tiles with entries), tile counts and
+// offsets, the survivor list (2 B per triangle), and the bin entries in what
+// remains of max_smem (at most kEntryCapMax).  False when fewer than
+// kEntryCapMin entries fit.
+bool revolve_layout(int nv, int nt, int W, int H, int max_smem, size_t* bytes, int* cap, int* vreg) {
     const int T = ((W + kTile - 1) / kTile) * ((H + kTile - 1) / kTile);
-    const size_t vreg = 3 * (size_t)nv > (size_t)(T + 1) / 2 ? 3 * (size_t)nv : (size_t)(T + 1) / 2;
-    return sizeof(TriRec) * (size_t)nt + sizeof(float) * vreg + 2 * sizeof(int) * (size_t)T +
-           sizeof(uint16_t) * kEntryCap + sizeof(float) * (size_t)nt + sizeof(uint32_t) * (size_t)nt;
+    const int vr = 3 * nv > nt + (T + 1) / 2 ? 3 * nv : nt + (T + 1) / 2;
+    const size_t fixed = (sizeof(TriRec) + sizeof(uint2) + sizeof(float)) * (size_t)nt +
+                         sizeof(float) * (size_t)vr + 2 * sizeof(int) * (size_t)T +
+                         sizeof(uint16_t) * (size_t)((nt + 1) & ~1);
+    const long long avail = (long long)max_smem - kStaticSmem - (long long)fixed;
+    const long long c = avail / (long long)sizeof(uint32_t);
+    if (c < kEntryCapMin) return false;
+    *cap = c < kEntryCapMax ? (int)c : kEntryCapMax;
+    *vreg = vr;
+    *bytes = fixed + sizeof(uint32_t) * (size_t)*cap;
+    return true;
 }
 
 void revolve_prepare(DevScene& sc, cudaStream_t s) {
     normals_kernel<<<(sc.nt + 255) / 256, 256, 0, s>>>(sc.verts, sc.tris, sc.nt, sc.tnrm);
-    sc.rv_smem = revolve_smem_bytes(sc.nv, sc.nt, sc.W, sc.H);
     cudaFuncSetAttribute(revolve_kernel<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sc.rv_smem);
     cudaFuncSetAttribute(revolve_kernel<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sc.rv_smem);
 }

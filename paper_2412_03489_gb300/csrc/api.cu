@@ -21,7 +21,6 @@ void launch_boxes_loss(const DevScene&, const RenderBatch&, cudaStream_t);
 void launch_boxes_image(const DevScene&, const float*, float*, cudaStream_t);
 void launch_revolve_loss(const DevScene&, const RenderBatch&, cudaStream_t);
 void launch_revolve_image(const DevScene&, const float*, float*, cudaStream_t);
-int revolve_tiles(int W, int H);
 void launch_tris2d_loss(const DevScene&, const RenderBatch&, cudaStream_t);
 void launch_tris2d_image(const DevScene&, const float*, float*, cudaStream_t);
 void launch_ptbox_loss(const DevScene&, const RenderBatch&, cudaStream_t);
@@ -507,7 +506,7 @@ hr_status hr_create_scene(const hr_scene_desc* d, hr_scene* out) {
             int dev = 0, maxsm = 0;
             cudaGetDevice(&dev);
             cudaDeviceGetAttribute(&maxsm, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
-            if (!revolve_layout(sc.nv, sc.nt, sc.W, sc.H, maxsm, &sc.rv_smem, &sc.rv_cap, &sc.rv_vreg)) {
+            if (!revolve_layout(sc, maxsm)) {
                 hr_destroy_scene(s);
                 return fail(HR_ERR_UNSUPPORTED, "mesh of %d triangles at %dx%d does not fit in %d B of shared memory",
                             sc.nt, sc.W, sc.H, maxsm);
@@ -515,7 +514,7 @@ hr_status hr_create_scene(const hr_scene_desc* d, hr_scene* out) {
             if ((e = upload(&sc.verts, d->vertices, 3 * (size_t)sc.nv)) != cudaSuccess) return bail(e, "vertices");
             if ((e = upload(&sc.tris, d->triangles, 3 * (size_t)sc.nt)) != cudaSuccess) return bail(e, "triangles");
             if ((e = cudaMalloc(&sc.tnrm, sizeof(float) * 3 * sc.nt)) != cudaSuccess) return bail(e, "normals");
-            if ((e = cudaMalloc(&sc.tile_t2, sizeof(float) * revolve_tiles(sc.W, sc.H))) != cudaSuccess)
+            if ((e = cudaMalloc(&sc.tile_t2, sizeof(float) * revolve_tiles(sc))) != cudaSuccess)
                 return bail(e, "tiles");
             if ((e = cudaMalloc(&sc.rv_stats, sizeof(unsigned long long))) != cudaSuccess) return bail(e, "stats");
             if ((e = cudaMemset(sc.rv_stats, 0, sizeof(unsigned long long))) != cudaSuccess) return bail(e, "stats");

@@ -162,6 +162,7 @@ struct DevScene {
     float eye_dist = 0.f, scale = 0.f;
     size_t rv_smem = 0;           // dynamic shared memory of one render
     int rv_cap = 0, rv_vreg = 0;  // bin entry capacity, vertex-region floats
+    int rv_th = 8;                // raster tile height (8 x rv_th pixel tiles)
     unsigned long long* rv_stats = nullptr;   // [1] renders that took the bin-overflow path
     // tris2d
     float* raw = nullptr;         // [n_tris][9]
@@ -188,9 +189,11 @@ struct DevScene {
 // launch-shape variants of a scene kind's render+loss kernel (1 = none)
 int render_variant_count(int kind);
 
-// shared-memory layout of one mesh render on a device with max_smem bytes of
-// opt-in shared memory per block; false if the mesh does not fit
-bool revolve_layout(int nv, int nt, int W, int H, int max_smem, size_t* bytes, int* cap, int* vreg);
+// shared-memory layout and tile height of one mesh render on a device with
+// max_smem bytes of opt-in shared memory per block (sets rv_smem, rv_cap,
+// rv_vreg, rv_th); false if the mesh does not fit
+bool revolve_layout(DevScene& sc, int max_smem);
+int revolve_tiles(const DevScene& sc);
 void revolve_prepare(DevScene& sc, cudaStream_t s);   // normals, kernel attributes
 void revolve_tile_t2(DevScene& sc, cudaStream_t s);   // after the target exists
 

@@ -10,17 +10,18 @@
 //   3. triangle setup: edge functions with their top-left thresholds, back-face
 //      cull, depth plane of 1/Z, pixel bounding box, flat Lambert shade; each
 //      record stays at its triangle's index in shared memory;
-//   4. binning into 8x8 pixel tiles (count, scan, fill; all in shared memory),
-//      skipping tiles that a conservative edge test shows the triangle misses;
-//      each bin entry carries the triangle index and the rows / columns of its
-//      tile that lie inside the triangle's bounding box; each bin is then
-//      sorted (triangle order);
-//   5. warp-per-tile raster, tiles fetched dynamically: the two half-warps
-//      take alternate bin entries, each lane testing 4 pixels of a row; nearest
-//      1/Z wins with a strict compare, which in triangle order gives ties to
-//      the lower index (half-warp winners merged by a shuffle with the
-//      explicit tie rule); (colour - target)^2 per tile; tiles with an empty
-//      bin take the precomputed sum of target^2;
+//   4. binning into 8x4 pixel tiles (8x8 where shared memory is short; count,
+//      scan, fill; all in shared memory), skipping tiles that a conservative
+//      edge test shows the triangle misses; each bin entry carries the
+//      triangle index and the rows / columns of its tile that lie inside the
+//      triangle's bounding box;
+//   5. group-per-tile raster (8 lanes per 8x4 tile, 16 per 8x8 tile), tiles
+//      fetched dynamically in groups ordered by entry count; each lane tests 4
+//      pixels of a row against every entry of its tile's bin; nearest 1/Z
+//      wins, ties to the lower triangle index (a strict compare, and a
+//      second walk of the rare tile where equal depths met); (colour -
+//      target)^2 per tile; tiles with an empty bin take the precomputed sum
+//      of target^2;
 //   6. per-tile losses summed in tile order, warp shuffle + block reduction to
 //      one FP32 loss per perturbation.
 // The FP32 sequences of steps 2-5 define the renderer (coverage and depth
@@ -36,7 +37,7 @@ namespace {
 
 constexpr int kThreads = 1024;
 constexpr int kWarps = kThreads / 32;
-constexpr int kTile = 8;
+constexpr int kTW = 8;              // tile width; tiles are 8 x 4 or 8 x 8 pixels
 constexpr int kEntryCapMax = 16384;  // bin entries per render (less where shared memory is short)
 constexpr int kEntryCapMin = 2048;
 constexpr int kStaticSmem = 1024;    // the kernel's static shared memory, rounded up
@@ -52,15 +53,15 @@ struct __align__(16) TriRec {
 };
 
 // bin entry: triangle << 16 | (tile rows inside the bounding box) << 8 |
-// (tile columns inside it); sorting entries sorts their triangles
+// (tile columns inside it)
 __device__ __forceinline__ uint32_t entry_word(int tri, uint32_t rows, uint32_t cols) {
     return ((uint32_t)tri << 16) | (rows << 8) | cols;
 }
 // bits lo..hi (clamped to 0..7) of a byte
 __device__ __forceinline__ uint32_t span_bits(int lo, int hi) {
     lo = max(lo, 0);
-    hi = min(hi, kTile - 1);
-    return lo > hi ? 0u : ((0xFFu >> (kTile - 1 - hi)) & (0xFFu << lo));
+    hi = min(hi, 7);
+    return lo > hi ? 0u : ((0xFFu >> (7 - hi)) & (0xFFu << lo));
 }
 __device__ __forceinline__ float tl_threshold(float A, float B) {
     return (A > 0.0f || (A == 0.0f && B > 0.0f)) ? -0x1p-149f : 0.0f;
@@ -75,6 +76,7 @@ struct RvArgs {
     int nv, nt, W, H, TX, TY, T;
     int cap;             // bin entry capacity
     int vreg;            // floats in the vertex region
+    int th;              // tile height (the kernel's template argument)
     uint64_t tx_recip;   // ceil(2^32 / TX): t / TX = (t tx_recip) >> 32 exactly for t, TX < 2^16
     unsigned long long* stats;   // [0]: renders whose bins overflowed (diagnostics)
     float alb0, alb1, alb2, l0, l1, l2, eye_dist, scale;
@@ -95,10 +97,11 @@ __device__ __forceinline__ bool pixel_range(float mn, float mx, int N, int& lo, 
 // a bound on its term magnitudes anywhere in the image; the FP32 errors of
 // the exact per-pixel test and of this test are below 3e-7 of that
 // magnitude, so no rejected tile holds a covered pixel.
+template <int kTH>
 __device__ __forceinline__ bool tile_hits(const float A[3], const float B[3], const float C[3], uint2 bb,
                                           const float neg[3], int tx, int ty) {
-    const int x0 = max(tx * kTile, (int)(bb.x & 0xffffu)), x1 = min(tx * kTile + kTile - 1, (int)(bb.x >> 16));
-    const int y0 = max(ty * kTile, (int)(bb.y & 0xffffu)), y1 = min(ty * kTile + kTile - 1, (int)(bb.y >> 16));
+    const int x0 = max(tx * kTW, (int)(bb.x & 0xffffu)), x1 = min(tx * kTW + kTW - 1, (int)(bb.x >> 16));
+    const int y0 = max(ty * kTH, (int)(bb.y & 0xffffu)), y1 = min(ty * kTH + kTH - 1, (int)(bb.y >> 16));
     const float fx0 = (float)x0 + 0.5f, fx1 = (float)x1 + 0.5f, fy0 = (float)y0 + 0.5f, fy1 = (float)y1 + 0.5f;
     bool hit = true;
 #pragma unroll
@@ -109,34 +112,14 @@ __device__ __forceinline__ bool tile_hits(const float A[3], const float B[3], co
     return hit;
 }
 
-// Batcher's odd-even merge sort of 16 values held in registers: the 63
-// compare-exchanges of the network, in its stage order
-__device__ __forceinline__ void sort16(uint32_t v[16]) {
-#define X(a, b)                                   \
-    do {                                          \
-        const uint32_t lo_ = min(v[a], v[b]);     \
-        v[b] = max(v[a], v[b]);                   \
-        v[a] = lo_;                               \
-    } while (0)
-    X(0, 1); X(2, 3); X(4, 5); X(6, 7); X(8, 9); X(10, 11); X(12, 13); X(14, 15);
-    X(0, 2); X(1, 3); X(4, 6); X(5, 7); X(8, 10); X(9, 11); X(12, 14); X(13, 15);
-    X(1, 2); X(5, 6); X(9, 10); X(13, 14); X(0, 4); X(1, 5); X(2, 6); X(3, 7);
-    X(8, 12); X(9, 13); X(10, 14); X(11, 15); X(2, 4); X(3, 5); X(10, 12); X(11, 13);
-    X(1, 2); X(3, 4); X(5, 6); X(9, 10); X(11, 12); X(13, 14); X(0, 8); X(1, 9);
-    X(2, 10); X(3, 11); X(4, 12); X(5, 13); X(6, 14); X(7, 15); X(4, 8); X(5, 9);
-    X(6, 10); X(7, 11); X(2, 4); X(3, 5); X(6, 8); X(7, 9); X(10, 12); X(11, 13);
-    X(1, 2); X(3, 4); X(5, 6); X(7, 8); X(9, 10); X(11, 12); X(13, 14);
-#undef X
-}
-
 constexpr int kCountClasses = 32;   // tiles ordered by entry count, counts >= 31 share a class
 
 // Exclusive scan of cnt[0..T) into off[0..T) and, in the same barriers, the
 // list of tiles with entries (olist[0..n_obj)) ordered by entry count,
 // largest first (a counting sort over count classes; the order within a
 // class is arbitrary, which only affects which warp takes which tile).  The
-// raster fetches tiles in pairs, one per half-warp, so pairs of nearly equal
-// counts waste few iterations, and the long tiles go first.  hist
+// raster fetches the tiles of a warp together, one per lane group, so groups
+// of nearly equal counts waste few iterations, and the long tiles go first.  hist
 // [kCountClasses] must be zero on entry.  Returns the total entry count (all
 // threads) and sets n_obj.
 __device__ int bin_scan(const int* cnt, int* off, uint16_t* olist, int T, int* warp_tot, int* hist, int* n_obj) {
@@ -220,23 +203,25 @@ __device__ __forceinline__ bool setup_triangle(const RvArgs& P, int t, const flo
     return true;
 }
 
-template <bool kImage>
+template <int kTH, bool kImage>
 __global__ void __launch_bounds__(kThreads, 1)
 revolve_kernel(RvArgs P, RenderBatch b, const float* __restrict__ img_params, float* __restrict__ img) {
+    constexpr int kG = 2 * kTH;          // lanes per tile: kTH rows x 2 four-pixel strips
+    constexpr int kPer = 32 / kG;        // tiles per warp
     extern __shared__ __align__(16) unsigned char smem[];
     TriRec* rec = reinterpret_cast<TriRec*>(smem);                // [nt] by triangle
     uint2* bbx = reinterpret_cast<uint2*>(rec + P.nt);           // [nt] pixel bounding box by triangle
-    float* tshade = reinterpret_cast<float*>(bbx + P.nt);        // [nt] flat shade by triangle
-    float* vx = tshade + P.nt;                                   // vertex region, P.vreg floats
+    float* vx = reinterpret_cast<float*>(bbx + P.nt);            // vertex region, P.vreg floats (8 B aligned)
     float* vy = vx + P.nv;
     float* viz = vy + P.nv;
-    int* tcnt = reinterpret_cast<int*>(vx + P.vreg);
+    float* tshade = vx + P.vreg;                                 // [nt] flat shade by triangle
+    int* tcnt = reinterpret_cast<int*>(tshade + P.nt);
     int* toff = tcnt + P.T;
     uint16_t* surv = reinterpret_cast<uint16_t*>(toff + P.T);   // [nt] surviving triangles (any order)
     uint32_t* ent = reinterpret_cast<uint32_t*>(surv + ((P.nt + 1) & ~1));   // [cap] bin entries
     // after the triangle setup the vertex region holds the count pass's tile
-    // masks [nt] (by survivor) and the list of tiles with entries [T]
-    uint32_t* tmask = reinterpret_cast<uint32_t*>(vx);
+    // masks [nt] (64-bit, by survivor) and the list of tiles with entries [T]
+    unsigned long long* tmask = reinterpret_cast<unsigned long long*>(vx);
     uint16_t* olist = reinterpret_cast<uint16_t*>(tmask + P.nt);
 
     __shared__ float s_cs[4], s_cs_next[4];
@@ -291,10 +276,10 @@ revolve_kernel(RvArgs P, RenderBatch b, const float* __restrict__ img_params, fl
         }
         __syncthreads();
         // ---- 3. triangle setup ------------------------------------------------
-        // records stay at their triangle's index (bin entries sorted by index
-        // are in triangle order); the survivors are listed for the binning,
-        // and a clipped, culled or off-image triangle gets an empty bounding
-        // box (lo > hi), which the all-triangles fallback of the raster skips
+        // records stay at their triangle's index (bin entries carry it for the
+        // tie rule); the survivors are listed for the binning, and a clipped,
+        // culled or off-image triangle gets an empty bounding box (lo > hi),
+        // which the all-triangles fallback of the raster skips
         for (int t = tid; t < P.nt; t += kThreads) {
             TriRec r;
             uint2 bb;
@@ -312,29 +297,29 @@ revolve_kernel(RvArgs P, RenderBatch b, const float* __restrict__ img_params, fl
         // ---- 4. binning -----------------------------------------------------
         // count pass: each survivor's tiles that pass the conservative edge
         // test go into a bit mask (row-major over its tile rectangle;
-        // rectangles of more than 32 tiles skip the test), reused by the fill
+        // rectangles of more than 64 tiles skip the test), reused by the fill
         for (int k = tid; k < count; k += kThreads) {
             const int s = surv[k];
             const uint2 bb = bbx[s];
             const float4* rp = reinterpret_cast<const float4*>(&rec[s]);
             const float4 q0 = rp[0], q1 = rp[1], q2 = rp[2];
             const float A[3] = {q0.x, q1.x, q2.x}, B[3] = {q0.y, q1.y, q2.y}, C[3] = {q0.z, q1.z, q2.z};
-            const int tx0 = (int)(bb.x & 0xffffu) / kTile, tx1 = (int)(bb.x >> 16) / kTile;
-            const int ty0 = (int)(bb.y & 0xffffu) / kTile, ty1 = (int)(bb.y >> 16) / kTile;
-            const bool test = (tx1 - tx0 + 1) * (ty1 - ty0 + 1) <= 32;
+            const int tx0 = (int)(bb.x & 0xffffu) / kTW, tx1 = (int)(bb.x >> 16) / kTW;
+            const int ty0 = (int)(bb.y & 0xffffu) / kTH, ty1 = (int)(bb.y >> 16) / kTH;
+            const bool test = (tx1 - tx0 + 1) * (ty1 - ty0 + 1) <= 64;
             const float fW = (float)P.W, fH = (float)P.H;
             float neg[3];
 #pragma unroll
             for (int i = 0; i < 3; ++i) neg[i] = -1e-5f * fmaf(fabsf(A[i]), fW, fmaf(fabsf(B[i]), fH, fabsf(C[i])));
-            uint32_t mask = 0;
+            unsigned long long mask = 0ull;
             int bit = 0;
             for (int ty = ty0; ty <= ty1; ++ty)
                 for (int tx = tx0; tx <= tx1; ++tx, ++bit)
-                    if (!test || tile_hits(A, B, C, bb, neg, tx, ty)) {
+                    if (!test || tile_hits<kTH>(A, B, C, bb, neg, tx, ty)) {
                         atomicAdd(&tcnt[ty * P.TX + tx], 1);
-                        if (test) mask |= 1u << bit;
+                        if (test) mask |= 1ull << bit;
                     }
-            tmask[k] = test ? mask : 0xFFFFFFFFu;
+            tmask[k] = test ? mask : ~0ull;
         }
         __syncthreads();
         int n_obj = 0;
@@ -347,60 +332,35 @@ revolve_kernel(RvArgs P, RenderBatch b, const float* __restrict__ img_params, fl
             for (int k = tid; k < count; k += kThreads) {
                 const int s = surv[k];
                 const uint2 bb = bbx[s];
-                const uint32_t mask = tmask[k];
+                const unsigned long long mask = tmask[k];
                 const int xlo = (int)(bb.x & 0xffffu), xhi = (int)(bb.x >> 16);
                 const int ylo = (int)(bb.y & 0xffffu), yhi = (int)(bb.y >> 16);
-                const int tx0 = xlo / kTile, tx1 = xhi / kTile, ty0 = ylo / kTile, ty1 = yhi / kTile;
+                const int tx0 = xlo / kTW, tx1 = xhi / kTW, ty0 = ylo / kTH, ty1 = yhi / kTH;
                 int bit = 0;
                 for (int ty = ty0; ty <= ty1; ++ty) {
-                    const uint32_t rows = span_bits(ylo - ty * kTile, yhi - ty * kTile);
+                    // rows of this tile inside the box (bits >= kTH are never tested)
+                    const uint32_t rows = span_bits(ylo - ty * kTH, yhi - ty * kTH);
                     for (int tx = tx0; tx <= tx1; ++tx, ++bit) {
-                        if (mask != 0xFFFFFFFFu && !((mask >> bit) & 1u)) continue;
+                        if (mask != ~0ull && !((mask >> bit) & 1ull)) continue;
                         const int tile = ty * P.TX + tx;
                         const int pos = atomicAdd(&tcnt[tile], 1);
-                        ent[toff[tile] + pos] = entry_word(s, rows, span_bits(xlo - tx * kTile, xhi - tx * kTile));
-                    }
-                }
-            }
-            __syncthreads();
-            // each bin in triangle order: a sorting network in registers for
-            // bins of up to 16 entries, insertion sort beyond
-            for (int t = tid; t < P.T; t += kThreads) {
-                const int n = tcnt[t];
-                if (n < 2) continue;
-                uint32_t* e = ent + toff[t];
-                if (n <= 16) {
-                    uint32_t v[16];
-#pragma unroll
-                    for (int i = 0; i < 16; ++i) v[i] = i < n ? e[i] : 0xFFFFFFFFu;
-                    sort16(v);
-#pragma unroll
-                    for (int i = 0; i < 16; ++i)
-                        if (i < n) e[i] = v[i];
-                } else {
-                    for (int i = 1; i < n; ++i) {
-                        const uint32_t v = e[i];
-                        int j = i - 1;
-                        while (j >= 0 && e[j] > v) { e[j + 1] = e[j]; --j; }
-                        e[j + 1] = v;
+                        ent[toff[tile] + pos] = entry_word(s, rows, span_bits(xlo - tx * kTW, xhi - tx * kTW));
                     }
                 }
             }
         }
         __syncthreads();
         // ---- 5. raster + loss ------------------------------------------------
-        // Warps fetch tiles dynamically in pairs from the count-ordered list,
-        // one tile per half-warp; each tile's loss goes to its own slot (the
-        // fill cursor array is free again) and the slots are summed in tile
-        // order below, so the loss does not depend on which warp took which
-        // tile.  Lane (row ry, half-row hx) of a half owns the 4 pixels
-        // (x0 .. x0 + 3, y) of its tile and walks the tile's whole bin in
-        // triangle order: the row term fma(B, y + 1/2, C) of each edge and of
-        // the depth plane is formed once per entry and shared by the 4
-        // pixels, and the strict depth compare keeps the lower triangle index
-        // on ties.
-        const int half = lane >> 4, hl = lane & 15;
-        const int ry = hl >> 1, hx = hl & 1;
+        // Warps fetch tiles dynamically, kPer at a time, from the
+        // count-ordered list, one tile per group of kG lanes; each tile's loss
+        // goes to its own slot (the fill cursor array is free again) and the
+        // slots are summed in tile order below, so the loss does not depend on
+        // which warp took which tile.  Lane (row ry, half-row hx) of a group
+        // owns the 4 pixels (x0 .. x0 + 3, y) of its tile and walks the tile's
+        // whole bin: the row term fma(B, y + 1/2, C) of each edge and of the
+        // depth plane is formed once per entry and shared by the 4 pixels.
+        const int grp = lane / kG, gl = lane % kG;
+        const int ry = gl >> 1, hx = gl & 1;
         // the FP64 cos / sin of this CTA's next perturbation, off the critical
         // path: one warp computes them before it joins the tile loop
         if (!kImage && warp == kWarps - 1 && lane < 4) {
@@ -418,13 +378,13 @@ revolve_kernel(RvArgs P, RenderBatch b, const float* __restrict__ img_params, fl
         const uint32_t row_bit = 1u << (8 + ry);
         const int col_shift = 4 * hx;
         const bool vec_target = (P.W & 3) == 0;
-        // each warp reserves its next pair of tiles when it starts the current
-        // one, so the shared atomic's latency overlaps the tiles' work
+        // each warp reserves its next tiles when it starts the current ones,
+        // so the shared atomic's latency overlaps the tiles' work
         int t_next = 0;
-        if (lane == 0) t_next = atomicAdd(&s_tile, 2);
+        if (lane == 0) t_next = atomicAdd(&s_tile, kPer);
         for (int it = __shfl_sync(0xffffffffu, t_next, 0); it < n_iter; it = __shfl_sync(0xffffffffu, t_next, 0)) {
-            if (lane == 0) t_next = atomicAdd(&s_tile, 2);
-            const int my = it + half;
+            if (lane == 0) t_next = atomicAdd(&s_tile, kPer);
+            const int my = it + grp;
             const bool has_tile = my < n_iter;
             const int t = !has_tile ? 0 : (all_tiles ? my : (int)olist[my]);
             const int beg = has_tile && !overflow ? toff[t] : 0;
@@ -432,7 +392,7 @@ revolve_kernel(RvArgs P, RenderBatch b, const float* __restrict__ img_params, fl
             // division by multiplication with the rounded-up reciprocal
             // (Granlund and Montgomery, PLDI 1994): exact for t, TX < 2^16
             const int ty = (int)(((uint64_t)(uint32_t)t * P.tx_recip) >> 32), tx = t - ty * P.TX;
-            const int x0 = tx * kTile + 4 * hx, y = ty * kTile + ry;
+            const int x0 = tx * kTW + 4 * hx, y = ty * kTH + ry;
             const float fy = __fadd_rn((float)y, 0.5f);
             float fx[4], bw[4];
             int bs[4];
@@ -442,8 +402,17 @@ revolve_kernel(RvArgs P, RenderBatch b, const float* __restrict__ img_params, fl
                 bw[c] = -INFINITY;
                 bs[c] = INT_MAX;
             }
-            // one bin entry against this lane's 4 pixels
-            auto raster_entry = [&](int s, uint32_t nib) {
+            // One bin entry against this lane's 4 pixels.  Bins are in fill
+            // (arbitrary) order, so the strict depth compare alone would give
+            // an exact depth tie to whichever triangle came first; every time
+            // a depth equals the pixel's current best (covered or not: one
+            // compare instead of two, at the price of re-walking about 4 % of
+            // the tile groups, where adjacent triangles' depth planes agree to
+            // the last bit) the lane notes it, and a tile group where any lane
+            // did is walked again with the full rule (larger 1/Z, lower index
+            // on equal 1/Z).
+            bool tie = false;
+            auto raster_entry = [&](int s, uint32_t nib, bool exact) {
                 const float4* rp = reinterpret_cast<const float4*>(&rec[s]);
                 const float4 q0 = rp[0], q1 = rp[1], q2 = rp[2], q3 = rp[3];
                 const float r0 = __fmaf_rn(q0.y, fy, q0.z);
@@ -456,32 +425,52 @@ revolve_kernel(RvArgs P, RenderBatch b, const float* __restrict__ img_params, fl
                     const float E1 = __fmaf_rn(q1.x, fx[c], r1);
                     const float E2 = __fmaf_rn(q2.x, fx[c], r2);
                     const float wz = __fmaf_rn(q3.x, fx[c], rw);
-                    const bool better =
-                        ((nib >> c) & 1u) && (E0 > q0.w) && (E1 > q1.w) && (E2 > q2.w) && (wz > bw[c]);
+                    const bool in = ((nib >> c) & 1u) && (E0 > q0.w) && (E1 > q1.w) && (E2 > q2.w);
+                    bool better;
+                    if (exact) {
+                        better = in && (wz > bw[c] || (wz == bw[c] && s < bs[c]));
+                    } else {
+                        better = in && (wz > bw[c]);
+                        tie = tie || (wz == bw[c]);
+                    }
                     bw[c] = better ? wz : bw[c];
                     bs[c] = better ? s : bs[c];
                 }
             };
             if (!overflow) {
-                const int n_max = max(n_mine, __shfl_xor_sync(0xffffffffu, n_mine, 16));
+                const int n_max = (int)__reduce_max_sync(0xffffffffu, (unsigned)n_mine);
                 for (int k = 0; k < n_max; ++k) {
                     if (k < n_mine) {
                         const uint32_t e = ent[beg + k];
                         // this lane's 4 columns inside the bounding box (none if its row is not)
-                        raster_entry((int)(e >> 16), (e & row_bit) ? (e >> col_shift) & 0xFu : 0u);
+                        raster_entry((int)(e >> 16), (e & row_bit) ? (e >> col_shift) & 0xFu : 0u, false);
+                    }
+                }
+                if (__any_sync(0xffffffffu, tie)) {
+#pragma unroll
+                    for (int c = 0; c < 4; ++c) {
+                        bw[c] = -INFINITY;
+                        bs[c] = INT_MAX;
+                    }
+                    for (int k = 0; k < n_max; ++k) {
+                        if (k < n_mine) {
+                            const uint32_t e = ent[beg + k];
+                            raster_entry((int)(e >> 16), (e & row_bit) ? (e >> col_shift) & 0xFu : 0u, true);
+                        }
                     }
                 }
             } else {
-                // every triangle in index order (culled ones have an empty box)
+                // every triangle in index order (culled ones have an empty
+                // box), so the strict compare already keeps the lower index
                 for (int s = 0; s < P.nt; ++s) {
                     const uint2 bb = bbx[s];
                     const int xlo = (int)(bb.x & 0xffffu), xhi = (int)(bb.x >> 16);
                     const int ylo = (int)(bb.y & 0xffffu), yhi = (int)(bb.y >> 16);
                     if (has_tile && xlo <= xhi && y >= ylo && y <= yhi)
-                        raster_entry(s, (span_bits(xlo - tx * kTile, xhi - tx * kTile) >> col_shift) & 0xFu);
+                        raster_entry(s, (span_bits(xlo - tx * kTW, xhi - tx * kTW) >> col_shift) & 0xFu, false);
                 }
             }
-            // (both halves run the shuffles below, a half without a tile too)
+            // (every group runs the shuffles below, a group without a tile too)
             float sh[4];
 #pragma unroll
             for (int c = 0; c < 4; ++c) sh[c] = bs[c] != INT_MAX ? tshade[bs[c]] : 0.0f;
@@ -516,10 +505,10 @@ revolve_kernel(RvArgs P, RenderBatch b, const float* __restrict__ img_params, fl
                         const float d2 = sh[c] * P.alb2 - tg[3 * c + 2];
                         acc += d0 * d0 + d1 * d1 + d2 * d2;
                     }
-                // sum over the half's 16 lanes
+                // sum over the group's kG lanes
 #pragma unroll
-                for (int o = 8; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
-                if (hl == 0 && has_tile) tile_loss[t] = acc;
+                for (int o = kG / 2; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
+                if (gl == 0 && has_tile) tile_loss[t] = acc;
             }
         }
         // ---- 6. reduction -----------------------------------------------------
@@ -560,14 +549,14 @@ __global__ void normals_kernel(const float* verts, const int32_t* tris, int nt, 
     tnrm[3 * t + 2] = (float)(n2 * inv);
 }
 
-__global__ void tile_t2_kernel(const float* target, int W, int H, int TX, int T, float* out) {
+__global__ void tile_t2_kernel(const float* target, int W, int H, int TX, int TH, int T, float* out) {
     const int t = blockIdx.x * blockDim.x + threadIdx.x;
     if (t >= T) return;
     const int ty = t / TX, tx = t - ty * TX;
     float s = 0.0f;
-    for (int yy = 0; yy < kTile; ++yy)
-        for (int xx = 0; xx < kTile; ++xx) {
-            const int x = tx * kTile + xx, y = ty * kTile + yy;
+    for (int yy = 0; yy < TH; ++yy)
+        for (int xx = 0; xx < kTW; ++xx) {
+            const int x = tx * kTW + xx, y = ty * TH + yy;
             if (x >= W || y >= H) continue;
             const size_t p = (size_t)y * W + x;
             for (int c = 0; c < 3; ++c) s += target[3 * p + c] * target[3 * p + c];
@@ -579,7 +568,8 @@ RvArgs make_args(const DevScene& sc) {
     RvArgs a;
     a.verts = sc.verts; a.tris = sc.tris; a.tnrm = sc.tnrm; a.target = sc.target; a.tile_t2 = sc.tile_t2;
     a.nv = sc.nv; a.nt = sc.nt; a.W = sc.W; a.H = sc.H;
-    a.TX = (sc.W + kTile - 1) / kTile; a.TY = (sc.H + kTile - 1) / kTile; a.T = a.TX * a.TY;
+    a.th = sc.rv_th;
+    a.TX = (sc.W + kTW - 1) / kTW; a.TY = (sc.H + sc.rv_th - 1) / sc.rv_th; a.T = a.TX * a.TY;
     a.tx_recip = ((uint64_t(1) << 32) + (uint64_t)a.TX - 1) / (uint64_t)a.TX;
     a.alb0 = sc.albedo[0]; a.alb1 = sc.albedo[1]; a.alb2 = sc.albedo[2];
     a.l0 = sc.light[0]; a.l1 = sc.light[1]; a.l2 = sc.light[2];
@@ -589,17 +579,10 @@ RvArgs make_args(const DevScene& sc) {
     return a;
 }
 
-}  // namespace
-
-// Shared-memory layout of one render: records (64 B), bounding boxes (8 B)
-// and shades (4 B) by triangle, the vertex region (the projected vertices,
-// later the tile masks and the list of tiles with entries), tile counts and
-// offsets, the survivor list (2 B per triangle), and the bin entries in what
-// remains of max_smem (at most kEntryCapMax).  False when fewer than
-// kEntryCapMin entries fit.
-bool revolve_layout(int nv, int nt, int W, int H, int max_smem, size_t* bytes, int* cap, int* vreg) {
-    const int T = ((W + kTile - 1) / kTile) * ((H + kTile - 1) / kTile);
-    const int vr = 3 * nv > nt + (T + 1) / 2 ? 3 * nv : nt + (T + 1) / 2;
+// bytes and entry capacity of one render's layout with tile height th
+bool layout_for(int nv, int nt, int W, int H, int th, int max_smem, size_t* bytes, int* cap, int* vreg) {
+    const int T = ((W + kTW - 1) / kTW) * ((H + th - 1) / th);
+    const int vr = 3 * nv > 2 * nt + (T + 1) / 2 ? 3 * nv : 2 * nt + (T + 1) / 2;
     const size_t fixed = (sizeof(TriRec) + sizeof(uint2) + sizeof(float)) * (size_t)nt +
                          sizeof(float) * (size_t)vr + 2 * sizeof(int) * (size_t)T +
                          sizeof(uint16_t) * (size_t)((nt + 1) & ~1);
@@ -612,27 +595,65 @@ bool revolve_layout(int nv, int nt, int W, int H, int max_smem, size_t* bytes, i
     return true;
 }
 
+}  // namespace
+
+// Shared-memory layout of one render: records (64 B) and bounding boxes (8 B)
+// by triangle, the vertex region (the projected vertices, later the 64-bit
+// tile masks and the list of tiles with entries), shades (4 B) by triangle,
+// tile counts and offsets, the survivor list (2 B per triangle), and the bin
+// entries in what remains of max_smem (at most kEntryCapMax).  8x4 tiles
+// when that leaves room for 8,192 entries, else 8x8 tiles; false when fewer
+// than kEntryCapMin entries fit either way.  The tile height is a function of
+// the scene's sizes only, so every render of a scene sums its loss in the
+// same order.
+bool revolve_layout(DevScene& sc, int max_smem) {
+    size_t bytes = 0;
+    int cap = 0, vreg = 0;
+    if (layout_for(sc.nv, sc.nt, sc.W, sc.H, 4, max_smem, &bytes, &cap, &vreg) && cap >= 8192) {
+        sc.rv_th = 4;
+    } else if (layout_for(sc.nv, sc.nt, sc.W, sc.H, 8, max_smem, &bytes, &cap, &vreg)) {
+        sc.rv_th = 8;
+    } else {
+        return false;
+    }
+    sc.rv_smem = bytes;
+    sc.rv_cap = cap;
+    sc.rv_vreg = vreg;
+    return true;
+}
+
 void revolve_prepare(DevScene& sc, cudaStream_t s) {
     normals_kernel<<<(sc.nt + 255) / 256, 256, 0, s>>>(sc.verts, sc.tris, sc.nt, sc.tnrm);
-    cudaFuncSetAttribute(revolve_kernel<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sc.rv_smem);
-    cudaFuncSetAttribute(revolve_kernel<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sc.rv_smem);
+    const int bytes = (int)sc.rv_smem;
+    cudaFuncSetAttribute(revolve_kernel<4, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
+    cudaFuncSetAttribute(revolve_kernel<4, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
+    cudaFuncSetAttribute(revolve_kernel<8, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
+    cudaFuncSetAttribute(revolve_kernel<8, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
 }
 
 void revolve_tile_t2(DevScene& sc, cudaStream_t s) {
-    const int TX = (sc.W + kTile - 1) / kTile, TY = (sc.H + kTile - 1) / kTile;
-    tile_t2_kernel<<<(TX * TY + 127) / 128, 128, 0, s>>>(sc.target, sc.W, sc.H, TX, TX * TY, sc.tile_t2);
+    const int TX = (sc.W + kTW - 1) / kTW, TY = (sc.H + sc.rv_th - 1) / sc.rv_th;
+    tile_t2_kernel<<<(TX * TY + 127) / 128, 128, 0, s>>>(sc.target, sc.W, sc.H, TX, sc.rv_th, TX * TY, sc.tile_t2);
 }
 
-int revolve_tiles(int W, int H) { return ((W + kTile - 1) / kTile) * ((H + kTile - 1) / kTile); }
+int revolve_tiles(const DevScene& sc) {
+    return ((sc.W + kTW - 1) / kTW) * ((sc.H + sc.rv_th - 1) / sc.rv_th);
+}
 
 void launch_revolve_loss(const DevScene& sc, const RenderBatch& b, cudaStream_t s) {
     const int grid = b.M < num_sms() ? b.M : num_sms();
-    revolve_kernel<false><<<grid, kThreads, sc.rv_smem, s>>>(make_args(sc), b, nullptr, nullptr);
+    if (sc.rv_th == 4)
+        revolve_kernel<4, false><<<grid, kThreads, sc.rv_smem, s>>>(make_args(sc), b, nullptr, nullptr);
+    else
+        revolve_kernel<8, false><<<grid, kThreads, sc.rv_smem, s>>>(make_args(sc), b, nullptr, nullptr);
 }
 
 void launch_revolve_image(const DevScene& sc, const float* params, float* img, cudaStream_t s) {
     RenderBatch b{};
-    revolve_kernel<true><<<1, kThreads, sc.rv_smem, s>>>(make_args(sc), b, params, img);
+    if (sc.rv_th == 4)
+        revolve_kernel<4, true><<<1, kThreads, sc.rv_smem, s>>>(make_args(sc), b, params, img);
+    else
+        revolve_kernel<8, true><<<1, kThreads, sc.rv_smem, s>>>(make_args(sc), b, params, img);
 }
 
 }  // namespace hr

@@ -399,6 +399,13 @@ hr_status hr_ncg_trace(hr_ncg st, double* h_g, double* h_d, double* h_Hd);
 hr_status hr_render(hr_scene scene, const double* h_params, uint64_t seed, uint32_t request, uint32_t sub,
                     uint32_t k, uint32_t tag, int32_t spp, float* h_img);
 
+/* Mesh scenes (REVOLVE3D) only: the index of the triangle each pixel shows
+ * at h_params [2] (rounded to FP32) into h_ids [H][W] (host), -1 for the
+ * background: the rasteriser's coverage and depth decisions (largest 1/Z,
+ * lower index on equal 1/Z) without shading, for exact comparison with
+ * another renderer.  HR_ERR_UNSUPPORTED for other kinds. */
+hr_status hr_render_ids(hr_scene scene, const double* h_params, int32_t* h_ids);
+
 /* ---------------------------------------------------------------------------
  * Serving with continuous batching.  A server owns one device arena of
  * hbm_budget bytes (allocated at creation) and a worker thread.  Submitted

@@ -80,6 +80,9 @@ def lib():
         L.or_boxes_loss.restype = ctypes.c_double
         L.or_revolve_loss.argtypes = [ctypes.POINTER(_RevolveScene), _f32p, _f32p, _f32p]
         L.or_revolve_loss.restype = ctypes.c_double
+        L.or_revolve_render.argtypes = [ctypes.POINTER(_RevolveScene), _f32p, _f32p, _f32p,
+                                        ctypes.POINTER(ctypes.c_int32)]
+        L.or_revolve_render.restype = ctypes.c_double
         L.or_tris2d_loss.argtypes = [ctypes.POINTER(_Tris2dScene), _f32p, _f32p, _f32p]
         L.or_tris2d_loss.restype = ctypes.c_double
         L.or_ptbox_render.argtypes = [ctypes.POINTER(_PtboxScene), _f32p, ctypes.c_int, ctypes.c_int,
@@ -271,6 +274,14 @@ class RevolveRenderer(Renderer):
     def loss(self, p, ctx=None):
         p = np.ascontiguousarray(p, np.float32)
         return lib().or_revolve_loss(ctypes.byref(self.s), _p(p, _f32p), _p(self.target, _f32p), None)
+
+    def ids(self, p):
+        """Index of the triangle each pixel shows (-1: background), [H*W]."""
+        out = np.zeros(self.W * self.H, np.int32)
+        p = np.ascontiguousarray(p, np.float32)
+        lib().or_revolve_render(ctypes.byref(self.s), _p(p, _f32p), None, None,
+                                out.ctypes.data_as(ctypes.POINTER(ctypes.c_int32)))
+        return out
 
 
 class Tris2dRenderer(Renderer):

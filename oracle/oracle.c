@@ -454,6 +454,13 @@ static float fmax3(float a, float b, float c) { float m = a > b ? a : b; return 
 /* ------------------------------------------------------------------------ */
 double or_revolve_loss(const or_revolve_scene* s, const float p[2], const float* target, float* img)
 {
+    return or_revolve_render(s, p, target, img, 0);
+}
+
+/* The mesh renderer; also writes, if ids is not NULL, the index of the
+ * triangle that each pixel shows (-1: background). */
+double or_revolve_render(const or_revolve_scene* s, const float p[2], const float* target, float* img, int* ids)
+{
     const int W = s->W, H = s->H, nv = s->nv, nt = s->nt;
     float ca = (float)cos((double)p[0]), sa = (float)sin((double)p[0]);
     float cb = (float)cos((double)p[1]), sb = (float)sin((double)p[1]);
@@ -547,6 +554,8 @@ double or_revolve_loss(const or_revolve_scene* s, const float p[2], const float*
             }
         }
     }
+    if (ids)
+        for (int i = 0; i < npx; ++i) ids[i] = best_t[i];
     free(sx); free(sy); free(iz); free(zc); free(best_w); free(best_t);
     return acc / ((double)npx * 3.0);
 }

@@ -80,6 +80,7 @@ typedef struct {
     float eye_dist, scale;
 } or_revolve_scene;
 double or_revolve_loss(const or_revolve_scene* s, const float p[2], const float* target, float* img);
+double or_revolve_render(const or_revolve_scene* s, const float p[2], const float* target, float* img, int* ids);
 
 typedef struct {
     int W, H, n_tris, n_params;

@@ -20,7 +20,7 @@ void launch_disc_image(const DevScene&, const float*, float*, cudaStream_t);
 void launch_boxes_loss(const DevScene&, const RenderBatch&, cudaStream_t);
 void launch_boxes_image(const DevScene&, const float*, float*, cudaStream_t);
 void launch_revolve_loss(const DevScene&, const RenderBatch&, cudaStream_t);
-void launch_revolve_image(const DevScene&, const float*, float*, cudaStream_t);
+void launch_revolve_image(const DevScene&, const float*, float*, int32_t*, cudaStream_t);
 void launch_tris2d_loss(const DevScene&, const RenderBatch&, cudaStream_t);
 void launch_tris2d_image(const DevScene&, const float*, float*, cudaStream_t);
 void launch_ptbox_loss(const DevScene&, const RenderBatch&, cudaStream_t);
@@ -57,7 +57,7 @@ void launch_render_image(const DevScene& sc, const float* d_params, uint64_t see
                          uint32_t k, uint32_t tag, int spp, float* d_img, cudaStream_t s) {
     switch (sc.kind) {
         case HR_SCENE_DISC2D: launch_disc_image(sc, d_params, d_img, s); break;
-        case HR_SCENE_REVOLVE3D: launch_revolve_image(sc, d_params, d_img, s); break;
+        case HR_SCENE_REVOLVE3D: launch_revolve_image(sc, d_params, d_img, nullptr, s); break;
         case HR_SCENE_TRIS2D: launch_tris2d_image(sc, d_params, d_img, s); break;
         case HR_SCENE_PTBOX: launch_ptbox_image(sc, d_params, seed, request, sub, k, tag, spp, d_img, s); break;
         case HR_SCENE_BOXES2D: launch_boxes_image(sc, d_params, d_img, s); break;
@@ -672,6 +672,28 @@ hr_status hr_estimate_hvp_fd(hr_scene s, const double* h_theta, const double* h_
     hr_status st = validate_opts(s, HR_GRAD, o);
     if (st != HR_OK) return st;
     return run_hvp_fd(s, h_theta, h_v, eps, o, h_out);
+}
+
+hr_status hr_render_ids(hr_scene s, const double* h_params, int32_t* h_ids) {
+    clear_error();
+    if (!s || !h_params || !h_ids) return fail(HR_ERR_INVALID_ARG, "NULL argument");
+    std::lock_guard<std::mutex> lk(s->mu);
+    DevScene& sc = s->sc;
+    if (sc.kind != HR_SCENE_REVOLVE3D) return fail(HR_ERR_UNSUPPORTED, "triangle indices exist for mesh scenes only");
+    const size_t npx = (size_t)sc.W * sc.H;
+    float p32[2] = {(float)h_params[0], (float)h_params[1]};
+    if (s->ws.render_img.reserve(sizeof(int32_t) * npx) != cudaSuccess ||
+        s->ws.render_params.reserve(sizeof(p32)) != cudaSuccess)
+        return fail(HR_ERR_OOM, "render buffers");
+    cudaError_t e = cudaMemcpy(s->ws.render_params.ptr, p32, sizeof(p32), cudaMemcpyHostToDevice);
+    if (e != cudaSuccess) return fail(HR_ERR_CUDA, "params: %s", cudaGetErrorString(e));
+    launch_revolve_image(sc, (const float*)s->ws.render_params.ptr, nullptr, (int32_t*)s->ws.render_img.ptr, s->stream);
+    if ((e = cudaGetLastError()) != cudaSuccess) return fail(HR_ERR_CUDA, "render: %s", cudaGetErrorString(e));
+    if ((e = cudaMemcpyAsync(h_ids, s->ws.render_img.ptr, sizeof(int32_t) * npx, cudaMemcpyDeviceToHost, s->stream)) !=
+            cudaSuccess ||
+        (e = cudaStreamSynchronize(s->stream)) != cudaSuccess)
+        return fail(HR_ERR_CUDA, "render: %s", cudaGetErrorString(e));
+    return HR_OK;
 }
 
 hr_status hr_render(hr_scene s, const double* h_params, uint64_t seed, uint32_t request, uint32_t sub, uint32_t k,

@@ -205,7 +205,8 @@ __device__ __forceinline__ bool setup_triangle(const RvArgs& P, int t, const flo
 
 template <int kTH, bool kImage>
 __global__ void __launch_bounds__(kThreads, 1)
-revolve_kernel(RvArgs P, RenderBatch b, const float* __restrict__ img_params, float* __restrict__ img) {
+revolve_kernel(RvArgs P, RenderBatch b, const float* __restrict__ img_params, float* __restrict__ img,
+               int32_t* __restrict__ ids) {
     constexpr int kG = 2 * kTH;          // lanes per tile: kTH rows x 2 four-pixel strips
     constexpr int kPer = 32 / kG;        // tiles per warp
     extern __shared__ __align__(16) unsigned char smem[];
@@ -479,8 +480,12 @@ revolve_kernel(RvArgs P, RenderBatch b, const float* __restrict__ img_params, fl
 #pragma unroll
                 for (int c = 0; c < 4; ++c)
                     if (rowv && x0 + c < P.W) {
-                        const size_t p = 3 * ((size_t)y * P.W + x0 + c);
-                        img[p] = sh[c] * P.alb0; img[p + 1] = sh[c] * P.alb1; img[p + 2] = sh[c] * P.alb2;
+                        const size_t q = (size_t)y * P.W + x0 + c;
+                        if (ids) {
+                            ids[q] = bs[c] != INT_MAX ? bs[c] : -1;
+                        } else {
+                            img[3 * q] = sh[c] * P.alb0; img[3 * q + 1] = sh[c] * P.alb1; img[3 * q + 2] = sh[c] * P.alb2;
+                        }
                     }
             } else {
                 float tg[12];
@@ -643,17 +648,19 @@ int revolve_tiles(const DevScene& sc) {
 void launch_revolve_loss(const DevScene& sc, const RenderBatch& b, cudaStream_t s) {
     const int grid = b.M < num_sms() ? b.M : num_sms();
     if (sc.rv_th == 4)
-        revolve_kernel<4, false><<<grid, kThreads, sc.rv_smem, s>>>(make_args(sc), b, nullptr, nullptr);
+        revolve_kernel<4, false><<<grid, kThreads, sc.rv_smem, s>>>(make_args(sc), b, nullptr, nullptr, nullptr);
     else
-        revolve_kernel<8, false><<<grid, kThreads, sc.rv_smem, s>>>(make_args(sc), b, nullptr, nullptr);
+        revolve_kernel<8, false><<<grid, kThreads, sc.rv_smem, s>>>(make_args(sc), b, nullptr, nullptr, nullptr);
 }
 
-void launch_revolve_image(const DevScene& sc, const float* params, float* img, cudaStream_t s) {
+// one image at params: colours into img [H][W][3], or, with ids non-null,
+// the index of the triangle each pixel shows (-1: background) into ids [H][W]
+void launch_revolve_image(const DevScene& sc, const float* params, float* img, int32_t* ids, cudaStream_t s) {
     RenderBatch b{};
     if (sc.rv_th == 4)
-        revolve_kernel<4, true><<<1, kThreads, sc.rv_smem, s>>>(make_args(sc), b, params, img);
+        revolve_kernel<4, true><<<1, kThreads, sc.rv_smem, s>>>(make_args(sc), b, params, img, ids);
     else
-        revolve_kernel<8, true><<<1, kThreads, sc.rv_smem, s>>>(make_args(sc), b, params, img);
+        revolve_kernel<8, true><<<1, kThreads, sc.rv_smem, s>>>(make_args(sc), b, params, img, ids);
 }
 
 }  // namespace hr

@@ -143,6 +143,7 @@ def lib() -> ctypes.CDLL:
         L.hr_ncg_theta.argtypes = [vp, _f64p]
         L.hr_ncg_trace.argtypes = [vp, _f64p, _f64p, _f64p]
         L.hr_scene_get_stats.argtypes = [vp, ctypes.POINTER(hr_scene_stats)]
+        L.hr_render_ids.argtypes = [vp, _f64p, ctypes.POINTER(ctypes.c_int32)]
         L.hr_autotune.argtypes = [vp, _f64p, ctypes.c_int32, ctypes.POINTER(hr_tune_info)]
         L.hr_set_tuning.argtypes = [vp, ctypes.c_int32, ctypes.c_int32]
         L.hr_profile_enable.argtypes = [vp, ctypes.c_int32]
@@ -160,7 +161,7 @@ def lib() -> ctypes.CDLL:
                      "hr_optstate_destroy", "hr_newton_cg_step", "hr_optstate_theta", "hr_profile_enable",
                      "hr_profile_last", "hr_server_create", "hr_server_destroy", "hr_server_submit",
                      "hr_server_wait", "hr_ncg_create", "hr_ncg_destroy", "hr_ncg_run", "hr_ncg_theta",
-                     "hr_autotune", "hr_set_tuning", "hr_scene_get_stats", "hr_optstate_trace", "hr_ncg_trace"):
+                     "hr_autotune", "hr_set_tuning", "hr_scene_get_stats", "hr_optstate_trace", "hr_ncg_trace", "hr_render_ids"):
             getattr(L, name).restype = ctypes.c_int32
         L.hr_version.restype = ctypes.c_int32
         _lib = L
@@ -247,6 +248,15 @@ def hr_estimate_dev_noalloc(handle, quantity: int, d_theta: int, d_v, opts: hr_o
 def hr_render(handle, params, seed, request, sub, k, tag, spp, out):
     check(lib().hr_render(handle, _ptr(params, _f64p), seed, request, sub, k, tag, spp, _ptr(out, _f32p)),
           "hr_render")
+
+
+def hr_render_ids(handle, params, W, H) -> np.ndarray:
+    """[H*W] index of the triangle each pixel shows (-1: background)."""
+    out = np.zeros(W * H, np.int32)
+    p = np.ascontiguousarray(params, np.float64)
+    check(lib().hr_render_ids(handle, _ptr(p, _f64p), out.ctypes.data_as(ctypes.POINTER(ctypes.c_int32))),
+          "hr_render_ids")
+    return out
 
 
 def hr_scene_get_stats(handle) -> hr_scene_stats:

@@ -143,6 +143,46 @@ def test_revolve_full_size_bench_configuration():
     assert_estimate_close(flat, ref, what="revolve full")
 
 
+def _ids_cases():
+    sc = wl.revolve_scene()
+    g = np.random.default_rng(3)
+    yield "bench mesh 256", sc, [np.asarray(sc["theta_query"]) + g.normal(0, 0.1, 2) for _ in range(3)]
+    yield "bench mesh 50x37", wl.revolve_scene(width=50, height=37), [np.asarray(sc["theta_target"])]
+    for W in (128, 512):
+        s2 = _sheets_scene(W)
+        yield f"sheets {W}", s2, [np.asarray(s2["theta_query"]) + g.normal(0, 0.2, 2) for _ in range(2)]
+    s3 = wl.revolve_scene(width=96, height=96)
+    v, t = wl.sheets_mesh(layers=3, grid=4)
+    s3["vertices"], s3["triangles"] = v, np.concatenate([t, t])
+    yield "duplicated sheets 96", s3, [np.asarray(s3["theta_query"]) + g.normal(0, 0.2, 2) for _ in range(2)]
+
+
+@pytest.mark.parametrize("case", range(5))
+def test_revolve_triangle_indices_bit_exact(case):
+    """The rasteriser's decisions, pixel by pixel: the index of the triangle
+    each pixel shows equals the oracle's, exactly (both decide coverage and
+    depth in FP32 with the same operation sequences).  Cases: the bench mesh
+    (8x4 tiles), a ragged size, stacked sheets with the binned raster and with
+    the bin-overflow fallback, and a mesh listed twice, where every covered
+    pixel is an exact depth tie that the lower index must win."""
+    name, sc, params = list(_ids_cases())[case]
+    Sc = hr.Scene(sc)
+    r = O.RevolveRenderer(sc)
+    for p in params:
+        gi = hr.hr_render_ids(Sc.handle, p, sc["width"], sc["height"])
+        oi = r.ids(np.asarray(p, np.float32))
+        assert (oi >= 0).any(), name
+        bad = np.count_nonzero(gi != oi)
+        assert bad == 0, f"{name}: {bad} pixels differ"
+    if name.startswith("duplicated"):
+        assert gi.max() < len(sc["triangles"]) // 2
+        flat, dbg, ref = run_both(sc, r, "hessian", 32, "aggregate", scene=Sc)
+        check_samples(dbg, ref)
+        assert_losses_close(dbg["losses"], ref.losses, 2e-5, "duplicated-mesh losses")
+        assert_estimate_close(flat, ref, what="duplicated mesh")
+    Sc.close()
+
+
 def _sheets_scene(W):
     sc = wl.revolve_scene(width=W, height=W)
     sc["vertices"], sc["triangles"] = wl.sheets_mesh(layers=8, grid=8)

@@ -75,6 +75,26 @@ def test_revolve_raster_matches_fp64_ray_cast():
     assert hitm.mean() > 0.1                            # the object is on screen
     diff = np.abs(col - img.reshape(-1, 3)).max(1)
     assert np.all(diff[safe] < 1e-5), np.count_nonzero(diff[safe] >= 1e-5)
+    # the triangle each pixel shows is the ray cast's nearest hit
+    ids = r.ids(p)
+    assert np.array_equal(ids[safe], best_i[safe])
+
+
+def test_revolve_depth_ties_go_to_the_lower_index():
+    """A mesh listed twice (the copy's indices shifted by T): copies have the
+    same vertices, hence the same FP32 edge functions and depth planes, so
+    every covered pixel is an exact depth tie between triangle i and i + T;
+    the lower index must win everywhere, giving the single mesh's picture."""
+    W = H = 72
+    sc = wl.revolve_scene(width=W, height=H)
+    sc["vertices"], sc["triangles"] = wl.sheets_mesh(layers=3, grid=4)
+    T = len(sc["triangles"])
+    dup = dict(sc, triangles=np.concatenate([sc["triangles"], sc["triangles"]]))
+    p = np.asarray(sc["theta_query"], np.float32)
+    one, two = O.RevolveRenderer(sc).ids(p), O.RevolveRenderer(dup).ids(p)
+    assert (one >= 0).mean() > 0.3
+    assert np.array_equal(one, two)
+    assert two.max() < T
 
 
 def test_tris2d_raster_matches_fp64_barycentric_painter():

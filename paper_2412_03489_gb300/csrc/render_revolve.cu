@@ -173,10 +173,11 @@ __device__ __forceinline__ float rotation_param(const RenderBatch& b, int m, int
     return __fadd_rn(pt.theta[d], pt.tau[d]);
 }
 
-// one triangle's setup; false if it is clipped, culled or outside the image
-__device__ __forceinline__ bool setup_triangle(const RvArgs& P, int t, const float* vx, const float* vy,
-                                               const float* viz, const float sL[3], TriRec& r, uint2& bb) {
-    const int ia = P.tris[3 * t], ib = P.tris[3 * t + 1], ic = P.tris[3 * t + 2];
+// one triangle's setup (vertex indices ia, ib, ic; model-space unit normal
+// n); false if it is clipped, culled or outside the image
+__device__ __forceinline__ bool setup_triangle(const RvArgs& P, int ia, int ib, int ic, const float n[3],
+                                               const float* vx, const float* vy, const float* viz, const float sL[3],
+                                               TriRec& r, uint2& bb) {
     const float iza = viz[ia], izb = viz[ib], izc = viz[ic];
     if (!(iza > 0.0f && izb > 0.0f && izc > 0.0f)) return false;
     const float ax = vx[ia], ay = vy[ia], bx = vx[ib], by = vy[ib], cx = vx[ic], cy = vy[ic];
@@ -196,7 +197,7 @@ __device__ __forceinline__ bool setup_triangle(const RvArgs& P, int t, const flo
     r.Aw = __fmul_rn(__fmaf_rn(e2.A, izc, __fmaf_rn(e1.A, izb, __fmul_rn(e0.A, iza))), invD);
     r.Bw = __fmul_rn(__fmaf_rn(e2.B, izc, __fmaf_rn(e1.B, izb, __fmul_rn(e0.B, iza))), invD);
     r.Cw = __fmul_rn(__fmaf_rn(e2.C, izc, __fmaf_rn(e1.C, izb, __fmul_rn(e0.C, iza))), invD);
-    const float sh = P.tnrm[3 * t] * sL[0] + P.tnrm[3 * t + 1] * sL[1] + P.tnrm[3 * t + 2] * sL[2];
+    const float sh = n[0] * sL[0] + n[1] * sL[1] + n[2] * sL[2];
     r.shade = fmaxf(sh, 0.0f);
     bb.x = (uint32_t)xlo | ((uint32_t)xhi << 16);
     bb.y = (uint32_t)ylo | ((uint32_t)yhi << 16);
@@ -247,6 +248,22 @@ revolve_kernel(RvArgs P, RenderBatch b, const float* __restrict__ img_params, fl
                 s_cs[tid] = s_cs_next[tid];   // computed during the previous raster phase
             }
         }
+        // scene constants this thread uses in the render (two vertices, two
+        // triangles, the target's sum of squares on two tiles), loaded now so
+        // that their latency overlaps the rotation
+        float pv[2][3], pn[2][3], pt2[2];
+        int pt[2][3];
+#pragma unroll
+        for (int k = 0; k < 2; ++k) {
+            const int v = tid + k * kThreads, t = tid + k * kThreads;
+#pragma unroll
+            for (int c = 0; c < 3; ++c) {
+                pv[k][c] = v < P.nv ? P.verts[3 * v + c] : 0.0f;
+                pt[k][c] = t < P.nt ? P.tris[3 * t + c] : 0;
+                pn[k][c] = t < P.nt ? P.tnrm[3 * t + c] : 0.0f;
+            }
+            pt2[k] = (!kImage && tid + k * kThreads < P.T) ? P.tile_t2[tid + k * kThreads] : 0.0f;
+        }
         for (int i = tid; i < P.T; i += kThreads) tcnt[i] = 0;
         if (tid < 33) s_hist[tid] = 0;
         if (tid == 0) { s_count = 0; s_tile = 0; }
@@ -264,8 +281,7 @@ revolve_kernel(RvArgs P, RenderBatch b, const float* __restrict__ img_params, fl
         __syncthreads();
         // ---- 2. vertices ---------------------------------------------------
         const float halfW = __fmul_rn((float)P.W, 0.5f), halfH = __fmul_rn((float)P.H, 0.5f);
-        for (int v = tid; v < P.nv; v += kThreads) {
-            const float x = P.verts[3 * v], y = P.verts[3 * v + 1], z = P.verts[3 * v + 2];
+        auto project = [&](int v, float x, float y, float z) {
             const float X = __fmaf_rn(sR[2], z, __fmaf_rn(sR[1], y, __fmul_rn(sR[0], x)));
             const float Y = __fmaf_rn(sR[5], z, __fmaf_rn(sR[4], y, __fmul_rn(sR[3], x)));
             const float w2 = __fmaf_rn(sR[8], z, __fmaf_rn(sR[7], y, __fmul_rn(sR[6], x)));
@@ -274,17 +290,22 @@ revolve_kernel(RvArgs P, RenderBatch b, const float* __restrict__ img_params, fl
             vx[v] = __fmaf_rn(P.scale, qx, halfW);
             vy[v] = __fmaf_rn(-P.scale, qy, halfH);
             viz[v] = (Z > 0.0f) ? __fdiv_rn(1.0f, Z) : -1.0f;
-        }
+        };
+#pragma unroll
+        for (int k = 0; k < 2; ++k)
+            if (tid + k * kThreads < P.nv) project(tid + k * kThreads, pv[k][0], pv[k][1], pv[k][2]);
+        for (int v = tid + 2 * kThreads; v < P.nv; v += kThreads)
+            project(v, P.verts[3 * v], P.verts[3 * v + 1], P.verts[3 * v + 2]);
         __syncthreads();
         // ---- 3. triangle setup ------------------------------------------------
         // records stay at their triangle's index (bin entries carry it for the
         // tie rule); the survivors are listed for the binning, and a clipped,
         // culled or off-image triangle gets an empty bounding box (lo > hi),
         // which the all-triangles fallback of the raster skips
-        for (int t = tid; t < P.nt; t += kThreads) {
+        auto setup = [&](int t, const int id[3], const float n[3]) {
             TriRec r;
             uint2 bb;
-            if (setup_triangle(P, t, vx, vy, viz, sL, r, bb)) {
+            if (setup_triangle(P, id[0], id[1], id[2], n, vx, vy, viz, sL, r, bb)) {
                 rec[t] = r;
                 tshade[t] = r.shade;
                 surv[atomicAdd(&s_count, 1)] = (uint16_t)t;
@@ -292,6 +313,14 @@ revolve_kernel(RvArgs P, RenderBatch b, const float* __restrict__ img_params, fl
                 bb = make_uint2(1u, 1u);
             }
             bbx[t] = bb;
+        };
+#pragma unroll
+        for (int k = 0; k < 2; ++k)
+            if (tid + k * kThreads < P.nt) setup(tid + k * kThreads, pt[k], pn[k]);
+        for (int t = tid + 2 * kThreads; t < P.nt; t += kThreads) {
+            const int id[3] = {P.tris[3 * t], P.tris[3 * t + 1], P.tris[3 * t + 2]};
+            const float n[3] = {P.tnrm[3 * t], P.tnrm[3 * t + 1], P.tnrm[3 * t + 2]};
+            setup(t, id, n);
         }
         __syncthreads();
         const int count = s_count;
@@ -314,12 +343,28 @@ revolve_kernel(RvArgs P, RenderBatch b, const float* __restrict__ img_params, fl
             for (int i = 0; i < 3; ++i) neg[i] = -1e-5f * fmaf(fabsf(A[i]), fW, fmaf(fabsf(B[i]), fH, fabsf(C[i])));
             unsigned long long mask = 0ull;
             int bit = 0;
-            for (int ty = ty0; ty <= ty1; ++ty)
-                for (int tx = tx0; tx <= tx1; ++tx, ++bit)
-                    if (!test || tile_hits<kTH>(A, B, C, bb, neg, tx, ty)) {
+            const int xlo = (int)(bb.x & 0xffffu), xhi = (int)(bb.x >> 16);
+            const int ylo = (int)(bb.y & 0xffffu), yhi = (int)(bb.y >> 16);
+            for (int ty = ty0; ty <= ty1; ++ty) {
+                // per edge, the row term at the (tile row ∩ box) edge where
+                // B y is largest: the tile test is fma(A, x*, rowterm)
+                const float fy0 = (float)max(ty * kTH, ylo) + 0.5f, fy1 = (float)min(ty * kTH + kTH - 1, yhi) + 0.5f;
+                float rt[3];
+#pragma unroll
+                for (int i = 0; i < 3; ++i) rt[i] = fmaf(B[i], B[i] > 0.0f ? fy1 : fy0, C[i]);
+                for (int tx = tx0; tx <= tx1; ++tx, ++bit) {
+                    bool hit = true;
+                    if (test) {
+                        const float fx0 = (float)max(tx * kTW, xlo) + 0.5f, fx1 = (float)min(tx * kTW + kTW - 1, xhi) + 0.5f;
+#pragma unroll
+                        for (int i = 0; i < 3; ++i) hit = hit && !(fmaf(A[i], A[i] > 0.0f ? fx1 : fx0, rt[i]) < neg[i]);
+                    }
+                    if (hit) {
                         atomicAdd(&tcnt[ty * P.TX + tx], 1);
                         if (test) mask |= 1ull << bit;
                     }
+                }
+            }
             tmask[k] = test ? mask : ~0ull;
         }
         __syncthreads();
@@ -330,6 +375,16 @@ revolve_kernel(RvArgs P, RenderBatch b, const float* __restrict__ img_params, fl
         for (int i = tid; i < P.T; i += kThreads) tcnt[i] = 0;   // becomes the fill cursor
         __syncthreads();
         if (!overflow) {
+            // tiles without entries keep the sum of target^2 as their loss
+            // (the raster writes the others)
+            float* tl = reinterpret_cast<float*>(tcnt);
+#pragma unroll
+            for (int k = 0; k < 2; ++k) {
+                const int t = tid + k * kThreads;
+                if (t < P.T && ((t + 1 < P.T) ? toff[t + 1] : total) == toff[t]) tl[t] = pt2[k];
+            }
+            for (int t = tid + 2 * kThreads; t < P.T; t += kThreads)
+                if (((t + 1 < P.T) ? toff[t + 1] : total) == toff[t]) tl[t] = P.tile_t2[t];
             for (int k = tid; k < count; k += kThreads) {
                 const int s = surv[k];
                 const uint2 bb = bbx[s];
@@ -521,10 +576,7 @@ revolve_kernel(RvArgs P, RenderBatch b, const float* __restrict__ img_params, fl
             __syncthreads();
             // thread i sums tiles i, i + 1024, ...; then a fixed shuffle tree
             float acc = 0.0f;
-            for (int t = tid; t < P.T; t += kThreads) {
-                const bool has = overflow || ((t + 1 < P.T) ? toff[t + 1] : total) > toff[t];
-                acc += has ? tile_loss[t] : P.tile_t2[t];
-            }
+            for (int t = tid; t < P.T; t += kThreads) acc += tile_loss[t];
             acc = warp_sum(acc);
             if (lane == 0) s_part[warp] = acc;
             __syncthreads();

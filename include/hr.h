@@ -458,13 +458,31 @@ hr_status hr_server_submit(hr_server srv, const hr_request* req, uint64_t* ticke
  * returned and the ticket stays valid.  A ticket can be waited for once. */
 hr_status hr_server_wait(hr_server srv, uint64_t ticket, void* h_out, hr_request_info* info, int32_t timeout_ms);
 
-/* Diagnostics of a scene since its creation (waits for the scene's own
- * stream).  mesh_overflow_renders: REVOLVE3D renders whose 8x8-tile bins
- * held more than 16,384 (triangle, tile) entries, so that the render took the
- * rasteriser's fallback in which every tile walks every surviving triangle
- * (same pixels, same decisions, slower); 0 for other kinds. */
+/* Diagnostics of a scene's mesh renders since its creation, summed over
+ * renders (waits for the device); all 0 for kinds other than REVOLVE3D.
+ *   mesh_overflow_renders   renders whose tile bins held more (triangle,
+ *                           tile) entries than the render's shared memory
+ *                           holds (at most 16,384), so that every tile walked
+ *                           every triangle (same pixels, same decisions,
+ *                           slower);
+ *   mesh_renders            renders of estimates (images not counted);
+ *   mesh_survivors          triangles that passed clipping, culling and the
+ *                           image bounds;
+ *   mesh_bin_entries        (triangle, tile) bin entries;
+ *   mesh_tiles_with_entries tiles with at least one entry;
+ *   mesh_raster_steps       raster loop trips of the warps (a warp's tiles
+ *                           take as many trips as the longest bin among
+ *                           them);
+ *   mesh_tile_height        rows of the 8-pixel-wide raster tiles (4 or 8).
+ * The sums divided by mesh_renders give per-render averages. */
 typedef struct {
     int64_t mesh_overflow_renders;
+    int64_t mesh_renders;
+    int64_t mesh_survivors;
+    int64_t mesh_bin_entries;
+    int64_t mesh_tiles_with_entries;
+    int64_t mesh_raster_steps;
+    int64_t mesh_tile_height;
 } hr_scene_stats;
 hr_status hr_scene_get_stats(hr_scene scene, hr_scene_stats* out);
 

@@ -52,10 +52,11 @@ struct __align__(16) TriRec {
     float Aw, Bw, Cw, shade;
 };
 
-// bin entry: triangle << 16 | (tile rows inside the bounding box) << 8 |
-// (tile columns inside it)
+// bin entry: triangle << 16 | (tile rows OUTSIDE the bounding box) << 8 |
+// (tile columns outside it): a pixel of the tile lies in the box iff neither
+// its row bit nor its column bit is set, one AND per pixel
 __device__ __forceinline__ uint32_t entry_word(int tri, uint32_t rows, uint32_t cols) {
-    return ((uint32_t)tri << 16) | (rows << 8) | cols;
+    return ((uint32_t)tri << 16) | ((~rows & 0xFFu) << 8) | (~cols & 0xFFu);
 }
 // bits lo..hi (clamped to 0..7) of a byte
 __device__ __forceinline__ uint32_t span_bits(int lo, int hi) {
@@ -78,7 +79,7 @@ struct RvArgs {
     int vreg;            // floats in the vertex region
     int th;              // tile height (the kernel's template argument)
     uint64_t tx_recip;   // ceil(2^32 / TX): t / TX = (t tx_recip) >> 32 exactly for t, TX < 2^16
-    unsigned long long* stats;   // [0]: renders whose bins overflowed (diagnostics)
+    unsigned long long* stats;   // diagnostics [6], see hr_scene_stats
     float alb0, alb1, alb2, l0, l1, l2, eye_dist, scale;
 };
 
@@ -165,6 +166,34 @@ __device__ int bin_scan(const int* cnt, int* off, uint16_t* olist, int T, int* w
     __syncthreads();
     *n_obj = hist[32];
     return warp_tot[32];
+}
+
+// One pixel against one bin entry, written as PTX predicate chains: the
+// pixel is in when its row and column bits of the entry's outside mask are
+// clear (column c, row bit row_out) and E_i > th_i for the three edges; it
+// takes the entry when also wz > bw (strict); t4 becomes non-zero when wz ==
+// bw (an exact depth tie, resolved by a second, exact walk of the tile).
+template <int c>
+__device__ __forceinline__ void pixel_test(float E0, float E1, float E2, float wz, float th0, float th1, float th2,
+                                           uint32_t outside, uint32_t row_out, int s, float& bw, int& bs,
+                                           uint32_t& t4) {
+    asm("{\n\t"
+        ".reg .pred p, q;\n\t"
+        ".reg .b32 m;\n\t"
+        "lop3.b32 m, %7, %8, %11, 0xE0;\n\t"        // outside & (row_out | column bit)
+        "setp.eq.u32 p, m, 0;\n\t"
+        "setp.gt.and.f32 p, %3, %4, p;\n\t"
+        "setp.gt.and.f32 p, %5, %6, p;\n\t"
+        "setp.gt.and.f32 p, %9, %10, p;\n\t"
+        "setp.eq.f32 q, %12, %0;\n\t"
+        "setp.gt.and.f32 p, %12, %0, p;\n\t"
+        "selp.f32 %0, %12, %0, p;\n\t"
+        "selp.b32 %1, %13, %1, p;\n\t"
+        "@q or.b32 %2, %2, 1;\n\t"
+        "}"
+        : "+f"(bw), "+r"(bs), "+r"(t4)
+        : "f"(E0), "f"(th0), "f"(E1), "f"(th1), "r"(outside), "r"(row_out), "f"(E2), "f"(th2), "n"(1u << c),
+          "f"(wz), "r"(s));
 }
 
 // rotation angle d of perturbation m: RN32(theta32 + tau)
@@ -371,7 +400,13 @@ revolve_kernel(RvArgs P, RenderBatch b, const float* __restrict__ img_params, fl
         int n_obj = 0;
         const int total = bin_scan(tcnt, toff, olist, P.T, s_wtot, s_hist, &n_obj);
         const bool overflow = total > P.cap;
-        if (overflow && tid == 0 && P.stats) atomicAdd(P.stats, 1ull);
+        if (!kImage && tid == 0 && P.stats) {   // diagnostics: see hr_scene_stats
+            if (overflow) atomicAdd(&P.stats[0], 1ull);
+            atomicAdd(&P.stats[1], 1ull);
+            atomicAdd(&P.stats[2], (unsigned long long)count);
+            atomicAdd(&P.stats[3], (unsigned long long)total);
+            atomicAdd(&P.stats[4], (unsigned long long)n_obj);
+        }
         for (int i = tid; i < P.T; i += kThreads) tcnt[i] = 0;   // becomes the fill cursor
         __syncthreads();
         if (!overflow) {
@@ -431,8 +466,8 @@ revolve_kernel(RvArgs P, RenderBatch b, const float* __restrict__ img_params, fl
         float* tile_loss = reinterpret_cast<float*>(tcnt);
         const bool all_tiles = kImage || overflow;
         const int n_iter = all_tiles ? P.T : n_obj;
-        const uint32_t row_bit = 1u << (8 + ry);
         const int col_shift = 4 * hx;
+        const uint32_t row_out = 1u << (8 + ry - col_shift);   // this lane's row bit after the shift
         const bool vec_target = (P.W & 3) == 0;
         // each warp reserves its next tiles when it starts the current ones,
         // so the shared atomic's latency overlaps the tiles' work
@@ -467,42 +502,52 @@ revolve_kernel(RvArgs P, RenderBatch b, const float* __restrict__ img_params, fl
             // the last bit) the lane notes it, and a tile group where any lane
             // did is walked again with the full rule (larger 1/Z, lower index
             // on equal 1/Z).
-            bool tie = false;
-            auto raster_entry = [&](int s, uint32_t nib, bool exact) {
+            uint32_t tie_u = 0u;
+            // (outside: the entry's complement masks shifted so that bit c is
+            // this lane's column c and bit 8 + ry - 4 hx its row)
+            auto raster_entry = [&](int s, uint32_t outside, bool exact) {
                 const float4* rp = reinterpret_cast<const float4*>(&rec[s]);
                 const float4 q0 = rp[0], q1 = rp[1], q2 = rp[2], q3 = rp[3];
                 const float r0 = __fmaf_rn(q0.y, fy, q0.z);
                 const float r1 = __fmaf_rn(q1.y, fy, q1.z);
                 const float r2 = __fmaf_rn(q2.y, fy, q2.z);
                 const float rw = __fmaf_rn(q3.y, fy, q3.z);
+                if (exact) {
 #pragma unroll
-                for (int c = 0; c < 4; ++c) {
-                    const float E0 = __fmaf_rn(q0.x, fx[c], r0);
-                    const float E1 = __fmaf_rn(q1.x, fx[c], r1);
-                    const float E2 = __fmaf_rn(q2.x, fx[c], r2);
-                    const float wz = __fmaf_rn(q3.x, fx[c], rw);
-                    const bool in = ((nib >> c) & 1u) && (E0 > q0.w) && (E1 > q1.w) && (E2 > q2.w);
-                    bool better;
-                    if (exact) {
-                        better = in && (wz > bw[c] || (wz == bw[c] && s < bs[c]));
-                    } else {
-                        better = in && (wz > bw[c]);
-                        tie = tie || (wz == bw[c]);
+                    for (int c = 0; c < 4; ++c) {
+                        const float E0 = __fmaf_rn(q0.x, fx[c], r0);
+                        const float E1 = __fmaf_rn(q1.x, fx[c], r1);
+                        const float E2 = __fmaf_rn(q2.x, fx[c], r2);
+                        const float wz = __fmaf_rn(q3.x, fx[c], rw);
+                        const bool in = ((outside & (row_out | (1u << c))) == 0u) && (E0 > q0.w) &&
+                                        (E1 > q1.w) && (E2 > q2.w);
+                        const bool better = in && (wz > bw[c] || (wz == bw[c] && s < bs[c]));
+                        bw[c] = better ? wz : bw[c];
+                        bs[c] = better ? s : bs[c];
                     }
-                    bw[c] = better ? wz : bw[c];
-                    bs[c] = better ? s : bs[c];
+                } else {
+                    uint32_t t4 = 0u;
+                    pixel_test<0>(__fmaf_rn(q0.x, fx[0], r0), __fmaf_rn(q1.x, fx[0], r1), __fmaf_rn(q2.x, fx[0], r2),
+                                  __fmaf_rn(q3.x, fx[0], rw), q0.w, q1.w, q2.w, outside, row_out, s, bw[0], bs[0], t4);
+                    pixel_test<1>(__fmaf_rn(q0.x, fx[1], r0), __fmaf_rn(q1.x, fx[1], r1), __fmaf_rn(q2.x, fx[1], r2),
+                                  __fmaf_rn(q3.x, fx[1], rw), q0.w, q1.w, q2.w, outside, row_out, s, bw[1], bs[1], t4);
+                    pixel_test<2>(__fmaf_rn(q0.x, fx[2], r0), __fmaf_rn(q1.x, fx[2], r1), __fmaf_rn(q2.x, fx[2], r2),
+                                  __fmaf_rn(q3.x, fx[2], rw), q0.w, q1.w, q2.w, outside, row_out, s, bw[2], bs[2], t4);
+                    pixel_test<3>(__fmaf_rn(q0.x, fx[3], r0), __fmaf_rn(q1.x, fx[3], r1), __fmaf_rn(q2.x, fx[3], r2),
+                                  __fmaf_rn(q3.x, fx[3], rw), q0.w, q1.w, q2.w, outside, row_out, s, bw[3], bs[3], t4);
+                    tie_u |= t4;
                 }
             };
             if (!overflow) {
                 const int n_max = (int)__reduce_max_sync(0xffffffffu, (unsigned)n_mine);
+                if (!kImage && lane == 0 && P.stats) atomicAdd(&P.stats[5], (unsigned long long)n_max);
                 for (int k = 0; k < n_max; ++k) {
                     if (k < n_mine) {
                         const uint32_t e = ent[beg + k];
-                        // this lane's 4 columns inside the bounding box (none if its row is not)
-                        raster_entry((int)(e >> 16), (e & row_bit) ? (e >> col_shift) & 0xFu : 0u, false);
+                        raster_entry((int)(e >> 16), e >> col_shift, false);
                     }
                 }
-                if (__any_sync(0xffffffffu, tie)) {
+                if (__any_sync(0xffffffffu, tie_u != 0u)) {
 #pragma unroll
                     for (int c = 0; c < 4; ++c) {
                         bw[c] = -INFINITY;
@@ -511,7 +556,7 @@ revolve_kernel(RvArgs P, RenderBatch b, const float* __restrict__ img_params, fl
                     for (int k = 0; k < n_max; ++k) {
                         if (k < n_mine) {
                             const uint32_t e = ent[beg + k];
-                            raster_entry((int)(e >> 16), (e & row_bit) ? (e >> col_shift) & 0xFu : 0u, true);
+                            raster_entry((int)(e >> 16), e >> col_shift, true);
                         }
                     }
                 }
@@ -523,7 +568,8 @@ revolve_kernel(RvArgs P, RenderBatch b, const float* __restrict__ img_params, fl
                     const int xlo = (int)(bb.x & 0xffffu), xhi = (int)(bb.x >> 16);
                     const int ylo = (int)(bb.y & 0xffffu), yhi = (int)(bb.y >> 16);
                     if (has_tile && xlo <= xhi && y >= ylo && y <= yhi)
-                        raster_entry(s, (span_bits(xlo - tx * kTW, xhi - tx * kTW) >> col_shift) & 0xFu, false);
+                        raster_entry(s, ((~span_bits(xlo - tx * kTW, xhi - tx * kTW) & 0xFFu) >> col_shift) & 0xFu,
+                                     false);
                 }
             }
             // (every group runs the shuffles below, a group without a tile too)

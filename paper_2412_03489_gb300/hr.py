@@ -79,7 +79,10 @@ class hr_ncg_info(ctypes.Structure):
 
 
 class hr_scene_stats(ctypes.Structure):
-    _fields_ = [("mesh_overflow_renders", ctypes.c_int64)]
+    _fields_ = [("mesh_overflow_renders", ctypes.c_int64), ("mesh_renders", ctypes.c_int64),
+                ("mesh_survivors", ctypes.c_int64), ("mesh_bin_entries", ctypes.c_int64),
+                ("mesh_tiles_with_entries", ctypes.c_int64), ("mesh_raster_steps", ctypes.c_int64),
+                ("mesh_tile_height", ctypes.c_int64)]
 
 
 class hr_tune_info(ctypes.Structure):

@@ -195,8 +195,8 @@ def test_revolve_stacked_sheets_and_bin_overflow(W, overflow):
     covered at several depths, and every triangle spans many tiles.  At 128^2
     the tile bins hold about 6,000 entries (the binned raster); at 512^2 more
     than 40,000, beyond the 16,384-entry bin capacity, so every render takes
-    the fallback in which each tile walks every surviving triangle.  The
-    scene's overflow counter shows which path ran.  Both paths against the
+    the fallback in which each tile walks every triangle.  The scene's
+    overflow counter shows which path ran.  Both paths against the
     oracle: images pixel by pixel (the depth winner decides each pixel's
     shade), then an aggregate Hessian on identical samples."""
     sc = _sheets_scene(W)
@@ -214,12 +214,15 @@ def test_revolve_stacked_sheets_and_bin_overflow(W, overflow):
     check_samples(dbg, ref)
     assert_losses_close(dbg["losses"], ref.losses, 2e-5, "sheets losses")
     assert_estimate_close(flat, ref, what=f"sheets {W}")
-    after = hr.hr_scene_get_stats(Sc.handle).mesh_overflow_renders
+    st = hr.hr_scene_get_stats(Sc.handle)
+    after = st.mesh_overflow_renders
     Sc.close()
+    assert st.mesh_renders == 16          # the estimate's renders (images are not counted)
     if overflow:
-        assert after - before >= 3 + 16, (before, after)
+        assert after - before == 16, (before, after)
     else:
         assert after == before == 0, (before, after)
+        assert 0 < st.mesh_bin_entries and st.mesh_raster_steps > 0
 
 
 # ---------------------------------------------------------------------------

@@ -17,6 +17,14 @@ library's own events; its algorithmic work is an FP32-operation count (see
 sums) on the same estimate with its renders split over all host threads, and
 on a bounded sample with one thread (`single_thread`).
 
+`secondary` (rank 0, after the headline's timed region; --no-secondary
+skips it) reports the other configurations compactly: the path-traced HVP
+(8,192 perturbations) with its roofline from counted rays, one batched
+Newton-CG step (64 instances, CUDA graph), and serving on a seeded stream
+of 1,200 requests against the same requests one at a time; the path
+tracer's
+sampled renders are checked against the oracle in the cpu_baseline leg.
+
 Multi-GPU: estimates are independent, so N ranks run N replicas (weak
 scaling, no collective on the data path); `value` = all ranks' estimates /
 the slowest rank's time.
@@ -83,6 +91,125 @@ def revolve_work(sc, theta):
     y1 = np.clip(np.floor(np.maximum(np.maximum(ay, by), cy) - 0.5), -1, H - 1)
     cand = np.where(front, np.maximum(0, x1 - x0 + 1) * np.maximum(0, y1 - y0 + 1), 0).sum()
     return 15 * len(V) + 40 * len(T) + 10 * float(cand) + 9 * W * H, float(cand)
+
+
+def ptbox_work(W, H, spp, hit_rays, shadow_rays, vertices):
+    """Algorithmic FP32 operations of one path-traced render from its ray
+    counts (measured by the counting build): 154 per closest-hit ray from
+    inside the box (3 forward walls, 6 block faces and the light at 10
+    operations each: subtract, multiply, two FMAs, six compares; 3 spheres at
+    18 each), 124 per shadow ray (the 6 block faces and the light; no wall
+    when the light lies inside them), 40 per shaded vertex (hit point,
+    normal, light sample, direction, distance, cosines, throughput), 33 per
+    continuation (disc sample, lift, orthonormal basis, direction), 12 per
+    camera ray and 12 per pixel (average, squared error).  The Philox words
+    (integer) are not counted."""
+    cam = W * H * spp
+    return (154.0 * hit_rays + 124.0 * shadow_rays + 40.0 * vertices + 33.0 * (hit_rays - cam) + 12.0 * cam
+            + 12.0 * W * H)
+
+
+def secondary_workloads(torch, hr, wl, stream, flush, peaks, n_sm):
+    """The other configurations, compactly, outside the headline's timed
+    region: the path-traced HVP (8,192 perturbations, 3 timed steps, roofline
+    from counted rays), one batched Newton-CG step (64 instances, graph, 3
+    timed steps), and serving on a 1,200-request seeded stream against the
+    same requests one at a time."""
+    out = {}
+    # path tracer
+    sc = wl.ptbox_scene()
+    S = hr.Scene(sc)
+    d_theta = torch.tensor(sc["theta_query"], dtype=torch.float64, device="cuda")
+    d_v = torch.tensor(sc["v"], dtype=torch.float64, device="cuda")
+    d_out = torch.zeros(6, dtype=torch.float64, device="cuda")
+    tuning = tune_scene(hr, S, sc["theta_query"], 2048)
+    hr.hr_profile_enable(S.handle, True)
+    M = 8192
+    stage = []
+
+    def pt_step(i):
+        o = hr.make_opts(sc["sigma"], M, hr.HR_AGGREGATE, SEED, i, stream=stream.cuda_stream)
+        hr.hr_estimate_dev(S.handle, hr.HR_HVP, d_theta.data_ptr(), d_v.data_ptr(), o, d_out.data_ptr())
+    times = []
+    for i in range(4):
+        flush.fill_(float(i))
+        ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        ev0.record(stream)
+        pt_step(i)
+        ev1.record(stream)
+        ev1.synchronize()
+        if i:
+            times.append(ev0.elapsed_time(ev1))
+            stage.append(hr.hr_profile_last(S.handle).astype(np.float64))
+    hr.hr_profile_enable(S.handle, False)
+    # work per render from the counting build (512 renders, other requests)
+    hr.hr_scene_count_work(S.handle, True)
+    S.estimate(hr.HR_HVP, np.asarray(sc["theta_query"]), sc["sigma"], 512, hr.HR_AGGREGATE, SEED, 7000, v=sc["v"])
+    hr.hr_scene_count_work(S.handle, False)
+    st = hr.hr_scene_get_stats(S.handle)
+    n = max(1, st.pt_counted_renders)
+    rays = (st.pt_hit_rays / n, st.pt_shadow_rays / n, st.pt_vertices / n)
+    ops = ptbox_work(sc["width"], sc["height"], sc["spp"], *rays)
+    render_ms = float(np.mean([x[1] for x in stage]))
+    peak_ops = n_sm * 128 * float(peaks.get("sm_max_mhz", 2070.0)) * 1e6
+    achieved = ops * M / (render_ms / 1e3)
+    t = float(np.mean(times))
+    out["ptbox_hvp"] = {
+        "workload": "path-traced box 128x128 RGB, 4 spp, depth 3, 6 params, sigma 0.05, aggregate HVP, "
+                    "8192 perturbations", "steps": len(times),
+        "estimates_per_s": 1e3 / t, "renders_per_s": M * 1e3 / t, "ms_per_estimate": t,
+        "stage_ms": dict(zip(("sample", "render_loss", "sums"), np.mean(stage, axis=0).tolist())),
+        "roofline": {"bound": "alu", "kernel": "ptbox_kernel (path tracing + loss)", "achieved": achieved / 1e12,
+                     "peak": peak_ops / 1e12, "unit": "TFLOP/s", "frac": achieved / peak_ops,
+                     "ops_per_render": ops, "rays_per_render": {"closest_hit": rays[0], "shadow": rays[1],
+                                                               "shaded_vertices": rays[2]}},
+        "tuning": tuning}
+    S.close()
+    # Newton-CG
+    sc = wl.tris2d_scene()
+    S = hr.Scene(sc)
+    B = 64
+    opts = hr.hr_cg_opts()
+    opts.sigma, opts.n_grad, opts.n_hvp, opts.cg_iters = sc["sigma"], 32, 32, 10
+    opts.lambda_rel, opts.trust_radius, opts.seed, opts.request_base = 1e-3, 0.05, SEED, 0
+    opts.use_graph, opts.stream = 1, stream.cuda_stream
+    st_ = hr.hr_optstate_create(S.handle, B, np.ascontiguousarray(sc["theta_init"], np.float64), opts)
+    times = _timed_steps(torch, stream, flush, lambda i: hr.hr_newton_cg_step(S.handle, st_, None), 3, 3)
+    hr.hr_optstate_destroy(st_)
+    S.close()
+    t = float(np.mean(times))
+    out["newton_cg"] = {
+        "workload": "16 coloured triangles 256x256, 64 params, 64 instances, 32 gradient + 10 x 32 HVP renders "
+                    "per instance-step, CUDA graph", "steps": len(times),
+        "launch_steps_per_s": 1e3 / t, "instance_steps_per_s": B * 1e3 / t, "ms_per_step": t,
+        "renders_per_s": B * (32 + 10 * 32) * 1e3 / t}
+    # serving
+    sv = serving_bench(torch, hr, wl, n_requests=1200, sweep=False)
+    out["serving"] = {"workload": sv["config"]["workload"] + " (1,200 requests)", "requests": sv["requests"],
+                      "plain_one_at_a_time_estimates_per_s": sv["plain_one_at_a_time"]["estimates_per_s"],
+                      "served_saturated_estimates_per_s": sv["served_saturated"]["estimates_per_s"],
+                      "speedup_vs_plain": sv["served_saturated"]["speedup_vs_plain"],
+                      "results_identical_to_plain": sv["served_saturated"]["results_identical_to_plain"]}
+    return out
+
+
+def ptbox_oracle_match(hr, wl):
+    """Sampled renders of the path-traced HVP request against the oracle's
+    path tracer on the same perturbations (cpu_baseline leg): 8 renders spread
+    over the 8,192, max relative loss difference."""
+    import oracle as O
+    sc = wl.ptbox_scene()
+    S = hr.Scene(sc)
+    theta = np.asarray(sc["theta_query"])
+    M = 8192
+    _, dbg = S.estimate(hr.HR_HVP, theta, sc["sigma"], M, hr.HR_AGGREGATE, SEED, 0, v=sc["v"], debug=True)
+    S.close()
+    r = O.PtboxRenderer(sc)
+    picks = [0, 1, 2047, 2048, 4095, 6000, 8190, 8191]
+    ref = np.array([r.loss(O.perturb(theta, dbg["tau"][m]), dict(seed=SEED, request=0, sub=0, k=m // 2))
+                    for m in picks])
+    rel = np.abs(dbg["losses"][picks].astype(np.float64) - ref) / np.abs(ref)
+    return {"renders_compared": len(picks), "max_rel_loss_err": float(rel.max()), "tolerance": 1e-4}
 
 
 class ClockSampler:
@@ -484,15 +611,15 @@ def boxes_variance_bench(hr, wl):
     return out
 
 
-def serving_bench(torch, hr, wl):
+def serving_bench(torch, hr, wl, n_requests=1200, sweep=True):
     """Poisson arrivals through the server versus the plain one-request-at-a-
     time entry points on the same request list (estimates of every kind and
-    Newton-CG steps on resident optimizer states); the arrival rate swept from
-    a quarter of the saturated rate to past it."""
+    Newton-CG steps on resident optimizer states); with `sweep`, the arrival
+    rate swept from a quarter of the saturated rate to past it."""
     import threading
     scenes = wl.serving_scenes()
     S = {k: hr.Scene(v) for k, v in scenes.items()}
-    reqs = wl.serving_requests(scenes, n_requests=1200)
+    reqs = wl.serving_requests(scenes, n_requests=n_requests)
     specs = wl.serving_newton_states(scenes)
 
     def new_states():
@@ -589,7 +716,7 @@ def serving_bench(torch, hr, wl):
                 "estimates_per_s": len(reqs) / dt,
                 "latency_ms": {"p50": float(np.percentile(lat, 50)), "p99": float(np.percentile(lat, 99))}}
 
-    sweep = [poisson(f, 0xC5 + k) for k, f in enumerate((0.25, 0.5, 0.7, 0.9, 1.1))]
+    sweep = [poisson(f, 0xC5 + k) for k, f in enumerate((0.25, 0.5, 0.7, 0.9, 1.1))] if sweep else []
     hr.hr_server_destroy(srv)
     for st in st_plain + st_srv:
         hr.hr_optstate_destroy(st)
@@ -615,6 +742,8 @@ def main():
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="native", choices=["native", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-secondary", action="store_true",
+                    help="skip the compact path-tracer, Newton-CG and serving measurements of the headline line")
     ap.add_argument("--workload", default="revolve", choices=["revolve", "disc", "ptbox", "newton", "serving", "boxes", "optimise"],
                     help="revolve (default) is the headline workload; the others report the remaining "
                          "configurations in their own JSON lines")
@@ -727,11 +856,15 @@ def main():
         line["converged_reference"] = {
             "perturbations": 1 << 20, "reference": Hc.tolist(), "estimate": He.tolist(),
             "max_abs_err_over_max_entry": float(np.max(np.abs(He - Hc)) / np.max(np.abs(Hc)))}
+        if not args.no_secondary:
+            line["secondary"] = secondary_workloads(torch, hr, wl, stream, flush, peaks, n_sm)
         if not args.no_cpu_baseline:
             threads = host_threads()
             line["cpu_baseline"] = cpu_baseline(sc, theta, sample=M_PERTURB, threads=threads, keep_estimate=True)
             line["oracle_match"] = oracle_match(hr, S, sc, theta, line["cpu_baseline"])
             line["cpu_baseline"]["single_thread"] = cpu_baseline(sc, theta, sample=256, threads=1)
+            if "secondary" in line:
+                line["secondary"]["ptbox_hvp"]["oracle_match"] = ptbox_oracle_match(hr, wl)
         print(json.dumps(line))
     S.close()
     if world > 1:

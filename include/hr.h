@@ -474,7 +474,14 @@ hr_status hr_server_wait(hr_server srv, uint64_t ticket, void* h_out, hr_request
  *                           take as many trips as the longest bin among
  *                           them);
  *   mesh_tile_height        rows of the 8-pixel-wide raster tiles (4 or 8).
- * The sums divided by mesh_renders give per-render averages. */
+ * The sums divided by mesh_renders give per-render averages.  Path-traced
+ * scenes (PTBOX) count their work only while hr_scene_count_work is on
+ * (those launches use a counting build of the default launch shape; the
+ * images and losses are the same):
+ *   pt_counted_renders      renders launched while counting;
+ *   pt_hit_rays             closest-hit rays (camera rays and continuations);
+ *   pt_shadow_rays          shadow rays of next-event estimation;
+ *   pt_vertices             shaded path vertices. */
 typedef struct {
     int64_t mesh_overflow_renders;
     int64_t mesh_renders;
@@ -483,8 +490,15 @@ typedef struct {
     int64_t mesh_tiles_with_entries;
     int64_t mesh_raster_steps;
     int64_t mesh_tile_height;
+    int64_t pt_counted_renders;
+    int64_t pt_hit_rays;
+    int64_t pt_shadow_rays;
+    int64_t pt_vertices;
 } hr_scene_stats;
 hr_status hr_scene_get_stats(hr_scene scene, hr_scene_stats* out);
+/* PTBOX only: on != 0 makes the scene's following render launches count
+ * their rays (see hr_scene_stats); HR_ERR_UNSUPPORTED for other kinds. */
+hr_status hr_scene_count_work(hr_scene scene, int32_t on);
 
 /* Stage timing: when enabled (on != 0), every estimate records CUDA events
  * on its stream around its three launches (sampler, render + loss, sums) and

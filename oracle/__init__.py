@@ -89,6 +89,10 @@ def lib():
                                       ctypes.c_uint64, ctypes.c_uint32, ctypes.c_uint32, ctypes.c_uint32,
                                       ctypes.c_uint32, _f32p, _f64p]
         L.or_ptbox_render.restype = ctypes.c_double
+        L.or_ptbox_render_counted.argtypes = [ctypes.POINTER(_PtboxScene), _f32p, ctypes.c_int, ctypes.c_int,
+                                              ctypes.c_uint64, ctypes.c_uint32, ctypes.c_uint32, ctypes.c_uint32,
+                                              ctypes.c_uint32, _f32p, _f64p, ctypes.POINTER(ctypes.c_longlong)]
+        L.or_ptbox_render_counted.restype = ctypes.c_double
         L.or_ptbox_intersect.argtypes = [ctypes.POINTER(_PtboxScene), _f32p, _f32p, _f32p, _f32p]
         L.or_ptbox_intersect.restype = ctypes.c_int
         L.or_ptbox_trace.argtypes = [ctypes.POINTER(_PtboxScene), _f32p, _f32p, _f32p, ctypes.c_int,
@@ -342,6 +346,16 @@ class PtboxRenderer(Renderer):
         return lib().or_ptbox_render(ctypes.byref(self.s), _p(p, _f32p), self.spp, self.depth, ctx["seed"],
                                      ctx["request"] & 0xFFFFFFFF, ctx["sub"], ctx["k"], TAG_PATH,
                                      _p(self.target, _f32p), None)
+
+    def count_rays(self, p, ctx):
+        """(closest-hit rays, shadow rays, shaded vertices) of the loss render
+        of perturbation context ctx, as the path tracer traces them."""
+        cnt = (ctypes.c_longlong * 3)()
+        p = np.ascontiguousarray(p, np.float32)
+        lib().or_ptbox_render_counted(ctypes.byref(self.s), _p(p, _f32p), self.spp, self.depth, ctx["seed"],
+                                      ctx["request"] & 0xFFFFFFFF, ctx["sub"], ctx["k"], TAG_PATH,
+                                      _p(self.target, _f32p), None, cnt)
+        return int(cnt[0]), int(cnt[1]), int(cnt[2])
 
     def intersect(self, p, o, d):
         t = np.zeros(1, np.float32)

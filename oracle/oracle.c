@@ -732,13 +732,16 @@ static void pt_normalize(float v[3])
 }
 
 /* one path sample; adds its radiance to L */
+/* cnt (may be NULL) counts closest-hit rays [0], shadow rays [1] and shaded
+ * vertices [2] */
 static void pt_path(const or_ptbox_scene* s, const pt_geom* g, int depth, uint64_t seed,
                     uint32_t request, uint32_t c2, uint32_t k, uint32_t idx,
-                    const float o0[3], const float d0[3], double L[3])
+                    const float o0[3], const float d0[3], double L[3], long long* cnt)
 {
     double beta[3] = {1.0, 1.0, 1.0};
     float o[3] = {o0[0], o0[1], o0[2]}, d[3] = {d0[0], d0[1], d0[2]};
     float t;
+    if (cnt) ++cnt[0];
     int prim = pt_intersect(g, o, d, &t);
     if (prim < 0) return;
     if (s->emit_all) {
@@ -754,6 +757,7 @@ static void pt_path(const or_ptbox_scene* s, const pt_geom* g, int depth, uint64
         pt_normal(g, prim, x, d, n);
         for (int c = 0; c < 3; ++c) o2[c] = fmaf(n[c], 1e-4f, x[c]);
         const float* rho = s->emit_all && prim == PT_LIGHT ? s->quad_albedo : pt_albedo(s, prim);
+        if (cnt) ++cnt[2];
         uint32_t w0[4];
         philox_words(seed, idx, (k << 8) | ((uint32_t)v << 4) | 0u, c2, request, w0);
         if (s->nee) {
@@ -770,6 +774,7 @@ static void pt_path(const or_ptbox_scene* s, const pt_geom* g, int depth, uint64
             float cosl = om[1];
             if (cosx > 0.0f && cosl > 0.0f) {
                 float ts;
+                if (cnt) ++cnt[1];
                 int ps = pt_intersect(g, o2, om, &ts);
                 if (ps == PT_LIGHT) {
                     double area = ((double)g->hi_u[PT_LIGHT] - g->lo_u[PT_LIGHT]) *
@@ -811,6 +816,7 @@ static void pt_path(const or_ptbox_scene* s, const pt_geom* g, int depth, uint64
         float nd[3];
         for (int c = 0; c < 3; ++c) nd[c] = fmaf(cz, n[c], fmaf(b, t2[c], a * t1[c]));
         for (int c = 0; c < 3; ++c) beta[c] *= (double)rho[c];
+        if (cnt) ++cnt[0];
         prim = pt_intersect(g, o2, nd, &t);
         if (prim < 0) return;
         if (s->emit_all)
@@ -822,6 +828,15 @@ static void pt_path(const or_ptbox_scene* s, const pt_geom* g, int depth, uint64
 double or_ptbox_render(const or_ptbox_scene* s, const float p[6], int spp, int depth,
                        uint64_t seed, uint32_t request, uint32_t sub, uint32_t k,
                        uint32_t tag, const float* target, double* img)
+{
+    return or_ptbox_render_counted(s, p, spp, depth, seed, request, sub, k, tag, target, img, 0);
+}
+
+/* The path tracer; also adds, if cnt is not NULL, its closest-hit rays,
+ * shadow rays and shaded vertices to cnt[0..2]. */
+double or_ptbox_render_counted(const or_ptbox_scene* s, const float p[6], int spp, int depth,
+                               uint64_t seed, uint32_t request, uint32_t sub, uint32_t k,
+                               uint32_t tag, const float* target, double* img, long long* cnt)
 {
     pt_geom g;
     pt_setup(s, p, &g);
@@ -840,7 +855,7 @@ double or_ptbox_render(const or_ptbox_scene* s, const float p[6], int spp, int d
                 float d[3] = {fmaf(fx, s->pix_scale, -s->tan_half), fmaf(-fy, s->pix_scale, s->tan_half), -1.0f};
                 pt_normalize(d);
                 float o[3] = {0.0f, 0.0f, s->cam_z};
-                pt_path(s, &g, depth, seed, request, c2, k, idx, o, d, L);
+                pt_path(s, &g, depth, seed, request, c2, k, idx, o, d, L, cnt);
             }
             int i = y * W + x;
             for (int c = 0; c < 3; ++c) {
@@ -872,7 +887,7 @@ void or_ptbox_trace(const or_ptbox_scene* s, const float p[6], const float o[3],
     pt_geom g;
     pt_setup(s, p, &g);
     out[0] = out[1] = out[2] = 0.0;
-    pt_path(s, &g, depth, seed, request, (tag << 24) | (sub & 0xFFFFFFu), k, idx, o, d, out);
+    pt_path(s, &g, depth, seed, request, (tag << 24) | (sub & 0xFFFFFFu), k, idx, o, d, out, 0);
 }
 
 /* p = RN32(RN32(theta) + tau): the perturbed parameters every renderer sees */

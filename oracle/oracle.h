@@ -109,6 +109,9 @@ typedef struct {
 double or_ptbox_render(const or_ptbox_scene* s, const float p[6], int spp, int depth,
                        uint64_t seed, uint32_t request, uint32_t sub, uint32_t k,
                        uint32_t tag, const float* target, double* img);
+double or_ptbox_render_counted(const or_ptbox_scene* s, const float p[6], int spp, int depth,
+                               uint64_t seed, uint32_t request, uint32_t sub, uint32_t k,
+                               uint32_t tag, const float* target, double* img, long long* cnt);
 
 /* one ray's closest primitive (-1 = none) and its distance */
 int or_ptbox_intersect(const or_ptbox_scene* s, const float p[6], const float o[3],

@@ -539,6 +539,8 @@ hr_status hr_create_scene(const hr_scene_desc* d, hr_scene* out) {
             sc.light_half = d->light_half; sc.cam_z = d->cam_z; sc.tan_half = d->tan_half; sc.pix_scale = d->pix_scale;
             for (int c = 0; c < 3; ++c) sc.emission[c] = d->emission[c];
             sc.spp = d->spp; sc.target_spp = d->target_spp; sc.depth = d->depth; sc.scene_seed = d->seed;
+            if ((e = cudaMalloc(&sc.pt_stats, 4 * sizeof(unsigned long long))) != cudaSuccess) return bail(e, "stats");
+            if ((e = cudaMemset(sc.pt_stats, 0, 4 * sizeof(unsigned long long))) != cudaSuccess) return bail(e, "stats");
             break;
         case HR_SCENE_QUADRATIC:
             if ((e = upload(&sc.qA, d->quad_A, (size_t)sc.n * sc.n)) != cudaSuccess) return bail(e, "A");
@@ -577,6 +579,7 @@ hr_status hr_destroy_scene(hr_scene s) {
     if (s->stream) cudaStreamSynchronize(s->stream);
     cudaFree(sc.target); cudaFree(sc.verts); cudaFree(sc.tris); cudaFree(sc.tnrm); cudaFree(sc.tile_t2);
     cudaFree(sc.raw); cudaFree(sc.pidx); cudaFree(sc.qA); cudaFree(sc.qb); cudaFree(sc.rv_stats);
+    cudaFree(sc.pt_stats);
     s->ws.release_all();
     for (cudaEvent_t& e : s->ev)
         if (e) cudaEventDestroy(e);
@@ -637,6 +640,25 @@ hr_status hr_scene_get_stats(hr_scene s, hr_scene_stats* out) {
         out->mesh_raster_steps = (int64_t)v[5];
         out->mesh_tile_height = s->sc.rv_th;
     }
+    if (s->sc.pt_stats) {
+        unsigned long long v[4] = {};
+        cudaError_t e = cudaDeviceSynchronize();
+        if (e == cudaSuccess) e = cudaMemcpy(v, s->sc.pt_stats, sizeof v, cudaMemcpyDeviceToHost);
+        if (e != cudaSuccess) return fail(HR_ERR_CUDA, "stats: %s", cudaGetErrorString(e));
+        out->pt_counted_renders = (int64_t)v[0];
+        out->pt_hit_rays = (int64_t)v[1];
+        out->pt_shadow_rays = (int64_t)v[2];
+        out->pt_vertices = (int64_t)v[3];
+    }
+    return HR_OK;
+}
+
+hr_status hr_scene_count_work(hr_scene s, int32_t on) {
+    clear_error();
+    if (!s) return fail(HR_ERR_INVALID_ARG, "NULL scene");
+    std::lock_guard<std::mutex> lk(s->mu);
+    if (s->sc.kind != HR_SCENE_PTBOX) return fail(HR_ERR_UNSUPPORTED, "work counting exists for path-traced scenes only");
+    s->sc.count_work = on ? 1 : 0;
     return HR_OK;
 }
 

@@ -177,6 +177,8 @@ struct DevScene {
     float emission[3] = {0, 0, 0};
     int spp = 0, target_spp = 0, depth = 0;
     uint64_t scene_seed = 0;
+    unsigned long long* pt_stats = nullptr;   // [4] work counters of the counting launches
+    int count_work = 0;                       // 1: path-tracer launches count their rays
     // analytic test functions
     double* qA = nullptr;         // [n][n] FP64 (QUADRATIC)
     double* qb = nullptr;         // [n] FP64

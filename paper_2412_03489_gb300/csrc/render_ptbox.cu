@@ -185,11 +185,18 @@ __device__ __forceinline__ bool sees_light(const PtShared& S, const float o[3], 
     return intersect_canon(S, o, d, t, walls) == kLight;
 }
 
-template <bool kCanon>
+// work counters of the counting instantiation (kCount): closest-hit rays,
+// shadow rays and shaded path vertices
+struct PtCount {
+    uint32_t hit = 0, shadow = 0, vert = 0;
+};
+
+template <bool kCanon, bool kCount>
 __device__ void radiance(const PtShared& S, int depth, uint64_t seed, uint32_t request, uint32_t c2, uint32_t k,
-                         uint32_t idx, float o[3], float d[3], float L[3]) {
+                         uint32_t idx, float o[3], float d[3], float L[3], PtCount& cnt) {
     float beta[3] = {1.0f, 1.0f, 1.0f};
     float t;
+    if (kCount) ++cnt.hit;
     int prim = closest_hit<kCanon>(S, o, d, t);
     if (prim < 0) return;
     if (prim == kLight) {
@@ -218,6 +225,7 @@ __device__ void radiance(const PtShared& S, int depth, uint64_t seed, uint32_t r
 #pragma unroll
         for (int c = 0; c < 3; ++c) o2[c] = __fmaf_rn(n[c], 1e-4f, x[c]);
         const float* rho = S.alb[prim];
+        if (kCount) ++cnt.vert;
         const uint32_t cbase = (k << 8) | ((uint32_t)v << 4);
         const u32x4 w0 = philox_seed(seed, idx, cbase, c2, request);
         // next-event estimation
@@ -231,6 +239,7 @@ __device__ void radiance(const PtShared& S, int depth, uint64_t seed, uint32_t r
             const float cosx = dot3(n, om);
             const float cosl = om[1];
             if (cosx > 0.0f && cosl > 0.0f) {
+                if (kCount) ++cnt.shadow;
                 if (sees_light<kCanon>(S, o2, om)) {
                     const float geo = cosx * cosl / dist2 * area * kInvPi;
 #pragma unroll
@@ -270,6 +279,7 @@ __device__ void radiance(const PtShared& S, int depth, uint64_t seed, uint32_t r
         for (int c = 0; c < 3; ++c) nd[c] = __fmaf_rn(cz, n[c], __fmaf_rn(b, t2[c], __fmul_rn(a, t1[c])));
 #pragma unroll
         for (int c = 0; c < 3; ++c) beta[c] *= rho[c];
+        if (kCount) ++cnt.hit;
         prim = closest_hit<kCanon>(S, o2, nd, t);
         if (prim < 0) return;
 #pragma unroll
@@ -286,6 +296,7 @@ struct PtArgs {
     float em[3];
     int W, H, spp, depth;
     const float* target;
+    unsigned long long* stats;   // counting instantiation only: see hr_scene_stats
 };
 
 __device__ void load_scene(const PtArgs& A, const float* p, PtShared& S) {
@@ -332,10 +343,11 @@ __device__ void load_scene(const PtArgs& A, const float* p, PtShared& S) {
     }
 }
 
-template <bool kImage, int kMinBlocks, bool kCanon>
+template <bool kImage, int kMinBlocks, bool kCanon, bool kCount = false>
 __global__ void __launch_bounds__(kThreads, kMinBlocks)
 ptbox_kernel(PtArgs A, RenderBatch b, const float* __restrict__ img_params, uint64_t seed_img, uint32_t req_img,
              uint32_t sub_img, uint32_t k_img, uint32_t tag_img, int spp_img, float* __restrict__ img) {
+    PtCount cnt;
     __shared__ PtShared S;
     __shared__ float s_p[8];
     __shared__ float s_part[kThreads / 32];
@@ -374,7 +386,7 @@ ptbox_kernel(PtArgs A, RenderBatch b, const float* __restrict__ img_params, uint
             const float il = __frcp_rn(__fsqrt_rn(dot3(d, d)));
             d[0] = __fmul_rn(d[0], il); d[1] = __fmul_rn(d[1], il); d[2] = __fmul_rn(d[2], il);
             float o[3] = {0.0f, 0.0f, A.cam_z};
-            radiance<kCanon>(S, A.depth, seed, request, c2, k, idx, o, d, L);
+            radiance<kCanon, kCount>(S, A.depth, seed, request, c2, k, idx, o, d, L, cnt);
         }
         const size_t p3 = 3 * (size_t)px;
         if (kImage) {
@@ -385,6 +397,17 @@ ptbox_kernel(PtArgs A, RenderBatch b, const float* __restrict__ img_params, uint
             const float d2 = L[2] * inv_spp - A.target[p3 + 2];
             acc += d0 * d0 + d1 * d1 + d2 * d2;
         }
+    }
+    if (kCount && A.stats) {   // [0] renders, [1] closest-hit rays, [2] shadow rays, [3] shaded vertices
+        const unsigned long long h = (unsigned long long)warp_sum_i((int)cnt.hit);
+        const unsigned long long sh = (unsigned long long)warp_sum_i((int)cnt.shadow);
+        const unsigned long long vt = (unsigned long long)warp_sum_i((int)cnt.vert);
+        if ((tid & 31) == 0) {
+            atomicAdd(&A.stats[1], h);
+            atomicAdd(&A.stats[2], sh);
+            atomicAdd(&A.stats[3], vt);
+        }
+        if (tid == 0) atomicAdd(&A.stats[0], 1ull);
     }
     if (!kImage) {
         acc = warp_sum(acc);
@@ -413,6 +436,7 @@ PtArgs make_args(const DevScene& sc) {
     for (int c = 0; c < 3; ++c) a.em[c] = sc.emission[c];
     a.W = sc.W; a.H = sc.H; a.spp = sc.spp; a.depth = sc.depth;
     a.target = sc.target;
+    a.stats = sc.pt_stats;
     return a;
 }
 
@@ -427,6 +451,10 @@ bool canonical_axes(const DevScene& sc) {
 template <bool kCanon>
 void launch_loss(const DevScene& sc, const RenderBatch& b, cudaStream_t s) {
     const PtArgs a = make_args(sc);
+    if (sc.count_work && a.stats) {   // work counting (diagnostics), default launch shape
+        ptbox_kernel<false, 3, kCanon, true><<<b.M, kThreads, 0, s>>>(a, b, nullptr, 0, 0, 0, 0, 0, 0, nullptr);
+        return;
+    }
     switch (sc.render_variant) {
         case 1: ptbox_kernel<false, 2, kCanon><<<b.M, kThreads, 0, s>>>(a, b, nullptr, 0, 0, 0, 0, 0, 0, nullptr); break;
         case 2: ptbox_kernel<false, 4, kCanon><<<b.M, kThreads, 0, s>>>(a, b, nullptr, 0, 0, 0, 0, 0, 0, nullptr); break;

@@ -82,7 +82,8 @@ class hr_scene_stats(ctypes.Structure):
     _fields_ = [("mesh_overflow_renders", ctypes.c_int64), ("mesh_renders", ctypes.c_int64),
                 ("mesh_survivors", ctypes.c_int64), ("mesh_bin_entries", ctypes.c_int64),
                 ("mesh_tiles_with_entries", ctypes.c_int64), ("mesh_raster_steps", ctypes.c_int64),
-                ("mesh_tile_height", ctypes.c_int64)]
+                ("mesh_tile_height", ctypes.c_int64), ("pt_counted_renders", ctypes.c_int64),
+                ("pt_hit_rays", ctypes.c_int64), ("pt_shadow_rays", ctypes.c_int64), ("pt_vertices", ctypes.c_int64)]
 
 
 class hr_tune_info(ctypes.Structure):
@@ -147,6 +148,7 @@ def lib() -> ctypes.CDLL:
         L.hr_ncg_trace.argtypes = [vp, _f64p, _f64p, _f64p]
         L.hr_scene_get_stats.argtypes = [vp, ctypes.POINTER(hr_scene_stats)]
         L.hr_render_ids.argtypes = [vp, _f64p, ctypes.POINTER(ctypes.c_int32)]
+        L.hr_scene_count_work.argtypes = [vp, ctypes.c_int32]
         L.hr_autotune.argtypes = [vp, _f64p, ctypes.c_int32, ctypes.POINTER(hr_tune_info)]
         L.hr_set_tuning.argtypes = [vp, ctypes.c_int32, ctypes.c_int32]
         L.hr_profile_enable.argtypes = [vp, ctypes.c_int32]
@@ -164,7 +166,7 @@ def lib() -> ctypes.CDLL:
                      "hr_optstate_destroy", "hr_newton_cg_step", "hr_optstate_theta", "hr_profile_enable",
                      "hr_profile_last", "hr_server_create", "hr_server_destroy", "hr_server_submit",
                      "hr_server_wait", "hr_ncg_create", "hr_ncg_destroy", "hr_ncg_run", "hr_ncg_theta",
-                     "hr_autotune", "hr_set_tuning", "hr_scene_get_stats", "hr_optstate_trace", "hr_ncg_trace", "hr_render_ids"):
+                     "hr_autotune", "hr_set_tuning", "hr_scene_get_stats", "hr_optstate_trace", "hr_ncg_trace", "hr_render_ids", "hr_scene_count_work"):
             getattr(L, name).restype = ctypes.c_int32
         L.hr_version.restype = ctypes.c_int32
         _lib = L
@@ -260,6 +262,10 @@ def hr_render_ids(handle, params, W, H) -> np.ndarray:
     check(lib().hr_render_ids(handle, _ptr(p, _f64p), out.ctypes.data_as(ctypes.POINTER(ctypes.c_int32))),
           "hr_render_ids")
     return out
+
+
+def hr_scene_count_work(handle, on: bool):
+    check(lib().hr_scene_count_work(handle, int(on)), "hr_scene_count_work")
 
 
 def hr_scene_get_stats(handle) -> hr_scene_stats:

@@ -293,6 +293,30 @@ def test_ptbox_hvp_small():
     assert_estimate_close(flat, ref, what="ptbox hvp")
 
 
+def test_ptbox_work_counts_match_oracle_and_leave_results_unchanged():
+    """The counting build of the path tracer (used to measure its work per
+    render) returns the same losses and estimate as the timed build, and its
+    closest-hit rays, shadow rays and shaded vertices equal the oracle path
+    tracer's counts on the same perturbations and path random numbers."""
+    sc = wl.ptbox_scene(width=24, height=20, spp=2, target_spp=4)
+    Sc = hr.Scene(sc)
+    theta, v, M = np.asarray(sc["theta_query"]), sc["v"], 16
+    out0, dbg0 = Sc.estimate(hr.HR_HVP, theta, sc["sigma"], M, hr.HR_AGGREGATE, 5, 6, 0, v=v, debug=True)
+    hr.hr_scene_count_work(Sc.handle, True)
+    out1, dbg1 = Sc.estimate(hr.HR_HVP, theta, sc["sigma"], M, hr.HR_AGGREGATE, 5, 6, 0, v=v, debug=True)
+    hr.hr_scene_count_work(Sc.handle, False)
+    st = hr.hr_scene_get_stats(Sc.handle)
+    Sc.close()
+    assert np.array_equal(dbg0["losses"], dbg1["losses"]) and np.array_equal(out0, out1)
+    r = O.PtboxRenderer(sc)
+    tau, _ = O.draw(1, 6, sc["sigma"], M // 2, 5, 6, 0)
+    ref = np.zeros(3, np.int64)
+    for m in range(M):
+        ref += r.count_rays(O.perturb(theta, tau[m]), dict(seed=5, request=6, sub=0, k=m // 2))
+    assert st.pt_counted_renders == M
+    assert (st.pt_hit_rays, st.pt_shadow_rays, st.pt_vertices) == tuple(int(x) for x in ref)
+
+
 def _host_threads():
     try:
         return len(os.sched_getaffinity(0))

@@ -50,8 +50,8 @@ METRIC = "Hessian/HVP estimates/s at oracle-matched error; perturbed renders/s; 
 # (read + write) of one render+loss launch, and the fraction of instruction
 # issue slots busy (smsp__issue_active) — the kernel is bound by compare /
 # select issue on the ALU pipe rather than by FP32 arithmetic.
-TRAFFIC_BYTES = None
-ISSUE_ACTIVE_NCU = None
+TRAFFIC_BYTES = 530176
+ISSUE_ACTIVE_NCU = 0.671
 M_PERTURB = 4096
 SEED = 2024
 

@@ -58,6 +58,8 @@ struct __align__(16) TriRec {
 __device__ __forceinline__ uint32_t entry_word(int tri, uint32_t rows, uint32_t cols) {
     return ((uint32_t)tri << 16) | ((~rows & 0xFFu) << 8) | (~cols & 0xFFu);
 }
+// an entry no pixel is in (record 0, every row and column outside)
+constexpr uint32_t kSentinel = 0x0000FFFFu;
 // bits lo..hi (clamped to 0..7) of a byte
 __device__ __forceinline__ uint32_t span_bits(int lo, int hi) {
     lo = max(lo, 0);
@@ -168,32 +170,46 @@ __device__ int bin_scan(const int* cnt, int* off, uint16_t* olist, int T, int* w
     return warp_tot[32];
 }
 
-// One pixel against one bin entry, written as PTX predicate chains: the
-// pixel is in when its row and column bits of the entry's outside mask are
-// clear (column c, row bit row_out) and E_i > th_i for the three edges; it
-// takes the entry when also wz > bw (strict); t4 becomes non-zero when wz ==
-// bw (an exact depth tie, resolved by a second, exact walk of the tile).
-template <int c>
-__device__ __forceinline__ void pixel_test(float E0, float E1, float E2, float wz, float th0, float th1, float th2,
-                                           uint32_t outside, uint32_t row_out, int s, float& bw, int& bs,
-                                           uint32_t& t4) {
+// The four pixels of a lane against one bin entry, as PTX predicate chains.
+// Pixel c (x coordinate fx_c) is in when its row and column bits of the
+// entry's outside mask are clear (row bit row_out, column bit c) and
+// E_i = fma(A_i, fx_c, r_i) > th_i for the three edges; it takes the entry
+// when also wz = fma(Aw, fx_c, rw) > bw_c (strict).  t4 becomes non-zero when
+// some wz == bw_c (an exact depth tie, resolved by a second, exact walk of
+// the tile).
+__device__ __forceinline__ void pixels4(const float4& q0, const float4& q1, const float4& q2, float Aw, float r0,
+                                        float r1, float r2, float rw, const float fx[4], uint32_t outside,
+                                        uint32_t row_out, int s, float bw[4], int bs[4], uint32_t& t4) {
     asm("{\n\t"
         ".reg .pred p, q;\n\t"
         ".reg .b32 m;\n\t"
-        "lop3.b32 m, %7, %8, %11, 0xE0;\n\t"        // outside & (row_out | column bit)
-        "setp.eq.u32 p, m, 0;\n\t"
-        "setp.gt.and.f32 p, %3, %4, p;\n\t"
-        "setp.gt.and.f32 p, %5, %6, p;\n\t"
-        "setp.gt.and.f32 p, %9, %10, p;\n\t"
-        "setp.eq.f32 q, %12, %0;\n\t"
-        "setp.gt.and.f32 p, %12, %0, p;\n\t"
-        "selp.f32 %0, %12, %0, p;\n\t"
-        "selp.b32 %1, %13, %1, p;\n\t"
-        "@q or.b32 %2, %2, 1;\n\t"
+        ".reg .f32 e0, e1, e2, w;\n\t"
+        "setp.ne.u32 q, 0, 0;\n\t"
+#define HR_PIXEL(C, FX, BW, BS)                                 \
+        "lop3.b32 m, %18, %19, " #C ", 0xE0;\n\t"              \
+        "setp.eq.u32 p, m, 0;\n\t"                             \
+        "fma.rn.f32 e0, %9, " FX ", %13;\n\t"                  \
+        "fma.rn.f32 e1, %10, " FX ", %14;\n\t"                 \
+        "fma.rn.f32 e2, %11, " FX ", %15;\n\t"                 \
+        "fma.rn.f32 w, %12, " FX ", %16;\n\t"                  \
+        "setp.gt.and.f32 p, e0, %21, p;\n\t"                   \
+        "setp.gt.and.f32 p, e1, %22, p;\n\t"                   \
+        "setp.gt.and.f32 p, e2, %23, p;\n\t"                   \
+        "setp.eq.or.f32 q, w, " BW ", q;\n\t"                  \
+        "setp.gt.and.f32 p, w, " BW ", p;\n\t"                 \
+        "selp.f32 " BW ", w, " BW ", p;\n\t"                   \
+        "selp.b32 " BS ", %20, " BS ", p;\n\t"
+        HR_PIXEL(1, "%17", "%0", "%4")
+        HR_PIXEL(2, "%24", "%1", "%5")
+        HR_PIXEL(4, "%25", "%2", "%6")
+        HR_PIXEL(8, "%26", "%3", "%7")
+#undef HR_PIXEL
+        "@q or.b32 %8, %8, 1;\n\t"
         "}"
-        : "+f"(bw), "+r"(bs), "+r"(t4)
-        : "f"(E0), "f"(th0), "f"(E1), "f"(th1), "r"(outside), "r"(row_out), "f"(E2), "f"(th2), "n"(1u << c),
-          "f"(wz), "r"(s));
+        : "+f"(bw[0]), "+f"(bw[1]), "+f"(bw[2]), "+f"(bw[3]), "+r"(bs[0]), "+r"(bs[1]), "+r"(bs[2]), "+r"(bs[3]),
+          "+r"(t4)
+        : "f"(q0.x), "f"(q1.x), "f"(q2.x), "f"(Aw), "f"(r0), "f"(r1), "f"(r2), "f"(rw), "f"(fx[0]), "r"(outside),
+          "r"(row_out), "r"(s), "f"(q0.w), "f"(q1.w), "f"(q2.w), "f"(fx[1]), "f"(fx[2]), "f"(fx[3]));
 }
 
 // rotation angle d of perturbation m: RN32(theta32 + tau)
@@ -527,25 +543,19 @@ revolve_kernel(RvArgs P, RenderBatch b, const float* __restrict__ img_params, fl
                     }
                 } else {
                     uint32_t t4 = 0u;
-                    pixel_test<0>(__fmaf_rn(q0.x, fx[0], r0), __fmaf_rn(q1.x, fx[0], r1), __fmaf_rn(q2.x, fx[0], r2),
-                                  __fmaf_rn(q3.x, fx[0], rw), q0.w, q1.w, q2.w, outside, row_out, s, bw[0], bs[0], t4);
-                    pixel_test<1>(__fmaf_rn(q0.x, fx[1], r0), __fmaf_rn(q1.x, fx[1], r1), __fmaf_rn(q2.x, fx[1], r2),
-                                  __fmaf_rn(q3.x, fx[1], rw), q0.w, q1.w, q2.w, outside, row_out, s, bw[1], bs[1], t4);
-                    pixel_test<2>(__fmaf_rn(q0.x, fx[2], r0), __fmaf_rn(q1.x, fx[2], r1), __fmaf_rn(q2.x, fx[2], r2),
-                                  __fmaf_rn(q3.x, fx[2], rw), q0.w, q1.w, q2.w, outside, row_out, s, bw[2], bs[2], t4);
-                    pixel_test<3>(__fmaf_rn(q0.x, fx[3], r0), __fmaf_rn(q1.x, fx[3], r1), __fmaf_rn(q2.x, fx[3], r2),
-                                  __fmaf_rn(q3.x, fx[3], rw), q0.w, q1.w, q2.w, outside, row_out, s, bw[3], bs[3], t4);
+                    pixels4(q0, q1, q2, q3.x, r0, r1, r2, rw, fx, outside, row_out, s, bw, bs, t4);
                     tie_u |= t4;
                 }
             };
             if (!overflow) {
                 const int n_max = (int)__reduce_max_sync(0xffffffffu, (unsigned)n_mine);
                 if (!kImage && lane == 0 && P.stats) atomicAdd(&P.stats[5], (unsigned long long)n_max);
+                // a group whose bin is shorter walks a sentinel entry (every
+                // row and column outside: no pixel is in) instead of
+                // branching around the step
                 for (int k = 0; k < n_max; ++k) {
-                    if (k < n_mine) {
-                        const uint32_t e = ent[beg + k];
-                        raster_entry((int)(e >> 16), e >> col_shift, false);
-                    }
+                    const uint32_t e = k < n_mine ? ent[beg + k] : kSentinel;
+                    raster_entry((int)(e >> 16), e >> col_shift, false);
                 }
                 if (__any_sync(0xffffffffu, tie_u != 0u)) {
 #pragma unroll
@@ -554,10 +564,8 @@ revolve_kernel(RvArgs P, RenderBatch b, const float* __restrict__ img_params, fl
                         bs[c] = INT_MAX;
                     }
                     for (int k = 0; k < n_max; ++k) {
-                        if (k < n_mine) {
-                            const uint32_t e = ent[beg + k];
-                            raster_entry((int)(e >> 16), e >> col_shift, true);
-                        }
+                        const uint32_t e = k < n_mine ? ent[beg + k] : kSentinel;
+                        raster_entry((int)(e >> 16), e >> col_shift, true);
                     }
                 }
             } else {

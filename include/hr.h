@@ -458,6 +458,57 @@ hr_status hr_server_submit(hr_server srv, const hr_request* req, uint64_t* ticke
  * returned and the ticket stays valid.  A ticket can be waited for once. */
 hr_status hr_server_wait(hr_server srv, uint64_t ticket, void* h_out, hr_request_info* info, int32_t timeout_ms);
 
+/* ---------------------------------------------------------------------------
+ * Persistent queue (disc scenes): estimate requests of one DISC2D scene served
+ * by one long-running kernel (Sec. 3.2-3.5 estimators, Sec. 4.1 disc task).
+ * A request's perturbations are sampled, rendered and summed inside that
+ * kernel, in units of 16 antithetic pairs taken by whichever warp is free;
+ * the warp that finishes a request's last unit forms its sums in the same
+ * order as hr_estimate_*, so the result is bit-identical to hr_estimate_* with
+ * the same options.  Submission makes no driver call: the descriptor goes into
+ * host-mapped memory that the kernel polls.
+ *
+ * The kernel leaves after idle_budget_us without a new request (its polling
+ * is bounded by clock64(), never an unbounded spin) and records HR_ERR_TIMEOUT
+ * as its exit status; the next hr_queue_submit or hr_queue_wait launches it
+ * again.  It occupies every SM while it runs, so other work on the GPU shares
+ * the SMs with it during that time.
+ *
+ * One queue per scene at a time; destroy the queue before its scene.  The
+ * functions may be called from several host threads (one lock per queue).
+ * ------------------------------------------------------------------------- */
+typedef struct hr_queue_s* hr_queue;
+
+typedef struct {
+    int32_t max_requests;    /* ring slots: requests submitted and not yet waited for, 1..65536 */
+    int32_t idle_budget_us;  /* the kernel leaves after this long without a new request, 1..10^7 */
+    int64_t arena_bytes;     /* device bytes for the perturbations, weights and losses of
+                                unfinished requests (>= 1 MiB); a request takes
+                                about G M (n + E + 1) 4 bytes */
+} hr_queue_opts;
+
+/* HR_ERR_UNSUPPORTED unless the scene is DISC2D; HR_ERR_OOM if the device or
+ * host-mapped memory cannot be had. */
+hr_status hr_queue_create(hr_scene scene, const hr_queue_opts* opts, hr_queue* out);
+/* Queue one estimate (HR_GRAD, HR_HESSIAN or HR_HVP; h_theta [n] and h_v [n]
+ * host, copied).  opts: sigma, n_perturb, strategy, seed, request_id and sub
+ * as in hr_estimate_*; stream and inspection outputs are ignored.  At most 4
+ * sample groups (element-wise Hessians of n = 2 have 3).  HR_ERR_BUSY, with
+ * nothing queued, when the ring slot of the next ticket still holds a result
+ * not waited for, or when the arena has no room until earlier requests
+ * finish: wait for an earlier ticket and submit again. */
+hr_status hr_queue_submit(hr_queue q, int32_t quantity, const double* h_theta, const double* h_v,
+                          const hr_opts* opts, uint64_t* ticket);
+/* Wait for a ticket; h_out (host) receives n doubles (gradient, HVP) or n*n
+ * (Hessian).  timeout_ms < 0 waits without limit; on timeout HR_ERR_TIMEOUT is
+ * returned and the ticket stays valid.  A ticket can be waited for once. */
+hr_status hr_queue_wait(hr_queue q, uint64_t ticket, double* h_out, int32_t timeout_ms);
+/* *kernel_status: 1 while the kernel runs; after it left, HR_ERR_TIMEOUT (idle
+ * budget spent) or HR_OK.  *launches (may be NULL): launches so far. */
+hr_status hr_queue_status(hr_queue q, int32_t* kernel_status, uint64_t* launches);
+/* Lets the kernel finish the requests already submitted, then frees the queue. */
+hr_status hr_queue_destroy(hr_queue q);
+
 /* Diagnostics of a scene's mesh renders since its creation, summed over
  * renders (waits for the device); all 0 for kinds other than REVOLVE3D.
  *   mesh_overflow_renders   renders whose tile bins held more (triangle,

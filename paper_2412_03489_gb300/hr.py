@@ -19,6 +19,7 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(HERE, "_build", "libhr.so")
 
 HR_OK = 0
+HR_ERR_INVALID_ARG, HR_ERR_OOM, HR_ERR_CUDA, HR_ERR_TIMEOUT, HR_ERR_BUSY, HR_ERR_UNSUPPORTED = -1, -2, -3, -4, -5, -6
 HR_ELEMENTWISE, HR_AGGREGATE, HR_PLAIN = 0, 1, 2
 HR_GRAD, HR_HESSIAN, HR_HVP = 0, 1, 2
 TAG_PATH, TAG_TARGET = 2, 3
@@ -96,6 +97,10 @@ class hr_server_opts(ctypes.Structure):
     _fields_ = [("hbm_budget", ctypes.c_int64), ("max_active", ctypes.c_int32), ("chunk", ctypes.c_int32)]
 
 
+class hr_queue_opts(ctypes.Structure):
+    _fields_ = [("max_requests", ctypes.c_int32), ("idle_budget_us", ctypes.c_int32), ("arena_bytes", ctypes.c_int64)]
+
+
 class hr_request(ctypes.Structure):
     _fields_ = [("scene", ctypes.c_void_p), ("quantity", ctypes.c_int32), ("h_theta", _f64p), ("h_v", _f64p),
                 ("opts", hr_opts), ("optstate", ctypes.c_void_p)]
@@ -110,7 +115,11 @@ HR_NEWTON_STEP = 3
 
 
 class HRError(RuntimeError):
-    pass
+    """A failed call; `status` holds the library's status code."""
+
+    def __init__(self, msg: str, status: int = 0):
+        super().__init__(msg)
+        self.status = status
 
 
 _lib = None
@@ -157,6 +166,12 @@ def lib() -> ctypes.CDLL:
         L.hr_server_destroy.argtypes = [vp]
         L.hr_server_submit.argtypes = [vp, ctypes.POINTER(hr_request), ctypes.POINTER(ctypes.c_uint64)]
         L.hr_server_wait.argtypes = [vp, ctypes.c_uint64, vp, ctypes.POINTER(hr_request_info), ctypes.c_int32]
+        L.hr_queue_create.argtypes = [vp, ctypes.POINTER(hr_queue_opts), ctypes.POINTER(vp)]
+        L.hr_queue_submit.argtypes = [vp, ctypes.c_int32, _f64p, _f64p, ctypes.POINTER(hr_opts),
+                                      ctypes.POINTER(ctypes.c_uint64)]
+        L.hr_queue_wait.argtypes = [vp, ctypes.c_uint64, _f64p, ctypes.c_int32]
+        L.hr_queue_status.argtypes = [vp, ctypes.POINTER(ctypes.c_int32), ctypes.POINTER(ctypes.c_uint64)]
+        L.hr_queue_destroy.argtypes = [vp]
         L.hr_last_error.argtypes = [ctypes.c_char_p, ctypes.c_size_t]
         L.hr_last_error.restype = ctypes.c_size_t
         for name in ("hr_create_scene", "hr_destroy_scene", "hr_estimate_grad", "hr_estimate_hessian",
@@ -166,7 +181,8 @@ def lib() -> ctypes.CDLL:
                      "hr_optstate_destroy", "hr_newton_cg_step", "hr_optstate_theta", "hr_profile_enable",
                      "hr_profile_last", "hr_server_create", "hr_server_destroy", "hr_server_submit",
                      "hr_server_wait", "hr_ncg_create", "hr_ncg_destroy", "hr_ncg_run", "hr_ncg_theta",
-                     "hr_autotune", "hr_set_tuning", "hr_scene_get_stats", "hr_optstate_trace", "hr_ncg_trace", "hr_render_ids", "hr_scene_count_work"):
+                     "hr_autotune", "hr_set_tuning", "hr_scene_get_stats", "hr_optstate_trace", "hr_ncg_trace", "hr_render_ids", "hr_scene_count_work",
+                     "hr_queue_create", "hr_queue_submit", "hr_queue_wait", "hr_queue_status", "hr_queue_destroy"):
             getattr(L, name).restype = ctypes.c_int32
         L.hr_version.restype = ctypes.c_int32
         _lib = L
@@ -181,7 +197,7 @@ def hr_last_error() -> str:
 
 def check(status: int, what: str = "") -> None:
     if status != HR_OK:
-        raise HRError(f"{what} failed with status {status}: {hr_last_error()}")
+        raise HRError(f"{what} failed with status {status}: {hr_last_error()}", status)
 
 
 def _ptr(a, t):
@@ -473,6 +489,43 @@ def hr_server_submit(srv: int, req: hr_request) -> int:
 def hr_server_wait(srv: int, ticket: int, out, info: hr_request_info, timeout_ms: int = 120000) -> None:
     ptr = None if out is None else (out.ctypes.data if isinstance(out, np.ndarray) else ctypes.addressof(out))
     check(lib().hr_server_wait(srv, ticket, ptr, ctypes.byref(info), int(timeout_ms)), "hr_server_wait")
+
+
+# ---------------------------------------------------------------------------
+# persistent queue (disc scenes)
+# ---------------------------------------------------------------------------
+def hr_queue_create(scene: "Scene", max_requests: int = 1024, idle_budget_us: int = 2000,
+                    arena_bytes: int = 256 << 20) -> int:
+    o = hr_queue_opts(int(max_requests), int(idle_budget_us), int(arena_bytes))
+    h = ctypes.c_void_p()
+    check(lib().hr_queue_create(scene.handle, ctypes.byref(o), ctypes.byref(h)), "hr_queue_create")
+    return h.value
+
+
+def hr_queue_submit(q: int, quantity: int, theta, v, opts: hr_opts) -> int:
+    """Queue one estimate; raises HRError with status HR_ERR_BUSY when the ring
+    or the arena is full (nothing queued)."""
+    t = ctypes.c_uint64()
+    th = np.ascontiguousarray(theta, np.float64)
+    vv = None if v is None else np.ascontiguousarray(v, np.float64)
+    check(lib().hr_queue_submit(q, int(quantity), _ptr(th, _f64p), _ptr(vv, _f64p), ctypes.byref(opts),
+                                ctypes.byref(t)), "hr_queue_submit")
+    return t.value
+
+
+def hr_queue_wait(q: int, ticket: int, out: np.ndarray, timeout_ms: int = 120000) -> None:
+    check(lib().hr_queue_wait(q, int(ticket), _ptr(out, _f64p), int(timeout_ms)), "hr_queue_wait")
+
+
+def hr_queue_status(q: int):
+    """(kernel status: 1 running, else its exit code; launches so far)."""
+    st, n = ctypes.c_int32(), ctypes.c_uint64()
+    check(lib().hr_queue_status(q, ctypes.byref(st), ctypes.byref(n)), "hr_queue_status")
+    return st.value, n.value
+
+
+def hr_queue_destroy(q: int) -> None:
+    check(lib().hr_queue_destroy(q), "hr_queue_destroy")
 
 
 def make_request(scene: "Scene", quantity: int, theta=None, v=None, opts: hr_opts = None, optstate=None):

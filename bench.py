@@ -20,10 +20,12 @@ on a bounded sample with one thread (`single_thread`).
 `secondary` (rank 0, after the headline's timed region; --no-secondary
 skips it) reports the other configurations compactly: the path-traced HVP
 (8,192 perturbations) with its roofline from counted rays, one batched
-Newton-CG step (64 instances, CUDA graph), and serving on a seeded stream
-of 1,200 requests against the same requests one at a time; the path
-tracer's
-sampled renders are checked against the oracle in the cpu_baseline leg.
+Newton-CG step (64 instances, CUDA graph), serving on a seeded stream of
+1,200 requests against the same requests one at a time, and the disc
+configuration's element-wise Hessians through the persistent queue (one
+resident launch, batched host submission) against the same requests one at
+a time; the path tracer's sampled renders are checked against the oracle in
+the cpu_baseline leg.
 
 Multi-GPU: estimates are independent, so N ranks run N replicas (weak
 scaling, no collective on the data path); `value` = all ranks' estimates /
@@ -32,6 +34,7 @@ the slowest rank's time.
 from __future__ import annotations
 
 import argparse
+import ctypes
 import json
 import math
 import os
@@ -50,8 +53,8 @@ METRIC = "Hessian/HVP estimates/s at oracle-matched error; perturbed renders/s; 
 # (read + write) of one render+loss launch, and the fraction of instruction
 # issue slots busy (smsp__issue_active) — the kernel is bound by compare /
 # select issue on the ALU pipe rather than by FP32 arithmetic.
-TRAFFIC_BYTES = 530176
-ISSUE_ACTIVE_NCU = 0.671
+TRAFFIC_BYTES = 528896
+ISSUE_ACTIVE_NCU = 0.651
 M_PERTURB = 4096
 SEED = 2024
 
@@ -190,7 +193,89 @@ def secondary_workloads(torch, hr, wl, stream, flush, peaks, n_sm):
                       "served_saturated_estimates_per_s": sv["served_saturated"]["estimates_per_s"],
                       "speedup_vs_plain": sv["served_saturated"]["speedup_vs_plain"],
                       "results_identical_to_plain": sv["served_saturated"]["results_identical_to_plain"]}
+    out["disc_queue"] = disc_queue_bench(torch, hr, wl, stream, flush)
     return out
+
+
+def disc_queue_bench(torch, hr, wl, stream, flush, n_requests=20000, batch=512, window=4096):
+    """The disc configuration's element-wise Hessians (64x64, n = 2, 3 x 1024
+    perturbations each) through the persistent queue, end to end from host
+    arrays to host results: requests go in with hr_queue_submit_many in
+    batches, at most `window` in flight, and come back with hr_queue_wait_many.
+    Beside it the same requests one at a time: through hr_estimate_dev timed
+    on the device (sampler, render, sums: three launches per estimate) and
+    through the host entry point hr_estimate_hessian.  A single request's
+    submit-to-result latency through the queue is sampled alone."""
+    sc = wl.disc_scene()
+    S = hr.Scene(sc)
+    M = 1024
+    g = np.random.default_rng(SEED)
+    thetas = np.asarray(sc["theta_query"], np.float64) + g.normal(0.0, 0.01, (n_requests, 2))
+    seeds = np.arange(n_requests) + SEED
+    arr = hr.opts_array(sc["sigma"], M, hr.HR_ELEMENTWISE, seeds, np.arange(n_requests))
+    osz = ctypes.sizeof(hr.hr_opts)
+    # plain, one request at a time: device-timed (hr_estimate_dev) and host entry point
+    d_theta = torch.tensor(thetas[0], dtype=torch.float64, device="cuda")
+    d_out = torch.zeros((2, 2), dtype=torch.float64, device="cuda")
+    n_dev = 2000
+
+    def dev_batch(i):
+        for k in range(n_dev):
+            o = hr.make_opts(sc["sigma"], M, hr.HR_ELEMENTWISE, int(seeds[k]), k, stream=stream.cuda_stream)
+            hr.hr_estimate_dev(S.handle, hr.HR_HESSIAN, d_theta.data_ptr(), None, o, d_out.data_ptr())
+    dev_ms = float(np.mean(_timed_steps(torch, stream, flush, dev_batch, 1, 2))) / n_dev
+    host_out = np.zeros((2, 2))
+    t0 = time.perf_counter()
+    for k in range(n_dev):
+        hr.hr_estimate_hessian(S.handle, thetas[k], arr[k], host_out)
+    host_s = (time.perf_counter() - t0) / n_dev
+    # through the queue
+    q = hr.hr_queue_create(S, max_requests=window, idle_budget_us=2000, arena_bytes=1 << 30)
+    out = np.zeros((n_requests, 4))
+
+    def run_all():
+        sub, waited, inflight = 0, 0, []
+        while waited < n_requests:
+            if sub < n_requests and sub - waited < window:
+                cnt = min(batch, n_requests - sub, window - (sub - waited))
+                view = (hr.hr_opts * cnt).from_buffer(arr, sub * osz)
+                t = hr.hr_queue_submit_many(q, hr.HR_HESSIAN, thetas[sub:sub + cnt], None, view)
+                if len(t):
+                    inflight.append((sub, t))
+                    sub += len(t)
+                if len(t) == cnt:
+                    continue
+            st, t = inflight.pop(0)
+            hr.hr_queue_wait_many(q, t, out[st:st + len(t)])
+            waited += len(t)
+    run_all()                                   # warm-up pass
+    t0 = time.perf_counter()
+    run_all()
+    q_s = time.perf_counter() - t0
+    lat = []
+    one = np.zeros((1, 4))
+    for k in range(300):
+        view = (hr.hr_opts * 1).from_buffer(arr, k * osz)
+        a = time.perf_counter()
+        t = hr.hr_queue_submit_many(q, hr.HR_HESSIAN, thetas[k:k + 1], None, view)
+        hr.hr_queue_wait_many(q, t, one)
+        lat.append(time.perf_counter() - a)
+    status, launches = hr.hr_queue_status(q)
+    hr.hr_queue_destroy(q)
+    same = True
+    for k in list(range(0, n_requests, n_requests // 64)) + [n_requests - 1]:
+        hr.hr_estimate_hessian(S.handle, thetas[k], arr[k], host_out)
+        same &= bool(np.array_equal(host_out.ravel(), out[k]))
+    S.close()
+    rate = n_requests / q_s
+    return {"workload": "disc2d 64x64 gray, r 0.2, 2 params, sigma 0.05, element-wise Hessian, 3 x 1024 "
+                        "perturbations", "requests": n_requests, "batch": batch, "window": window,
+            "queue_estimates_per_s": rate, "queue_renders_per_s": rate * 3 * M,
+            "plain_device_estimates_per_s": 1e3 / dev_ms, "plain_host_estimates_per_s": 1.0 / host_s,
+            "speedup_vs_plain_device": rate * dev_ms / 1e3,
+            "alone_latency_us": {"p50": 1e6 * float(np.percentile(lat, 50)),
+                                 "p99": 1e6 * float(np.percentile(lat, 99))},
+            "launches": int(launches), "results_identical_to_plain": same}
 
 
 def ptbox_oracle_match(hr, wl):
@@ -459,6 +544,8 @@ def run_secondary(args):
                                          "p99": float(np.percentile(times, 99))},
                           "stage_ms": dict(zip(("sample", "render_loss", "sums"),
                                                np.mean(stage, axis=0).tolist()))}
+        if args.workload == "disc":
+            line["queue"] = disc_queue_bench(torch, hr, wl, stream, flush)
         line["config"] = ({"workload": "disc2d 64x64 gray, r 0.2, 2 params, sigma 0.05"} if args.workload == "disc"
                           else {"workload": "path-traced box 128x128 RGB, 4 spp, depth 3, 6 params, sigma 0.05, "
                                             "aggregate HVP, 8192 perturbations"})

@@ -499,10 +499,23 @@ hr_status hr_queue_create(hr_scene scene, const hr_queue_opts* opts, hr_queue* o
  * finish: wait for an earlier ticket and submit again. */
 hr_status hr_queue_submit(hr_queue q, int32_t quantity, const double* h_theta, const double* h_v,
                           const hr_opts* opts, uint64_t* ticket);
+/* Queue count estimates of one quantity in one call: h_theta [count][n],
+ * h_v [count][n] (HVP, else NULL), opts [count] (host).  All are checked
+ * first (HR_ERR_INVALID_ARG queues none); then they are queued in order until
+ * the ring or the arena is full.  *submitted receives how many were queued and
+ * tickets [0, *submitted) their tickets; HR_ERR_BUSY when fewer than count. */
+hr_status hr_queue_submit_many(hr_queue q, int32_t count, int32_t quantity, const double* h_theta,
+                               const double* h_v, const hr_opts* opts, uint64_t* tickets, int32_t* submitted);
 /* Wait for a ticket; h_out (host) receives n doubles (gradient, HVP) or n*n
  * (Hessian).  timeout_ms < 0 waits without limit; on timeout HR_ERR_TIMEOUT is
  * returned and the ticket stays valid.  A ticket can be waited for once. */
 hr_status hr_queue_wait(hr_queue q, uint64_t ticket, double* h_out, int32_t timeout_ms);
+/* Wait for count tickets in order; result i goes to h_out + i * out_stride
+ * (host; out_stride >= every result's size, else HR_ERR_INVALID_ARG before any
+ * wait).  timeout_ms bounds the whole call; on an error, the results of the
+ * tickets before the failing one have been delivered. */
+hr_status hr_queue_wait_many(hr_queue q, int32_t count, const uint64_t* tickets, double* h_out,
+                             int32_t out_stride, int32_t timeout_ms);
 /* *kernel_status: 1 while the kernel runs; after it left, HR_ERR_TIMEOUT (idle
  * budget spent) or HR_OK.  *launches (may be NULL): launches so far. */
 hr_status hr_queue_status(hr_queue q, int32_t* kernel_status, uint64_t* launches);

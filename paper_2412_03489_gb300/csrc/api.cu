@@ -567,6 +567,8 @@ hr_status hr_create_scene(const hr_scene_desc* d, hr_scene* out) {
         if (e != cudaSuccess) return bail(e, "target render");
     }
     if (sc.kind == HR_SCENE_REVOLVE3D) revolve_tile_t2(sc, s->stream);
+    if (sc.kind == HR_SCENE_DISC2D && (e = disc_prepare_target(sc, s->stream)) != cudaSuccess)
+        return bail(e, "target bits");
     if ((e = cudaStreamSynchronize(s->stream)) != cudaSuccess) return bail(e, "scene setup");
     if ((e = cudaGetLastError()) != cudaSuccess) return bail(e, "scene setup launch");
     *out = s;
@@ -579,7 +581,7 @@ hr_status hr_destroy_scene(hr_scene s) {
     if (s->stream) cudaStreamSynchronize(s->stream);
     cudaFree(sc.target); cudaFree(sc.verts); cudaFree(sc.tris); cudaFree(sc.tnrm); cudaFree(sc.tile_t2);
     cudaFree(sc.raw); cudaFree(sc.pidx); cudaFree(sc.qA); cudaFree(sc.qb); cudaFree(sc.rv_stats);
-    cudaFree(sc.pt_stats);
+    cudaFree(sc.pt_stats); cudaFree(sc.tbits);
     s->ws.release_all();
     for (cudaEvent_t& e : s->ev)
         if (e) cudaEventDestroy(e);

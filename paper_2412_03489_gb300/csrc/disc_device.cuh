@@ -112,14 +112,110 @@ __device__ __forceinline__ float disc_rows(const float* __restrict__ target, int
     return acc;
 }
 
+// Binary targets (every pixel exactly 0 or 1).  Each pixel's squared
+// difference is then 0 or 1, so the per-pixel FP32 sum is the count of pixels
+// where the disc and the target differ: an integer below 2^24, exact in any
+// order.  Row y of the disc is an interval of columns.  With dx = px - cx
+// rounded to FP32, the test fma(dx, dx, dy^2) < r^2 is non-increasing in x
+// left of the centre column xc (the first column with px >= cx) and
+// non-decreasing from xc on, because rounding is monotone; so the covered
+// columns are [a, e) for the first covered column a of [0, xc) (xc if none)
+// and the first uncovered column e of [xc, W) (W if none).  Both ends are
+// found by the exact test itself, started from the real-arithmetic ends
+// (cx -+ sqrt(r^2 - dy^2)) W - 1/2 and stepped at most kSpanSteps columns;
+// a start further off falls back to a binary search on the same predicate.
+// The row's count is then popc(target bits XOR span bits) over its words.
+constexpr int kSpanSteps = 4;
+
+struct DiscRow {
+    const float* px;
+    float cx, dy2, r2;
+    __device__ __forceinline__ bool cov(int x) const {
+        const float dx = __fsub_rn(px[x], cx);
+        return __fmaf_rn(dx, dx, dy2) < r2;
+    }
+};
+
+// clamp of a float column estimate to [lo, hi] (NaN to lo)
+__device__ __forceinline__ int clamp_col(float f, int lo, int hi) {
+    return (int)fminf(fmaxf(f, (float)lo), (float)hi);
+}
+
+// first x in [lo, hi) with pred(x) true (hi if none), pred false..false true..true
+template <class Pred>
+__device__ __forceinline__ int first_true(int lo, int hi, Pred pred) {
+    while (lo < hi) {
+        const int mid = (lo + hi) >> 1;
+        if (pred(mid)) hi = mid;
+        else lo = mid + 1;
+    }
+    return lo;
+}
+
+// covered columns [a, e) of one row (empty when dy^2 >= r^2: the test is never true)
+__device__ __forceinline__ void disc_span(const float* px, int W, float fW, float cx, float dy2, float r2,
+                                          int& a, int& e) {
+    a = e = 0;
+    if (!(dy2 < r2)) return;
+    const DiscRow R{px, cx, dy2, r2};
+    // centre column: first x with px[x] >= cx (px strictly increasing)
+    int xc = clamp_col(ceilf(__fmaf_rn(cx, fW, -0.5f)), 0, W);
+    int k = 0;
+    for (; k < kSpanSteps && xc > 0 && px[xc - 1] >= cx; ++k) --xc;
+    for (; k < kSpanSteps && xc < W && px[xc] < cx; ++k) ++xc;
+    if (k == kSpanSteps) xc = first_true(0, W, [&](int x) { return px[x] >= cx; });
+    const float h = sqrtf(__fsub_rn(r2, dy2));
+    // left end: first covered column of [0, xc)
+    a = clamp_col(ceilf(__fmaf_rn(__fsub_rn(cx, h), fW, -0.5f)), 0, xc);
+    k = 0;
+    for (; k < kSpanSteps && a > 0 && R.cov(a - 1); ++k) --a;
+    for (; k < kSpanSteps && a < xc && !R.cov(a); ++k) ++a;
+    if (k == kSpanSteps) a = first_true(0, xc, [&](int x) { return R.cov(x); });
+    // right end: first uncovered column of [xc, W)
+    e = clamp_col(ceilf(__fmaf_rn(__fadd_rn(cx, h), fW, -0.5f)), xc, W);
+    k = 0;
+    for (; k < kSpanSteps && e > xc && !R.cov(e - 1); ++k) --e;
+    for (; k < kSpanSteps && e < W && R.cov(e); ++k) ++e;
+    if (k == kSpanSteps) e = first_true(xc, W, [&](int x) { return !R.cov(x); });
+}
+
+// Mismatch count of this lane's rows y = lane, lane + 32, ... against the
+// bit-packed target (bit x % 32 of word x / 32 of a row: pixel x is 1).
+__device__ __forceinline__ int disc_lane_mismatch(const uint32_t* __restrict__ tbits, int W, int H,
+                                                  const float* px, const float* py, float cx, float cy,
+                                                  float r2, int lane) {
+    const int words = (W + 31) >> 5;
+    const float fW = (float)W;
+    int cnt = 0;
+    for (int y = lane; y < H; y += 32) {
+        const float dy = __fsub_rn(py[y], cy);
+        int a, e;
+        disc_span(px, W, fW, cx, __fmul_rn(dy, dy), r2, a, e);
+        const uint32_t* row = tbits + (size_t)y * words;
+        for (int j = 0; j < words; ++j) {
+            const int lo = min(max(a - 32 * j, 0), 32), hi = min(max(e - 32 * j, 0), 32);
+            const uint32_t m = (uint32_t)(((1ull << hi) - 1ull) & ~((1ull << lo) - 1ull));
+            cnt += __popc(__ldg(row + j) ^ m);
+        }
+    }
+    return cnt;
+}
+
 // Loss of the disc at centre (cx, cy) against the target, by one warp (all
 // 32 lanes call; every lane returns the loss): the FP32 sum of the squared
-// differences over the image, per lane in pixel order, then a shuffle tree,
-// divided by the pixel count.
-__device__ __forceinline__ float disc_loss_warp(const float* __restrict__ target, int W, int H, float radius,
-                                                const float* px, const float* py, float cx, float cy, int lane) {
+// differences over the image, divided by the pixel count.  With a binary
+// target (tbits non-null: its bit-packed rows) the sum is the exact mismatch
+// count of the row spans; otherwise each lane sums its pixels in pixel order,
+// then a shuffle tree adds the lanes.
+__device__ __forceinline__ float disc_loss_warp(const float* __restrict__ target, const uint32_t* __restrict__ tbits,
+                                                int W, int H, float radius, const float* px, const float* py,
+                                                float cx, float cy, int lane) {
     const float r2 = __fmul_rn(radius, radius);
     const int npx = W * H;
+    if (tbits) {
+        const int cnt = __reduce_add_sync(0xffffffffu, disc_lane_mismatch(tbits, W, H, px, py, cx, cy, r2, lane));
+        return __fdiv_rn((float)cnt, (float)npx);
+    }
     auto value = [cx, cy, r2](float px_, float py_) {
         const float dx = __fsub_rn(px_, cx);
         const float dy = __fsub_rn(py_, cy);

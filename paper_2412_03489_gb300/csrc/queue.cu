@@ -96,6 +96,7 @@ struct QArgs {
     int W, H;
     float radius;
     const float* target;
+    const uint32_t* tbits;           // bit-packed binary target, or null
     long long budget;                // dispatcher idle budget, clock64 cycles
     long long safety;                // worker wait bound, clock64 cycles
 };
@@ -278,7 +279,7 @@ __global__ void __launch_bounds__(32 * kQWarps) queue_disc_kernel(QArgs A) {
                 const float* t = R.sa.tau + (size_t)m * R.n;
                 const float cx = __fadd_rn(R.theta32[0], t[0]);
                 const float cy = __fadd_rn(R.theta32[1], t[1]);
-                const float loss = disc_loss_warp(A.target, A.W, A.H, A.radius, s_px, s_py, cx, cy, lane);
+                const float loss = disc_loss_warp(A.target, A.tbits, A.W, A.H, A.radius, s_px, s_py, cx, cy, lane);
                 if (lane == 0) R.loss[m] = loss;
             }
             // 3. count the unit (weights and losses visible GPU-wide first); the
@@ -413,6 +414,7 @@ hr_status ensure_running(hr_queue_s* q) {
     a.H = sc.H;
     a.radius = sc.radius;
     a.target = sc.target;
+    a.tbits = sc.tbinary ? sc.tbits : nullptr;
     a.budget = q->budget;
     a.safety = q->safety;
     queue_disc_kernel<<<q->grid, 32 * kQWarps, 0, q->kstream>>>(a);
@@ -442,83 +444,10 @@ void free_queue(hr_queue_s* q) {
     delete q;
 }
 
-}  // namespace
-
-extern "C" {
-
-hr_status hr_queue_create(hr_scene scene, const hr_queue_opts* o, hr_queue* out) {
-    clear_error();
-    if (!scene || !o || !out) return fail(HR_ERR_INVALID_ARG, "NULL argument");
-    *out = nullptr;
-    if (scene->sc.kind != HR_SCENE_DISC2D) return fail(HR_ERR_UNSUPPORTED, "the persistent queue serves disc scenes");
-    if (o->max_requests < 1 || o->max_requests > 65536)
-        return fail(HR_ERR_INVALID_ARG, "max_requests must be 1..65536");
-    if (o->arena_bytes < (1 << 20)) return fail(HR_ERR_INVALID_ARG, "arena_bytes must be at least 1 MiB");
-    if (o->idle_budget_us < 1 || o->idle_budget_us > 10000000)
-        return fail(HR_ERR_INVALID_ARG, "idle_budget_us must be 1..10^7");
-    hr_queue_s* q = new hr_queue_s();
-    q->scene = scene;
-    q->cap = o->max_requests;
-    q->arena_bytes = (size_t)o->arena_bytes;
-    int dev = 0, clock_khz = 0, sms = 0, per_sm = 0;
-    cudaError_t e = cudaGetDevice(&dev);
-    auto step = [&](cudaError_t x) { if (e == cudaSuccess) e = x; };
-    step(cudaDeviceGetAttribute(&clock_khz, cudaDevAttrClockRate, dev));
-    step(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
-    step(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, queue_disc_kernel, 32 * kQWarps, 0));
-    q->grid = sms * std::max(per_sm, 1);
-    // clock64() counts SM cycles; the budget is converted at the maximum clock
-    // (a lower clock only makes the wall-clock wait longer)
-    const long long khz = clock_khz > 0 ? clock_khz : 2070000;
-    q->budget = (long long)o->idle_budget_us * khz / 1000;
-    q->safety = 4 * q->budget + 200LL * khz;   // the budget x 4 + 200 ms
-    step(cudaStreamCreateWithFlags(&q->kstream, cudaStreamNonBlocking));
-    step(cudaEventCreateWithFlags(&q->kdone, cudaEventDisableTiming));
-    step(cudaMalloc((void**)&q->ctl, sizeof(QCtl)));
-    step(cudaMemset(q->ctl, 0, sizeof(QCtl)));
-    step(cudaMalloc((void**)&q->d_ring, sizeof(QReq) * q->cap));
-    step(cudaMalloc((void**)&q->unit_ring, sizeof(unsigned long long) * kQUnitRing));
-    step(cudaMalloc((void**)&q->done, sizeof(unsigned) * q->cap));
-    step(cudaMemset(q->done, 0, sizeof(unsigned) * q->cap));
-    step(cudaMalloc((void**)&q->arena, q->arena_bytes));
-    step(cudaHostAlloc((void**)&q->host, sizeof(QHost), cudaHostAllocMapped));
-    step(cudaHostAlloc((void**)&q->h_ring, sizeof(QReq) * q->cap, cudaHostAllocMapped));
-    step(cudaHostAlloc((void**)&q->h_res, sizeof(double) * kQMaxResult * q->cap, cudaHostAllocMapped));
-    step(cudaHostAlloc((void**)&q->h_flag, sizeof(int) * q->cap, cudaHostAllocMapped));
-    step(cudaHostAlloc((void**)&q->h_init, 4 * sizeof(int), cudaHostAllocDefault));
-    if (e == cudaSuccess) {
-        step(cudaHostGetDevicePointer((void**)&q->dv_host, q->host, 0));
-        step(cudaHostGetDevicePointer((void**)&q->dv_ring, q->h_ring, 0));
-        step(cudaHostGetDevicePointer((void**)&q->dv_res, q->h_res, 0));
-        step(cudaHostGetDevicePointer((void**)&q->dv_flag, q->h_flag, 0));
-    }
-    step(cudaDeviceSynchronize());
-    if (e != cudaSuccess) {
-        free_queue(q);
-        return fail(HR_ERR_OOM, "queue: %s", cudaGetErrorString(e));
-    }
-    memset(q->host, 0, sizeof(QHost));
-    memset(q->h_flag, 0, sizeof(int) * q->cap);
-    q->slot_ticket.assign(q->cap, 0);
-    q->slot_count.assign(q->cap, 0);
-    *out = q;
-    return HR_OK;
-}
-
-hr_status hr_queue_submit(hr_queue q, int32_t quantity, const double* h_theta, const double* h_v, const hr_opts* o,
-                          uint64_t* ticket) {
-    clear_error();
-    if (!q || !h_theta || !o || !ticket) return fail(HR_ERR_INVALID_ARG, "NULL argument");
-    if (quantity != HR_GRAD && quantity != HR_HESSIAN && quantity != HR_HVP)
-        return fail(HR_ERR_INVALID_ARG, "unknown quantity %d", quantity);
-    if (quantity == HR_HVP && !h_v) return fail(HR_ERR_INVALID_ARG, "an HVP needs v");
-    std::lock_guard<std::mutex> lk(q->mu);
-    hr_status st;
-    {
-        std::lock_guard<std::mutex> lk2(q->scene->mu);
-        st = validate_opts(q->scene, quantity, o);
-    }
-    if (st != HR_OK) return st;
+// Checks one request and writes its descriptor into the host ring; the
+// caller holds the queue lock, has checked the options, and publishes.
+hr_status queue_push(hr_queue_s* q, int32_t quantity, const double* h_theta, const double* h_v, const hr_opts* o,
+                     uint64_t* ticket) {
     const int n = q->scene->sc.n;
     const int E = n_elements(quantity, n);
     const int G = o->strategy == HR_ELEMENTWISE ? E : 1;
@@ -601,9 +530,131 @@ hr_status hr_queue_submit(hr_queue q, int32_t quantity, const double* h_theta, c
     q->units_next += (uint64_t)units;
     q->head = start + bytes;
     *ticket = q->next++;
-    // publish: the descriptor's stores come before the count (release)
+    return HR_OK;
+}
+
+// Checks of one request that need no queue state.
+hr_status queue_check(hr_queue_s* q, int32_t quantity, const double* h_theta, const double* h_v, const hr_opts* o) {
+    if (!h_theta || !o) return fail(HR_ERR_INVALID_ARG, "NULL argument");
+    if (quantity != HR_GRAD && quantity != HR_HESSIAN && quantity != HR_HVP)
+        return fail(HR_ERR_INVALID_ARG, "unknown quantity %d", quantity);
+    if (quantity == HR_HVP && !h_v) return fail(HR_ERR_INVALID_ARG, "an HVP needs v");
+    return validate_opts(q->scene, quantity, o);
+}
+
+void queue_publish(hr_queue_s* q) {
+    // the descriptors' stores come before the count (release)
     __atomic_store_n(&q->host->submitted, (unsigned long long)q->next, __ATOMIC_RELEASE);
+}
+
+}  // namespace
+
+extern "C" {
+
+hr_status hr_queue_create(hr_scene scene, const hr_queue_opts* o, hr_queue* out) {
+    clear_error();
+    if (!scene || !o || !out) return fail(HR_ERR_INVALID_ARG, "NULL argument");
+    *out = nullptr;
+    if (scene->sc.kind != HR_SCENE_DISC2D) return fail(HR_ERR_UNSUPPORTED, "the persistent queue serves disc scenes");
+    if (o->max_requests < 1 || o->max_requests > 65536)
+        return fail(HR_ERR_INVALID_ARG, "max_requests must be 1..65536");
+    if (o->arena_bytes < (1 << 20)) return fail(HR_ERR_INVALID_ARG, "arena_bytes must be at least 1 MiB");
+    if (o->idle_budget_us < 1 || o->idle_budget_us > 10000000)
+        return fail(HR_ERR_INVALID_ARG, "idle_budget_us must be 1..10^7");
+    hr_queue_s* q = new hr_queue_s();
+    q->scene = scene;
+    q->cap = o->max_requests;
+    q->arena_bytes = (size_t)o->arena_bytes;
+    int dev = 0, clock_khz = 0, sms = 0, per_sm = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    auto step = [&](cudaError_t x) { if (e == cudaSuccess) e = x; };
+    step(cudaDeviceGetAttribute(&clock_khz, cudaDevAttrClockRate, dev));
+    step(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
+    step(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, queue_disc_kernel, 32 * kQWarps, 0));
+    q->grid = sms * std::max(per_sm, 1);
+    // clock64() counts SM cycles; the budget is converted at the maximum clock
+    // (a lower clock only makes the wall-clock wait longer)
+    const long long khz = clock_khz > 0 ? clock_khz : 2070000;
+    q->budget = (long long)o->idle_budget_us * khz / 1000;
+    q->safety = 4 * q->budget + 200LL * khz;   // the budget x 4 + 200 ms
+    step(cudaStreamCreateWithFlags(&q->kstream, cudaStreamNonBlocking));
+    step(cudaEventCreateWithFlags(&q->kdone, cudaEventDisableTiming));
+    step(cudaMalloc((void**)&q->ctl, sizeof(QCtl)));
+    step(cudaMemset(q->ctl, 0, sizeof(QCtl)));
+    step(cudaMalloc((void**)&q->d_ring, sizeof(QReq) * q->cap));
+    step(cudaMalloc((void**)&q->unit_ring, sizeof(unsigned long long) * kQUnitRing));
+    step(cudaMalloc((void**)&q->done, sizeof(unsigned) * q->cap));
+    step(cudaMemset(q->done, 0, sizeof(unsigned) * q->cap));
+    step(cudaMalloc((void**)&q->arena, q->arena_bytes));
+    step(cudaHostAlloc((void**)&q->host, sizeof(QHost), cudaHostAllocMapped));
+    step(cudaHostAlloc((void**)&q->h_ring, sizeof(QReq) * q->cap, cudaHostAllocMapped));
+    step(cudaHostAlloc((void**)&q->h_res, sizeof(double) * kQMaxResult * q->cap, cudaHostAllocMapped));
+    step(cudaHostAlloc((void**)&q->h_flag, sizeof(int) * q->cap, cudaHostAllocMapped));
+    step(cudaHostAlloc((void**)&q->h_init, 4 * sizeof(int), cudaHostAllocDefault));
+    if (e == cudaSuccess) {
+        step(cudaHostGetDevicePointer((void**)&q->dv_host, q->host, 0));
+        step(cudaHostGetDevicePointer((void**)&q->dv_ring, q->h_ring, 0));
+        step(cudaHostGetDevicePointer((void**)&q->dv_res, q->h_res, 0));
+        step(cudaHostGetDevicePointer((void**)&q->dv_flag, q->h_flag, 0));
+    }
+    step(cudaDeviceSynchronize());
+    if (e != cudaSuccess) {
+        free_queue(q);
+        return fail(HR_ERR_OOM, "queue: %s", cudaGetErrorString(e));
+    }
+    memset(q->host, 0, sizeof(QHost));
+    memset(q->h_flag, 0, sizeof(int) * q->cap);
+    q->slot_ticket.assign(q->cap, 0);
+    q->slot_count.assign(q->cap, 0);
+    *out = q;
+    return HR_OK;
+}
+
+hr_status hr_queue_submit(hr_queue q, int32_t quantity, const double* h_theta, const double* h_v, const hr_opts* o,
+                          uint64_t* ticket) {
+    clear_error();
+    if (!q || !ticket) return fail(HR_ERR_INVALID_ARG, "NULL argument");
+    std::lock_guard<std::mutex> lk(q->mu);
+    hr_status st;
+    {
+        std::lock_guard<std::mutex> lk2(q->scene->mu);
+        st = queue_check(q, quantity, h_theta, h_v, o);
+    }
+    if (st == HR_OK) st = queue_push(q, quantity, h_theta, h_v, o, ticket);
+    if (st != HR_OK) return st;
+    queue_publish(q);
     return ensure_running(q);
+}
+
+hr_status hr_queue_submit_many(hr_queue q, int32_t count, int32_t quantity, const double* h_theta, const double* h_v,
+                               const hr_opts* opts, uint64_t* tickets, int32_t* submitted) {
+    clear_error();
+    if (!q || !tickets || !submitted || !opts || count < 0) return fail(HR_ERR_INVALID_ARG, "NULL argument or count < 0");
+    *submitted = 0;
+    if (count == 0) return HR_OK;
+    if (!h_theta) return fail(HR_ERR_INVALID_ARG, "NULL argument");
+    std::lock_guard<std::mutex> lk(q->mu);
+    const int n = q->scene->sc.n;
+    hr_status st = HR_OK;
+    {
+        std::lock_guard<std::mutex> lk2(q->scene->mu);
+        for (int i = 0; i < count && st == HR_OK; ++i)
+            st = queue_check(q, quantity, h_theta + (size_t)i * n, h_v ? h_v + (size_t)i * n : nullptr, opts + i);
+    }
+    if (st != HR_OK) return st;
+    int k = 0;
+    for (; k < count; ++k) {
+        st = queue_push(q, quantity, h_theta + (size_t)k * n, h_v ? h_v + (size_t)k * n : nullptr, opts + k,
+                        tickets + k);
+        if (st != HR_OK) break;
+    }
+    *submitted = k;
+    if (k > 0) {
+        queue_publish(q);
+        const hr_status rs = ensure_running(q);
+        if (rs != HR_OK) return rs;
+    }
+    return st;
 }
 
 hr_status hr_queue_wait(hr_queue q, uint64_t ticket, double* h_out, int32_t timeout_ms) {
@@ -630,6 +681,35 @@ hr_status hr_queue_wait(hr_queue q, uint64_t ticket, double* h_out, int32_t time
         if (spin > 1000) std::this_thread::sleep_for(std::chrono::microseconds(20));
         else std::this_thread::yield();
     }
+}
+
+hr_status hr_queue_wait_many(hr_queue q, int32_t count, const uint64_t* tickets, double* h_out, int32_t out_stride,
+                             int32_t timeout_ms) {
+    clear_error();
+    if (!q || (count > 0 && (!tickets || !h_out)) || count < 0) return fail(HR_ERR_INVALID_ARG, "NULL argument or count < 0");
+    {
+        std::lock_guard<std::mutex> lk(q->mu);
+        for (int i = 0; i < count; ++i) {
+            const int slot = (int)(tickets[i] % (uint64_t)q->cap);
+            if (tickets[i] >= q->next || q->slot_ticket[slot] != tickets[i] + 1)
+                return fail(HR_ERR_INVALID_ARG, "unknown ticket %llu or already waited for",
+                            (unsigned long long)tickets[i]);
+            if (q->slot_count[slot] > out_stride)
+                return fail(HR_ERR_INVALID_ARG, "out_stride %d below a result's %d doubles", out_stride,
+                            q->slot_count[slot]);
+        }
+    }
+    const auto t0 = std::chrono::steady_clock::now();
+    for (int i = 0; i < count; ++i) {
+        int32_t left = timeout_ms;
+        if (timeout_ms >= 0) {
+            const auto used = std::chrono::duration_cast<std::chrono::milliseconds>(std::chrono::steady_clock::now() - t0);
+            left = (int32_t)std::max<long long>(0, timeout_ms - (long long)used.count());
+        }
+        const hr_status st = hr_queue_wait(q, tickets[i], h_out + (size_t)i * out_stride, left);
+        if (st != HR_OK) return st;
+    }
+    return HR_OK;
 }
 
 hr_status hr_queue_status(hr_queue q, int32_t* kernel_status, uint64_t* launches) {

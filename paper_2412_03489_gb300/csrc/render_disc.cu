@@ -13,7 +13,8 @@ namespace {
 
 template <int kW>
 __global__ void __launch_bounds__(32 * kW) disc_loss_kernel(RenderBatch b, int W, int H, float radius,
-                                                            const float* __restrict__ target) {
+                                                            const float* __restrict__ target,
+                                                            const uint32_t* __restrict__ tbits) {
     __shared__ float s_px[HR_MAX_IMAGE_SIDE], s_py[HR_MAX_IMAGE_SIDE];
     centre_tables(s_px, s_py, W, H);
     __syncthreads();
@@ -23,8 +24,26 @@ __global__ void __launch_bounds__(32 * kW) disc_loss_kernel(RenderBatch b, int W
     const Pert pt = resolve(b, m);
     const float cx = __fadd_rn(pt.theta[0], pt.tau[0]);
     const float cy = __fadd_rn(pt.theta[1], pt.tau[1]);
-    const float loss = disc_loss_warp(target, W, H, radius, s_px, s_py, cx, cy, lane);
+    const float loss = disc_loss_warp(target, tbits, W, H, radius, s_px, s_py, cx, cy, lane);
     if (lane == 0) *pt.loss = loss;
+}
+
+// Bit-packed target rows (bit x % 32 of word x / 32 of row y: pixel (x, y) is
+// 1) and a flag raised by any pixel other than 0 or 1.
+__global__ void disc_bits_kernel(const float* __restrict__ target, int W, int H, int words, uint32_t* bits,
+                                 int* non_binary) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= words * H) return;
+    const int y = i / words, j = i - y * words;
+    uint32_t b = 0u;
+    bool bad = false;
+    for (int k = 0; k < 32 && 32 * j + k < W; ++k) {
+        const float t = target[(size_t)y * W + 32 * j + k];
+        if (t == 1.0f) b |= 1u << k;
+        else if (t != 0.0f) bad = true;
+    }
+    bits[i] = b;
+    if (bad) atomicOr(non_binary, 1);
 }
 
 __global__ void disc_image_kernel(const float* params, int W, int H, float radius, float* img) {
@@ -98,11 +117,30 @@ void launch_boxes_image(const DevScene& sc, const float* params, float* img, cud
 }
 
 void launch_disc_loss(const DevScene& sc, const RenderBatch& b, cudaStream_t s) {
+    const uint32_t* tb = sc.tbinary ? sc.tbits : nullptr;
     switch (sc.render_variant) {
-        case 1: disc_loss_kernel<4><<<(b.M + 3) / 4, 128, 0, s>>>(b, sc.W, sc.H, sc.radius, sc.target); break;
-        case 2: disc_loss_kernel<16><<<(b.M + 15) / 16, 512, 0, s>>>(b, sc.W, sc.H, sc.radius, sc.target); break;
-        default: disc_loss_kernel<8><<<(b.M + 7) / 8, 256, 0, s>>>(b, sc.W, sc.H, sc.radius, sc.target); break;
+        case 1: disc_loss_kernel<4><<<(b.M + 3) / 4, 128, 0, s>>>(b, sc.W, sc.H, sc.radius, sc.target, tb); break;
+        case 2: disc_loss_kernel<16><<<(b.M + 15) / 16, 512, 0, s>>>(b, sc.W, sc.H, sc.radius, sc.target, tb); break;
+        default: disc_loss_kernel<8><<<(b.M + 7) / 8, 256, 0, s>>>(b, sc.W, sc.H, sc.radius, sc.target, tb); break;
     }
+}
+
+cudaError_t disc_prepare_target(DevScene& sc, cudaStream_t s) {
+    const int words = (sc.W + 31) / 32;
+    int* d_flag = nullptr;
+    cudaError_t e = cudaMalloc((void**)&sc.tbits, sizeof(uint32_t) * words * sc.H);
+    if (e == cudaSuccess) e = cudaMalloc((void**)&d_flag, sizeof(int));
+    if (e == cudaSuccess) e = cudaMemsetAsync(d_flag, 0, sizeof(int), s);
+    if (e == cudaSuccess) {
+        disc_bits_kernel<<<(words * sc.H + 255) / 256, 256, 0, s>>>(sc.target, sc.W, sc.H, words, sc.tbits, d_flag);
+        e = cudaGetLastError();
+    }
+    int non_binary = 1;
+    if (e == cudaSuccess) e = cudaMemcpyAsync(&non_binary, d_flag, sizeof(int), cudaMemcpyDeviceToHost, s);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+    cudaFree(d_flag);
+    sc.tbinary = e == cudaSuccess && non_binary == 0;
+    return e;
 }
 
 void launch_disc_image(const DevScene& sc, const float* params, float* img, cudaStream_t s) {

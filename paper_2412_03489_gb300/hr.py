@@ -170,6 +170,10 @@ def lib() -> ctypes.CDLL:
         L.hr_queue_submit.argtypes = [vp, ctypes.c_int32, _f64p, _f64p, ctypes.POINTER(hr_opts),
                                       ctypes.POINTER(ctypes.c_uint64)]
         L.hr_queue_wait.argtypes = [vp, ctypes.c_uint64, _f64p, ctypes.c_int32]
+        L.hr_queue_submit_many.argtypes = [vp, ctypes.c_int32, ctypes.c_int32, _f64p, _f64p, ctypes.POINTER(hr_opts),
+                                           ctypes.POINTER(ctypes.c_uint64), ctypes.POINTER(ctypes.c_int32)]
+        L.hr_queue_wait_many.argtypes = [vp, ctypes.c_int32, ctypes.POINTER(ctypes.c_uint64), _f64p, ctypes.c_int32,
+                                         ctypes.c_int32]
         L.hr_queue_status.argtypes = [vp, ctypes.POINTER(ctypes.c_int32), ctypes.POINTER(ctypes.c_uint64)]
         L.hr_queue_destroy.argtypes = [vp]
         L.hr_last_error.argtypes = [ctypes.c_char_p, ctypes.c_size_t]
@@ -182,7 +186,8 @@ def lib() -> ctypes.CDLL:
                      "hr_profile_last", "hr_server_create", "hr_server_destroy", "hr_server_submit",
                      "hr_server_wait", "hr_ncg_create", "hr_ncg_destroy", "hr_ncg_run", "hr_ncg_theta",
                      "hr_autotune", "hr_set_tuning", "hr_scene_get_stats", "hr_optstate_trace", "hr_ncg_trace", "hr_render_ids", "hr_scene_count_work",
-                     "hr_queue_create", "hr_queue_submit", "hr_queue_wait", "hr_queue_status", "hr_queue_destroy"):
+                     "hr_queue_create", "hr_queue_submit", "hr_queue_wait", "hr_queue_status", "hr_queue_destroy",
+                     "hr_queue_submit_many", "hr_queue_wait_many"):
             getattr(L, name).restype = ctypes.c_int32
         L.hr_version.restype = ctypes.c_int32
         _lib = L
@@ -515,6 +520,42 @@ def hr_queue_submit(q: int, quantity: int, theta, v, opts: hr_opts) -> int:
 
 def hr_queue_wait(q: int, ticket: int, out: np.ndarray, timeout_ms: int = 120000) -> None:
     check(lib().hr_queue_wait(q, int(ticket), _ptr(out, _f64p), int(timeout_ms)), "hr_queue_wait")
+
+
+def opts_array(sigma, M, strategy, seeds, requests, subs=None):
+    """A ctypes array of hr_opts, one per (seed, request[, sub])."""
+    arr = (hr_opts * len(seeds))()
+    for i, (sd, rq) in enumerate(zip(seeds, requests)):
+        o = arr[i]
+        o.sigma, o.n_perturb, o.strategy = float(sigma), int(M), int(strategy)
+        o.seed, o.request_id = int(sd), int(rq) & 0xFFFFFFFF
+        o.sub = 0 if subs is None else int(subs[i])
+    return arr
+
+
+def hr_queue_submit_many(q: int, quantity: int, thetas, vs, opts_array) -> np.ndarray:
+    """Queue len(opts_array) estimates (thetas [count][n], vs [count][n] or None,
+    opts_array a ctypes array of hr_opts); returns the tickets of those queued
+    (fewer than count when the ring or the arena filled up)."""
+    count = len(opts_array)
+    th = np.ascontiguousarray(thetas, np.float64)
+    vv = None if vs is None else np.ascontiguousarray(vs, np.float64)
+    tickets = np.zeros(count, np.uint64)
+    done = ctypes.c_int32()
+    st = lib().hr_queue_submit_many(q, count, int(quantity), _ptr(th, _f64p), _ptr(vv, _f64p), opts_array,
+                                    tickets.ctypes.data_as(ctypes.POINTER(ctypes.c_uint64)), ctypes.byref(done))
+    if st not in (HR_OK, HR_ERR_BUSY):
+        check(st, "hr_queue_submit_many")
+    return tickets[:done.value]
+
+
+def hr_queue_wait_many(q: int, tickets, out: np.ndarray, timeout_ms: int = 120000) -> None:
+    """Wait for tickets; out [count][stride] receives their results."""
+    t = np.ascontiguousarray(tickets, np.uint64)
+    assert out.flags.c_contiguous and out.dtype == np.float64 and out.shape[0] >= len(t)
+    stride = int(np.prod(out.shape[1:])) if out.ndim > 1 else 1
+    check(lib().hr_queue_wait_many(q, len(t), t.ctypes.data_as(ctypes.POINTER(ctypes.c_uint64)), _ptr(out, _f64p),
+                                   stride, int(timeout_ms)), "hr_queue_wait_many")
 
 
 def hr_queue_status(q: int):

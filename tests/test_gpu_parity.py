@@ -86,6 +86,37 @@ def test_disc_ragged_and_minimum(W, H, M):
     assert_estimate_close(flat, ref, what="disc ragged")
 
 
+@pytest.mark.parametrize("W,H,radius,sigma,target", [
+    (64, 64, 5.0 / 64.0, 1e-6, "disc"),      # centre on a pixel centre, r a whole number of pixels:
+    (64, 64, 0.2, 1e-7, "disc"),             #   boundary pixels within rounding of d^2 = r^2
+    (37, 23, 0.2, 0.3, "disc"),              # wide perturbations: discs cut by every image edge
+    (100, 50, 0.7, 0.2, "random"),           # spans over word boundaries, arbitrary 0/1 target
+    (1024, 3, 0.004, 0.05, "random"),        # sub-pixel radius, 32 words per row
+    (33, 40, 1.5, 0.5, "random"),            # discs larger than the image
+    (1, 1, 0.2, 0.3, "disc")])
+def test_disc_binary_target_spans(W, H, radius, sigma, target):
+    """Binary targets take the span path (row intervals of the FP32 pixel test,
+    mismatch counts by popcount): every loss equals the oracle's per-pixel
+    count, including pixels within rounding of the disc's edge."""
+    sc = wl.disc_scene(width=W, height=H, radius=radius)
+    sc["sigma"] = sigma
+    g = np.random.default_rng(W * 7 + H)
+    if sigma < 1e-5:   # theta on a pixel centre
+        sc["theta_query"] = np.array([(W // 2 + 0.5) / W, (H // 3 + 0.5) / H])
+    tgt = None
+    if target == "random":
+        tgt = (g.uniform(size=W * H) < 0.4).astype(np.float32)
+    Sc = hr.Scene(sc, target_image=tgt) if tgt is not None else hr.Scene(sc)
+    ren = O.DiscRenderer(sc, target=tgt) if tgt is not None else O.DiscRenderer(sc)
+    flat, dbg, ref = run_both(sc, ren, "hessian", 256, "aggregate", scene=Sc)
+    Sc.close()
+    check_samples(dbg, ref)
+    npx = W * H
+    assert np.array_equal(np.rint(dbg["losses"].astype(np.float64) * npx), np.rint(ref.losses * npx))
+    assert np.all(np.abs(dbg["losses"] - ref.losses) <= np.spacing(np.float32(ref.losses)))
+    assert_estimate_close(flat, ref, what="disc spans")
+
+
 @pytest.mark.parametrize("W,H", [(64, 21), (96, 10), (128, 7), (512, 3)])
 def test_disc_grey_target(W, H):
     """A caller's target image with grey levels (the renderer's own targets are

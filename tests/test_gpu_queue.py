@@ -3,6 +3,7 @@ sums disc requests.  Every result is bit-identical to hr_estimate_* with the
 same options, alone and in a mix, through arena wrap-around and from several
 host threads; the idle budget ends the kernel with HR_ERR_TIMEOUT in its status
 word and the next request launches it again; full rings answer HR_ERR_BUSY."""
+import ctypes
 import threading
 import time
 
@@ -229,4 +230,39 @@ def test_queue_validation_and_destroy_with_pending_work():
     # the scene still renders through the plain path afterwards
     out = S.estimate(hr.HR_HESSIAN, theta, sc["sigma"], 64, hr.HR_AGGREGATE, 1, 1)
     assert np.all(np.isfinite(out))
+    S.close()
+
+
+def test_queue_batches():
+    """hr_queue_submit_many / hr_queue_wait_many: every result bit-identical to
+    the plain path; a batch larger than the ring queues what fits (HR_ERR_BUSY
+    for the rest) and the remainder goes in after the first results are read."""
+    sc = wl.disc_scene()
+    S = hr.Scene(sc)
+    g = np.random.default_rng(21)
+    count = 300
+    thetas = np.asarray(sc["theta_query"], np.float64) + g.normal(0, 0.02, (count, 2))
+    seeds, reqs = np.arange(count) + 500, np.arange(count) * 3 + 1
+    for quantity, strat, M in [(hr.HR_HESSIAN, hr.HR_ELEMENTWISE, 1024), (hr.HR_HVP, hr.HR_AGGREGATE, 66)]:
+        vs = g.normal(size=(count, 2)) if quantity == hr.HR_HVP else None
+        arr = hr.opts_array(sc["sigma"], M, strat, seeds, reqs)
+        ref = [S.estimate(quantity, thetas[i], sc["sigma"], M, strat, int(seeds[i]), int(reqs[i]),
+                          v=None if vs is None else vs[i]) for i in range(count)]
+        q = hr.hr_queue_create(S, max_requests=128, idle_budget_us=5000)
+        try:
+            out = np.zeros((count, 4))
+            done = 0
+            while done < count:
+                sub = (hr.hr_opts * (count - done)).from_buffer(arr, done * ctypes.sizeof(hr.hr_opts))
+                t = hr.hr_queue_submit_many(q, quantity, thetas[done:], None if vs is None else vs[done:], sub)
+                assert len(t) > 0
+                if done == 0:
+                    assert len(t) == 128          # the ring's slots
+                hr.hr_queue_wait_many(q, t, out[done:done + len(t)])
+                done += len(t)
+            for i in range(count):
+                e = np.asarray(ref[i]).ravel()
+                assert np.array_equal(out[i, :e.size], e), (i, out[i], e)
+        finally:
+            hr.hr_queue_destroy(q)
     S.close()

@@ -526,9 +526,9 @@ hr_status hr_queue_destroy(hr_queue q);
  * renders (waits for the device); all 0 for kinds other than REVOLVE3D.
  *   mesh_overflow_renders   renders whose tile bins held more (triangle,
  *                           tile) entries than the render's shared memory
- *                           holds (at most 16,384), so that every tile walked
- *                           every triangle (same pixels, same decisions,
- *                           slower);
+ *                           holds at once (at most 16,384), so that they were
+ *                           binned and rastered in bands of tile rows that fit
+ *                           (same pixels, same decisions);
  *   mesh_renders            renders of estimates (images not counted);
  *   mesh_survivors          triangles that passed clipping, culling and the
  *                           image bounds;
@@ -537,7 +537,10 @@ hr_status hr_queue_destroy(hr_queue q);
  *   mesh_raster_steps       raster loop trips of the warps (a warp's tiles
  *                           take as many trips as the longest bin among
  *                           them);
- *   mesh_tile_height        rows of the 8-pixel-wide raster tiles (4 or 8).
+ *   mesh_tile_height        rows of the 8-pixel-wide raster tiles (4 or 8);
+ *   mesh_walk_all_renders   renders with a tile row whose entries alone did
+ *                           not fit, so that its tiles walked every triangle
+ *                           (same pixels, same decisions, slower).
  * The sums divided by mesh_renders give per-render averages.  Path-traced
  * scenes (PTBOX) count their work only while hr_scene_count_work is on
  * (those launches use a counting build of the default launch shape; the
@@ -558,6 +561,7 @@ typedef struct {
     int64_t pt_hit_rays;
     int64_t pt_shadow_rays;
     int64_t pt_vertices;
+    int64_t mesh_walk_all_renders;
 } hr_scene_stats;
 hr_status hr_scene_get_stats(hr_scene scene, hr_scene_stats* out);
 /* PTBOX only: on != 0 makes the scene's following render launches count

@@ -516,8 +516,8 @@ hr_status hr_create_scene(const hr_scene_desc* d, hr_scene* out) {
             if ((e = cudaMalloc(&sc.tnrm, sizeof(float) * 3 * sc.nt)) != cudaSuccess) return bail(e, "normals");
             if ((e = cudaMalloc(&sc.tile_t2, sizeof(float) * revolve_tiles(sc))) != cudaSuccess)
                 return bail(e, "tiles");
-            if ((e = cudaMalloc(&sc.rv_stats, 6 * sizeof(unsigned long long))) != cudaSuccess) return bail(e, "stats");
-            if ((e = cudaMemset(sc.rv_stats, 0, 6 * sizeof(unsigned long long))) != cudaSuccess) return bail(e, "stats");
+            if ((e = cudaMalloc(&sc.rv_stats, 7 * sizeof(unsigned long long))) != cudaSuccess) return bail(e, "stats");
+            if ((e = cudaMemset(sc.rv_stats, 0, 7 * sizeof(unsigned long long))) != cudaSuccess) return bail(e, "stats");
             revolve_prepare(sc, s->stream);
             break;
         }
@@ -630,7 +630,7 @@ hr_status hr_scene_get_stats(hr_scene s, hr_scene_stats* out) {
     std::lock_guard<std::mutex> lk(s->mu);
     memset(out, 0, sizeof(*out));
     if (s->sc.rv_stats) {
-        unsigned long long v[6] = {};
+        unsigned long long v[7] = {};
         cudaError_t e = cudaDeviceSynchronize();
         if (e == cudaSuccess) e = cudaMemcpy(v, s->sc.rv_stats, sizeof v, cudaMemcpyDeviceToHost);
         if (e != cudaSuccess) return fail(HR_ERR_CUDA, "stats: %s", cudaGetErrorString(e));
@@ -641,6 +641,7 @@ hr_status hr_scene_get_stats(hr_scene s, hr_scene_stats* out) {
         out->mesh_tiles_with_entries = (int64_t)v[4];
         out->mesh_raster_steps = (int64_t)v[5];
         out->mesh_tile_height = s->sc.rv_th;
+        out->mesh_walk_all_renders = (int64_t)v[6];
     }
     if (s->sc.pt_stats) {
         unsigned long long v[4] = {};

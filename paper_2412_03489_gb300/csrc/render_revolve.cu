@@ -14,7 +14,8 @@
 //      scan, fill; all in shared memory), skipping tiles that a conservative
 //      edge test shows the triangle misses; each bin entry carries the
 //      triangle index and the rows / columns of its tile that lie inside the
-//      triangle's bounding box;
+//      triangle's bounding box; bins that do not fit at once are filled and
+//      rastered in bands of tile rows;
 //   5. group-per-tile raster (8 lanes per 8x4 tile, 16 per 8x8 tile), tiles
 //      fetched dynamically in groups ordered by entry count; each lane tests 4
 //      pixels of a row against every entry of its tile's bin; nearest 1/Z
@@ -81,7 +82,7 @@ struct RvArgs {
     int vreg;            // floats in the vertex region
     int th;              // tile height (the kernel's template argument)
     uint64_t tx_recip;   // ceil(2^32 / TX): t / TX = (t tx_recip) >> 32 exactly for t, TX < 2^16
-    unsigned long long* stats;   // diagnostics [6], see hr_scene_stats
+    unsigned long long* stats;   // diagnostics [7], see hr_scene_stats
     float alb0, alb1, alb2, l0, l1, l2, eye_dist, scale;
 };
 
@@ -279,6 +280,7 @@ revolve_kernel(RvArgs P, RenderBatch b, const float* __restrict__ img_params, fl
     __shared__ int s_hist[33];
     __shared__ float s_part[kWarps];
     __shared__ int s_tile;
+    __shared__ int s_band[2];   // the current band's end row and whether it walks every triangle
 
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     const int M = kImage ? 1 : b.M;
@@ -415,221 +417,266 @@ revolve_kernel(RvArgs P, RenderBatch b, const float* __restrict__ img_params, fl
         __syncthreads();
         int n_obj = 0;
         const int total = bin_scan(tcnt, toff, olist, P.T, s_wtot, s_hist, &n_obj);
-        const bool overflow = total > P.cap;
+        // Bins that do not fit the shared memory at once are filled and
+        // rastered in bands of whole tile rows, each with at most capb entries;
+        // meanwhile the count pass's per-row totals sit at the end of the
+        // entry array.  A tile row whose entries alone exceed capb is a band of
+        // its own whose tiles walk every triangle.  A band only decides which
+        // tiles are rastered together: every pixel's decisions are the same.
+        const bool banded = total > P.cap;
+        const int capb = banded ? P.cap - P.TY : P.cap;
+        int* rowtot = reinterpret_cast<int*>(ent) + capb;
+        if (banded) {
+            for (int r = warp; r < P.TY; r += kWarps) {
+                int sum = 0;
+                for (int tx = lane; tx < P.TX; tx += 32) sum += tcnt[r * P.TX + tx];
+                sum = __reduce_add_sync(0xffffffffu, sum);
+                if (lane == 0) rowtot[r] = sum;
+            }
+        }
         if (!kImage && tid == 0 && P.stats) {   // diagnostics: see hr_scene_stats
-            if (overflow) atomicAdd(&P.stats[0], 1ull);
+            if (banded) atomicAdd(&P.stats[0], 1ull);
             atomicAdd(&P.stats[1], 1ull);
             atomicAdd(&P.stats[2], (unsigned long long)count);
             atomicAdd(&P.stats[3], (unsigned long long)total);
             atomicAdd(&P.stats[4], (unsigned long long)n_obj);
         }
-        for (int i = tid; i < P.T; i += kThreads) tcnt[i] = 0;   // becomes the fill cursor
-        __syncthreads();
-        if (!overflow) {
-            // tiles without entries keep the sum of target^2 as their loss
-            // (the raster writes the others)
-            float* tl = reinterpret_cast<float*>(tcnt);
-#pragma unroll
-            for (int k = 0; k < 2; ++k) {
-                const int t = tid + k * kThreads;
-                if (t < P.T && ((t + 1 < P.T) ? toff[t + 1] : total) == toff[t]) tl[t] = pt2[k];
-            }
-            for (int t = tid + 2 * kThreads; t < P.T; t += kThreads)
-                if (((t + 1 < P.T) ? toff[t + 1] : total) == toff[t]) tl[t] = P.tile_t2[t];
-            for (int k = tid; k < count; k += kThreads) {
-                const int s = surv[k];
-                const uint2 bb = bbx[s];
-                const unsigned long long mask = tmask[k];
-                const int xlo = (int)(bb.x & 0xffffu), xhi = (int)(bb.x >> 16);
-                const int ylo = (int)(bb.y & 0xffffu), yhi = (int)(bb.y >> 16);
-                const int tx0 = xlo / kTW, tx1 = xhi / kTW, ty0 = ylo / kTH, ty1 = yhi / kTH;
-                int bit = 0;
-                for (int ty = ty0; ty <= ty1; ++ty) {
-                    // rows of this tile inside the box (bits >= kTH are never tested)
-                    const uint32_t rows = span_bits(ylo - ty * kTH, yhi - ty * kTH);
-                    for (int tx = tx0; tx <= tx1; ++tx, ++bit) {
-                        if (mask != ~0ull && !((mask >> bit) & 1ull)) continue;
-                        const int tile = ty * P.TX + tx;
-                        const int pos = atomicAdd(&tcnt[tile], 1);
-                        ent[toff[tile] + pos] = entry_word(s, rows, span_bits(xlo - tx * kTW, xhi - tx * kTW));
-                    }
+        bool walked = false;   // some band walked every triangle
+        for (int r0 = 0, r1 = P.TY; r0 < P.TY; r0 = r1) {
+            int total_b = total;
+            bool walk_all = false;
+            if (banded) {
+                __syncthreads();   // row totals written; the previous band's raster done
+                if (tid == 0) {
+                    int r = r0, sum = 0;
+                    while (r < P.TY && sum + rowtot[r] <= capb) sum += rowtot[r++];
+                    s_band[0] = r > r0 ? r : r0 + 1;
+                    s_band[1] = r > r0 ? 0 : 1;
                 }
+                if (tid < 33) s_hist[tid] = 0;
+                __syncthreads();
+                r1 = s_band[0];
+                walk_all = s_band[1] != 0;
+                walked = walked || walk_all;
+                if (!walk_all)
+                    total_b = bin_scan(tcnt + r0 * P.TX, toff + r0 * P.TX, olist, (r1 - r0) * P.TX, s_wtot, s_hist,
+                                       &n_obj);
             }
-        }
-        __syncthreads();
-        // ---- 5. raster + loss ------------------------------------------------
-        // Warps fetch tiles dynamically, kPer at a time, from the
-        // count-ordered list, one tile per group of kG lanes; each tile's loss
-        // goes to its own slot (the fill cursor array is free again) and the
-        // slots are summed in tile order below, so the loss does not depend on
-        // which warp took which tile.  Lane (row ry, half-row hx) of a group
-        // owns the 4 pixels (x0 .. x0 + 3, y) of its tile and walks the tile's
-        // whole bin: the row term fma(B, y + 1/2, C) of each edge and of the
-        // depth plane is formed once per entry and shared by the 4 pixels.
-        const int grp = lane / kG, gl = lane % kG;
-        const int ry = gl >> 1, hx = gl & 1;
-        // the FP64 cos / sin of this CTA's next perturbation, off the critical
-        // path: one warp computes them before it joins the tile loop
-        if (!kImage && warp == kWarps - 1 && lane < 4) {
-            const int mn = m + (int)gridDim.x;
-            if (mn < M) {
-                const double a = (double)rotation_param(b, mn, lane >> 1);
-                s_cs_next[lane] = (float)((lane & 1) ? sin(a) : cos(a));
-            }
-        }
-        // tiles without entries are not visited: their loss, the sum of
-        // target^2, is taken in the reduction (an image visits every tile)
-        float* tile_loss = reinterpret_cast<float*>(tcnt);
-        const bool all_tiles = kImage || overflow;
-        const int n_iter = all_tiles ? P.T : n_obj;
-        const int col_shift = 4 * hx;
-        const uint32_t row_out = 1u << (8 + ry - col_shift);   // this lane's row bit after the shift
-        const bool vec_target = (P.W & 3) == 0;
-        // each warp reserves its next tiles when it starts the current ones,
-        // so the shared atomic's latency overlaps the tiles' work
-        int t_next = 0;
-        if (lane == 0) t_next = atomicAdd(&s_tile, kPer);
-        for (int it = __shfl_sync(0xffffffffu, t_next, 0); it < n_iter; it = __shfl_sync(0xffffffffu, t_next, 0)) {
-            if (lane == 0) t_next = atomicAdd(&s_tile, kPer);
-            const int my = it + grp;
-            const bool has_tile = my < n_iter;
-            const int t = !has_tile ? 0 : (all_tiles ? my : (int)olist[my]);
-            const int beg = has_tile && !overflow ? toff[t] : 0;
-            const int n_mine = has_tile && !overflow ? ((t + 1 < P.T) ? toff[t + 1] : total) - beg : 0;
-            // division by multiplication with the rounded-up reciprocal
-            // (Granlund and Montgomery, PLDI 1994): exact for t, TX < 2^16
-            const int ty = (int)(((uint64_t)(uint32_t)t * P.tx_recip) >> 32), tx = t - ty * P.TX;
-            const int x0 = tx * kTW + 4 * hx, y = ty * kTH + ry;
-            const float fy = __fadd_rn((float)y, 0.5f);
-            float fx[4], bw[4];
-            int bs[4];
+            const int tb = r0 * P.TX, Tb = (r1 - r0) * P.TX;   // the band's tiles [tb, tb + Tb)
+            for (int i = tid; i < Tb; i += kThreads) tcnt[tb + i] = 0;   // becomes the fill cursor
+            if (tid == 0) s_tile = 0;
+            __syncthreads();
+            if (!walk_all) {
+                // tiles without entries keep the sum of target^2 as their loss
+                // (the raster writes the others)
+                float* tl = reinterpret_cast<float*>(tcnt);
+                auto empty = [&](int i) { return ((i + 1 < Tb) ? toff[tb + i + 1] : total_b) == toff[tb + i]; };
 #pragma unroll
-            for (int c = 0; c < 4; ++c) {
-                fx[c] = __fadd_rn((float)(x0 + c), 0.5f);
-                bw[c] = -INFINITY;
-                bs[c] = INT_MAX;
-            }
-            // One bin entry against this lane's 4 pixels.  Bins are in fill
-            // (arbitrary) order, so the strict depth compare alone would give
-            // an exact depth tie to whichever triangle came first; every time
-            // a depth equals the pixel's current best (covered or not: one
-            // compare instead of two, at the price of re-walking about 4 % of
-            // the tile groups, where adjacent triangles' depth planes agree to
-            // the last bit) the lane notes it, and a tile group where any lane
-            // did is walked again with the full rule (larger 1/Z, lower index
-            // on equal 1/Z).
-            uint32_t tie_u = 0u;
-            // (outside: the entry's complement masks shifted so that bit c is
-            // this lane's column c and bit 8 + ry - 4 hx its row)
-            auto raster_entry = [&](int s, uint32_t outside, bool exact) {
-                const float4* rp = reinterpret_cast<const float4*>(&rec[s]);
-                const float4 q0 = rp[0], q1 = rp[1], q2 = rp[2], q3 = rp[3];
-                const float r0 = __fmaf_rn(q0.y, fy, q0.z);
-                const float r1 = __fmaf_rn(q1.y, fy, q1.z);
-                const float r2 = __fmaf_rn(q2.y, fy, q2.z);
-                const float rw = __fmaf_rn(q3.y, fy, q3.z);
-                if (exact) {
-#pragma unroll
-                    for (int c = 0; c < 4; ++c) {
-                        const float E0 = __fmaf_rn(q0.x, fx[c], r0);
-                        const float E1 = __fmaf_rn(q1.x, fx[c], r1);
-                        const float E2 = __fmaf_rn(q2.x, fx[c], r2);
-                        const float wz = __fmaf_rn(q3.x, fx[c], rw);
-                        const bool in = ((outside & (row_out | (1u << c))) == 0u) && (E0 > q0.w) &&
-                                        (E1 > q1.w) && (E2 > q2.w);
-                        const bool better = in && (wz > bw[c] || (wz == bw[c] && s < bs[c]));
-                        bw[c] = better ? wz : bw[c];
-                        bs[c] = better ? s : bs[c];
-                    }
-                } else {
-                    uint32_t t4 = 0u;
-                    pixels4(q0, q1, q2, q3.x, r0, r1, r2, rw, fx, outside, row_out, s, bw, bs, t4);
-                    tie_u |= t4;
+                for (int k = 0; k < 2; ++k) {
+                    const int i = tid + k * kThreads;
+                    if (i < Tb && empty(i)) tl[tb + i] = tb == 0 ? pt2[k] : P.tile_t2[tb + i];
                 }
-            };
-            if (!overflow) {
-                const int n_max = (int)__reduce_max_sync(0xffffffffu, (unsigned)n_mine);
-                if (!kImage && lane == 0 && P.stats) atomicAdd(&P.stats[5], (unsigned long long)n_max);
-                // a group whose bin is shorter walks a sentinel entry (every
-                // row and column outside: no pixel is in) instead of
-                // branching around the step
-                for (int k = 0; k < n_max; ++k) {
-                    const uint32_t e = k < n_mine ? ent[beg + k] : kSentinel;
-                    raster_entry((int)(e >> 16), e >> col_shift, false);
-                }
-                if (__any_sync(0xffffffffu, tie_u != 0u)) {
-#pragma unroll
-                    for (int c = 0; c < 4; ++c) {
-                        bw[c] = -INFINITY;
-                        bs[c] = INT_MAX;
-                    }
-                    for (int k = 0; k < n_max; ++k) {
-                        const uint32_t e = k < n_mine ? ent[beg + k] : kSentinel;
-                        raster_entry((int)(e >> 16), e >> col_shift, true);
-                    }
-                }
-            } else {
-                // every triangle in index order (culled ones have an empty
-                // box), so the strict compare already keeps the lower index
-                for (int s = 0; s < P.nt; ++s) {
+                for (int i = tid + 2 * kThreads; i < Tb; i += kThreads)
+                    if (empty(i)) tl[tb + i] = P.tile_t2[tb + i];
+                for (int k = tid; k < count; k += kThreads) {
+                    const int s = surv[k];
                     const uint2 bb = bbx[s];
                     const int xlo = (int)(bb.x & 0xffffu), xhi = (int)(bb.x >> 16);
                     const int ylo = (int)(bb.y & 0xffffu), yhi = (int)(bb.y >> 16);
-                    if (has_tile && xlo <= xhi && y >= ylo && y <= yhi)
-                        raster_entry(s, ((~span_bits(xlo - tx * kTW, xhi - tx * kTW) & 0xFFu) >> col_shift) & 0xFu,
-                                     false);
-                }
-            }
-            // (every group runs the shuffles below, a group without a tile too)
-            float sh[4];
-#pragma unroll
-            for (int c = 0; c < 4; ++c) sh[c] = bs[c] != INT_MAX ? tshade[bs[c]] : 0.0f;
-            const bool rowv = has_tile && y < P.H;
-            if (kImage) {
-#pragma unroll
-                for (int c = 0; c < 4; ++c)
-                    if (rowv && x0 + c < P.W) {
-                        const size_t q = (size_t)y * P.W + x0 + c;
-                        if (ids) {
-                            ids[q] = bs[c] != INT_MAX ? bs[c] : -1;
-                        } else {
-                            img[3 * q] = sh[c] * P.alb0; img[3 * q + 1] = sh[c] * P.alb1; img[3 * q + 2] = sh[c] * P.alb2;
+                    const int tx0 = xlo / kTW, tx1 = xhi / kTW, ty0 = ylo / kTH, ty1 = yhi / kTH;
+                    const int ya = max(ty0, r0), yb = min(ty1, r1 - 1);
+                    if (ya > yb) continue;
+                    const unsigned long long mask = tmask[k];
+                    int bit = (ya - ty0) * (tx1 - tx0 + 1);   // row-major over the whole tile rectangle
+                    for (int ty = ya; ty <= yb; ++ty) {
+                        // rows of this tile inside the box (bits >= kTH are never tested)
+                        const uint32_t rows = span_bits(ylo - ty * kTH, yhi - ty * kTH);
+                        for (int tx = tx0; tx <= tx1; ++tx, ++bit) {
+                            if (mask != ~0ull && !((mask >> bit) & 1ull)) continue;
+                            const int tile = ty * P.TX + tx;
+                            const int pos = atomicAdd(&tcnt[tile], 1);
+                            ent[toff[tile] + pos] = entry_word(s, rows, span_bits(xlo - tx * kTW, xhi - tx * kTW));
                         }
                     }
-            } else {
-                float tg[12];
-                if (rowv && vec_target && x0 + 3 < P.W) {
-                    const float4* tp = reinterpret_cast<const float4*>(P.target + 3 * ((size_t)y * P.W + x0));
-                    const float4 a0 = tp[0], a1 = tp[1], a2 = tp[2];
-                    tg[0] = a0.x; tg[1] = a0.y; tg[2] = a0.z; tg[3] = a0.w;
-                    tg[4] = a1.x; tg[5] = a1.y; tg[6] = a1.z; tg[7] = a1.w;
-                    tg[8] = a2.x; tg[9] = a2.y; tg[10] = a2.z; tg[11] = a2.w;
-                } else {
-#pragma unroll
-                    for (int c = 0; c < 4; ++c)
-#pragma unroll
-                        for (int ch = 0; ch < 3; ++ch)
-                            tg[3 * c + ch] = (rowv && x0 + c < P.W) ? P.target[3 * ((size_t)y * P.W + x0 + c) + ch] : 0.0f;
                 }
-                float acc = 0.0f;
-#pragma unroll
-                for (int c = 0; c < 4; ++c)
-                    if (rowv && x0 + c < P.W) {
-                        const float d0 = sh[c] * P.alb0 - tg[3 * c], d1 = sh[c] * P.alb1 - tg[3 * c + 1];
-                        const float d2 = sh[c] * P.alb2 - tg[3 * c + 2];
-                        acc += d0 * d0 + d1 * d1 + d2 * d2;
+            }
+            __syncthreads();
+            // ---- 5. raster + loss ------------------------------------------------
+            // Warps fetch tiles dynamically, kPer at a time, from the
+            // count-ordered list, one tile per group of kG lanes; each tile's loss
+            // goes to its own slot (the fill cursor array is free again) and the
+            // slots are summed in tile order below, so the loss does not depend on
+            // which warp took which tile.  Lane (row ry, half-row hx) of a group
+            // owns the 4 pixels (x0 .. x0 + 3, y) of its tile and walks the tile's
+            // whole bin: the row term fma(B, y + 1/2, C) of each edge and of the
+            // depth plane is formed once per entry and shared by the 4 pixels.
+            const int grp = lane / kG, gl = lane % kG;
+            const int ry = gl >> 1, hx = gl & 1;
+            // the FP64 cos / sin of this CTA's next perturbation, off the critical
+            // path: one warp computes them before it joins the tile loop
+            if (!kImage && r0 == 0 && warp == kWarps - 1 && lane < 4) {
+                const int mn = m + (int)gridDim.x;
+                if (mn < M) {
+                    const double a = (double)rotation_param(b, mn, lane >> 1);
+                    s_cs_next[lane] = (float)((lane & 1) ? sin(a) : cos(a));
+                }
+            }
+            // tiles without entries are not visited: their loss, the sum of
+            // target^2, is taken in the reduction (an image visits every tile)
+            float* tile_loss = reinterpret_cast<float*>(tcnt);
+            const bool all_tiles = kImage || walk_all;
+            const int n_iter = all_tiles ? Tb : n_obj;
+            const int col_shift = 4 * hx;
+            const uint32_t row_out = 1u << (8 + ry - col_shift);   // this lane's row bit after the shift
+            const bool vec_target = (P.W & 3) == 0;
+            // each warp reserves its next tiles when it starts the current ones,
+            // so the shared atomic's latency overlaps the tiles' work
+            int t_next = 0;
+            if (lane == 0) t_next = atomicAdd(&s_tile, kPer);
+            for (int it = __shfl_sync(0xffffffffu, t_next, 0); it < n_iter; it = __shfl_sync(0xffffffffu, t_next, 0)) {
+                if (lane == 0) t_next = atomicAdd(&s_tile, kPer);
+                const int my = it + grp;
+                const bool has_tile = my < n_iter;
+                const int t = !has_tile ? 0 : tb + (all_tiles ? my : (int)olist[my]);
+                const int beg = has_tile && !walk_all ? toff[t] : 0;
+                const int n_mine = has_tile && !walk_all ? ((t + 1 < tb + Tb) ? toff[t + 1] : total_b) - beg : 0;
+                // division by multiplication with the rounded-up reciprocal
+                // (Granlund and Montgomery, PLDI 1994): exact for t, TX < 2^16
+                const int ty = (int)(((uint64_t)(uint32_t)t * P.tx_recip) >> 32), tx = t - ty * P.TX;
+                const int x0 = tx * kTW + 4 * hx, y = ty * kTH + ry;
+                const float fy = __fadd_rn((float)y, 0.5f);
+                float fx[4], bw[4];
+                int bs[4];
+    #pragma unroll
+                for (int c = 0; c < 4; ++c) {
+                    fx[c] = __fadd_rn((float)(x0 + c), 0.5f);
+                    bw[c] = -INFINITY;
+                    bs[c] = INT_MAX;
+                }
+                // One bin entry against this lane's 4 pixels.  Bins are in fill
+                // (arbitrary) order, so the strict depth compare alone would give
+                // an exact depth tie to whichever triangle came first; every time
+                // a depth equals the pixel's current best (covered or not: one
+                // compare instead of two, at the price of re-walking about 4 % of
+                // the tile groups, where adjacent triangles' depth planes agree to
+                // the last bit) the lane notes it, and a tile group where any lane
+                // did is walked again with the full rule (larger 1/Z, lower index
+                // on equal 1/Z).
+                uint32_t tie_u = 0u;
+                // (outside: the entry's complement masks shifted so that bit c is
+                // this lane's column c and bit 8 + ry - 4 hx its row)
+                auto raster_entry = [&](int s, uint32_t outside, bool exact) {
+                    const float4* rp = reinterpret_cast<const float4*>(&rec[s]);
+                    const float4 q0 = rp[0], q1 = rp[1], q2 = rp[2], q3 = rp[3];
+                    const float r0 = __fmaf_rn(q0.y, fy, q0.z);
+                    const float r1 = __fmaf_rn(q1.y, fy, q1.z);
+                    const float r2 = __fmaf_rn(q2.y, fy, q2.z);
+                    const float rw = __fmaf_rn(q3.y, fy, q3.z);
+                    if (exact) {
+    #pragma unroll
+                        for (int c = 0; c < 4; ++c) {
+                            const float E0 = __fmaf_rn(q0.x, fx[c], r0);
+                            const float E1 = __fmaf_rn(q1.x, fx[c], r1);
+                            const float E2 = __fmaf_rn(q2.x, fx[c], r2);
+                            const float wz = __fmaf_rn(q3.x, fx[c], rw);
+                            const bool in = ((outside & (row_out | (1u << c))) == 0u) && (E0 > q0.w) &&
+                                            (E1 > q1.w) && (E2 > q2.w);
+                            const bool better = in && (wz > bw[c] || (wz == bw[c] && s < bs[c]));
+                            bw[c] = better ? wz : bw[c];
+                            bs[c] = better ? s : bs[c];
+                        }
+                    } else {
+                        uint32_t t4 = 0u;
+                        pixels4(q0, q1, q2, q3.x, r0, r1, r2, rw, fx, outside, row_out, s, bw, bs, t4);
+                        tie_u |= t4;
                     }
-                // sum over the group's kG lanes
-#pragma unroll
-                for (int o = kG / 2; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
-                if (gl == 0 && has_tile) tile_loss[t] = acc;
+                };
+                if (!walk_all) {
+                    const int n_max = (int)__reduce_max_sync(0xffffffffu, (unsigned)n_mine);
+                    if (!kImage && lane == 0 && P.stats) atomicAdd(&P.stats[5], (unsigned long long)n_max);
+                    // a group whose bin is shorter walks a sentinel entry (every
+                    // row and column outside: no pixel is in) instead of
+                    // branching around the step
+                    for (int k = 0; k < n_max; ++k) {
+                        const uint32_t e = k < n_mine ? ent[beg + k] : kSentinel;
+                        raster_entry((int)(e >> 16), e >> col_shift, false);
+                    }
+                    if (__any_sync(0xffffffffu, tie_u != 0u)) {
+    #pragma unroll
+                        for (int c = 0; c < 4; ++c) {
+                            bw[c] = -INFINITY;
+                            bs[c] = INT_MAX;
+                        }
+                        for (int k = 0; k < n_max; ++k) {
+                            const uint32_t e = k < n_mine ? ent[beg + k] : kSentinel;
+                            raster_entry((int)(e >> 16), e >> col_shift, true);
+                        }
+                    }
+                } else {
+                    // every triangle in index order (culled ones have an empty
+                    // box), so the strict compare already keeps the lower index
+                    for (int s = 0; s < P.nt; ++s) {
+                        const uint2 bb = bbx[s];
+                        const int xlo = (int)(bb.x & 0xffffu), xhi = (int)(bb.x >> 16);
+                        const int ylo = (int)(bb.y & 0xffffu), yhi = (int)(bb.y >> 16);
+                        if (has_tile && xlo <= xhi && y >= ylo && y <= yhi)
+                            raster_entry(s, ((~span_bits(xlo - tx * kTW, xhi - tx * kTW) & 0xFFu) >> col_shift) & 0xFu,
+                                         false);
+                    }
+                }
+                // (every group runs the shuffles below, a group without a tile too)
+                float sh[4];
+    #pragma unroll
+                for (int c = 0; c < 4; ++c) sh[c] = bs[c] != INT_MAX ? tshade[bs[c]] : 0.0f;
+                const bool rowv = has_tile && y < P.H;
+                if (kImage) {
+    #pragma unroll
+                    for (int c = 0; c < 4; ++c)
+                        if (rowv && x0 + c < P.W) {
+                            const size_t q = (size_t)y * P.W + x0 + c;
+                            if (ids) {
+                                ids[q] = bs[c] != INT_MAX ? bs[c] : -1;
+                            } else {
+                                img[3 * q] = sh[c] * P.alb0; img[3 * q + 1] = sh[c] * P.alb1; img[3 * q + 2] = sh[c] * P.alb2;
+                            }
+                        }
+                } else {
+                    float tg[12];
+                    if (rowv && vec_target && x0 + 3 < P.W) {
+                        const float4* tp = reinterpret_cast<const float4*>(P.target + 3 * ((size_t)y * P.W + x0));
+                        const float4 a0 = tp[0], a1 = tp[1], a2 = tp[2];
+                        tg[0] = a0.x; tg[1] = a0.y; tg[2] = a0.z; tg[3] = a0.w;
+                        tg[4] = a1.x; tg[5] = a1.y; tg[6] = a1.z; tg[7] = a1.w;
+                        tg[8] = a2.x; tg[9] = a2.y; tg[10] = a2.z; tg[11] = a2.w;
+                    } else {
+    #pragma unroll
+                        for (int c = 0; c < 4; ++c)
+    #pragma unroll
+                            for (int ch = 0; ch < 3; ++ch)
+                                tg[3 * c + ch] = (rowv && x0 + c < P.W) ? P.target[3 * ((size_t)y * P.W + x0 + c) + ch] : 0.0f;
+                    }
+                    float acc = 0.0f;
+    #pragma unroll
+                    for (int c = 0; c < 4; ++c)
+                        if (rowv && x0 + c < P.W) {
+                            const float d0 = sh[c] * P.alb0 - tg[3 * c], d1 = sh[c] * P.alb1 - tg[3 * c + 1];
+                            const float d2 = sh[c] * P.alb2 - tg[3 * c + 2];
+                            acc += d0 * d0 + d1 * d1 + d2 * d2;
+                        }
+                    // sum over the group's kG lanes
+    #pragma unroll
+                    for (int o = kG / 2; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
+                    if (gl == 0 && has_tile) tile_loss[t] = acc;
+                }
             }
         }
+        if (!kImage && tid == 0 && P.stats && walked) atomicAdd(&P.stats[6], 1ull);
         // ---- 6. reduction -----------------------------------------------------
         if (!kImage) {
             __syncthreads();
             // thread i sums tiles i, i + 1024, ...; then a fixed shuffle tree
             float acc = 0.0f;
+            const float* tile_loss = reinterpret_cast<const float*>(tcnt);
             for (int t = tid; t < P.T; t += kThreads) acc += tile_loss[t];
             acc = warp_sum(acc);
             if (lane == 0) s_part[warp] = acc;

@@ -220,40 +220,53 @@ def _sheets_scene(W):
     return sc
 
 
-@pytest.mark.parametrize("W,overflow", [(128, False), (512, True)])
-def test_revolve_stacked_sheets_and_bin_overflow(W, overflow):
+@pytest.mark.parametrize("W,banded", [(128, False), (512, True)])
+def test_revolve_stacked_sheets_binned_and_banded(W, banded):
     """Eight stacked, tilted sheets of 128 triangles each: every pixel is
     covered at several depths, and every triangle spans many tiles.  At 128^2
-    the tile bins hold about 6,000 entries (the binned raster); at 512^2 more
-    than 40,000, beyond the 16,384-entry bin capacity, so every render takes
-    the fallback in which each tile walks every triangle.  The scene's
-    overflow counter shows which path ran.  Both paths against the
-    oracle: images pixel by pixel (the depth winner decides each pixel's
-    shade), then an aggregate Hessian on identical samples."""
+    the tile bins hold about 6,000 entries (one binned pass); at 512^2 more
+    than 40,000, beyond the bin capacity, so every render is binned and
+    rastered in bands of tile rows.  The scene's counters show which path
+    ran.  Both against the oracle: images pixel by pixel (the depth winner
+    decides each pixel's shade), then an aggregate Hessian on identical
+    samples."""
     sc = _sheets_scene(W)
+    _check_mesh_paths(sc, W, W, 16, banded, False)
+
+
+def test_revolve_tile_row_beyond_capacity_walks_every_triangle():
+    """A 512 x 4 image (one row of tiles) in front of 1,000 stacked, tilted
+    full-frame sheets (2,000 triangles): the row alone holds more than ten
+    times the entries the bins can take, so its tiles walk every triangle.
+    Images and an estimate against the oracle."""
+    sc = wl.revolve_scene(width=512, height=4)
+    sc["vertices"], sc["triangles"] = wl.sheets_mesh(layers=1000, grid=1)
+    sc["scale"] = np.float32(1024.0)
+    _check_mesh_paths(sc, 512, 4, 8, True, True)
+
+
+def _check_mesh_paths(sc, W, H, M, banded, walked):
     Sc = hr.Scene(sc)
     r = O.RevolveRenderer(sc)
-    before = hr.hr_scene_get_stats(Sc.handle).mesh_overflow_renders
+    before = hr.hr_scene_get_stats(Sc.handle)
     g = np.random.default_rng(7)
     for _ in range(3):
         p = np.asarray(sc["theta_query"]) + g.normal(0, 0.2, 2)
-        gi = Sc.render(p).reshape(W, W, 3)
-        oi = r.image(p.astype(np.float32)).reshape(W, W, 3)
+        gi = Sc.render(p).reshape(H, W, 3)
+        oi = r.image(p.astype(np.float32)).reshape(H, W, 3)
         assert np.array_equal(gi.sum(-1) > 0, oi.sum(-1) > 0), "coverage differs"
         assert np.allclose(gi, oi, rtol=1e-5, atol=1e-6), "a different triangle won some pixel"
-    flat, dbg, ref = run_both(sc, r, "hessian", 16, "aggregate", scene=Sc)
+    flat, dbg, ref = run_both(sc, r, "hessian", M, "aggregate", scene=Sc)
     check_samples(dbg, ref)
-    assert_losses_close(dbg["losses"], ref.losses, 2e-5, "sheets losses")
-    assert_estimate_close(flat, ref, what=f"sheets {W}")
+    assert_losses_close(dbg["losses"], ref.losses, 2e-5, "mesh losses")
+    assert_estimate_close(flat, ref, what=f"mesh {W}x{H}")
     st = hr.hr_scene_get_stats(Sc.handle)
-    after = st.mesh_overflow_renders
     Sc.close()
-    assert st.mesh_renders == 16          # the estimate's renders (images are not counted)
-    if overflow:
-        assert after - before == 16, (before, after)
-    else:
-        assert after == before == 0, (before, after)
-        assert 0 < st.mesh_bin_entries and st.mesh_raster_steps > 0
+    assert st.mesh_renders - before.mesh_renders == M   # the estimate's renders (images are not counted)
+    assert st.mesh_overflow_renders - before.mesh_overflow_renders == (M if banded else 0)
+    assert st.mesh_walk_all_renders - before.mesh_walk_all_renders == (M if walked else 0)
+    assert st.mesh_bin_entries > 0
+    assert (st.mesh_raster_steps > 0) != walked   # binned raster steps are counted; a walk has none
 
 
 # ---------------------------------------------------------------------------

@@ -544,7 +544,7 @@ def run_secondary(args):
                                          "p99": float(np.percentile(times, 99))},
                           "stage_ms": dict(zip(("sample", "render_loss", "sums"),
                                                np.mean(stage, axis=0).tolist()))}
-        if args.workload == "disc":
+        if args.workload == "disc" and not args.no_queue:
             line["queue"] = disc_queue_bench(torch, hr, wl, stream, flush)
         line["config"] = ({"workload": "disc2d 64x64 gray, r 0.2, 2 params, sigma 0.05"} if args.workload == "disc"
                           else {"workload": "path-traced box 128x128 RGB, 4 spp, depth 3, 6 params, sigma 0.05, "
@@ -829,6 +829,8 @@ def main():
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="native", choices=["native", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-queue", action="store_true",
+                    help="--workload disc: skip the persistent-queue measurement")
     ap.add_argument("--no-secondary", action="store_true",
                     help="skip the compact path-tracer, Newton-CG and serving measurements of the headline line")
     ap.add_argument("--workload", default="revolve", choices=["revolve", "disc", "ptbox", "newton", "serving", "boxes", "optimise"],

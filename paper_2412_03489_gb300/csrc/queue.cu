@@ -114,6 +114,14 @@ __device__ __forceinline__ unsigned long long ld_acquire_gpu(const unsigned long
 __device__ __forceinline__ void st_release_gpu(unsigned long long* p, unsigned long long v) {
     asm volatile("st.release.gpu.global.u64 [%0], %1;" ::"l"(p), "l"(v) : "memory");
 }
+__device__ __forceinline__ void st_release_gpu(int* p, int v) {
+    asm volatile("st.release.gpu.global.s32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
+}
+__device__ __forceinline__ int ld_acquire_gpu(const int* p) {
+    int v;
+    asm volatile("ld.acquire.gpu.global.s32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+    return v;
+}
 __device__ __forceinline__ void st_release_sys(int* p, int v) {
     asm volatile("st.release.sys.global.s32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
 }
@@ -216,7 +224,8 @@ __global__ void __launch_bounds__(32 * kQWarps) queue_disc_kernel(QArgs A) {
     if (blockIdx.x == 0 && warp == 0) {
         code = dispatch_loop(A, lane);
         // no more units get published: the workers leave once they run out
-        if (lane == 0) *reinterpret_cast<volatile int*>(&A.ctl->stop) = 1;
+        // (stop is released after the last published count)
+        if (lane == 0) st_release_gpu(&A.ctl->stop, 1);
     } else {
         QReq& R = s_req[warp];
         for (;;) {
@@ -237,7 +246,11 @@ __global__ void __launch_bounds__(32 * kQWarps) queue_disc_kernel(QArgs A) {
                         last = pub;
                         t0 = clock64();
                     }
-                    if (ld_volatile(&A.ctl->stop)) break;
+                    if (ld_acquire_gpu(&A.ctl->stop)) {
+                        // the count read after stop is final: a ticket below it still runs
+                        if (u < ld_acquire_gpu(&A.ctl->units)) got = 1;
+                        break;
+                    }
                     if (clock64() - t0 > A.safety) { got = -1; break; }
                     __nanosleep(ns);
                     ns = min(2u * ns, 4096u);
@@ -367,10 +380,16 @@ bool slot_finished(const hr_queue_s* q, int slot) {
     return __atomic_load_n(q->h_flag + slot, __ATOMIC_ACQUIRE) != 0;
 }
 
+// A request has finished when its flag is set, or when its slot no longer
+// carries its ticket (its result was read and the slot may hold a newer one).
+bool request_finished(const hr_queue_s* q, uint64_t ticket) {
+    const int slot = (int)(ticket % (uint64_t)q->cap);
+    return q->slot_ticket[slot] != ticket + 1 || slot_finished(q, slot);
+}
+
 // Arena blocks come back in submission order, as requests finish.
 void retire(hr_queue_s* q) {
-    while (!q->inflight.empty() && slot_finished(q, (int)(q->inflight.front().ticket % (uint64_t)q->cap)))
-        q->inflight.pop_front();
+    while (!q->inflight.empty() && request_finished(q, q->inflight.front().ticket)) q->inflight.pop_front();
     if (q->inflight.empty()) q->head = 0;
 }
 

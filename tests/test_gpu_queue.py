@@ -266,3 +266,31 @@ def test_queue_batches():
         finally:
             hr.hr_queue_destroy(q)
     S.close()
+
+
+def test_queue_exits_and_relaunches_under_bursts():
+    """A 50 us idle budget with bursts of requests separated by pauses: the
+    kernel leaves and is launched again many times, with requests arriving
+    around its exits.  Every request completes (a unit lost at an exit would
+    leave its request waiting) and matches the plain path bit for bit."""
+    sc = wl.disc_scene()
+    S = hr.Scene(sc)
+    reqs = requests(sc, 60, seed=17)
+    ref = [plain(S, sc, r) for r in reqs]
+    q = hr.hr_queue_create(S, max_requests=128, idle_budget_us=50)
+    outs = [out_for(r) for r in reqs]
+    try:
+        tickets = []
+        for b in range(0, len(reqs), 3):
+            for r in reqs[b:b + 3]:
+                tickets.append(hr.hr_queue_submit(q, r["q"], r["theta"], r["v"], opts(sc, r)))
+            time.sleep(0.0002 * (b % 4))
+        for t, o in zip(tickets, outs):
+            hr.hr_queue_wait(q, t, o, timeout_ms=20000)
+        for r, o, e in zip(reqs, outs, ref):
+            assert np.array_equal(o, e), (r, o, e)
+        status, launches = hr.hr_queue_status(q)
+        assert launches >= 2
+    finally:
+        hr.hr_queue_destroy(q)
+        S.close()

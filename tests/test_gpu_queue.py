@@ -294,3 +294,26 @@ def test_queue_exits_and_relaunches_under_bursts():
     finally:
         hr.hr_queue_destroy(q)
         S.close()
+
+
+@pytest.mark.parametrize("W,H,grey", [(64, 64, True), (37, 23, False), (96, 10, True), (512, 3, False)])
+def test_queue_other_sizes_and_grey_targets(W, H, grey):
+    """The queue's renders take the same loss paths as the plain kernel: row
+    spans for 0/1 targets, the per-pixel loops for grey ones (fixed columns
+    per lane at W = 64, the general loop at W = 96), ragged and wide images."""
+    sc = wl.disc_scene(width=W, height=H)
+    tgt = np.random.default_rng(W + H).uniform(0.0, 1.0, size=W * H).astype(np.float32) if grey else None
+    S = hr.Scene(sc, target_image=tgt) if grey else hr.Scene(sc)
+    reqs = requests(sc, 10, seed=W * H)
+    ref = [plain(S, sc, r) for r in reqs]
+    q = hr.hr_queue_create(S, max_requests=16, idle_budget_us=2000)
+    try:
+        tickets = [hr.hr_queue_submit(q, r["q"], r["theta"], r["v"], opts(sc, r)) for r in reqs]
+        outs = [out_for(r) for r in reqs]
+        for t, o in zip(tickets, outs):
+            hr.hr_queue_wait(q, t, o)
+        for r, o, e in zip(reqs, outs, ref):
+            assert np.array_equal(o, e), (r, o, e)
+    finally:
+        hr.hr_queue_destroy(q)
+        S.close()

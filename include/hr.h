@@ -480,7 +480,8 @@ hr_status hr_server_wait(hr_server srv, uint64_t ticket, void* h_out, hr_request
 typedef struct hr_queue_s* hr_queue;
 
 typedef struct {
-    int32_t max_requests;    /* ring slots: requests submitted and not yet waited for, 1..65536 */
+    int32_t max_requests;    /* ring slots: requests submitted and not yet waited for, 1..16384
+                                (4 KiB of device memory and 0.5 KiB host-mapped each) */
     int32_t idle_budget_us;  /* the kernel leaves after this long without a new request, 1..10^7 */
     int64_t arena_bytes;     /* device bytes for the perturbations, weights and losses of
                                 unfinished requests (>= 1 MiB); a request takes

@@ -581,7 +581,7 @@ hr_status hr_destroy_scene(hr_scene s) {
     if (s->stream) cudaStreamSynchronize(s->stream);
     cudaFree(sc.target); cudaFree(sc.verts); cudaFree(sc.tris); cudaFree(sc.tnrm); cudaFree(sc.tile_t2);
     cudaFree(sc.raw); cudaFree(sc.pidx); cudaFree(sc.qA); cudaFree(sc.qb); cudaFree(sc.rv_stats);
-    cudaFree(sc.pt_stats); cudaFree(sc.tbits);
+    cudaFree(sc.pt_stats); cudaFree(sc.tbits); cudaFree(sc.trowpop);
     s->ws.release_all();
     for (cudaEvent_t& e : s->ev)
         if (e) cudaEventDestroy(e);

@@ -115,28 +115,35 @@ __device__ __forceinline__ float disc_rows(const float* __restrict__ target, int
 // Binary targets (every pixel exactly 0 or 1).  Each pixel's squared
 // difference is then 0 or 1, so the per-pixel FP32 sum is the count of pixels
 // where the disc and the target differ: an integer below 2^24, exact in any
-// order.  Row y of the disc is an interval of columns.  With dx = px - cx
-// rounded to FP32, the test fma(dx, dx, dy^2) < r^2 is non-increasing in x
-// left of the centre column xc (the first column with px >= cx) and
-// non-decreasing from xc on, because rounding is monotone; so the covered
-// columns are [a, e) for the first covered column a of [0, xc) (xc if none)
-// and the first uncovered column e of [xc, W) (W if none).  Both ends are
-// found by the exact test itself, started from the real-arithmetic ends
-// (cx -+ sqrt(r^2 - dy^2)) W - 1/2 and stepped at most kSpanSteps columns;
-// a start further off falls back to a binary search on the same predicate.
-// The row's count is then popc(target bits XOR span bits) over its words.
+// order.  Both tests the pixel test is made of are monotone on either side of
+// the disc's centre, because rounding is monotone:
+//   - in a row, with dx = px - cx rounded to FP32, fma(dx, dx, dy^2) < r^2 is
+//     non-increasing in x left of the centre column (the first column with
+//     px >= cx) and non-decreasing from it, so the row's covered columns are
+//     one interval [a, e);
+//   - only rows with dy^2 = (py - cy)^2 < r^2 (rounded) can hold a covered
+//     pixel, because fma(dx, dx, dy^2) >= dy^2.  The FP32 roundings of those
+//     tests and of the band below move a row's position by less than
+//     (|cy| + r) H 2^-22 + 1 rows, so every such row lies inside the
+//     real-arithmetic band (cy -+ r) H - 1/2 widened by 2 + (|cy| + r) H 2^-20
+//     rows; the rows [y0, y1) of that band are the only ones tested.
+// A row's span ends are found with the exact test itself, started from the
+// real-arithmetic ends cx -+ sqrt(r^2 - dy^2) and stepped at most kSpanSteps
+// columns; a start further off falls back to a binary search on the same
+// predicate.  Rows outside [y0, y1) differ from the target in its set pixels
+// (a prefix sum of the rows' popcounts); a row inside differs in
+// popc(target bits XOR span bits) over its words (an empty span when its
+// dy^2 >= r^2).
 constexpr int kSpanSteps = 4;
 
-struct DiscRow {
-    const float* px;
-    float cx, dy2, r2;
-    __device__ __forceinline__ bool cov(int x) const {
-        const float dx = __fsub_rn(px[x], cx);
-        return __fmaf_rn(dx, dx, dy2) < r2;
-    }
+// The bit-packed target of a binary image: bit x % 32 of word x / 32 of row y
+// is pixel (x, y); rowpop [H + 1] the prefix sums of the rows' popcounts.
+struct DiscBits {
+    const uint32_t* bits;   // null: the target is not binary
+    const int* rowpop;
 };
 
-// clamp of a float column estimate to [lo, hi] (NaN to lo)
+// clamp of a float index estimate to [lo, hi] (NaN to lo)
 __device__ __forceinline__ int clamp_col(float f, int lo, int hi) {
     return (int)fminf(fmaxf(f, (float)lo), (float)hi);
 }
@@ -152,70 +159,77 @@ __device__ __forceinline__ int first_true(int lo, int hi, Pred pred) {
     return lo;
 }
 
-// covered columns [a, e) of one row (empty when dy^2 >= r^2: the test is never true)
-__device__ __forceinline__ void disc_span(const float* px, int W, float fW, float cx, float dy2, float r2,
-                                          int& a, int& e) {
-    a = e = 0;
-    if (!(dy2 < r2)) return;
-    const DiscRow R{px, cx, dy2, r2};
-    // centre column: first x with px[x] >= cx (px strictly increasing)
-    int xc = clamp_col(ceilf(__fmaf_rn(cx, fW, -0.5f)), 0, W);
+// [a, e): the indices i of the centre table ctr [N] (strictly increasing, the
+// FP32 centres (i + 1/2)/N) where the test in(i) holds, given that in() is
+// non-increasing in i below the first centre >= c and non-decreasing from it;
+// half is the real-arithmetic half-width of the interval around c.
+template <class In>
+__device__ __forceinline__ void exact_span(const float* ctr, int N, float fN, float c, float half, In in, int& a,
+                                           int& e) {
+    // centre index: first i with ctr[i] >= c
+    int ic = clamp_col(ceilf(__fmaf_rn(c, fN, -0.5f)), 0, N);
     int k = 0;
-    for (; k < kSpanSteps && xc > 0 && px[xc - 1] >= cx; ++k) --xc;
-    for (; k < kSpanSteps && xc < W && px[xc] < cx; ++k) ++xc;
-    if (k == kSpanSteps) xc = first_true(0, W, [&](int x) { return px[x] >= cx; });
-    const float h = sqrtf(__fsub_rn(r2, dy2));
-    // left end: first covered column of [0, xc)
-    a = clamp_col(ceilf(__fmaf_rn(__fsub_rn(cx, h), fW, -0.5f)), 0, xc);
+    for (; k < kSpanSteps && ic > 0 && ctr[ic - 1] >= c; ++k) --ic;
+    for (; k < kSpanSteps && ic < N && ctr[ic] < c; ++k) ++ic;
+    if (k == kSpanSteps) ic = first_true(0, N, [&](int i) { return ctr[i] >= c; });
+    // lower end: first i of [0, ic) where the test holds
+    a = clamp_col(ceilf(__fmaf_rn(__fsub_rn(c, half), fN, -0.5f)), 0, ic);
     k = 0;
-    for (; k < kSpanSteps && a > 0 && R.cov(a - 1); ++k) --a;
-    for (; k < kSpanSteps && a < xc && !R.cov(a); ++k) ++a;
-    if (k == kSpanSteps) a = first_true(0, xc, [&](int x) { return R.cov(x); });
-    // right end: first uncovered column of [xc, W)
-    e = clamp_col(ceilf(__fmaf_rn(__fadd_rn(cx, h), fW, -0.5f)), xc, W);
+    for (; k < kSpanSteps && a > 0 && in(a - 1); ++k) --a;
+    for (; k < kSpanSteps && a < ic && !in(a); ++k) ++a;
+    if (k == kSpanSteps) a = first_true(0, ic, in);
+    // upper end: first i of [ic, N) where it fails
+    e = clamp_col(ceilf(__fmaf_rn(__fadd_rn(c, half), fN, -0.5f)), ic, N);
     k = 0;
-    for (; k < kSpanSteps && e > xc && !R.cov(e - 1); ++k) --e;
-    for (; k < kSpanSteps && e < W && R.cov(e); ++k) ++e;
-    if (k == kSpanSteps) e = first_true(xc, W, [&](int x) { return !R.cov(x); });
+    for (; k < kSpanSteps && e > ic && !in(e - 1); ++k) --e;
+    for (; k < kSpanSteps && e < N && in(e); ++k) ++e;
+    if (k == kSpanSteps) e = first_true(ic, N, [&](int i) { return !in(i); });
 }
 
-// Mismatch count of this lane's rows y = lane, lane + 32, ... against the
-// bit-packed target (bit x % 32 of word x / 32 of a row: pixel x is 1).
-__device__ __forceinline__ int disc_lane_mismatch(const uint32_t* __restrict__ tbits, int W, int H,
-                                                  const float* px, const float* py, float cx, float cy,
-                                                  float r2, int lane) {
+// Mismatch count of the disc at (cx, cy) against a binary target, summed over
+// the warp (every lane returns it): the rows [y0, y1) of the widened band go
+// to lanes y0 + lane, y0 + lane + 32, ...; the others come from the prefix sums.
+__device__ __forceinline__ int disc_mismatch_warp(const DiscBits& tb, int W, int H, const float* px,
+                                                  const float* py, float cx, float cy, float radius, float r2,
+                                                  int lane) {
     const int words = (W + 31) >> 5;
     const float fW = (float)W;
-    int cnt = 0;
-    for (int y = lane; y < H; y += 32) {
+    const float fH = (float)H;
+    const float mg = 2.0f + (fabsf(cy) + radius) * fH * 0x1p-20f;   // rows of margin (NaN: no rows)
+    const int y0 = clamp_col(floorf(__fmaf_rn(__fsub_rn(cy, radius), fH, -0.5f) - mg), 0, H);
+    const int y1 = max(y0, clamp_col(ceilf(__fmaf_rn(__fadd_rn(cy, radius), fH, -0.5f) + mg) + 1.0f, 0, H));
+    int cnt = lane == 0 ? __ldg(tb.rowpop + H) - (__ldg(tb.rowpop + y1) - __ldg(tb.rowpop + y0)) : 0;
+    for (int y = y0 + lane; y < y1; y += 32) {
         const float dy = __fsub_rn(py[y], cy);
-        int a, e;
-        disc_span(px, W, fW, cx, __fmul_rn(dy, dy), r2, a, e);
-        const uint32_t* row = tbits + (size_t)y * words;
+        const float dy2 = __fmul_rn(dy, dy);
+        int a = 0, e = 0;
+        if (dy2 < r2)
+            exact_span(px, W, fW, cx, sqrtf(__fsub_rn(r2, dy2)), [&](int x) {
+                const float dx = __fsub_rn(px[x], cx);
+                return __fmaf_rn(dx, dx, dy2) < r2;
+            }, a, e);
+        const uint32_t* row = tb.bits + (size_t)y * words;
         for (int j = 0; j < words; ++j) {
             const int lo = min(max(a - 32 * j, 0), 32), hi = min(max(e - 32 * j, 0), 32);
             const uint32_t m = (uint32_t)(((1ull << hi) - 1ull) & ~((1ull << lo) - 1ull));
             cnt += __popc(__ldg(row + j) ^ m);
         }
     }
-    return cnt;
+    return __reduce_add_sync(0xffffffffu, cnt);
 }
 
 // Loss of the disc at centre (cx, cy) against the target, by one warp (all
 // 32 lanes call; every lane returns the loss): the FP32 sum of the squared
 // differences over the image, divided by the pixel count.  With a binary
-// target (tbits non-null: its bit-packed rows) the sum is the exact mismatch
-// count of the row spans; otherwise each lane sums its pixels in pixel order,
-// then a shuffle tree adds the lanes.
-__device__ __forceinline__ float disc_loss_warp(const float* __restrict__ target, const uint32_t* __restrict__ tbits,
-                                                int W, int H, float radius, const float* px, const float* py,
-                                                float cx, float cy, int lane) {
+// target (tb.bits non-null) the sum is the exact mismatch count of the spans;
+// otherwise each lane sums its pixels in pixel order, then a shuffle tree adds
+// the lanes.
+__device__ __forceinline__ float disc_loss_warp(const float* __restrict__ target, const DiscBits& tb, int W, int H,
+                                                float radius, const float* px, const float* py, float cx, float cy,
+                                                int lane) {
     const float r2 = __fmul_rn(radius, radius);
     const int npx = W * H;
-    if (tbits) {
-        const int cnt = __reduce_add_sync(0xffffffffu, disc_lane_mismatch(tbits, W, H, px, py, cx, cy, r2, lane));
-        return __fdiv_rn((float)cnt, (float)npx);
-    }
+    if (tb.bits) return __fdiv_rn((float)disc_mismatch_warp(tb, W, H, px, py, cx, cy, radius, r2, lane), (float)npx);
     auto value = [cx, cy, r2](float px_, float py_) {
         const float dx = __fsub_rn(px_, cx);
         const float dy = __fsub_rn(py_, cy);

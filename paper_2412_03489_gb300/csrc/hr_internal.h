@@ -153,6 +153,7 @@ struct DevScene {
     // disc
     float radius = 0.f;
     uint32_t* tbits = nullptr;    // [H][(W + 31) / 32] bit-packed target (bit set: pixel is 1)
+    int* trowpop = nullptr;       // [H + 1] prefix sums of the packed rows' popcounts
     int tbinary = 0;              // 1: every target pixel is 0 or 1 (the loss is a mismatch count)
     // revolve
     float* verts = nullptr;       // [nv][3]
@@ -200,7 +201,7 @@ bool revolve_layout(DevScene& sc, int max_smem);
 int revolve_tiles(const DevScene& sc);
 void revolve_prepare(DevScene& sc, cudaStream_t s);   // normals, kernel attributes
 void revolve_tile_t2(DevScene& sc, cudaStream_t s);   // after the target exists
-// disc scenes, after the target exists: sc.tbits and sc.tbinary
+// disc scenes, after the target exists: sc.tbits, sc.trowpop and sc.tbinary
 cudaError_t disc_prepare_target(DevScene& sc, cudaStream_t s);
 
 int num_sms();

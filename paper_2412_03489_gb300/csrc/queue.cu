@@ -53,9 +53,23 @@ constexpr int kQMaxResult = kQMaxN * kQMaxN;
 constexpr int kQUnitBits = 24;       // unit ring entry = request << 24 | unit
 constexpr unsigned long long kQUnitMask = (1ull << kQUnitBits) - 1ull;
 constexpr int kQUnitRing = 1 << 20;  // unit ring entries
+constexpr int kQReplicas = 8;        // device copies of each descriptor (unit k reads copy k % 8)
+constexpr int kQBatch = 4;           // descriptors the dispatcher loads per round
+
+// The sampler's inputs of a request (the fields sample_leg reads).
+struct QSample {
+    int32_t n, E;
+    uint64_t seed;
+    const double* v;                 // set to QReq::vv on the device
+    float* tau;                      // [G M][n]
+    float* w;                        // [G M][E]
+    float* invS;                     // null
+    uint2* meta;                     // null
+    const int32_t* step;             // null
+};
 
 struct __align__(16) QReq {
-    SampleArgs sa;                   // n, E, sigma, seed, tau, w (v is set to vv on the device)
+    QSample sa;
     Lobes lobes;
     SampleGroup groups[kQMaxGroups];
     double vv[kQMaxN];               // HVP direction
@@ -67,6 +81,10 @@ struct __align__(16) QReq {
     int units, G, P, E, n, elementwise, hessian, pad;
     double inv2P;
 };
+
+// one 16-byte load per lane copies a descriptor
+static_assert(sizeof(QReq) <= 32 * 16, "a queue descriptor is at most 512 bytes");
+constexpr int kQInt4 = (int)(sizeof(QReq) / 16);
 
 // Device control block; the claim counter (atomics) and the published counts
 // (polled by idle warps) sit on separate 128-byte lines.
@@ -90,13 +108,13 @@ struct QArgs {
     QCtl* ctl;
     QHost* host;                     // device view of the host-mapped block
     const QReq* h_ring;              // device view of the host ring
-    QReq* d_ring;
+    QReq* d_ring;                    // [cap][kQReplicas]
     unsigned long long* unit_ring;   // [kQUnitRing] request << 24 | unit
     int cap;                         // request ring slots
     int W, H;
     float radius;
     const float* target;
-    const uint32_t* tbits;           // bit-packed binary target, or null
+    DiscBits tb;                     // bit-packed binary target (bits null: not binary)
     long long budget;                // dispatcher idle budget, clock64 cycles
     long long safety;                // worker wait bound, clock64 cycles
 };
@@ -186,21 +204,40 @@ __device__ int dispatch_loop(const QArgs& A, int lane) {
         hs = __shfl_sync(0xffffffffu, hs, 0);
         stop = __shfl_sync(0xffffffffu, stop, 0);
         if (hs > seen) {
-            for (unsigned long long r = seen; r < hs; ++r) {
-                const int slot = (int)(r % (unsigned long long)A.cap);
-                const int4* s = reinterpret_cast<const int4*>(A.h_ring + slot);
-                int4* d = reinterpret_cast<int4*>(A.d_ring + slot);
-                for (int i = lane; i < (int)(sizeof(QReq) / 16); i += 32) __stcg(d + i, __ldcv(s + i));
-                const int units = __ldcv(&A.h_ring[slot].units);
-                for (int k = lane; k < units; k += 32)
-                    __stcg(A.unit_ring + ((U + (unsigned long long)k) % kQUnitRing), (r << kQUnitBits) | (unsigned)k);
-                U += (unsigned long long)units;
-            }
-            __threadfence();
-            __syncwarp();
-            if (lane == 0) {
-                st_release_gpu(&A.ctl->reqs, hs);
-                st_release_gpu(&A.ctl->units, U);
+            // kQBatch descriptors per round: their host-memory loads are in
+            // flight together; each is stored as kQReplicas device copies on
+            // different lines, so that the warps taking one request's units
+            // spread their loads over the L2
+            for (unsigned long long r0 = seen; r0 < hs; r0 += kQBatch) {
+                const int cnt = (int)min((unsigned long long)kQBatch, hs - r0);
+                int4 v[kQBatch];
+                int un[kQBatch];
+#pragma unroll
+                for (int j = 0; j < kQBatch; ++j) {
+                    if (j >= cnt) break;
+                    const int slot = (int)((r0 + j) % (unsigned long long)A.cap);
+                    if (lane < kQInt4) v[j] = __ldcv(reinterpret_cast<const int4*>(A.h_ring + slot) + lane);
+                    un[j] = __ldcv(&A.h_ring[slot].units);
+                }
+#pragma unroll
+                for (int j = 0; j < kQBatch; ++j) {
+                    if (j >= cnt) break;
+                    const unsigned long long r = r0 + j;
+                    const int slot = (int)(r % (unsigned long long)A.cap);
+                    if (lane < kQInt4)
+                        for (int c = 0; c < kQReplicas; ++c)
+                            __stcg(reinterpret_cast<int4*>(A.d_ring + (size_t)slot * kQReplicas + c) + lane, v[j]);
+                    for (int k = lane; k < un[j]; k += 32)
+                        __stcg(A.unit_ring + ((U + (unsigned long long)k) % kQUnitRing), (r << kQUnitBits) | (unsigned)k);
+                    U += (unsigned long long)un[j];
+                }
+                // publish each round, so that workers start on a long backlog
+                __threadfence();
+                __syncwarp();
+                if (lane == 0) {
+                    st_release_gpu(&A.ctl->reqs, r0 + (unsigned long long)cnt);
+                    st_release_gpu(&A.ctl->units, U);
+                }
             }
             seen = hs;
             t0 = clock64();
@@ -214,9 +251,62 @@ __device__ int dispatch_loop(const QArgs& A, int lane) {
     }
 }
 
-__global__ void __launch_bounds__(32 * kQWarps) queue_disc_kernel(QArgs A) {
+__device__ __forceinline__ void cp_async16(void* smem_dst, const void* gsrc) {
+    const unsigned d = (unsigned)__cvta_generic_to_shared(smem_dst);
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(d), "l"(gsrc) : "memory");
+}
+__device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_all;" ::: "memory"); }
+
+// Ticket u: 1 when its unit is published (acquired), 0 when it will not be
+// (block: the dispatcher stopped with u at or past the final count; !block:
+// not yet published), -1 when a blocking wait passed the safety bound without
+// any newly published unit.  Every lane returns the same value.
+__device__ int ticket_wait(const QArgs& A, int lane, unsigned long long u, bool block) {
+    int got = 0;
+    if (lane == 0) {
+        if (!block) {
+            got = u < ld_acquire_gpu(&A.ctl->units) ? 1 : 0;
+        } else {
+            long long t0 = clock64();
+            unsigned long long last = ~0ull;
+            unsigned ns = 128;
+            for (;;) {
+                const unsigned long long pub = ld_acquire_gpu(&A.ctl->units);
+                if (u < pub) { got = 1; break; }
+                if (pub != last) {
+                    last = pub;
+                    t0 = clock64();
+                }
+                if (ld_acquire_gpu(&A.ctl->stop)) {
+                    // the count read after stop is final: a ticket below it still runs
+                    if (u < ld_acquire_gpu(&A.ctl->units)) got = 1;
+                    break;
+                }
+                if (clock64() - t0 > A.safety) { got = -1; break; }
+                __nanosleep(ns);
+                ns = min(2u * ns, 4096u);
+            }
+        }
+        if (got > 0) __threadfence();
+    }
+    __syncwarp();
+    return __shfl_sync(0xffffffffu, got, 0);
+}
+
+// Start copying the descriptor of published ticket u into dst (completed by
+// cp_async_wait_all); returns the unit's index within its request.
+__device__ __forceinline__ int fetch_desc(const QArgs& A, int lane, unsigned long long u, QReq* dst) {
+    const unsigned long long ent = __ldcg(A.unit_ring + (u % kQUnitRing));
+    const int slot = (int)((ent >> kQUnitBits) % (unsigned long long)A.cap);
+    const int unit = (int)(ent & kQUnitMask);
+    const int4* src = reinterpret_cast<const int4*>(A.d_ring + (size_t)slot * kQReplicas + unit % kQReplicas);
+    if (lane < kQInt4) cp_async16(reinterpret_cast<int4*>(dst) + lane, src + lane);
+    return unit;
+}
+
+__global__ void __launch_bounds__(32 * kQWarps, 3) queue_disc_kernel(QArgs A) {
     __shared__ float s_px[HR_MAX_IMAGE_SIDE], s_py[HR_MAX_IMAGE_SIDE];
-    __shared__ QReq s_req[kQWarps];
+    __shared__ QReq s_req[kQWarps][2];
     centre_tables(s_px, s_py, A.W, A.H);
     __syncthreads();
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
@@ -227,54 +317,27 @@ __global__ void __launch_bounds__(32 * kQWarps) queue_disc_kernel(QArgs A) {
         // (stop is released after the last published count)
         if (lane == 0) st_release_gpu(&A.ctl->stop, 1);
     } else {
-        QReq& R = s_req[warp];
-        for (;;) {
-            // take a ticket and wait until its unit is published; leave on stop
-            // or after the safety bound
-            unsigned long long u = 0;
-            int got = 0;
-            if (lane == 0) {
-                u = atomicAdd(&A.ctl->claim, 1ull);
-                // the safety bound counts time without a newly published unit
-                long long t0 = clock64();
-                unsigned long long last = ~0ull;
-                unsigned ns = 128;
-                for (;;) {
-                    const unsigned long long pub = ld_acquire_gpu(&A.ctl->units);
-                    if (u < pub) { got = 1; break; }
-                    if (pub != last) {
-                        last = pub;
-                        t0 = clock64();
-                    }
-                    if (ld_acquire_gpu(&A.ctl->stop)) {
-                        // the count read after stop is final: a ticket below it still runs
-                        if (u < ld_acquire_gpu(&A.ctl->units)) got = 1;
-                        break;
-                    }
-                    if (clock64() - t0 > A.safety) { got = -1; break; }
-                    __nanosleep(ns);
-                    ns = min(2u * ns, 4096u);
-                }
-                __threadfence();
-            }
+        // Two descriptor buffers per warp: while one unit is sampled and
+        // rendered, the next ticket's descriptor (when already published)
+        // is on its way into the other buffer.
+        unsigned long long u = 0;
+        if (lane == 0) u = atomicAdd(&A.ctl->claim, 1ull);
+        u = __shfl_sync(0xffffffffu, u, 0);
+        int got = ticket_wait(A, lane, u, true);
+        int cur = 0;
+        int unit = got > 0 ? fetch_desc(A, lane, u, &s_req[warp][0]) : 0;
+        while (got > 0) {
+            cp_async_wait_all();
             __syncwarp();
-            got = __shfl_sync(0xffffffffu, got, 0);
-            if (got <= 0) {
-                if (got < 0) code = HR_ERR_TIMEOUT;
-                break;
-            }
-            u = __shfl_sync(0xffffffffu, u, 0);
-            const unsigned long long ent = __ldcg(A.unit_ring + (u % kQUnitRing));
-            const int slot = (int)((ent >> kQUnitBits) % (unsigned long long)A.cap);
-            const int unit = (int)(ent & kQUnitMask);
-            {
-                const int4* s = reinterpret_cast<const int4*>(A.d_ring + slot);
-                int4* d = reinterpret_cast<int4*>(&R);
-                for (int i = lane; i < (int)(sizeof(QReq) / 16); i += 32) d[i] = __ldcg(s + i);
-                __syncwarp();
-                if (lane == 0) R.sa.v = R.vv;
-                __syncwarp();
-            }
+            QReq& R = s_req[warp][cur];
+            if (lane == 0) R.sa.v = R.vv;
+            __syncwarp();
+            // the next ticket; its descriptor is fetched now if it is published
+            unsigned long long un = 0;
+            if (lane == 0) un = atomicAdd(&A.ctl->claim, 1ull);
+            un = __shfl_sync(0xffffffffu, un, 0);
+            const int ready = ticket_wait(A, lane, un, false);
+            int unit_n = ready > 0 ? fetch_desc(A, lane, un, &s_req[warp][1 - cur]) : 0;
             // 1. sample: lane l draws leg l & 1 of pair 16 unit + l / 2, row
             //    m = 2 p + leg (groups are contiguous: group g starts at row 2 g P)
             const int pairs = R.G * R.P;
@@ -292,7 +355,7 @@ __global__ void __launch_bounds__(32 * kQWarps) queue_disc_kernel(QArgs A) {
                 const float* t = R.sa.tau + (size_t)m * R.n;
                 const float cx = __fadd_rn(R.theta32[0], t[0]);
                 const float cy = __fadd_rn(R.theta32[1], t[1]);
-                const float loss = disc_loss_warp(A.target, A.tbits, A.W, A.H, A.radius, s_px, s_py, cx, cy, lane);
+                const float loss = disc_loss_warp(A.target, A.tb, A.W, A.H, A.radius, s_px, s_py, cx, cy, lane);
                 if (lane == 0) R.loss[m] = loss;
             }
             // 3. count the unit (weights and losses visible GPU-wide first); the
@@ -315,7 +378,15 @@ __global__ void __launch_bounds__(32 * kQWarps) queue_disc_kernel(QArgs A) {
                 }
             }
             __syncwarp();
+            // the next unit: wait for it unless its descriptor is already coming
+            if (ready <= 0) {
+                got = ticket_wait(A, lane, un, true);
+                if (got > 0) unit_n = fetch_desc(A, lane, un, &s_req[warp][1 - cur]);
+            }
+            cur = 1 - cur;
+            unit = unit_n;
         }
+        if (got < 0) code = HR_ERR_TIMEOUT;
     }
     // the last warp to leave rewinds the claim counter and records why the
     // launch ended
@@ -433,7 +504,7 @@ hr_status ensure_running(hr_queue_s* q) {
     a.H = sc.H;
     a.radius = sc.radius;
     a.target = sc.target;
-    a.tbits = sc.tbinary ? sc.tbits : nullptr;
+    a.tb = DiscBits{sc.tbinary ? sc.tbits : nullptr, sc.trowpop};
     a.budget = q->budget;
     a.safety = q->safety;
     queue_disc_kernel<<<q->grid, 32 * kQWarps, 0, q->kstream>>>(a);
@@ -507,16 +578,15 @@ hr_status queue_push(hr_queue_s* q, int32_t quantity, const double* h_theta, con
         for (int i = 0; i < n; ++i) R.vv[i] = h_v[i];
     R.sa.n = n;
     R.sa.E = E;
-    R.sa.sigma = o->sigma;
-    const double s2 = o->sigma * o->sigma;
-    R.sa.Zg = std::sqrt(2.0 / M_PI) / o->sigma;
-    R.sa.Zd = 4.0 * std::exp(-0.5) / (std::sqrt(2.0 * M_PI) * s2);
-    R.sa.Zo = R.sa.Zg * R.sa.Zg;
     R.sa.seed = o->seed;
+    // the lobe constants as the estimate path forms them
+    const double s2 = o->sigma * o->sigma;
+    const double Zg = std::sqrt(2.0 / M_PI) / o->sigma;
+    const double Zd = 4.0 * std::exp(-0.5) / (std::sqrt(2.0 * M_PI) * s2);
     R.sa.tau = reinterpret_cast<float*>(base);
     R.sa.w = reinterpret_cast<float*>(base + up256(sizeof(float) * Mt * n));
     R.loss = reinterpret_cast<float*>(base + up256(sizeof(float) * Mt * n) + up256(sizeof(float) * Mt * E));
-    R.lobes = make_lobes(o->sigma, R.sa.Zg, R.sa.Zd, R.sa.Zo, n);
+    R.lobes = make_lobes(o->sigma, Zg, Zd, Zg * Zg, n);
     for (int g = 0; g < G; ++g) {
         SampleGroup& gr = R.groups[g];
         gr.m0 = (int32_t)(g * o->n_perturb);
@@ -575,8 +645,8 @@ hr_status hr_queue_create(hr_scene scene, const hr_queue_opts* o, hr_queue* out)
     if (!scene || !o || !out) return fail(HR_ERR_INVALID_ARG, "NULL argument");
     *out = nullptr;
     if (scene->sc.kind != HR_SCENE_DISC2D) return fail(HR_ERR_UNSUPPORTED, "the persistent queue serves disc scenes");
-    if (o->max_requests < 1 || o->max_requests > 65536)
-        return fail(HR_ERR_INVALID_ARG, "max_requests must be 1..65536");
+    if (o->max_requests < 1 || o->max_requests > 16384)
+        return fail(HR_ERR_INVALID_ARG, "max_requests must be 1..16384");
     if (o->arena_bytes < (1 << 20)) return fail(HR_ERR_INVALID_ARG, "arena_bytes must be at least 1 MiB");
     if (o->idle_budget_us < 1 || o->idle_budget_us > 10000000)
         return fail(HR_ERR_INVALID_ARG, "idle_budget_us must be 1..10^7");
@@ -600,7 +670,7 @@ hr_status hr_queue_create(hr_scene scene, const hr_queue_opts* o, hr_queue* out)
     step(cudaEventCreateWithFlags(&q->kdone, cudaEventDisableTiming));
     step(cudaMalloc((void**)&q->ctl, sizeof(QCtl)));
     step(cudaMemset(q->ctl, 0, sizeof(QCtl)));
-    step(cudaMalloc((void**)&q->d_ring, sizeof(QReq) * q->cap));
+    step(cudaMalloc((void**)&q->d_ring, sizeof(QReq) * kQReplicas * q->cap));
     step(cudaMalloc((void**)&q->unit_ring, sizeof(unsigned long long) * kQUnitRing));
     step(cudaMalloc((void**)&q->done, sizeof(unsigned) * q->cap));
     step(cudaMemset(q->done, 0, sizeof(unsigned) * q->cap));

@@ -3,6 +3,8 @@
 // ((x + 1/2)/W, (y + 1/2)/H) is inside when fma(dx, dx, dy*dy) < r*r in FP32,
 // value 1 inside, 0 outside.  With a 0/1 target every (v - t)^2 is 0 or 1 and
 // the FP32 sum is an exact integer count.
+#include <vector>
+
 #include "disc_device.cuh"
 #include "hr.h"
 #include "hr_device.cuh"
@@ -14,7 +16,7 @@ namespace {
 template <int kW>
 __global__ void __launch_bounds__(32 * kW) disc_loss_kernel(RenderBatch b, int W, int H, float radius,
                                                             const float* __restrict__ target,
-                                                            const uint32_t* __restrict__ tbits) {
+                                                            DiscBits tb) {
     __shared__ float s_px[HR_MAX_IMAGE_SIDE], s_py[HR_MAX_IMAGE_SIDE];
     centre_tables(s_px, s_py, W, H);
     __syncthreads();
@@ -24,7 +26,7 @@ __global__ void __launch_bounds__(32 * kW) disc_loss_kernel(RenderBatch b, int W
     const Pert pt = resolve(b, m);
     const float cx = __fadd_rn(pt.theta[0], pt.tau[0]);
     const float cy = __fadd_rn(pt.theta[1], pt.tau[1]);
-    const float loss = disc_loss_warp(target, tbits, W, H, radius, s_px, s_py, cx, cy, lane);
+    const float loss = disc_loss_warp(target, tb, W, H, radius, s_px, s_py, cx, cy, lane);
     if (lane == 0) *pt.loss = loss;
 }
 
@@ -117,7 +119,7 @@ void launch_boxes_image(const DevScene& sc, const float* params, float* img, cud
 }
 
 void launch_disc_loss(const DevScene& sc, const RenderBatch& b, cudaStream_t s) {
-    const uint32_t* tb = sc.tbinary ? sc.tbits : nullptr;
+    const DiscBits tb{sc.tbinary ? sc.tbits : nullptr, sc.trowpop};
     switch (sc.render_variant) {
         case 1: disc_loss_kernel<4><<<(b.M + 3) / 4, 128, 0, s>>>(b, sc.W, sc.H, sc.radius, sc.target, tb); break;
         case 2: disc_loss_kernel<16><<<(b.M + 15) / 16, 512, 0, s>>>(b, sc.W, sc.H, sc.radius, sc.target, tb); break;
@@ -139,6 +141,19 @@ cudaError_t disc_prepare_target(DevScene& sc, cudaStream_t s) {
     if (e == cudaSuccess) e = cudaMemcpyAsync(&non_binary, d_flag, sizeof(int), cudaMemcpyDeviceToHost, s);
     if (e == cudaSuccess) e = cudaStreamSynchronize(s);
     cudaFree(d_flag);
+    // prefix sums of the rows' popcounts (rows the disc cannot reach differ
+    // from the target in exactly its set pixels)
+    std::vector<uint32_t> bits((size_t)words * sc.H);
+    std::vector<int> pop((size_t)sc.H + 1, 0);
+    if (e == cudaSuccess)
+        e = cudaMemcpy(bits.data(), sc.tbits, sizeof(uint32_t) * bits.size(), cudaMemcpyDeviceToHost);
+    for (int y = 0; y < sc.H; ++y) {
+        int c = 0;
+        for (int j = 0; j < words; ++j) c += __builtin_popcount(bits[(size_t)y * words + j]);
+        pop[y + 1] = pop[y] + c;
+    }
+    if (e == cudaSuccess) e = cudaMalloc((void**)&sc.trowpop, sizeof(int) * pop.size());
+    if (e == cudaSuccess) e = cudaMemcpy(sc.trowpop, pop.data(), sizeof(int) * pop.size(), cudaMemcpyHostToDevice);
     sc.tbinary = e == cudaSuccess && non_binary == 0;
     return e;
 }

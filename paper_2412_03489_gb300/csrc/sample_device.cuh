@@ -191,7 +191,10 @@ __device__ double hess_mixture(const float* t, int n, const Lobes& L) {
     return (sd * L.is4 * L.iZd + (off > 0.0 ? off : 0.0) * L.is4 * L.iZo) * L.inv_n2;
 }
 
-__device__ void write_weights(const SampleArgs& a, const Lobes& L, const SampleGroup& G, int m, const float* t,
+// Args: SampleArgs, or any type with the fields read here and in sample_leg
+// (n, E, seed, v, tau, w, invS, meta, step).
+template <class Args>
+__device__ void write_weights(const Args& a, const Lobes& L, const SampleGroup& G, int m, const float* t,
                               double sign) {
     const int n = a.n;
     const double s2 = L.s2, is2 = L.is2, is4 = L.is4;
@@ -276,7 +279,8 @@ __device__ void write_weights(const SampleArgs& a, const Lobes& L, const SampleG
 // One leg (0: + lobe, 1: - lobe) of antithetic pair k of group G: its
 // perturbation, path key and weights (Sec. 3.2-3.5).  Called by the sampler
 // kernel (two threads per pair) and by the persistent serving kernel.
-__device__ __forceinline__ void sample_leg(const SampleArgs& a, const SampleGroup& G, const Lobes& L, int k, int leg) {
+template <class Args>
+__device__ __forceinline__ void sample_leg(const Args& a, const SampleGroup& G, const Lobes& L, int k, int leg) {
     const int n = a.n;
     const uint32_t sub = G.sub + (a.step ? 64u * (uint32_t)(*a.step) : 0u);
     const uint32_t c2 = (TAG_SAMPLE << 24) | (sub & 0xFFFFFFu);

@@ -93,6 +93,7 @@ def test_disc_ragged_and_minimum(W, H, M):
     (100, 50, 0.7, 0.2, "random"),           # spans over word boundaries, arbitrary 0/1 target
     (1024, 3, 0.004, 0.05, "random"),        # sub-pixel radius, 32 words per row
     (33, 40, 1.5, 0.5, "random"),            # discs larger than the image
+    (64, 48, 1000.0, 0.05, "far"),           # radius 1000 centred 1000.5 below the top: its edge crosses the image
     (1, 1, 0.2, 0.3, "disc")])
 def test_disc_binary_target_spans(W, H, radius, sigma, target):
     """Binary targets take the span path (row intervals of the FP32 pixel test,
@@ -103,8 +104,10 @@ def test_disc_binary_target_spans(W, H, radius, sigma, target):
     g = np.random.default_rng(W * 7 + H)
     if sigma < 1e-5:   # theta on a pixel centre
         sc["theta_query"] = np.array([(W // 2 + 0.5) / W, (H // 3 + 0.5) / H])
+    if target == "far":
+        sc["theta_query"] = np.array([0.5, 1000.5])
     tgt = None
-    if target == "random":
+    if target in ("random", "far"):
         tgt = (g.uniform(size=W * H) < 0.4).astype(np.float32)
     Sc = hr.Scene(sc, target_image=tgt) if tgt is not None else hr.Scene(sc)
     ren = O.DiscRenderer(sc, target=tgt) if tgt is not None else O.DiscRenderer(sc)

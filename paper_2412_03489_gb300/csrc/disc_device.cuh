@@ -127,15 +127,12 @@ __device__ __forceinline__ float disc_rows(const float* __restrict__ target, int
 //     (|cy| + r) H 2^-22 + 1 rows, so every such row lies inside the
 //     real-arithmetic band (cy -+ r) H - 1/2 widened by 2 + (|cy| + r) H 2^-20
 //     rows; the rows [y0, y1) of that band are the only ones tested.
-// A row's span ends are found with the exact test itself, started from the
-// real-arithmetic ends cx -+ sqrt(r^2 - dy^2) and stepped at most kSpanSteps
-// columns; a start further off falls back to a binary search on the same
-// predicate.  Rows outside [y0, y1) differ from the target in its set pixels
+// A row's span ends are found with the exact test itself, in a window of four
+// columns around the real-arithmetic ends cx -+ sqrt(r^2 - dy^2); an end
+// outside the window falls back to a binary search on the same predicate.  Rows outside [y0, y1) differ from the target in its set pixels
 // (a prefix sum of the rows' popcounts); a row inside differs in
 // popc(target bits XOR span bits) over its words (an empty span when its
 // dy^2 >= r^2).
-constexpr int kSpanSteps = 4;
-
 // The bit-packed target of a binary image: bit x % 32 of word x / 32 of row y
 // is pixel (x, y); rowpop [H + 1] the prefix sums of the rows' popcounts.
 struct DiscBits {
@@ -159,6 +156,26 @@ __device__ __forceinline__ int first_true(int lo, int hi, Pred pred) {
     return lo;
 }
 
+// First index of [lo, hi) where in() holds (hi if none), for in() false..false
+// true..true on [lo, hi), looked for around the guess g: the four tests of the
+// window [w, w + 4) (w = g - 2, moved inside the range) are independent, so
+// their latencies overlap; when the window does not hold the change from false
+// to true, a binary search on the same predicate finds it.
+template <class In>
+__device__ __forceinline__ int first_in(int lo, int hi, int g, In in) {
+    if (hi - lo <= 0) return hi;
+    const int w = max(lo, min(g - 2, hi - 4));
+    bool t[4];
+#pragma unroll
+    for (int j = 0; j < 4; ++j) t[j] = w + j >= hi || in(w + j);
+    if (t[0]) return w == lo ? lo : first_true(lo, w, in);
+    if (!t[3]) return first_true(w + 4, hi, in);
+    return w + 1 + (t[1] ? 0 : 1 + (t[2] ? 0 : 1));
+}
+
+// integer guess from a float estimate, clamped to [lo, hi] (NaN to lo)
+__device__ __forceinline__ int guess_index(float f, int lo, int hi) { return clamp_col(ceilf(f), lo, hi); }
+
 // [a, e): the indices i of the centre table ctr [N] (strictly increasing, the
 // FP32 centres (i + 1/2)/N) where the test in(i) holds, given that in() is
 // non-increasing in i below the first centre >= c and non-decreasing from it;
@@ -167,23 +184,11 @@ template <class In>
 __device__ __forceinline__ void exact_span(const float* ctr, int N, float fN, float c, float half, In in, int& a,
                                            int& e) {
     // centre index: first i with ctr[i] >= c
-    int ic = clamp_col(ceilf(__fmaf_rn(c, fN, -0.5f)), 0, N);
-    int k = 0;
-    for (; k < kSpanSteps && ic > 0 && ctr[ic - 1] >= c; ++k) --ic;
-    for (; k < kSpanSteps && ic < N && ctr[ic] < c; ++k) ++ic;
-    if (k == kSpanSteps) ic = first_true(0, N, [&](int i) { return ctr[i] >= c; });
-    // lower end: first i of [0, ic) where the test holds
-    a = clamp_col(ceilf(__fmaf_rn(__fsub_rn(c, half), fN, -0.5f)), 0, ic);
-    k = 0;
-    for (; k < kSpanSteps && a > 0 && in(a - 1); ++k) --a;
-    for (; k < kSpanSteps && a < ic && !in(a); ++k) ++a;
-    if (k == kSpanSteps) a = first_true(0, ic, in);
-    // upper end: first i of [ic, N) where it fails
-    e = clamp_col(ceilf(__fmaf_rn(__fadd_rn(c, half), fN, -0.5f)), ic, N);
-    k = 0;
-    for (; k < kSpanSteps && e > ic && !in(e - 1); ++k) --e;
-    for (; k < kSpanSteps && e < N && in(e); ++k) ++e;
-    if (k == kSpanSteps) e = first_true(ic, N, [&](int i) { return !in(i); });
+    const int ic = first_in(0, N, guess_index(__fmaf_rn(c, fN, -0.5f), 0, N), [&](int i) { return ctr[i] >= c; });
+    // lower end: first i of [0, ic) where the test holds; upper end: first i
+    // of [ic, N) where it fails
+    a = first_in(0, ic, guess_index(__fmaf_rn(__fsub_rn(c, half), fN, -0.5f), 0, N), in);
+    e = first_in(ic, N, guess_index(__fmaf_rn(__fadd_rn(c, half), fN, -0.5f), 0, N), [&](int i) { return !in(i); });
 }
 
 // Mismatch count of the disc at (cx, cy) against a binary target, summed over

@@ -54,7 +54,7 @@ constexpr int kQUnitBits = 24;       // unit ring entry = request << 24 | unit
 constexpr unsigned long long kQUnitMask = (1ull << kQUnitBits) - 1ull;
 constexpr int kQUnitRing = 1 << 20;  // unit ring entries
 constexpr int kQReplicas = 8;        // device copies of each descriptor (unit k reads copy k % 8)
-constexpr int kQBatch = 4;           // descriptors the dispatcher loads per round
+constexpr int kQBatch = 4;           // descriptors the dispatcher loads per pass
 
 // The sampler's inputs of a request (the fields sample_leg reads).
 struct QSample {
@@ -204,7 +204,7 @@ __device__ int dispatch_loop(const QArgs& A, int lane) {
         hs = __shfl_sync(0xffffffffu, hs, 0);
         stop = __shfl_sync(0xffffffffu, stop, 0);
         if (hs > seen) {
-            // kQBatch descriptors per round: their host-memory loads are in
+            // kQBatch descriptors per pass: their host-memory loads are in
             // flight together; each is stored as kQReplicas device copies on
             // different lines, so that the warps taking one request's units
             // spread their loads over the L2
@@ -231,7 +231,7 @@ __device__ int dispatch_loop(const QArgs& A, int lane) {
                         __stcg(A.unit_ring + ((U + (unsigned long long)k) % kQUnitRing), (r << kQUnitBits) | (unsigned)k);
                     U += (unsigned long long)un[j];
                 }
-                // publish each round, so that workers start on a long backlog
+                // publish each pass, so that workers start on a long backlog
                 __threadfence();
                 __syncwarp();
                 if (lane == 0) {

@@ -459,8 +459,9 @@ hr_status hr_server_submit(hr_server srv, const hr_request* req, uint64_t* ticke
 hr_status hr_server_wait(hr_server srv, uint64_t ticket, void* h_out, hr_request_info* info, int32_t timeout_ms);
 
 /* ---------------------------------------------------------------------------
- * Persistent queue (disc scenes): estimate requests of one DISC2D scene served
- * by one long-running kernel (Sec. 3.2-3.5 estimators, Sec. 4.1 disc task).
+ * Persistent queue (disc and squares scenes): estimate requests of one DISC2D
+ * or BOXES2D scene (at most 8 parameters) served by one long-running kernel
+ * (Sec. 3.2-3.5 estimators, Sec. 4.1 Box2 task).
  * A request's perturbations are sampled, rendered and summed inside that
  * kernel, in units of 16 antithetic pairs taken by whichever warp is free;
  * the warp that finishes a request's last unit forms its sums in the same
@@ -488,8 +489,8 @@ typedef struct {
                                 about G M (n + E + 1) 4 bytes */
 } hr_queue_opts;
 
-/* HR_ERR_UNSUPPORTED unless the scene is DISC2D; HR_ERR_OOM if the device or
- * host-mapped memory cannot be had. */
+/* HR_ERR_UNSUPPORTED unless the scene is DISC2D, or BOXES2D with at most 4
+ * squares; HR_ERR_OOM if the device or host-mapped memory cannot be had. */
 hr_status hr_queue_create(hr_scene scene, const hr_queue_opts* opts, hr_queue* out);
 /* Queue one estimate (HR_GRAD, HR_HESSIAN or HR_HVP; h_theta [n] and h_v [n]
  * host, copied).  opts: sigma, n_perturb, strategy, seed, request_id and sub

@@ -1,5 +1,5 @@
-// Device code of the hard-edged disc renderer fused with the L2 loss,
-// shared by the disc kernels (render_disc.cu) and the persistent serving
+// Device code of the hard-edged disc and squares renderers fused with the L2
+// loss, shared by their kernels (render_disc.cu) and the persistent serving
 // kernel (queue.cu).  One warp renders one perturbation: pixel centre
 // ((x + 1/2)/W, (y + 1/2)/H) is inside when fma(dx, dx, dy*dy) < r*r in FP32,
 // value 1 inside, 0 outside.
@@ -251,6 +251,25 @@ __device__ __forceinline__ float disc_loss_warp(const float* __restrict__ target
             acc = W >= 32 ? lane_l2<true>(target, W, npx, lane, px, py, value)
                           : lane_l2<false>(target, W, npx, lane, px, py, value);
     }
+    acc = warp_sum(acc);
+    return __fdiv_rn(acc, (float)npx);
+}
+
+// Squares (Box2 / Box10): K axis-aligned squares of half-size h centred at
+// c[2k], c[2k + 1]; a pixel centre is 1 when |px - cx| < h and |py - cy| < h
+// for some square (FP32).  Loss of one perturbation by one warp (every lane
+// returns it): each lane sums its pixels in pixel order, then a shuffle tree.
+__device__ __forceinline__ float boxes_loss_warp(const float* __restrict__ target, int W, int H, float h,
+                                                 const float* px, const float* py, const float* c, int K,
+                                                 int lane) {
+    const int npx = W * H;
+    auto value = [c, K, h](float px_, float py_) {
+        for (int k = 0; k < K; ++k)
+            if (fabsf(__fsub_rn(px_, c[2 * k])) < h && fabsf(__fsub_rn(py_, c[2 * k + 1])) < h) return 1.0f;
+        return 0.0f;
+    };
+    float acc = W >= 32 ? lane_l2<true>(target, W, npx, lane, px, py, value)
+                        : lane_l2<false>(target, W, npx, lane, px, py, value);
     acc = warp_sum(acc);
     return __fdiv_rn(acc, (float)npx);
 }

@@ -1,5 +1,5 @@
 // K10: persistent serving queue (hr_queue_*): many small estimate requests on
-// a disc scene served by one long-running launch.
+// a disc or squares scene served by one long-running launch.
 //
 // Submission costs no driver call.  The host writes a request's descriptor
 // into a ring in host-mapped memory and then release-stores the count of
@@ -11,8 +11,9 @@
 //     runs the unit with that index once it is published.
 // A unit is 16 antithetic pairs of one request; the warp that holds it
 // (1) samples the 32 perturbations, one pair leg per lane, with the sampler's
-// code (Sec. 3.2-3.5), (2) renders each of them with the disc renderer fused
-// with the L2 loss, one warp per render, and (3) counts the unit as finished.
+// code (Sec. 3.2-3.5), (2) renders each of them with the scene's renderer
+// fused with the L2 loss (the plain kernels' code), one warp per render, and
+// (3) counts the unit as finished.
 // The warp that finishes a request's last unit forms the estimator sums in the
 // sum kernel's order: 256 Kahan chunks, then the same FP64 tree.  It writes
 // the result and a completion flag to host-mapped memory.  A request's
@@ -304,8 +305,11 @@ __device__ __forceinline__ int fetch_desc(const QArgs& A, int lane, unsigned lon
     return unit;
 }
 
-__global__ void __launch_bounds__(32 * kQWarps, 3) queue_disc_kernel(QArgs A) {
+// kKind: HR_SCENE_DISC2D or HR_SCENE_BOXES2D (the renders of the plain kernels)
+template <int kKind>
+__global__ void __launch_bounds__(32 * kQWarps, 3) queue_kernel(QArgs A) {
     __shared__ float s_px[HR_MAX_IMAGE_SIDE], s_py[HR_MAX_IMAGE_SIDE];
+    __shared__ float s_c[kQWarps][kQMaxN];   // squares: the perturbed centres of the current render
     __shared__ QReq s_req[kQWarps][2];
     centre_tables(s_px, s_py, A.W, A.H);
     __syncthreads();
@@ -353,9 +357,17 @@ __global__ void __launch_bounds__(32 * kQWarps, 3) queue_disc_kernel(QArgs A) {
             for (int q = 0; q < rows; ++q) {
                 const int m = 2 * p0 + q;
                 const float* t = R.sa.tau + (size_t)m * R.n;
-                const float cx = __fadd_rn(R.theta32[0], t[0]);
-                const float cy = __fadd_rn(R.theta32[1], t[1]);
-                const float loss = disc_loss_warp(A.target, A.tb, A.W, A.H, A.radius, s_px, s_py, cx, cy, lane);
+                float loss;
+                if (kKind == HR_SCENE_DISC2D) {
+                    const float cx = __fadd_rn(R.theta32[0], t[0]);
+                    const float cy = __fadd_rn(R.theta32[1], t[1]);
+                    loss = disc_loss_warp(A.target, A.tb, A.W, A.H, A.radius, s_px, s_py, cx, cy, lane);
+                } else {
+                    if (lane < R.n) s_c[warp][lane] = __fadd_rn(R.theta32[lane], t[lane]);
+                    __syncwarp();
+                    loss = boxes_loss_warp(A.target, A.W, A.H, A.radius, s_px, s_py, s_c[warp], R.n / 2, lane);
+                    __syncwarp();
+                }
                 if (lane == 0) R.loss[m] = loss;
             }
             // 3. count the unit (weights and losses visible GPU-wide first); the
@@ -507,7 +519,8 @@ hr_status ensure_running(hr_queue_s* q) {
     a.tb = DiscBits{sc.tbinary ? sc.tbits : nullptr, sc.trowpop};
     a.budget = q->budget;
     a.safety = q->safety;
-    queue_disc_kernel<<<q->grid, 32 * kQWarps, 0, q->kstream>>>(a);
+    if (q->scene->sc.kind == HR_SCENE_DISC2D) queue_kernel<HR_SCENE_DISC2D><<<q->grid, 32 * kQWarps, 0, q->kstream>>>(a);
+    else queue_kernel<HR_SCENE_BOXES2D><<<q->grid, 32 * kQWarps, 0, q->kstream>>>(a);
     if ((e = cudaGetLastError()) == cudaSuccess) e = cudaEventRecord(q->kdone, q->kstream);
     if (e != cudaSuccess) {
         __atomic_store_n(&q->host->status, (int)HR_ERR_CUDA, __ATOMIC_RELEASE);
@@ -644,7 +657,9 @@ hr_status hr_queue_create(hr_scene scene, const hr_queue_opts* o, hr_queue* out)
     clear_error();
     if (!scene || !o || !out) return fail(HR_ERR_INVALID_ARG, "NULL argument");
     *out = nullptr;
-    if (scene->sc.kind != HR_SCENE_DISC2D) return fail(HR_ERR_UNSUPPORTED, "the persistent queue serves disc scenes");
+    if (scene->sc.kind != HR_SCENE_DISC2D && scene->sc.kind != HR_SCENE_BOXES2D)
+        return fail(HR_ERR_UNSUPPORTED, "the persistent queue serves disc and squares scenes");
+    if (scene->sc.n > kQMaxN) return fail(HR_ERR_UNSUPPORTED, "queued scenes have at most %d parameters", kQMaxN);
     if (o->max_requests < 1 || o->max_requests > 16384)
         return fail(HR_ERR_INVALID_ARG, "max_requests must be 1..16384");
     if (o->arena_bytes < (1 << 20)) return fail(HR_ERR_INVALID_ARG, "arena_bytes must be at least 1 MiB");
@@ -659,7 +674,10 @@ hr_status hr_queue_create(hr_scene scene, const hr_queue_opts* o, hr_queue* out)
     auto step = [&](cudaError_t x) { if (e == cudaSuccess) e = x; };
     step(cudaDeviceGetAttribute(&clock_khz, cudaDevAttrClockRate, dev));
     step(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
-    step(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, queue_disc_kernel, 32 * kQWarps, 0));
+    if (scene->sc.kind == HR_SCENE_DISC2D)
+        step(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, queue_kernel<HR_SCENE_DISC2D>, 32 * kQWarps, 0));
+    else
+        step(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, queue_kernel<HR_SCENE_BOXES2D>, 32 * kQWarps, 0));
     q->grid = sms * std::max(per_sm, 1);
     // clock64() counts SM cycles; the budget is converted at the maximum clock
     // (a lower clock only makes the wall-clock wait longer)

@@ -80,18 +80,8 @@ __global__ void __launch_bounds__(32 * kW) boxes_loss_kernel(RenderBatch b, int 
     const Pert pt = resolve(b, m);
     for (int d = lane; d < b.n; d += 32) s_c[warp][d] = __fadd_rn(pt.theta[d], pt.tau[d]);
     __syncwarp();
-    const int K = b.n / 2;
-    const float* c = s_c[warp];
-    const int npx = W * H;
-    auto value = [c, K, h](float px, float py) {
-        for (int k = 0; k < K; ++k)
-            if (fabsf(__fsub_rn(px, c[2 * k])) < h && fabsf(__fsub_rn(py, c[2 * k + 1])) < h) return 1.0f;
-        return 0.0f;
-    };
-    float acc = W >= 32 ? lane_l2<true>(target, W, npx, lane, s_px, s_py, value)
-                        : lane_l2<false>(target, W, npx, lane, s_px, s_py, value);
-    acc = warp_sum(acc);
-    if (lane == 0) *pt.loss = __fdiv_rn(acc, (float)npx);
+    const float loss = boxes_loss_warp(target, W, H, h, s_px, s_py, s_c[warp], b.n / 2, lane);
+    if (lane == 0) *pt.loss = loss;
 }
 
 __global__ void boxes_image_kernel(const float* params, int K, int W, int H, float h, float* img) {

@@ -317,3 +317,39 @@ def test_queue_other_sizes_and_grey_targets(W, H, grey):
     finally:
         hr.hr_queue_destroy(q)
         S.close()
+
+
+@pytest.mark.parametrize("n_boxes", [1, 4])
+def test_queue_squares_scenes(n_boxes):
+    """Squares scenes (Box2 with one square; four squares, n = 8) through the
+    queue: each request bit-identical to the plain path (the same render
+    code); ten squares (n = 20) are beyond the queue's parameter limit."""
+    sc = wl.boxes_scene(n_boxes=n_boxes)
+    S = hr.Scene(sc)
+    n = sc["n_params"]
+    g = np.random.default_rng(n_boxes)
+    kinds = [(hr.HR_HESSIAN, hr.HR_AGGREGATE, 512), (hr.HR_GRAD, hr.HR_AGGREGATE, 66),
+             (hr.HR_HVP, hr.HR_AGGREGATE, 258), (hr.HR_HESSIAN, hr.HR_PLAIN, 34)]
+    if n_boxes == 1:   # element-wise: n or n(n+1)/2 sample groups, at most 4 in the queue
+        kinds += [(hr.HR_HESSIAN, hr.HR_ELEMENTWISE, 256), (hr.HR_GRAD, hr.HR_ELEMENTWISE, 66)]
+    reqs = []
+    for i, (quantity, strat, M) in enumerate(kinds * 2):
+        theta = np.asarray(sc["theta_query"], np.float64) + g.normal(0, 0.02, n)
+        v = g.normal(size=n) if quantity == hr.HR_HVP else None
+        reqs.append(dict(q=quantity, strat=strat, M=M, theta=theta, v=v, seed=70 + i, req=i, sub=0))
+    ref = [plain(S, sc, r) for r in reqs]
+    q = hr.hr_queue_create(S, max_requests=32, idle_budget_us=2000)
+    try:
+        tickets = [hr.hr_queue_submit(q, r["q"], r["theta"], r["v"], opts(sc, r)) for r in reqs]
+        for r, t, e in zip(reqs, tickets, ref):
+            o = np.zeros((n, n) if r["q"] == hr.HR_HESSIAN else n)
+            hr.hr_queue_wait(q, t, o)
+            assert np.array_equal(o, e), (r, o, e)
+    finally:
+        hr.hr_queue_destroy(q)
+        S.close()
+    S10 = hr.Scene(wl.boxes_scene(n_boxes=10))
+    with pytest.raises(hr.HRError) as ei:
+        hr.hr_queue_create(S10)
+    assert ei.value.status == hr.HR_ERR_UNSUPPORTED
+    S10.close()

@@ -441,27 +441,9 @@ revolve_kernel(RvArgs P, RenderBatch b, const float* __restrict__ img_params, fl
             atomicAdd(&P.stats[3], (unsigned long long)total);
             atomicAdd(&P.stats[4], (unsigned long long)n_obj);
         }
-        bool walked = false;   // some band walked every triangle
-        for (int r0 = 0, r1 = P.TY; r0 < P.TY; r0 = r1) {
-            int total_b = total;
-            bool walk_all = false;
-            if (banded) {
-                __syncthreads();   // row totals written; the previous band's raster done
-                if (tid == 0) {
-                    int r = r0, sum = 0;
-                    while (r < P.TY && sum + rowtot[r] <= capb) sum += rowtot[r++];
-                    s_band[0] = r > r0 ? r : r0 + 1;
-                    s_band[1] = r > r0 ? 0 : 1;
-                }
-                if (tid < 33) s_hist[tid] = 0;
-                __syncthreads();
-                r1 = s_band[0];
-                walk_all = s_band[1] != 0;
-                walked = walked || walk_all;
-                if (!walk_all)
-                    total_b = bin_scan(tcnt + r0 * P.TX, toff + r0 * P.TX, olist, (r1 - r0) * P.TX, s_wtot, s_hist,
-                                       &n_obj);
-            }
+        // one band: fill and raster of tile rows [r0, r1), the whole image when
+        // the bins fit (then every argument but the row count is a constant)
+        auto band = [&](const int r0, const int r1, const int total_b, const bool walk_all) {
             const int tb = r0 * P.TX, Tb = (r1 - r0) * P.TX;   // the band's tiles [tb, tb + Tb)
             for (int i = tid; i < Tb; i += kThreads) tcnt[tb + i] = 0;   // becomes the fill cursor
             if (tid == 0) s_tile = 0;
@@ -668,6 +650,29 @@ revolve_kernel(RvArgs P, RenderBatch b, const float* __restrict__ img_params, fl
                     for (int o = kG / 2; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
                     if (gl == 0 && has_tile) tile_loss[t] = acc;
                 }
+            }
+        };
+        bool walked = false;   // some band walked every triangle
+        if (!banded) {
+            band(0, P.TY, total, false);
+        } else {
+            for (int r0 = 0, r1 = 0; r0 < P.TY; r0 = r1) {
+                __syncthreads();   // row totals written; the previous band's raster done
+                if (tid == 0) {
+                    int r = r0, sum = 0;
+                    while (r < P.TY && sum + rowtot[r] <= capb) sum += rowtot[r++];
+                    s_band[0] = r > r0 ? r : r0 + 1;
+                    s_band[1] = r > r0 ? 0 : 1;
+                }
+                if (tid < 33) s_hist[tid] = 0;
+                __syncthreads();
+                r1 = s_band[0];
+                const bool walk_all = s_band[1] != 0;
+                walked = walked || walk_all;
+                const int total_b = walk_all ? 0
+                                             : bin_scan(tcnt + r0 * P.TX, toff + r0 * P.TX, olist, (r1 - r0) * P.TX,
+                                                        s_wtot, s_hist, &n_obj);
+                band(r0, r1, total_b, walk_all);
             }
         }
         if (!kImage && tid == 0 && P.stats && walked) atomicAdd(&P.stats[6], 1ull);

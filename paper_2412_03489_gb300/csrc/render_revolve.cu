@@ -281,9 +281,11 @@ revolve_kernel(RvArgs P, RenderBatch b, const float* __restrict__ img_params, fl
     __shared__ float s_part[kWarps];
     __shared__ int s_tile;
     __shared__ int s_band[2];   // the current band's end row and whether it walks every triangle
+    __shared__ unsigned long long s_steps[kWarps];   // raster steps of each warp (diagnostics)
 
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     const int M = kImage ? 1 : b.M;
+    if (lane == 0) s_steps[warp] = 0ull;
     for (int m = kImage ? 0 : (int)blockIdx.x; m < M; m += kImage ? 1 : (int)gridDim.x) {
         // ---- 1. parameters and rotation ----------------------------------
         if (tid < 4) {   // ca, sa, cb, sb
@@ -575,7 +577,7 @@ revolve_kernel(RvArgs P, RenderBatch b, const float* __restrict__ img_params, fl
                 };
                 if (!walk_all) {
                     const int n_max = (int)__reduce_max_sync(0xffffffffu, (unsigned)n_mine);
-                    if (!kImage && lane == 0 && P.stats) atomicAdd(&P.stats[5], (unsigned long long)n_max);
+                    if (!kImage && lane == 0) s_steps[warp] += (unsigned long long)n_max;
                     // a group whose bin is shorter walks a sentinel entry (every
                     // row and column outside: no pixel is in) instead of
                     // branching around the step
@@ -694,6 +696,8 @@ revolve_kernel(RvArgs P, RenderBatch b, const float* __restrict__ img_params, fl
         }
         __syncthreads();
     }
+    // each warp's raster steps go to the diagnostics once per launch
+    if (!kImage && lane == 0 && P.stats && s_steps[warp]) atomicAdd(&P.stats[5], s_steps[warp]);
 }
 
 __global__ void normals_kernel(const float* verts, const int32_t* tris, int nt, float* tnrm) {

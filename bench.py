@@ -53,8 +53,8 @@ METRIC = "Hessian/HVP estimates/s at oracle-matched error; perturbed renders/s; 
 # (read + write) of one render+loss launch, and the fraction of instruction
 # issue slots busy (smsp__issue_active) — the kernel is bound by compare /
 # select issue on the ALU pipe rather than by FP32 arithmetic.
-TRAFFIC_BYTES = 543744
-ISSUE_ACTIVE_NCU = 0.663
+TRAFFIC_BYTES = 549632
+ISSUE_ACTIVE_NCU = 0.668
 M_PERTURB = 4096
 SEED = 2024
 

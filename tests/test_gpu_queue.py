@@ -353,3 +353,46 @@ def test_queue_squares_scenes(n_boxes):
         hr.hr_queue_create(S10)
     assert ei.value.status == hr.HR_ERR_UNSUPPORTED
     S10.close()
+
+
+def test_queue_unit_ring_fills_and_wraps():
+    """Requests of 3 x 2^18 perturbations (24,576 units of 16 pairs each):
+    about 43 of them fill the 2^20-entry unit ring, so a submit is refused
+    with HR_ERR_BUSY ("unit ring full") before the slots or the 1 GiB arena
+    run out; after the first results are read, more requests go in and the
+    ring's indices wrap.  Sampled results against the plain path."""
+    sc = wl.disc_scene()
+    S = hr.Scene(sc)
+    theta = np.asarray(sc["theta_query"], np.float64)
+    M = 1 << 18
+    q = hr.hr_queue_create(S, max_requests=64, idle_budget_us=20000, arena_bytes=1 << 30)
+    try:
+        tickets, busy = [], None
+        for i in range(64):
+            try:
+                tickets.append(hr.hr_queue_submit(q, hr.HR_HESSIAN, theta, None,
+                                                  hr.make_opts(sc["sigma"], M, hr.HR_ELEMENTWISE, 900 + i, i)))
+            except hr.HRError as e:
+                busy = e
+                break
+        assert busy is not None and busy.status == hr.HR_ERR_BUSY and "unit ring" in str(busy), busy
+        assert 40 <= len(tickets) <= 43, len(tickets)
+        outs = {}
+        for k, t in enumerate(tickets[:20]):
+            o = np.zeros((2, 2))
+            hr.hr_queue_wait(q, t, o)
+            outs[k] = o
+        # the ring has room again: these units take indices past 2^20
+        more = [hr.hr_queue_submit(q, hr.HR_HESSIAN, theta, None,
+                                   hr.make_opts(sc["sigma"], M, hr.HR_ELEMENTWISE, 900 + len(tickets) + j,
+                                                len(tickets) + j)) for j in range(10)]
+        for k, t in enumerate(tickets[20:] + more, start=20):
+            o = np.zeros((2, 2))
+            hr.hr_queue_wait(q, t, o)
+            outs[k] = o
+        for k in (0, 19, 20, len(tickets) - 1, len(tickets) + 9):
+            e = S.estimate(hr.HR_HESSIAN, theta, sc["sigma"], M, hr.HR_ELEMENTWISE, 900 + k, k)
+            assert np.array_equal(outs[k], e), (k, outs[k], e)
+    finally:
+        hr.hr_queue_destroy(q)
+        S.close()

@@ -567,7 +567,8 @@ hr_status hr_create_scene(const hr_scene_desc* d, hr_scene* out) {
         if (e != cudaSuccess) return bail(e, "target render");
     }
     if (sc.kind == HR_SCENE_REVOLVE3D) revolve_tile_t2(sc, s->stream);
-    if (sc.kind == HR_SCENE_DISC2D && (e = disc_prepare_target(sc, s->stream)) != cudaSuccess)
+    if ((sc.kind == HR_SCENE_DISC2D || sc.kind == HR_SCENE_BOXES2D) &&
+        (e = disc_prepare_target(sc, s->stream)) != cudaSuccess)
         return bail(e, "target bits");
     if ((e = cudaStreamSynchronize(s->stream)) != cudaSuccess) return bail(e, "scene setup");
     if ((e = cudaGetLastError()) != cudaSuccess) return bail(e, "scene setup launch");

@@ -258,11 +258,41 @@ __device__ __forceinline__ float disc_loss_warp(const float* __restrict__ target
 // Squares (Box2 / Box10): K axis-aligned squares of half-size h centred at
 // c[2k], c[2k + 1]; a pixel centre is 1 when |px - cx| < h and |py - cy| < h
 // for some square (FP32).  Loss of one perturbation by one warp (every lane
-// returns it): each lane sums its pixels in pixel order, then a shuffle tree.
-__device__ __forceinline__ float boxes_loss_warp(const float* __restrict__ target, int W, int H, float h,
-                                                 const float* px, const float* py, const float* c, int K,
-                                                 int lane) {
+// returns it).  With a binary target (tb.bits non-null) the sum is the exact
+// mismatch count: |RN(px - cx)| is non-increasing in x left of the first
+// column with px >= cx and non-decreasing from it, so square k covers the
+// columns [a_k, e_k) in every row where |RN(py - cy_k)| < h; a row's covered
+// pixels are the union of those intervals, its mismatches popc(target bits
+// XOR union bits).  The intervals go to sp [2K] (this warp's shared memory).
+// Otherwise each lane sums its pixels in pixel order, then a shuffle tree.
+__device__ __forceinline__ float boxes_loss_warp(const float* __restrict__ target, const DiscBits& tb, int W, int H,
+                                                 float h, const float* px, const float* py, const float* c, int* sp,
+                                                 int K, int lane) {
     const int npx = W * H;
+    if (tb.bits) {
+        const float fW = (float)W;
+        for (int k = lane; k < K; k += 32) {
+            const float cx = c[2 * k];
+            exact_span(px, W, fW, cx, h, [&](int x) { return fabsf(__fsub_rn(px[x], cx)) < h; }, sp[2 * k],
+                       sp[2 * k + 1]);
+        }
+        __syncwarp();
+        const int words = (W + 31) >> 5;
+        int cnt = 0;
+        for (int y = lane; y < H; y += 32) {
+            const uint32_t* row = tb.bits + (size_t)y * words;
+            for (int j = 0; j < words; ++j) {
+                uint32_t m = 0u;
+                for (int k = 0; k < K; ++k)
+                    if (fabsf(__fsub_rn(py[y], c[2 * k + 1])) < h) {
+                        const int lo = min(max(sp[2 * k] - 32 * j, 0), 32), hi = min(max(sp[2 * k + 1] - 32 * j, 0), 32);
+                        m |= (uint32_t)(((1ull << hi) - 1ull) & ~((1ull << lo) - 1ull));
+                    }
+                cnt += __popc(__ldg(row + j) ^ m);
+            }
+        }
+        return __fdiv_rn((float)__reduce_add_sync(0xffffffffu, cnt), (float)npx);
+    }
     auto value = [c, K, h](float px_, float py_) {
         for (int k = 0; k < K; ++k)
             if (fabsf(__fsub_rn(px_, c[2 * k])) < h && fabsf(__fsub_rn(py_, c[2 * k + 1])) < h) return 1.0f;

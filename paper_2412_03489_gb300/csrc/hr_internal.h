@@ -201,7 +201,7 @@ bool revolve_layout(DevScene& sc, int max_smem);
 int revolve_tiles(const DevScene& sc);
 void revolve_prepare(DevScene& sc, cudaStream_t s);   // normals, kernel attributes
 void revolve_tile_t2(DevScene& sc, cudaStream_t s);   // after the target exists
-// disc scenes, after the target exists: sc.tbits, sc.trowpop and sc.tbinary
+// disc and squares scenes, after the target exists: sc.tbits, sc.trowpop and sc.tbinary
 cudaError_t disc_prepare_target(DevScene& sc, cudaStream_t s);
 
 int num_sms();

@@ -310,6 +310,7 @@ template <int kKind>
 __global__ void __launch_bounds__(32 * kQWarps, 3) queue_kernel(QArgs A) {
     __shared__ float s_px[HR_MAX_IMAGE_SIDE], s_py[HR_MAX_IMAGE_SIDE];
     __shared__ float s_c[kQWarps][kQMaxN];   // squares: the perturbed centres of the current render
+    __shared__ int s_sp[kQWarps][kQMaxN];    // squares: their column intervals
     __shared__ QReq s_req[kQWarps][2];
     centre_tables(s_px, s_py, A.W, A.H);
     __syncthreads();
@@ -365,7 +366,8 @@ __global__ void __launch_bounds__(32 * kQWarps, 3) queue_kernel(QArgs A) {
                 } else {
                     if (lane < R.n) s_c[warp][lane] = __fadd_rn(R.theta32[lane], t[lane]);
                     __syncwarp();
-                    loss = boxes_loss_warp(A.target, A.W, A.H, A.radius, s_px, s_py, s_c[warp], R.n / 2, lane);
+                    loss = boxes_loss_warp(A.target, A.tb, A.W, A.H, A.radius, s_px, s_py, s_c[warp], s_sp[warp],
+                                           R.n / 2, lane);
                     __syncwarp();
                 }
                 if (lane == 0) R.loss[m] = loss;

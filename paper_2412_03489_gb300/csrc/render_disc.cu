@@ -69,8 +69,9 @@ constexpr int kMaxBoxParams = 64;
 
 template <int kW>
 __global__ void __launch_bounds__(32 * kW) boxes_loss_kernel(RenderBatch b, int W, int H, float h,
-                                                             const float* __restrict__ target) {
+                                                             const float* __restrict__ target, DiscBits tb) {
     __shared__ float s_c[kW][kMaxBoxParams];
+    __shared__ int s_sp[kW][kMaxBoxParams];
     __shared__ float s_px[HR_MAX_IMAGE_SIDE], s_py[HR_MAX_IMAGE_SIDE];
     centre_tables(s_px, s_py, W, H);
     __syncthreads();
@@ -80,7 +81,7 @@ __global__ void __launch_bounds__(32 * kW) boxes_loss_kernel(RenderBatch b, int 
     const Pert pt = resolve(b, m);
     for (int d = lane; d < b.n; d += 32) s_c[warp][d] = __fadd_rn(pt.theta[d], pt.tau[d]);
     __syncwarp();
-    const float loss = boxes_loss_warp(target, W, H, h, s_px, s_py, s_c[warp], b.n / 2, lane);
+    const float loss = boxes_loss_warp(target, tb, W, H, h, s_px, s_py, s_c[warp], s_sp[warp], b.n / 2, lane);
     if (lane == 0) *pt.loss = loss;
 }
 
@@ -96,10 +97,11 @@ __global__ void boxes_image_kernel(const float* params, int K, int W, int H, flo
 // Launch-shape variants (autotuner): 8, 4 or 16 warps per CTA; one warp
 // renders one perturbation in every shape, so the choice never changes a result.
 void launch_boxes_loss(const DevScene& sc, const RenderBatch& b, cudaStream_t s) {
+    const DiscBits tb{sc.tbinary ? sc.tbits : nullptr, sc.trowpop};
     switch (sc.render_variant) {
-        case 1: boxes_loss_kernel<4><<<(b.M + 3) / 4, 128, 0, s>>>(b, sc.W, sc.H, sc.radius, sc.target); break;
-        case 2: boxes_loss_kernel<16><<<(b.M + 15) / 16, 512, 0, s>>>(b, sc.W, sc.H, sc.radius, sc.target); break;
-        default: boxes_loss_kernel<8><<<(b.M + 7) / 8, 256, 0, s>>>(b, sc.W, sc.H, sc.radius, sc.target); break;
+        case 1: boxes_loss_kernel<4><<<(b.M + 3) / 4, 128, 0, s>>>(b, sc.W, sc.H, sc.radius, sc.target, tb); break;
+        case 2: boxes_loss_kernel<16><<<(b.M + 15) / 16, 512, 0, s>>>(b, sc.W, sc.H, sc.radius, sc.target, tb); break;
+        default: boxes_loss_kernel<8><<<(b.M + 7) / 8, 256, 0, s>>>(b, sc.W, sc.H, sc.radius, sc.target, tb); break;
     }
 }
 

@@ -613,6 +613,41 @@ def test_boxes_parity(n_boxes, strategy):
     Sc.close()
 
 
+@pytest.mark.parametrize("W,H,n_boxes,half,sigma,target", [
+    (64, 64, 1, 5.0 / 64.0, 1e-6, "own"),     # square edges on pixel centres, tiny perturbations
+    (37, 23, 3, 0.2, 0.3, "own"),             # wide perturbations: squares cut by the image edges
+    (100, 50, 5, 0.15, 0.2, "random"),        # overlapping squares, spans over word boundaries
+    (33, 40, 2, 1.5, 0.5, "random"),          # squares larger than the image
+    (96, 10, 4, 0.1, 0.1, "grey")])           # a grey target keeps the per-pixel loop
+def test_boxes_binary_target_spans(W, H, n_boxes, half, sigma, target):
+    """Squares against binary targets take the span path (one exact column
+    interval per square, rows by the exact row test, mismatch counts by
+    popcount): every loss equals the oracle's per-pixel count; a grey target
+    is checked within FP32 rounding."""
+    sc = wl.boxes_scene(n_boxes=n_boxes, width=W, height=H, half_size=half)
+    sc["sigma"] = sigma
+    g = np.random.default_rng(W * 11 + H)
+    if sigma < 1e-5:   # centres on pixel centres
+        sc["theta_query"] = np.array([(W // 2 + 0.5) / W, (H // 3 + 0.5) / H] * n_boxes)
+    tgt = None
+    if target == "random":
+        tgt = (g.uniform(size=W * H) < 0.4).astype(np.float32)
+    elif target == "grey":
+        tgt = g.uniform(0.0, 1.0, size=W * H).astype(np.float32)
+    Sc = hr.Scene(sc, target_image=tgt) if tgt is not None else hr.Scene(sc)
+    ren = O.BoxesRenderer(sc, target=tgt) if tgt is not None else O.BoxesRenderer(sc)
+    flat, dbg, ref = run_both(sc, ren, "hessian", 128, "aggregate", scene=Sc)
+    Sc.close()
+    check_samples(dbg, ref)
+    if target == "grey":
+        assert_losses_close(dbg["losses"], ref.losses, 2e-6, "boxes grey-target losses")
+    else:
+        npx = W * H
+        assert np.array_equal(np.rint(dbg["losses"].astype(np.float64) * npx), np.rint(ref.losses * npx))
+        assert np.all(np.abs(dbg["losses"] - ref.losses) <= np.spacing(np.float32(ref.losses)))
+    assert_estimate_close(flat, ref, what="boxes spans")
+
+
 # ---------------------------------------------------------------------------
 # grey-box composition
 # ---------------------------------------------------------------------------

@@ -62,3 +62,30 @@ def test_binding_fails_loudly_without_library(monkeypatch, tmp_path):
     monkeypatch.setattr(hr, "LIB_PATH", str(tmp_path / "missing.so"))
     with pytest.raises(hr.HRError):
         hr.lib()
+
+
+def test_queue_entry_points_check_arguments_on_the_host():
+    """The persistent queue's calls reject missing handles and arguments
+    before any device call (so they run without a GPU)."""
+    hb.build()
+    L = hr.lib()
+    h = ctypes.c_void_p()
+    o = hr.hr_queue_opts(8, 1000, 1 << 20)
+    assert L.hr_queue_create(None, ctypes.byref(o), ctypes.byref(h)) == hr.HR_ERR_INVALID_ARG
+    assert L.hr_queue_create(None, None, None) == hr.HR_ERR_INVALID_ARG
+    t = ctypes.c_uint64()
+    th = np.zeros(2)
+    opts = hr.make_opts(0.05, 64, hr.HR_AGGREGATE, 1, 1)
+    assert L.hr_queue_submit(None, hr.HR_HESSIAN, th.ctypes.data_as(ctypes.POINTER(ctypes.c_double)), None,
+                             ctypes.byref(opts), ctypes.byref(t)) == hr.HR_ERR_INVALID_ARG
+    n = ctypes.c_int32()
+    assert L.hr_queue_submit_many(None, 1, hr.HR_HESSIAN, None, None, None, None, ctypes.byref(n)) == \
+        hr.HR_ERR_INVALID_ARG
+    out = np.zeros(4)
+    assert L.hr_queue_wait(None, 0, out.ctypes.data_as(ctypes.POINTER(ctypes.c_double)), 0) == \
+        hr.HR_ERR_INVALID_ARG
+    assert L.hr_queue_wait_many(None, 1, None, None, 4, 0) == hr.HR_ERR_INVALID_ARG
+    st = ctypes.c_int32()
+    assert L.hr_queue_status(None, ctypes.byref(st), None) == hr.HR_ERR_INVALID_ARG
+    assert L.hr_queue_destroy(None) == hr.HR_OK
+    assert "NULL" in hr.hr_last_error()

@@ -542,7 +542,17 @@ hr_status hr_queue_destroy(hr_queue q);
  *   mesh_tile_height        rows of the 8-pixel-wide raster tiles (4 or 8);
  *   mesh_walk_all_renders   renders with a tile row whose entries alone did
  *                           not fit, so that its tiles walked every triangle
- *                           (same pixels, same decisions, slower).
+ *                           (same pixels, same decisions, slower);
+ *   mesh_redo_renders       renders that did not fit the compact layout
+ *                           (more survivors than its slots, or more entries
+ *                           than it holds) and were rendered again in the
+ *                           full layout (counted once in mesh_renders);
+ *   mesh_compact_slots      survivor slots of the scene's compact layout,
+ *                           which puts two renders on an SM with the records
+ *                           of surviving triangles only (0: the scene's mesh
+ *                           or image is too large for it, every render uses
+ *                           the full layout).  Both layouts take the same
+ *                           coverage and depth decisions.
  * The sums divided by mesh_renders give per-render averages.  Path-traced
  * scenes (PTBOX) count their work only while hr_scene_count_work is on
  * (those launches use a counting build of the default launch shape; the
@@ -564,6 +574,8 @@ typedef struct {
     int64_t pt_shadow_rays;
     int64_t pt_vertices;
     int64_t mesh_walk_all_renders;
+    int64_t mesh_redo_renders;
+    int64_t mesh_compact_slots;
 } hr_scene_stats;
 hr_status hr_scene_get_stats(hr_scene scene, hr_scene_stats* out);
 /* PTBOX only: on != 0 makes the scene's following render launches count

@@ -503,10 +503,11 @@ hr_status hr_create_scene(const hr_scene_desc* d, hr_scene* out) {
             sc.nv = d->n_vertices; sc.nt = d->n_triangles;
             for (int c = 0; c < 3; ++c) { sc.albedo[c] = d->albedo[c]; sc.light[c] = d->light[c]; }
             sc.eye_dist = d->eye_dist; sc.scale = d->scale;
-            int dev = 0, maxsm = 0;
+            int dev = 0, maxsm = 0, smpm = 0;
             cudaGetDevice(&dev);
             cudaDeviceGetAttribute(&maxsm, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
-            if (!revolve_layout(sc, maxsm)) {
+            cudaDeviceGetAttribute(&smpm, cudaDevAttrMaxSharedMemoryPerMultiprocessor, dev);
+            if (!revolve_layout(sc, maxsm, smpm)) {
                 hr_destroy_scene(s);
                 return fail(HR_ERR_UNSUPPORTED, "mesh of %d triangles at %dx%d does not fit in %d B of shared memory",
                             sc.nt, sc.W, sc.H, maxsm);
@@ -516,8 +517,8 @@ hr_status hr_create_scene(const hr_scene_desc* d, hr_scene* out) {
             if ((e = cudaMalloc(&sc.tnrm, sizeof(float) * 3 * sc.nt)) != cudaSuccess) return bail(e, "normals");
             if ((e = cudaMalloc(&sc.tile_t2, sizeof(float) * revolve_tiles(sc))) != cudaSuccess)
                 return bail(e, "tiles");
-            if ((e = cudaMalloc(&sc.rv_stats, 7 * sizeof(unsigned long long))) != cudaSuccess) return bail(e, "stats");
-            if ((e = cudaMemset(sc.rv_stats, 0, 7 * sizeof(unsigned long long))) != cudaSuccess) return bail(e, "stats");
+            if ((e = cudaMalloc(&sc.rv_stats, 8 * sizeof(unsigned long long))) != cudaSuccess) return bail(e, "stats");
+            if ((e = cudaMemset(sc.rv_stats, 0, 8 * sizeof(unsigned long long))) != cudaSuccess) return bail(e, "stats");
             revolve_prepare(sc, s->stream);
             break;
         }
@@ -631,7 +632,7 @@ hr_status hr_scene_get_stats(hr_scene s, hr_scene_stats* out) {
     std::lock_guard<std::mutex> lk(s->mu);
     memset(out, 0, sizeof(*out));
     if (s->sc.rv_stats) {
-        unsigned long long v[7] = {};
+        unsigned long long v[8] = {};
         cudaError_t e = cudaDeviceSynchronize();
         if (e == cudaSuccess) e = cudaMemcpy(v, s->sc.rv_stats, sizeof v, cudaMemcpyDeviceToHost);
         if (e != cudaSuccess) return fail(HR_ERR_CUDA, "stats: %s", cudaGetErrorString(e));
@@ -643,6 +644,8 @@ hr_status hr_scene_get_stats(hr_scene s, hr_scene_stats* out) {
         out->mesh_raster_steps = (int64_t)v[5];
         out->mesh_tile_height = s->sc.rv_th;
         out->mesh_walk_all_renders = (int64_t)v[6];
+        out->mesh_redo_renders = (int64_t)v[7];
+        out->mesh_compact_slots = s->sc.rv_cslots;
     }
     if (s->sc.pt_stats) {
         unsigned long long v[4] = {};

@@ -166,6 +166,8 @@ struct DevScene {
     size_t rv_smem = 0;           // dynamic shared memory of one render
     int rv_cap = 0, rv_vreg = 0;  // bin entry capacity, vertex-region floats
     int rv_th = 8;                // raster tile height (8 x rv_th pixel tiles)
+    size_t rv_csmem = 0;          // compact layout (two renders per SM): shared memory, 0 = none
+    int rv_ccap = 0, rv_cslots = 0;   // its bin entry capacity and survivor slots
     unsigned long long* rv_stats = nullptr;   // [1] renders that took the bin-overflow path
     // tris2d
     float* raw = nullptr;         // [n_tris][9]
@@ -196,8 +198,10 @@ int render_variant_count(int kind);
 
 // shared-memory layout and tile height of one mesh render on a device with
 // max_smem bytes of opt-in shared memory per block (sets rv_smem, rv_cap,
-// rv_vreg, rv_th); false if the mesh does not fit
-bool revolve_layout(DevScene& sc, int max_smem);
+// rv_vreg, rv_th) and, where it fits, of the compact layout that puts two
+// renders on an SM (rv_csmem, rv_ccap, rv_cslots); false if the mesh does
+// not fit
+bool revolve_layout(DevScene& sc, int max_smem, int smem_per_sm);
 int revolve_tiles(const DevScene& sc);
 void revolve_prepare(DevScene& sc, cudaStream_t s);   // normals, kernel attributes
 void revolve_tile_t2(DevScene& sc, cudaStream_t s);   // after the target exists

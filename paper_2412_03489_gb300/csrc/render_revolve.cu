@@ -2,14 +2,25 @@
 // the Mug task of Sec. 4.1) fused with the per-pixel L2 loss and the block
 // reduction, so that no image is written to HBM.
 //
-// One CTA (1024 threads, one per SM, persistent over perturbations) renders a
-// whole perturbation:
+// One CTA (persistent over perturbations) renders a whole perturbation.  Two
+// shared-memory layouts:
+//   compact  records of surviving triangles only, by slot, in half an SM's
+//            shared memory: two CTAs of 512 threads per SM, so that one's
+//            barrier-bound set-up phases overlap the other's raster; a render
+//            with more survivors than slots or more bin entries than fit is
+//            handed over (its loss set to a marker NaN);
+//   full     records by triangle, one CTA of 1024 threads per SM, bins that do
+//            not fit rastered in bands; it renders the handed-over
+//            perturbations (a second launch that reads the loss words), every
+//            scene too large for the compact layout, and images.
+// Both take the same coverage and depth decisions:
 //   1. rotation R = Rx(p0) Ry(p1) from RN32 of FP64 cos / sin (for every
 //      perturbation after a CTA's first, computed during the previous raster);
 //   2. vertex transform and projection (FP32, fixed operation order);
 //   3. triangle setup: edge functions with their top-left thresholds, back-face
 //      cull, depth plane of 1/Z, pixel bounding box, flat Lambert shade; each
-//      record stays at its triangle's index in shared memory;
+//      record stays at its triangle's index (full) or takes the next slot
+//      (compact, where the record carries the triangle's index);
 //   4. binning into 8x4 pixel tiles (8x8 where shared memory is short; count,
 //      scan, fill; all in shared memory), skipping tiles that a conservative
 //      edge test shows the triangle misses; each bin entry carries the
@@ -27,8 +38,10 @@
 //      one FP32 loss per perturbation.
 // The FP32 sequences of steps 2-5 define the renderer (coverage and depth
 // decisions), so they use explicitly rounded intrinsics.
+#include <algorithm>
 #include <climits>
 #include <cmath>
+#include <type_traits>
 
 #include "hr_device.cuh"
 #include "hr_internal.h"
@@ -36,16 +49,26 @@
 namespace hr {
 namespace {
 
-constexpr int kThreads = 1024;
-constexpr int kWarps = kThreads / 32;
+constexpr int kThreads = 1024;      // full layout: one CTA per SM
+constexpr int kCompactThreads = 512; // compact layout: two CTAs per SM
 constexpr int kTW = 8;              // tile width; tiles are 8 x 4 or 8 x 8 pixels
 constexpr int kEntryCapMax = 16384;  // bin entries per render (less where shared memory is short)
 constexpr int kEntryCapMin = 2048;
 constexpr int kStaticSmem = 1024;    // the kernel's static shared memory, rounded up
+// compact layout: at least this many bin entries, and slots for at least
+// half the triangles (a closed mesh shows about half of them)
+constexpr int kCompactCapMin = 4096;
+// loss written by a compact-layout render that did not fit (more survivors
+// than slots, or more entries than the entry array holds): a NaN no
+// arithmetic produces, which the full-layout launch that follows renders again
+constexpr uint32_t kRedoLoss = 0x7FC0DEADu;
 
 // One surviving triangle.  E > 0, or E == 0 on a top-left edge, is one
 // compare: E > th with th = 0 or th = -(smallest subnormal) (no float lies
-// strictly between the two).
+// strictly between the two).  The last word is the flat shade (full layout:
+// records by triangle) or the triangle's index (compact layout: records by
+// survivor slot, the index decides depth ties); the raster reads the shades
+// from their own array.
 struct __align__(16) TriRec {
     float A0, B0, C0, th0;
     float A1, B1, C1, th1;
@@ -81,8 +104,10 @@ struct RvArgs {
     int cap;             // bin entry capacity
     int vreg;            // floats in the vertex region
     int th;              // tile height (the kernel's template argument)
+    int slots;           // compact layout: survivor slots (records by slot)
+    int redo;            // full layout: render only the perturbations whose loss is kRedoLoss
     uint64_t tx_recip;   // ceil(2^32 / TX): t / TX = (t tx_recip) >> 32 exactly for t, TX < 2^16
-    unsigned long long* stats;   // diagnostics [7], see hr_scene_stats
+    unsigned long long* stats;   // diagnostics [8], see hr_scene_stats
     float alb0, alb1, alb2, l0, l1, l2, eye_dist, scale;
 };
 
@@ -126,8 +151,9 @@ constexpr int kCountClasses = 32;   // tiles ordered by entry count, counts >= 3
 // of nearly equal counts waste few iterations, and the long tiles go first.  hist
 // [kCountClasses] must be zero on entry.  Returns the total entry count (all
 // threads) and sets n_obj.
-__device__ int bin_scan(const int* cnt, int* off, uint16_t* olist, int T, int* warp_tot, int* hist, int* n_obj) {
-    const int per = (T + kThreads - 1) / kThreads;
+template <int kT, class OffT>
+__device__ int bin_scan(const int* cnt, OffT* off, uint16_t* olist, int T, int* warp_tot, int* hist, int* n_obj) {
+    const int per = (T + kT - 1) / kT;
     const int b = threadIdx.x * per;
     int local = 0;
     for (int i = 0; i < per; ++i)
@@ -147,7 +173,7 @@ __device__ int bin_scan(const int* cnt, int* off, uint16_t* olist, int T, int* w
     __syncthreads();
     if (warp < 2) {   // warp 0: offsets of the warps' tile ranges; warp 1: the count classes
         int* arr = warp == 0 ? warp_tot : hist;
-        const int wv = arr[lane];
+        const int wv = (warp == 0 && lane >= kT / 32) ? 0 : arr[lane];
         int wi = wv;
 #pragma unroll
         for (int o = 1; o < 32; o <<= 1) {
@@ -162,7 +188,7 @@ __device__ int bin_scan(const int* cnt, int* off, uint16_t* olist, int T, int* w
     for (int i = 0; i < per; ++i)
         if (b + i < T) {
             const int c = cnt[b + i];
-            off[b + i] = run;
+            off[b + i] = (OffT)run;
             if (c > 0) olist[atomicAdd(&hist[kCountClasses - 1 - min(c, kCountClasses - 1)], 1)] = (uint16_t)(b + i);
             run += c;
         }
@@ -250,27 +276,57 @@ __device__ __forceinline__ bool setup_triangle(const RvArgs& P, int ia, int ib, 
     return true;
 }
 
-template <int kTH, bool kImage>
-__global__ void __launch_bounds__(kThreads, 1)
+// kCompact: records by survivor slot in about half the shared memory, so
+// that two CTAs of 512 threads share an SM and one's barrier-bound set-up
+// phases overlap the other's raster; a render that does not fit (more
+// survivors than slots, more bin entries than the entry array) writes
+// kRedoLoss instead of its loss.  Otherwise (full layout) records by
+// triangle, one 1024-thread CTA per SM, bins too large for the shared memory
+// rastered in bands; with P.redo only the kRedoLoss perturbations are rendered.
+template <int kTH, bool kImage, bool kCompact>
+__global__ void __launch_bounds__(kCompact ? kCompactThreads : kThreads, kCompact ? 2 : 1)
 revolve_kernel(RvArgs P, RenderBatch b, const float* __restrict__ img_params, float* __restrict__ img,
                int32_t* __restrict__ ids) {
+    constexpr int kT = kCompact ? kCompactThreads : kThreads;   // threads per CTA
+    constexpr int kW = kT / 32;
     constexpr int kG = 2 * kTH;          // lanes per tile: kTH rows x 2 four-pixel strips
     constexpr int kPer = 32 / kG;        // tiles per warp
+    using OffT = typename std::conditional<kCompact, uint16_t, int>::type;   // bin offsets (< kEntryCapMax)
     extern __shared__ __align__(16) unsigned char smem[];
-    TriRec* rec = reinterpret_cast<TriRec*>(smem);                // [nt] by triangle
-    uint2* bbx = reinterpret_cast<uint2*>(rec + P.nt);           // [nt] pixel bounding box by triangle
-    float* vx = reinterpret_cast<float*>(bbx + P.nt);            // vertex region, P.vreg floats (8 B aligned)
+    const int nrec = kCompact ? P.slots : P.nt;
+    TriRec* rec = reinterpret_cast<TriRec*>(smem);      // [nrec] by triangle (full) or by slot (compact)
+    uint2* bbx = reinterpret_cast<uint2*>(rec + nrec);  // [nrec] pixel bounding boxes
+    float* vx;            // projected vertices x, y, 1/Z [nv] each
+    float* tshade;        // [nrec] flat shades
+    int* tcnt;            // [T] bin counts, then fill cursors, then tile losses
+    OffT* toff;           // [T] bin offsets
+    uint16_t* surv = nullptr;              // full: [nt] surviving triangles (any order)
+    uint32_t* ent;                         // [cap] bin entries
+    unsigned long long* tmask = nullptr;   // full: [nt] tile masks of the count pass, by survivor
+    uint16_t* tm16 = nullptr;              // compact: [slots] tile masks of rectangles of <= 16 tiles
+    uint16_t* olist;                       // [T] tiles with entries, ordered by entry count
+    if constexpr (kCompact) {
+        tshade = reinterpret_cast<float*>(bbx + nrec);
+        tcnt = reinterpret_cast<int*>(tshade + nrec);
+        toff = reinterpret_cast<OffT*>(tcnt + P.T);
+        olist = reinterpret_cast<uint16_t*>(toff + P.T);
+        tm16 = olist + P.T;
+        ent = reinterpret_cast<uint32_t*>(tm16 + ((nrec + 1) & ~1));
+        vx = reinterpret_cast<float*>(ent);   // the vertices are dead before the first entry is written
+    } else {
+        vx = reinterpret_cast<float*>(bbx + nrec);   // vertex region, P.vreg floats (8 B aligned)
+        tshade = vx + P.vreg;
+        tcnt = reinterpret_cast<int*>(tshade + nrec);
+        toff = reinterpret_cast<OffT*>(tcnt + P.T);
+        surv = reinterpret_cast<uint16_t*>(toff + P.T);
+        ent = reinterpret_cast<uint32_t*>(surv + ((P.nt + 1) & ~1));
+        // after the triangle setup the vertex region holds the count pass's
+        // tile masks and the list of tiles with entries
+        tmask = reinterpret_cast<unsigned long long*>(vx);
+        olist = reinterpret_cast<uint16_t*>(tmask + P.nt);
+    }
     float* vy = vx + P.nv;
     float* viz = vy + P.nv;
-    float* tshade = vx + P.vreg;                                 // [nt] flat shade by triangle
-    int* tcnt = reinterpret_cast<int*>(tshade + P.nt);
-    int* toff = tcnt + P.T;
-    uint16_t* surv = reinterpret_cast<uint16_t*>(toff + P.T);   // [nt] surviving triangles (any order)
-    uint32_t* ent = reinterpret_cast<uint32_t*>(surv + ((P.nt + 1) & ~1));   // [cap] bin entries
-    // after the triangle setup the vertex region holds the count pass's tile
-    // masks [nt] (64-bit, by survivor) and the list of tiles with entries [T]
-    unsigned long long* tmask = reinterpret_cast<unsigned long long*>(vx);
-    uint16_t* olist = reinterpret_cast<uint16_t*>(tmask + P.nt);
 
     __shared__ float s_cs[4], s_cs_next[4];
     __shared__ float sR[9];
@@ -278,18 +334,40 @@ revolve_kernel(RvArgs P, RenderBatch b, const float* __restrict__ img_params, fl
     __shared__ int s_count;
     __shared__ int s_wtot[33];
     __shared__ int s_hist[33];
-    __shared__ float s_part[kWarps];
+    __shared__ float s_part[kW];
     __shared__ int s_tile;
     __shared__ int s_band[2];   // the current band's end row and whether it walks every triangle
-    __shared__ unsigned long long s_steps[kWarps];   // raster steps of each warp (diagnostics)
+    __shared__ unsigned long long s_steps[kW];   // raster steps of each warp (diagnostics)
 
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     const int M = kImage ? 1 : b.M;
     if (lane == 0) s_steps[warp] = 0ull;
-    for (int m = kImage ? 0 : (int)blockIdx.x; m < M; m += kImage ? 1 : (int)gridDim.x) {
+    // Redo mode: the first of this CTA's perturbations m0, m0 + G, ... (G the
+    // grid) whose loss is kRedoLoss, M if none; warp 0 reads 32 loss words at
+    // a time.  Every thread calls it (one barrier); s_next is rewritten only
+    // by the next call, after the render's barriers.
+    __shared__ int s_next;
+    auto next_redo = [&](int m0) -> int {
+        if (warp == 0) {
+            const int G = (int)gridDim.x;
+            int found = M;
+            for (int base = m0; base < M && found == M; base += 32 * G) {
+                const int mm = base + lane * G;
+                const bool want = mm < M && __float_as_uint(*resolve(b, mm).loss) == kRedoLoss;
+                const unsigned bal = __ballot_sync(0xffffffffu, want);
+                if (bal) found = base + (__ffs(bal) - 1) * G;
+            }
+            if (lane == 0) s_next = found;
+        }
+        __syncthreads();
+        return s_next;
+    };
+    const bool redo = !kImage && !kCompact && P.redo;
+    for (int m = kImage ? 0 : (redo ? next_redo((int)blockIdx.x) : (int)blockIdx.x); m < M;
+         m = kImage ? m + 1 : (redo ? next_redo(m + (int)gridDim.x) : m + (int)gridDim.x)) {
         // ---- 1. parameters and rotation ----------------------------------
         if (tid < 4) {   // ca, sa, cb, sb
-            if (kImage || m == (int)blockIdx.x) {
+            if (kImage || m == (int)blockIdx.x || P.redo) {
                 const float p = kImage ? img_params[tid >> 1] : rotation_param(b, m, tid >> 1);
                 const double a = (double)p;
                 s_cs[tid] = (float)((tid & 1) ? sin(a) : cos(a));
@@ -304,16 +382,16 @@ revolve_kernel(RvArgs P, RenderBatch b, const float* __restrict__ img_params, fl
         int pt[2][3];
 #pragma unroll
         for (int k = 0; k < 2; ++k) {
-            const int v = tid + k * kThreads, t = tid + k * kThreads;
+            const int v = tid + k * kT, t = tid + k * kT;
 #pragma unroll
             for (int c = 0; c < 3; ++c) {
                 pv[k][c] = v < P.nv ? P.verts[3 * v + c] : 0.0f;
                 pt[k][c] = t < P.nt ? P.tris[3 * t + c] : 0;
                 pn[k][c] = t < P.nt ? P.tnrm[3 * t + c] : 0.0f;
             }
-            pt2[k] = (!kImage && tid + k * kThreads < P.T) ? P.tile_t2[tid + k * kThreads] : 0.0f;
+            pt2[k] = (!kImage && tid + k * kT < P.T) ? P.tile_t2[tid + k * kT] : 0.0f;
         }
-        for (int i = tid; i < P.T; i += kThreads) tcnt[i] = 0;
+        for (int i = tid; i < P.T; i += kT) tcnt[i] = 0;
         if (tid < 33) s_hist[tid] = 0;
         if (tid == 0) { s_count = 0; s_tile = 0; }
         __syncthreads();
@@ -342,8 +420,8 @@ revolve_kernel(RvArgs P, RenderBatch b, const float* __restrict__ img_params, fl
         };
 #pragma unroll
         for (int k = 0; k < 2; ++k)
-            if (tid + k * kThreads < P.nv) project(tid + k * kThreads, pv[k][0], pv[k][1], pv[k][2]);
-        for (int v = tid + 2 * kThreads; v < P.nv; v += kThreads)
+            if (tid + k * kT < P.nv) project(tid + k * kT, pv[k][0], pv[k][1], pv[k][2]);
+        for (int v = tid + 2 * kT; v < P.nv; v += kT)
             project(v, P.verts[3 * v], P.verts[3 * v + 1], P.verts[3 * v + 2]);
         __syncthreads();
         // ---- 3. triangle setup ------------------------------------------------
@@ -351,41 +429,79 @@ revolve_kernel(RvArgs P, RenderBatch b, const float* __restrict__ img_params, fl
         // tie rule); the survivors are listed for the binning, and a clipped,
         // culled or off-image triangle gets an empty bounding box (lo > hi),
         // which the all-triangles fallback of the raster skips
+        // (compact layout: a survivor takes the next slot; past the last slot
+        // it is only counted, and the render is handed to the full layout)
         auto setup = [&](int t, const int id[3], const float n[3]) {
             TriRec r;
             uint2 bb;
-            if (setup_triangle(P, id[0], id[1], id[2], n, vx, vy, viz, sL, r, bb)) {
-                rec[t] = r;
-                tshade[t] = r.shade;
-                surv[atomicAdd(&s_count, 1)] = (uint16_t)t;
+            if constexpr (kCompact) {
+                if (setup_triangle(P, id[0], id[1], id[2], n, vx, vy, viz, sL, r, bb)) {
+                    const int k = atomicAdd(&s_count, 1);
+                    if (k < nrec) {
+                        tshade[k] = r.shade;
+                        r.shade = __int_as_float(t);
+                        rec[k] = r;
+                        bbx[k] = bb;
+                    }
+                }
             } else {
-                bb = make_uint2(1u, 1u);
+                if (setup_triangle(P, id[0], id[1], id[2], n, vx, vy, viz, sL, r, bb)) {
+                    rec[t] = r;
+                    tshade[t] = r.shade;
+                    surv[atomicAdd(&s_count, 1)] = (uint16_t)t;
+                } else {
+                    bb = make_uint2(1u, 1u);
+                }
+                bbx[t] = bb;
             }
-            bbx[t] = bb;
         };
 #pragma unroll
         for (int k = 0; k < 2; ++k)
-            if (tid + k * kThreads < P.nt) setup(tid + k * kThreads, pt[k], pn[k]);
-        for (int t = tid + 2 * kThreads; t < P.nt; t += kThreads) {
+            if (tid + k * kT < P.nt) setup(tid + k * kT, pt[k], pn[k]);
+        for (int t = tid + 2 * kT; t < P.nt; t += kT) {
             const int id[3] = {P.tris[3 * t], P.tris[3 * t + 1], P.tris[3 * t + 2]};
             const float n[3] = {P.tnrm[3 * t], P.tnrm[3 * t + 1], P.tnrm[3 * t + 2]};
             setup(t, id, n);
         }
         __syncthreads();
         const int count = s_count;
+        // A compact-layout render that does not fit writes kRedoLoss (the full
+        // layout renders it again) and computes the rotation of the CTA's next
+        // perturbation, which its skipped raster phase would have computed.
+        auto hand_over = [&]() {
+            if (tid == 0) {
+                *resolve(b, m).loss = __uint_as_float(kRedoLoss);
+                if (P.stats) atomicAdd(&P.stats[7], 1ull);
+            }
+            if (warp == kW - 1 && lane < 4) {
+                const int mn = m + (int)gridDim.x;
+                if (mn < M) {
+                    const double a = (double)rotation_param(b, mn, lane >> 1);
+                    s_cs_next[lane] = (float)((lane & 1) ? sin(a) : cos(a));
+                }
+            }
+            __syncthreads();
+        };
+        if constexpr (kCompact) {
+            if (count > nrec) {
+                hand_over();
+                continue;
+            }
+        }
         // ---- 4. binning -----------------------------------------------------
         // count pass: each survivor's tiles that pass the conservative edge
         // test go into a bit mask (row-major over its tile rectangle;
-        // rectangles of more than 64 tiles skip the test), reused by the fill
-        for (int k = tid; k < count; k += kThreads) {
-            const int s = surv[k];
+        // rectangles of more than 64 tiles, 16 in the compact layout, skip the
+        // test), reused by the fill
+        for (int k = tid; k < count; k += kT) {
+            const int s = kCompact ? k : (int)surv[k];
             const uint2 bb = bbx[s];
             const float4* rp = reinterpret_cast<const float4*>(&rec[s]);
             const float4 q0 = rp[0], q1 = rp[1], q2 = rp[2];
             const float A[3] = {q0.x, q1.x, q2.x}, B[3] = {q0.y, q1.y, q2.y}, C[3] = {q0.z, q1.z, q2.z};
             const int tx0 = (int)(bb.x & 0xffffu) / kTW, tx1 = (int)(bb.x >> 16) / kTW;
             const int ty0 = (int)(bb.y & 0xffffu) / kTH, ty1 = (int)(bb.y >> 16) / kTH;
-            const bool test = (tx1 - tx0 + 1) * (ty1 - ty0 + 1) <= 64;
+            const bool test = (tx1 - tx0 + 1) * (ty1 - ty0 + 1) <= (kCompact ? 16 : 64);
             const float fW = (float)P.W, fH = (float)P.H;
             float neg[3];
 #pragma unroll
@@ -414,22 +530,29 @@ revolve_kernel(RvArgs P, RenderBatch b, const float* __restrict__ img_params, fl
                     }
                 }
             }
-            tmask[k] = test ? mask : ~0ull;
+            if constexpr (kCompact) tm16[k] = (uint16_t)mask;
+            else tmask[k] = test ? mask : ~0ull;
         }
         __syncthreads();
         int n_obj = 0;
-        const int total = bin_scan(tcnt, toff, olist, P.T, s_wtot, s_hist, &n_obj);
+        const int total = bin_scan<kT>(tcnt, toff, olist, P.T, s_wtot, s_hist, &n_obj);
+        if constexpr (kCompact) {
+            if (total > P.cap) {
+                hand_over();
+                continue;
+            }
+        }
         // Bins that do not fit the shared memory at once are filled and
         // rastered in bands of whole tile rows, each with at most capb entries;
         // meanwhile the count pass's per-row totals sit at the end of the
         // entry array.  A tile row whose entries alone exceed capb is a band of
         // its own whose tiles walk every triangle.  A band only decides which
         // tiles are rastered together: every pixel's decisions are the same.
-        const bool banded = total > P.cap;
+        const bool banded = !kCompact && total > P.cap;
         const int capb = banded ? P.cap - P.TY : P.cap;
         int* rowtot = reinterpret_cast<int*>(ent) + capb;
         if (banded) {
-            for (int r = warp; r < P.TY; r += kWarps) {
+            for (int r = warp; r < P.TY; r += kW) {
                 int sum = 0;
                 for (int tx = lane; tx < P.TX; tx += 32) sum += tcnt[r * P.TX + tx];
                 sum = __reduce_add_sync(0xffffffffu, sum);
@@ -447,7 +570,7 @@ revolve_kernel(RvArgs P, RenderBatch b, const float* __restrict__ img_params, fl
         // the bins fit (then every argument but the row count is a constant)
         auto band = [&](const int r0, const int r1, const int total_b, const bool walk_all) {
             const int tb = r0 * P.TX, Tb = (r1 - r0) * P.TX;   // the band's tiles [tb, tb + Tb)
-            for (int i = tid; i < Tb; i += kThreads) tcnt[tb + i] = 0;   // becomes the fill cursor
+            for (int i = tid; i < Tb; i += kT) tcnt[tb + i] = 0;   // becomes the fill cursor
             if (tid == 0) s_tile = 0;
             __syncthreads();
             if (!walk_all) {
@@ -457,20 +580,22 @@ revolve_kernel(RvArgs P, RenderBatch b, const float* __restrict__ img_params, fl
                 auto empty = [&](int i) { return ((i + 1 < Tb) ? toff[tb + i + 1] : total_b) == toff[tb + i]; };
 #pragma unroll
                 for (int k = 0; k < 2; ++k) {
-                    const int i = tid + k * kThreads;
+                    const int i = tid + k * kT;
                     if (i < Tb && empty(i)) tl[tb + i] = tb == 0 ? pt2[k] : P.tile_t2[tb + i];
                 }
-                for (int i = tid + 2 * kThreads; i < Tb; i += kThreads)
+                for (int i = tid + 2 * kT; i < Tb; i += kT)
                     if (empty(i)) tl[tb + i] = P.tile_t2[tb + i];
-                for (int k = tid; k < count; k += kThreads) {
-                    const int s = surv[k];
+                for (int k = tid; k < count; k += kT) {
+                    const int s = kCompact ? k : (int)surv[k];
                     const uint2 bb = bbx[s];
                     const int xlo = (int)(bb.x & 0xffffu), xhi = (int)(bb.x >> 16);
                     const int ylo = (int)(bb.y & 0xffffu), yhi = (int)(bb.y >> 16);
                     const int tx0 = xlo / kTW, tx1 = xhi / kTW, ty0 = ylo / kTH, ty1 = yhi / kTH;
                     const int ya = max(ty0, r0), yb = min(ty1, r1 - 1);
                     if (ya > yb) continue;
-                    const unsigned long long mask = tmask[k];
+                    unsigned long long mask;   // ~0: every tile of the rectangle (not tested)
+                    if constexpr (kCompact) mask = (tx1 - tx0 + 1) * (ty1 - ty0 + 1) <= 16 ? tm16[k] : ~0ull;
+                    else mask = tmask[k];
                     int bit = (ya - ty0) * (tx1 - tx0 + 1);   // row-major over the whole tile rectangle
                     for (int ty = ya; ty <= yb; ++ty) {
                         // rows of this tile inside the box (bits >= kTH are never tested)
@@ -498,7 +623,7 @@ revolve_kernel(RvArgs P, RenderBatch b, const float* __restrict__ img_params, fl
             const int ry = gl >> 1, hx = gl & 1;
             // the FP64 cos / sin of this CTA's next perturbation, off the critical
             // path: one warp computes them before it joins the tile loop
-            if (!kImage && r0 == 0 && warp == kWarps - 1 && lane < 4) {
+            if (!kImage && !P.redo && r0 == 0 && warp == kW - 1 && lane < 4) {
                 const int mn = m + (int)gridDim.x;
                 if (mn < M) {
                     const double a = (double)rotation_param(b, mn, lane >> 1);
@@ -565,7 +690,14 @@ revolve_kernel(RvArgs P, RenderBatch b, const float* __restrict__ img_params, fl
                             const float wz = __fmaf_rn(q3.x, fx[c], rw);
                             const bool in = ((outside & (row_out | (1u << c))) == 0u) && (E0 > q0.w) &&
                                             (E1 > q1.w) && (E2 > q2.w);
-                            const bool better = in && (wz > bw[c] || (wz == bw[c] && s < bs[c]));
+                            // equal depths: the lower triangle index (records by
+                            // slot carry it in their last word)
+                            bool lower;
+                            if constexpr (kCompact)
+                                lower = bs[c] == INT_MAX || __float_as_int(rec[s].shade) < __float_as_int(rec[bs[c]].shade);
+                            else
+                                lower = s < bs[c];
+                            const bool better = in && (wz > bw[c] || (wz == bw[c] && lower));
                             bw[c] = better ? wz : bw[c];
                             bs[c] = better ? s : bs[c];
                         }
@@ -596,7 +728,7 @@ revolve_kernel(RvArgs P, RenderBatch b, const float* __restrict__ img_params, fl
                             raster_entry((int)(e >> 16), e >> col_shift, true);
                         }
                     }
-                } else {
+                } else if constexpr (!kCompact) {
                     // every triangle in index order (culled ones have an empty
                     // box), so the strict compare already keeps the lower index
                     for (int s = 0; s < P.nt; ++s) {
@@ -672,7 +804,7 @@ revolve_kernel(RvArgs P, RenderBatch b, const float* __restrict__ img_params, fl
                 const bool walk_all = s_band[1] != 0;
                 walked = walked || walk_all;
                 const int total_b = walk_all ? 0
-                                             : bin_scan(tcnt + r0 * P.TX, toff + r0 * P.TX, olist, (r1 - r0) * P.TX,
+                                             : bin_scan<kT>(tcnt + r0 * P.TX, toff + r0 * P.TX, olist, (r1 - r0) * P.TX,
                                                         s_wtot, s_hist, &n_obj);
                 band(r0, r1, total_b, walk_all);
             }
@@ -684,12 +816,12 @@ revolve_kernel(RvArgs P, RenderBatch b, const float* __restrict__ img_params, fl
             // thread i sums tiles i, i + 1024, ...; then a fixed shuffle tree
             float acc = 0.0f;
             const float* tile_loss = reinterpret_cast<const float*>(tcnt);
-            for (int t = tid; t < P.T; t += kThreads) acc += tile_loss[t];
+            for (int t = tid; t < P.T; t += kT) acc += tile_loss[t];
             acc = warp_sum(acc);
             if (lane == 0) s_part[warp] = acc;
             __syncthreads();
             if (warp == 0) {
-                float v = s_part[lane];
+                float v = lane < kW ? s_part[lane] : 0.0f;
                 v = warp_sum(v);
                 if (lane == 0) *resolve(b, m).loss = v / (float)(P.W * P.H * 3);
             }
@@ -731,7 +863,7 @@ __global__ void tile_t2_kernel(const float* target, int W, int H, int TX, int TH
     out[t] = s;
 }
 
-RvArgs make_args(const DevScene& sc) {
+RvArgs make_args(const DevScene& sc, bool compact = false, bool redo = false) {
     RvArgs a;
     a.verts = sc.verts; a.tris = sc.tris; a.tnrm = sc.tnrm; a.target = sc.target; a.tile_t2 = sc.tile_t2;
     a.nv = sc.nv; a.nt = sc.nt; a.W = sc.W; a.H = sc.H;
@@ -741,9 +873,39 @@ RvArgs make_args(const DevScene& sc) {
     a.alb0 = sc.albedo[0]; a.alb1 = sc.albedo[1]; a.alb2 = sc.albedo[2];
     a.l0 = sc.light[0]; a.l1 = sc.light[1]; a.l2 = sc.light[2];
     a.eye_dist = sc.eye_dist; a.scale = sc.scale;
-    a.cap = sc.rv_cap; a.vreg = sc.rv_vreg;
+    a.cap = compact ? sc.rv_ccap : sc.rv_cap;
+    a.vreg = sc.rv_vreg;
+    a.slots = sc.rv_cslots;
+    a.redo = redo ? 1 : 0;
     a.stats = sc.rv_stats;
     return a;
+}
+
+// Compact layout of one render with tile height th in `budget` bytes:
+// records (64 B), bounding boxes (8 B), shades (4 B) and 16-bit tile masks
+// by survivor slot, tile counts (4 B), offsets and the list of tiles with
+// entries (2 B each) by tile, and the bin entries, which first hold the
+// projected vertices.  Slots for every triangle when they fit (the rest
+// of the budget to entries, at most kEntryCapMax), else kCompactCapMin
+// entries and the rest to slots; false under half the triangles' slots.
+bool compact_layout_for(int nv, int nt, int W, int H, int th, long long budget, size_t* bytes, int* cap,
+                        int* slots) {
+    const long long T = (long long)((W + kTW - 1) / kTW) * ((H + th - 1) / th);
+    const long long per_slot = (long long)(sizeof(TriRec) + sizeof(uint2) + sizeof(float) + sizeof(uint16_t));
+    const long long fixed = (long long)(sizeof(int) + 2 * sizeof(uint16_t)) * T + 4;   // + the mask array's padding
+    const long long cap_min = std::max<long long>(kCompactCapMin, 3LL * nv);   // the vertices live in the entries
+    if (cap_min > kEntryCapMax) return false;
+    long long s = (budget - kStaticSmem - fixed - 4 * cap_min) / per_slot;
+    long long c = cap_min;
+    if (s >= nt) {
+        s = nt;
+        c = std::min<long long>(kEntryCapMax, (budget - kStaticSmem - fixed - per_slot * nt) / 4);
+    }
+    if (s < 1 || 2 * s < nt) return false;
+    *slots = (int)s;
+    *cap = (int)c;
+    *bytes = (size_t)(per_slot * s + fixed + 4 * c);
+    return true;
 }
 
 // bytes and entry capacity of one render's layout with tile height th
@@ -773,7 +935,11 @@ bool layout_for(int nv, int nt, int W, int H, int th, int max_smem, size_t* byte
 // than kEntryCapMin entries fit either way.  The tile height is a function of
 // the scene's sizes only, so every render of a scene sums its loss in the
 // same order.
-bool revolve_layout(DevScene& sc, int max_smem) {
+//
+// The compact layout (two CTAs per SM, each with half of smem_per_sm less
+// the 1 KB the hardware reserves per CTA) serves the renders it fits, with
+// the same tile height; the full layout renders the rest and every image.
+bool revolve_layout(DevScene& sc, int max_smem, int smem_per_sm) {
     size_t bytes = 0;
     int cap = 0, vreg = 0;
     if (layout_for(sc.nv, sc.nt, sc.W, sc.H, 4, max_smem, &bytes, &cap, &vreg) && cap >= 8192) {
@@ -786,16 +952,36 @@ bool revolve_layout(DevScene& sc, int max_smem) {
     sc.rv_smem = bytes;
     sc.rv_cap = cap;
     sc.rv_vreg = vreg;
+    size_t cbytes = 0;
+    int ccap = 0, cslots = 0;
+    const long long budget = std::min<long long>(max_smem, smem_per_sm / 2 - 1024);
+    if (compact_layout_for(sc.nv, sc.nt, sc.W, sc.H, sc.rv_th, budget, &cbytes, &ccap, &cslots)) {
+        sc.rv_csmem = cbytes;
+        sc.rv_ccap = ccap;
+        sc.rv_cslots = cslots;
+    } else {
+        sc.rv_csmem = 0;
+        sc.rv_ccap = 0;
+        sc.rv_cslots = 0;
+    }
     return true;
 }
 
 void revolve_prepare(DevScene& sc, cudaStream_t s) {
     normals_kernel<<<(sc.nt + 255) / 256, 256, 0, s>>>(sc.verts, sc.tris, sc.nt, sc.tnrm);
     const int bytes = (int)sc.rv_smem;
-    cudaFuncSetAttribute(revolve_kernel<4, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
-    cudaFuncSetAttribute(revolve_kernel<4, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
-    cudaFuncSetAttribute(revolve_kernel<8, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
-    cudaFuncSetAttribute(revolve_kernel<8, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
+    cudaFuncSetAttribute(revolve_kernel<4, false, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
+    cudaFuncSetAttribute(revolve_kernel<4, true, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
+    cudaFuncSetAttribute(revolve_kernel<8, false, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
+    cudaFuncSetAttribute(revolve_kernel<8, true, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
+    if (sc.rv_csmem) {
+        const int cb = (int)sc.rv_csmem;
+        cudaFuncSetAttribute(revolve_kernel<4, false, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, cb);
+        cudaFuncSetAttribute(revolve_kernel<8, false, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, cb);
+        // all of the SM's unified memory as shared memory, so that two CTAs fit
+        cudaFuncSetAttribute(revolve_kernel<4, false, true>, cudaFuncAttributePreferredSharedMemoryCarveout, 100);
+        cudaFuncSetAttribute(revolve_kernel<8, false, true>, cudaFuncAttributePreferredSharedMemoryCarveout, 100);
+    }
 }
 
 void revolve_tile_t2(DevScene& sc, cudaStream_t s) {
@@ -807,12 +993,27 @@ int revolve_tiles(const DevScene& sc) {
     return ((sc.W + kTW - 1) / kTW) * ((sc.H + sc.rv_th - 1) / sc.rv_th);
 }
 
+// With a compact layout: the compact launch (two CTAs per SM), then the
+// full-layout launch in redo mode, which renders only the perturbations the
+// compact one handed over (its CTAs read M loss words when there are none).
 void launch_revolve_loss(const DevScene& sc, const RenderBatch& b, cudaStream_t s) {
     const int grid = b.M < num_sms() ? b.M : num_sms();
+    const bool compact = sc.rv_csmem != 0;
+    if (compact) {
+        const int cgrid = b.M < 2 * num_sms() ? b.M : 2 * num_sms();
+        if (sc.rv_th == 4)
+            revolve_kernel<4, false, true><<<cgrid, kCompactThreads, sc.rv_csmem, s>>>(make_args(sc, true), b, nullptr,
+                                                                                        nullptr, nullptr);
+        else
+            revolve_kernel<8, false, true><<<cgrid, kCompactThreads, sc.rv_csmem, s>>>(make_args(sc, true), b, nullptr,
+                                                                                        nullptr, nullptr);
+    }
     if (sc.rv_th == 4)
-        revolve_kernel<4, false><<<grid, kThreads, sc.rv_smem, s>>>(make_args(sc), b, nullptr, nullptr, nullptr);
+        revolve_kernel<4, false, false><<<grid, kThreads, sc.rv_smem, s>>>(make_args(sc, false, compact), b, nullptr,
+                                                                           nullptr, nullptr);
     else
-        revolve_kernel<8, false><<<grid, kThreads, sc.rv_smem, s>>>(make_args(sc), b, nullptr, nullptr, nullptr);
+        revolve_kernel<8, false, false><<<grid, kThreads, sc.rv_smem, s>>>(make_args(sc, false, compact), b, nullptr,
+                                                                           nullptr, nullptr);
 }
 
 // one image at params: colours into img [H][W][3], or, with ids non-null,
@@ -820,9 +1021,9 @@ void launch_revolve_loss(const DevScene& sc, const RenderBatch& b, cudaStream_t 
 void launch_revolve_image(const DevScene& sc, const float* params, float* img, int32_t* ids, cudaStream_t s) {
     RenderBatch b{};
     if (sc.rv_th == 4)
-        revolve_kernel<4, true><<<1, kThreads, sc.rv_smem, s>>>(make_args(sc), b, params, img, ids);
+        revolve_kernel<4, true, false><<<1, kThreads, sc.rv_smem, s>>>(make_args(sc), b, params, img, ids);
     else
-        revolve_kernel<8, true><<<1, kThreads, sc.rv_smem, s>>>(make_args(sc), b, params, img, ids);
+        revolve_kernel<8, true, false><<<1, kThreads, sc.rv_smem, s>>>(make_args(sc), b, params, img, ids);
 }
 
 }  // namespace hr

@@ -85,7 +85,8 @@ class hr_scene_stats(ctypes.Structure):
                 ("mesh_tiles_with_entries", ctypes.c_int64), ("mesh_raster_steps", ctypes.c_int64),
                 ("mesh_tile_height", ctypes.c_int64), ("pt_counted_renders", ctypes.c_int64),
                 ("pt_hit_rays", ctypes.c_int64), ("pt_shadow_rays", ctypes.c_int64), ("pt_vertices", ctypes.c_int64),
-                ("mesh_walk_all_renders", ctypes.c_int64)]
+                ("mesh_walk_all_renders", ctypes.c_int64), ("mesh_redo_renders", ctypes.c_int64),
+                ("mesh_compact_slots", ctypes.c_int64)]
 
 
 class hr_tune_info(ctypes.Structure):

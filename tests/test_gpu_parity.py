@@ -169,12 +169,21 @@ def test_revolve_small(strategy):
 
 def test_revolve_full_size_bench_configuration():
     """256 x 256, 2048 triangles, sigma 0.1, 4096 aggregate samples: the bench
-    workload in its launch configuration, compared in full."""
+    workload in its launch configuration, compared in full.  Every render
+    runs in the compact layout (two renders per SM, records of the ~900
+    surviving triangles only): none is handed to the full layout."""
     sc = wl.revolve_scene()
-    flat, dbg, ref = run_both(sc, O.RevolveRenderer(sc), "hessian", 4096, "aggregate", seed=2024, request=0)
+    Sc = hr.Scene(sc)
+    before = hr.hr_scene_get_stats(Sc.handle)
+    flat, dbg, ref = run_both(sc, O.RevolveRenderer(sc), "hessian", 4096, "aggregate", seed=2024, request=0, scene=Sc)
+    st = hr.hr_scene_get_stats(Sc.handle)
+    Sc.close()
     check_samples(dbg, ref)
     assert_losses_close(dbg["losses"], ref.losses, 2e-5, "revolve losses")
     assert_estimate_close(flat, ref, what="revolve full")
+    assert st.mesh_compact_slots >= len(sc["triangles"]) // 2
+    assert st.mesh_renders - before.mesh_renders == 4096
+    assert st.mesh_redo_renders - before.mesh_redo_renders == 0
 
 
 def _ids_cases():
@@ -248,6 +257,25 @@ def test_revolve_tile_row_beyond_capacity_walks_every_triangle():
     _check_mesh_paths(sc, 512, 4, 8, True, True)
 
 
+@pytest.mark.parametrize("layers", [9, 16])
+def test_revolve_compact_layout_hands_over_what_does_not_fit(layers):
+    """Stacked full-frame sheets at 128^2 (every triangle faces the camera).
+    With 9 sheets (1,152 triangles) the compact layout has a slot for every
+    triangle but not room for the ~6,800 bin entries; with 16 (2,048) the
+    survivors outnumber its slots.  Either way every render is handed over
+    and rendered again in the full layout: images and an aggregate Hessian
+    against the oracle, and the counters show the hand-overs."""
+    sc = wl.revolve_scene(width=128, height=128)
+    sc["vertices"], sc["triangles"] = wl.sheets_mesh(layers=layers, grid=8)
+    Sc = hr.Scene(sc)
+    slots = hr.hr_scene_get_stats(Sc.handle).mesh_compact_slots
+    Sc.close()
+    assert 0 < slots
+    assert (slots >= len(sc["triangles"])) == (layers == 9)
+    st = _check_mesh_paths(sc, 128, 128, 16, None, False)
+    assert st.mesh_redo_renders == 16
+
+
 def _check_mesh_paths(sc, W, H, M, banded, walked):
     Sc = hr.Scene(sc)
     r = O.RevolveRenderer(sc)
@@ -266,10 +294,12 @@ def _check_mesh_paths(sc, W, H, M, banded, walked):
     st = hr.hr_scene_get_stats(Sc.handle)
     Sc.close()
     assert st.mesh_renders - before.mesh_renders == M   # the estimate's renders (images are not counted)
-    assert st.mesh_overflow_renders - before.mesh_overflow_renders == (M if banded else 0)
+    if banded is not None:
+        assert st.mesh_overflow_renders - before.mesh_overflow_renders == (M if banded else 0)
     assert st.mesh_walk_all_renders - before.mesh_walk_all_renders == (M if walked else 0)
     assert st.mesh_bin_entries > 0
     assert (st.mesh_raster_steps > 0) != walked   # binned raster steps are counted; a walk has none
+    return st
 
 
 # ---------------------------------------------------------------------------

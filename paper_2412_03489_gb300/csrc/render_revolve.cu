@@ -62,6 +62,11 @@ constexpr int kCompactCapMin = 4096;
 // than slots, or more entries than the entry array holds): a NaN no
 // arithmetic produces, which the full-layout launch that follows renders again
 constexpr uint32_t kRedoLoss = 0x7FC0DEADu;
+// compact layout: a launch's loss words start as kFreeLoss (marked by a kernel
+// that runs first); a CTA claims a perturbation by turning its word into
+// kTakenLoss with one compare-and-swap, then writes the loss over it
+constexpr uint32_t kFreeLoss = 0x7FC0F4EEu;
+constexpr uint32_t kTakenLoss = 0x7FC07A4Eu;
 
 // One surviving triangle.  E > 0, or E == 0 on a top-left edge, is one
 // compare: E > th with th = 0 or th = -(smallest subnormal) (no float lies
@@ -363,11 +368,73 @@ revolve_kernel(RvArgs P, RenderBatch b, const float* __restrict__ img_params, fl
         return s_next;
     };
     const bool redo = !kImage && !kCompact && P.redo;
-    for (int m = kImage ? 0 : (redo ? next_redo((int)blockIdx.x) : (int)blockIdx.x); m < M;
-         m = kImage ? m + 1 : (redo ? next_redo(m + (int)gridDim.x) : m + (int)gridDim.x)) {
+    // Compact layout: CTA c walks its perturbations c, c + G, ... and renders
+    // those it claims (one compare-and-swap on the loss word; the next one is
+    // claimed during the raster, with its rotation); after its own it steals
+    // free ones among the last 2G, so that CTAs that drew cheaper renders
+    // take over the last renders of the others.  Each perturbation is
+    // claimed, and rendered, exactly once.
+    __shared__ int s_pref;   // the perturbation claimed ahead (its rotation in s_cs_next), M if none
+    auto claim = [&](int i) -> bool {
+        unsigned int* w = reinterpret_cast<unsigned int*>(resolve(b, i).loss);
+        return atomicCAS(w, kFreeLoss, kTakenLoss) == kFreeLoss;
+    };
+    auto claim_from = [&](int i) -> int {   // one thread: the first of i, i + G, ... it claims, M if none
+        for (; i < M; i += (int)gridDim.x)
+            if (claim(i)) return i;
+        return M;
+    };
+    auto steal = [&]() -> int {   // every thread (one barrier); warp 0 scans 32 loss words at a time
+        if (warp == 0) {
+            const int lo = max(0, M - 2 * (int)gridDim.x);
+            int got = M;
+            for (int top = M - 1; top >= lo && got == M; top -= 32) {
+                const int i = top - lane;
+                const bool is_free =
+                    i >= lo && __ldcv(reinterpret_cast<const unsigned int*>(resolve(b, i).loss)) == kFreeLoss;
+                unsigned bal = __ballot_sync(0xffffffffu, is_free);
+                while (bal && got == M) {
+                    const int src = __ffs(bal) - 1;
+                    int ok = 0;
+                    if (lane == src) ok = claim(i) ? 1 : 0;
+                    if (__shfl_sync(0xffffffffu, ok, src)) got = top - src;
+                    bal &= bal - 1;
+                }
+            }
+            if (lane == 0) s_next = got;
+        }
+        __syncthreads();
+        return s_next;
+    };
+    bool have_cs = false;   // compact: s_cs_next holds this perturbation's rotation
+    auto first_m = [&]() -> int {
+        if constexpr (kImage) {
+            return 0;
+        } else if constexpr (kCompact) {
+            if (tid == 0) s_next = claim_from((int)blockIdx.x);
+            __syncthreads();
+            const int f = s_next;
+            __syncthreads();
+            return f < M ? f : steal();
+        } else {
+            return redo ? next_redo((int)blockIdx.x) : (int)blockIdx.x;
+        }
+    };
+    auto next_m = [&](int m) -> int {
+        if constexpr (kImage) {
+            return m + 1;
+        } else if constexpr (kCompact) {
+            const int p = s_pref;
+            have_cs = p < M;
+            return p < M ? p : steal();
+        } else {
+            return redo ? next_redo(m + (int)gridDim.x) : m + (int)gridDim.x;
+        }
+    };
+    for (int m = first_m(); m < M; m = next_m(m)) {
         // ---- 1. parameters and rotation ----------------------------------
         if (tid < 4) {   // ca, sa, cb, sb
-            if (kImage || m == (int)blockIdx.x || P.redo) {
+            if (kCompact ? !have_cs : (kImage || m == (int)blockIdx.x || P.redo)) {
                 const float p = kImage ? img_params[tid >> 1] : rotation_param(b, m, tid >> 1);
                 const double a = (double)p;
                 s_cs[tid] = (float)((tid & 1) ? sin(a) : cos(a));
@@ -465,21 +532,33 @@ revolve_kernel(RvArgs P, RenderBatch b, const float* __restrict__ img_params, fl
         }
         __syncthreads();
         const int count = s_count;
+        // (one warp, before the raster) the CTA's next perturbation and the
+        // FP64 cos / sin of its rotation, off the critical path: full layout
+        // m + G; compact, the next of its own that it claims (s_pref)
+        auto prefetch_next = [&]() {
+            int mn;
+            if constexpr (kCompact) {
+                mn = M;
+                if (lane == 0) mn = claim_from(m + (int)gridDim.x);
+                mn = __shfl_sync(0xffffffffu, mn, 0);
+                if (lane == 0) s_pref = mn;
+            } else {
+                mn = m + (int)gridDim.x;
+            }
+            if (lane < 4 && mn < M) {
+                const double a = (double)rotation_param(b, mn, lane >> 1);
+                s_cs_next[lane] = (float)((lane & 1) ? sin(a) : cos(a));
+            }
+        };
         // A compact-layout render that does not fit writes kRedoLoss (the full
-        // layout renders it again) and computes the rotation of the CTA's next
-        // perturbation, which its skipped raster phase would have computed.
+        // layout renders it again) and claims the CTA's next perturbation,
+        // which its skipped raster phase would have done.
         auto hand_over = [&]() {
             if (tid == 0) {
                 *resolve(b, m).loss = __uint_as_float(kRedoLoss);
                 if (P.stats) atomicAdd(&P.stats[7], 1ull);
             }
-            if (warp == kW - 1 && lane < 4) {
-                const int mn = m + (int)gridDim.x;
-                if (mn < M) {
-                    const double a = (double)rotation_param(b, mn, lane >> 1);
-                    s_cs_next[lane] = (float)((lane & 1) ? sin(a) : cos(a));
-                }
-            }
+            if (warp == kW - 1) prefetch_next();
             __syncthreads();
         };
         if constexpr (kCompact) {
@@ -621,15 +700,9 @@ revolve_kernel(RvArgs P, RenderBatch b, const float* __restrict__ img_params, fl
             // depth plane is formed once per entry and shared by the 4 pixels.
             const int grp = lane / kG, gl = lane % kG;
             const int ry = gl >> 1, hx = gl & 1;
-            // the FP64 cos / sin of this CTA's next perturbation, off the critical
-            // path: one warp computes them before it joins the tile loop
-            if (!kImage && !P.redo && r0 == 0 && warp == kW - 1 && lane < 4) {
-                const int mn = m + (int)gridDim.x;
-                if (mn < M) {
-                    const double a = (double)rotation_param(b, mn, lane >> 1);
-                    s_cs_next[lane] = (float)((lane & 1) ? sin(a) : cos(a));
-                }
-            }
+            // the next perturbation and its rotation: one warp, before it joins
+            // the tile loop
+            if (!kImage && !P.redo && r0 == 0 && warp == kW - 1) prefetch_next();
             // tiles without entries are not visited: their loss, the sum of
             // target^2, is taken in the reduction (an image visits every tile)
             float* tile_loss = reinterpret_cast<float*>(tcnt);
@@ -832,6 +905,12 @@ revolve_kernel(RvArgs P, RenderBatch b, const float* __restrict__ img_params, fl
     if (!kImage && lane == 0 && P.stats && s_steps[warp]) atomicAdd(&P.stats[5], s_steps[warp]);
 }
 
+// every loss word of the launch to kFreeLoss (before a compact-layout launch)
+__global__ void mark_free_kernel(RenderBatch b) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < b.M) *reinterpret_cast<unsigned int*>(resolve(b, i).loss) = kFreeLoss;
+}
+
 __global__ void normals_kernel(const float* verts, const int32_t* tris, int nt, float* tnrm) {
     const int t = blockIdx.x * blockDim.x + threadIdx.x;
     if (t >= nt) return;
@@ -993,13 +1072,15 @@ int revolve_tiles(const DevScene& sc) {
     return ((sc.W + kTW - 1) / kTW) * ((sc.H + sc.rv_th - 1) / sc.rv_th);
 }
 
-// With a compact layout: the compact launch (two CTAs per SM), then the
-// full-layout launch in redo mode, which renders only the perturbations the
-// compact one handed over (its CTAs read M loss words when there are none).
+// With a compact layout: the loss words marked free, the compact launch (two
+// CTAs per SM), then the full-layout launch in redo mode, which renders only
+// the perturbations the compact one handed over (its CTAs read M loss words
+// when there are none).
 void launch_revolve_loss(const DevScene& sc, const RenderBatch& b, cudaStream_t s) {
     const int grid = b.M < num_sms() ? b.M : num_sms();
     const bool compact = sc.rv_csmem != 0;
     if (compact) {
+        mark_free_kernel<<<(b.M + 255) / 256, 256, 0, s>>>(b);
         const int cgrid = b.M < 2 * num_sms() ? b.M : 2 * num_sms();
         if (sc.rv_th == 4)
             revolve_kernel<4, false, true><<<cgrid, kCompactThreads, sc.rv_csmem, s>>>(make_args(sc, true), b, nullptr,

@@ -48,13 +48,14 @@ ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
 METRIC = "Hessian/HVP estimates/s at oracle-matched error; perturbed renders/s; p50/p99 latency"
-# From the ncu capture of the current mesh kernel; set to None when the
-# kernel changes until it is captured again: DRAM bytes
-# (read + write) of one render+loss launch, and the fraction of instruction
-# issue slots busy (smsp__issue_active) — the kernel is bound by compare /
-# select issue on the ALU pipe rather than by FP32 arithmetic.
-TRAFFIC_BYTES = 549632
-ISSUE_ACTIVE_NCU = 0.668
+# From the ncu capture of the current mesh kernel (its compact-layout launch,
+# which does the renders of this workload); set to None when the kernel
+# changes until it is captured again: DRAM bytes (read + write) of one
+# render+loss launch, and the fraction of instruction issue slots busy
+# (smsp__issue_active) — the kernel is bound by compare / select issue on the
+# ALU pipe rather than by FP32 arithmetic.
+TRAFFIC_BYTES = 543488
+ISSUE_ACTIVE_NCU = 0.724
 M_PERTURB = 4096
 SEED = 2024
 
@@ -865,6 +866,7 @@ def main():
     d_out = torch.zeros((2, 2), dtype=torch.float64, device="cuda")
     flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda")
     tuning = tune_scene(hr, S, theta, 1024)
+    compact_slots = int(hr.hr_scene_get_stats(S.handle).mesh_compact_slots)
     hr.hr_profile_enable(S.handle, True)
 
     def step(i):
@@ -924,7 +926,10 @@ def main():
                 "config": workload_config(sc),
                 "renders_per_s": value * M_PERTURB,
                 "latency_ms": {"p50": float(np.percentile(times, 50)), "p99": float(np.percentile(times, 99))},
-                "roofline": {"bound": "alu", "kernel": "revolve_kernel (render + loss)",
+                "roofline": {"bound": "alu",
+                             "kernel": ("revolve_kernel (render + loss; compact layout, two CTAs per SM, "
+                                        "then the full layout for renders handed over)") if compact_slots
+                             else "revolve_kernel (render + loss)",
                              "achieved": achieved / 1e12, "peak": peak_ops / 1e12, "unit": "TFLOP/s",
                              "frac": achieved / peak_ops, "traffic": TRAFFIC_BYTES,
                              "peak_source": f"{n_sm} SMs x 128 FP32 lanes x {peaks.get('sm_max_mhz', 2070.0)} MHz "
@@ -935,7 +940,10 @@ def main():
                 "e2e": {"value": e2e_rate, "unit": "estimates/s", "h2d_bytes_per_step": 8 + 40,
                         "d2h_bytes_per_step": 32},
                 "stage_ms": dict(zip(("sample", "render_loss", "sums"), np.mean(stage_ms, axis=0).tolist())),
-                "gpu_launches": 3 * args.steps,   # sampler (also writes theta in FP32), render + loss, sums
+                # sampler (also writes theta in FP32), render + loss (with a compact
+                # layout: loss words marked free, compact launch, full-layout redo
+                # launch), sums
+                "gpu_launches": (5 if compact_slots else 3) * args.steps,
                 "tuning": tuning,
                 "clocks": clk}
         # statistical error of one estimate against a converged reference: the

@@ -342,11 +342,10 @@ revolve_kernel(RvArgs P, RenderBatch b, const float* __restrict__ img_params, fl
     __shared__ float s_part[kW];
     __shared__ int s_tile;
     __shared__ int s_band[2];   // the current band's end row and whether it walks every triangle
-    __shared__ unsigned long long s_steps[kW];   // raster steps of each warp (diagnostics)
 
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     const int M = kImage ? 1 : b.M;
-    if (lane == 0) s_steps[warp] = 0ull;
+    unsigned long long steps = 0ull;   // lane 0: this warp's raster steps (diagnostics)
     // Redo mode: the first of this CTA's perturbations m0, m0 + G, ... (G the
     // grid) whose loss is kRedoLoss, M if none; warp 0 reads 32 loss words at
     // a time.  Every thread calls it (one barrier); s_next is rewritten only
@@ -727,11 +726,12 @@ revolve_kernel(RvArgs P, RenderBatch b, const float* __restrict__ img_params, fl
                 const int ty = (int)(((uint64_t)(uint32_t)t * P.tx_recip) >> 32), tx = t - ty * P.TX;
                 const int x0 = tx * kTW + 4 * hx, y = ty * kTH + ry;
                 const float fy = __fadd_rn((float)y, 0.5f);
+                const float fx0 = __fadd_rn((float)x0, 0.5f);
                 float fx[4], bw[4];
                 int bs[4];
     #pragma unroll
                 for (int c = 0; c < 4; ++c) {
-                    fx[c] = __fadd_rn((float)(x0 + c), 0.5f);
+                    fx[c] = __fadd_rn(fx0, (float)c);   // exact: small integers + 1/2
                     bw[c] = -INFINITY;
                     bs[c] = INT_MAX;
                 }
@@ -782,13 +782,16 @@ revolve_kernel(RvArgs P, RenderBatch b, const float* __restrict__ img_params, fl
                 };
                 if (!walk_all) {
                     const int n_max = (int)__reduce_max_sync(0xffffffffu, (unsigned)n_mine);
-                    if (!kImage && lane == 0) s_steps[warp] += (unsigned long long)n_max;
+                    if (!kImage && lane == 0) steps += (unsigned long long)n_max;
                     // a group whose bin is shorter walks a sentinel entry (every
                     // row and column outside: no pixel is in) instead of
                     // branching around the step
+                    // (the next entry is loaded one step ahead)
+                    uint32_t e = 0 < n_mine ? ent[beg] : kSentinel;
                     for (int k = 0; k < n_max; ++k) {
-                        const uint32_t e = k < n_mine ? ent[beg + k] : kSentinel;
+                        const uint32_t en = k + 1 < n_mine ? ent[beg + k + 1] : kSentinel;
                         raster_entry((int)(e >> 16), e >> col_shift, false);
+                        e = en;
                     }
                     if (__any_sync(0xffffffffu, tie_u != 0u)) {
     #pragma unroll
@@ -902,7 +905,7 @@ revolve_kernel(RvArgs P, RenderBatch b, const float* __restrict__ img_params, fl
         __syncthreads();
     }
     // each warp's raster steps go to the diagnostics once per launch
-    if (!kImage && lane == 0 && P.stats && s_steps[warp]) atomicAdd(&P.stats[5], s_steps[warp]);
+    if (!kImage && lane == 0 && P.stats && steps) atomicAdd(&P.stats[5], steps);
 }
 
 // every loss word of the launch to kFreeLoss (before a compact-layout launch)

@@ -1080,6 +1080,7 @@ int revolve_tiles(const DevScene& sc) {
 // the perturbations the compact one handed over (its CTAs read M loss words
 // when there are none).
 void launch_revolve_loss(const DevScene& sc, const RenderBatch& b, cudaStream_t s) {
+    if (b.M <= 0) return;   // nothing to render (and no empty grid to launch)
     const int grid = b.M < num_sms() ? b.M : num_sms();
     const bool compact = sc.rv_csmem != 0;
     if (compact) {

@@ -122,11 +122,19 @@ typedef struct {
     /* REVOLVE3D: model-space vertices [n_vertices][3], triangles [n_triangles][3]
        (outward winding), albedo RGB, unit light direction, camera distance on +z
        and projection scale (pixels per unit of X/Z).  One render's triangle
-       records, projected vertices and tile bins live in shared memory
-       (72 B per triangle + 12 B per vertex + 8 B per 8x8 tile + 32 KB of bins,
-       within 227 KB): about 2,400 triangles at 256x256 on a GB300; larger
-       meshes are rejected with HR_ERR_UNSUPPORTED.  At most HR_MAX_VERTICES
-       vertices and HR_MAX_TRIANGLES triangles (else HR_ERR_INVALID_ARG). */
+       records, projected vertices and tile bins live in shared memory: 78 B
+       per triangle, 12 B per vertex, 8 B per raster tile (8x4 pixels, or 8x8
+       where fewer than 8,192 bin entries would fit) and at least 2,048 bin
+       entries of 4 B, within the 227 KB one CTA may use: about 2,400 triangles
+       at 256x256 on a GB300; larger meshes are rejected with
+       HR_ERR_UNSUPPORTED.  Where records of half the triangles (the ones that
+       survive culling, by slot) and 4,096 bin entries also fit half an SM,
+       two renders share each SM (the compact layout; mesh_compact_slots in
+       hr_scene_stats), and a render that does not fit it is rendered again
+       in the full layout.  Both layouts take the same coverage and depth
+       decisions; they sum the per-tile losses in different orders.  At most
+       HR_MAX_VERTICES vertices and HR_MAX_TRIANGLES triangles (else
+       HR_ERR_INVALID_ARG). */
     const float* vertices;
     int32_t n_vertices;
     const int32_t* triangles;

@@ -54,8 +54,8 @@ METRIC = "Hessian/HVP estimates/s at oracle-matched error; perturbed renders/s; 
 # render+loss launch, and the fraction of instruction issue slots busy
 # (smsp__issue_active) — the kernel is bound by compare / select issue on the
 # ALU pipe rather than by FP32 arithmetic.
-TRAFFIC_BYTES = 543488
-ISSUE_ACTIVE_NCU = 0.724
+TRAFFIC_BYTES = 543232
+ISSUE_ACTIVE_NCU = 0.727
 M_PERTURB = 4096
 SEED = 2024
 

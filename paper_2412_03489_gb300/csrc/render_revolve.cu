@@ -889,7 +889,7 @@ revolve_kernel(RvArgs P, RenderBatch b, const float* __restrict__ img_params, fl
         // ---- 6. reduction -----------------------------------------------------
         if (!kImage) {
             __syncthreads();
-            // thread i sums tiles i, i + 1024, ...; then a fixed shuffle tree
+            // thread i sums tiles i, i + kT, ...; then a fixed shuffle tree
             float acc = 0.0f;
             const float* tile_loss = reinterpret_cast<const float*>(tcnt);
             for (int t = tid; t < P.T; t += kT) acc += tile_loss[t];
@@ -1015,8 +1015,9 @@ bool layout_for(int nv, int nt, int W, int H, int th, int max_smem, size_t* byte
 // entries in what remains of max_smem (at most kEntryCapMax).  8x4 tiles
 // when that leaves room for 8,192 entries, else 8x8 tiles; false when fewer
 // than kEntryCapMin entries fit either way.  The tile height is a function of
-// the scene's sizes only, so every render of a scene sums its loss in the
-// same order.
+// the scene's sizes only (both layouts use it), so each layout sums a render's
+// loss in one fixed order, and which layout renders a perturbation depends on
+// that render's own survivors and entries only: results are deterministic.
 //
 // The compact layout (two CTAs per SM, each with half of smem_per_sm less
 // the 1 KB the hardware reserves per CTA) serves the renders it fits, with

@@ -257,6 +257,25 @@ def test_revolve_tile_row_beyond_capacity_walks_every_triangle():
     _check_mesh_paths(sc, 512, 4, 8, True, True)
 
 
+def test_revolve_compact_claims_give_the_same_result_every_time():
+    """Compact-layout CTAs claim perturbations by compare-and-swap and steal
+    the last ones, so which CTA renders which perturbation changes from run to
+    run; each loss depends on its perturbation only, so repeated estimates on
+    the same samples are bit-identical, losses included."""
+    sc = wl.revolve_scene()
+    Sc = hr.Scene(sc)
+    theta = np.asarray(sc["theta_query"], np.float64)
+    runs = [Sc.estimate(Q["hessian"], theta, sc["sigma"], 4096, S["aggregate"], 2024, 5, 0, debug=True)
+            for _ in range(4)]
+    st = hr.hr_scene_get_stats(Sc.handle)
+    Sc.close()
+    assert st.mesh_compact_slots > 0 and st.mesh_redo_renders == 0
+    out0, dbg0 = runs[0]
+    for out, dbg in runs[1:]:
+        assert np.array_equal(dbg["losses"], dbg0["losses"])
+        assert np.array_equal(out, out0)
+
+
 @pytest.mark.parametrize("layers", [9, 16])
 def test_revolve_compact_layout_hands_over_what_does_not_fit(layers):
     """Stacked full-frame sheets at 128^2 (every triangle faces the camera).
